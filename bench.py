@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Throughput of the SPH strength step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp32k|fp64] [--scale S]
+
+Workload: the 2,000,000-particle basalt impact (1.8M target + 0.2M impactor
+at 5 km/s and 45 degrees, Tillotson basalt with strength, radial g field),
+seeded and synthetic. One step is the whole hot path: drift, cell list
+(Morton keys, radix sort, permutation), density / smoothing-length solve,
+EOS + yield + radial return, the full-stress pair loop with its finalize,
+and the kicks with rescaling and FP64 reductions.
+
+Metric: particle-steps/s = particles x steps / device time of the K timed
+steps (whole job over all ranks; with N > 1 every rank runs its own
+replica of the impact, no data-path collective). The state (~450 MB) is far
+larger than L2, so no flush is needed between steps.
+
+The JSON line also carries: e2e (the same metric through sph_step_host with
+pinned host buffers, copies inside the timed region), roofline (the
+dominant kernel's algorithmic FLOP/s over the FP32 or FP64 ALU peak from
+unit counts and clock), cpu_baseline (the FP64 C oracle on a bounded
+spatial sub-volume of the same impact) and the SM clocks sampled during the
+timed region. --impl reference times the oracle itself.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FLOPs per in-range pair, counted from the arithmetic of
+# Eq. 1-3 (density) and Eq. 4-8, 18-21 (forces) in their contracted form;
+# candidate rejection, compensation and index work are not counted.
+FLOPS_DENSITY_PAIR = 26
+FLOPS_FORCE_PAIR = 151
+# B300 unit counts: 148 SMs x 128 FP32 lanes, 2 FLOP per FMA; FP64 at the
+# nominal 1.25 TFLOP/s at the 2032 MHz maximum clock.
+N_SM, FP32_LANES, MAX_MHZ = 148, 128, 2032.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(mhz: float) -> float:
+    return FP64_NOMINAL_TFLOPS * mhz / MAX_MHZ
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                mhz.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ------------------------------------------------------------ workloads
+def make_workload(scale: float, precision: int):
+    from paper_2603_19764_b300 import workloads as wl
+    return wl.impact(int(1_800_000 * scale), int(200_000 * scale), precision=precision)
+
+
+def contact_subvolume(w, n_sub: int) -> dict:
+    """The n_sub particles nearest the initial contact point of the impact."""
+    a = w.arrays
+    x = np.stack([a["x"], a["y"], a["z"]], 1)
+    nt = w.systems[0][1] if w.systems else w.n
+    imp = a["id"] >= int(round(0.9 * nt))
+    c_t, c_i = x[~imp].mean(0), x[imp].mean(0)
+    r_t = np.sqrt(((x[~imp] - c_t) ** 2).sum(1)).max()
+    r_i = np.sqrt(((x[imp] - c_i) ** 2).sum(1)).max()
+    contact = c_t + (c_i - c_t) * r_t / (r_t + r_i)
+    d = np.sqrt(((x - contact) ** 2).sum(1))
+    sel = np.argsort(d, kind="stable")[:n_sub]
+    sel.sort()
+    sub = {k: v[sel].copy() for k, v in a.items()}
+    sub["id"] = np.arange(sel.size, dtype=np.int64)
+    return sub
+
+
+def cpu_baseline(w, n_sub: int = 100_000, budget_s: float = 12.0, max_steps: int = 20,
+                 fixed_steps: int | None = None) -> dict:
+    """The FP64 C oracle, as it stands, on a bounded sub-volume."""
+    import oracle
+    sub = contact_subvolume(w, min(n_sub, w.n))
+    p = dict(w.params, h_tol=1e-10)
+    st, _ = oracle.derivatives(p, w.materials, sub)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        st, _ = oracle.step(p, w.materials, st, w.dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if fixed_steps is not None:
+            if steps >= fixed_steps:
+                break
+        elif el >= budget_s or steps >= max_steps:
+            break
+    n = sub["x"].shape[0]
+    return {"value": n * steps / el, "unit": "particle-steps/s", "cores": oracle.threads(),
+            "kind": "oracle", "seconds": el,
+            "sample": "%d FP64 oracle steps (OpenMP) of the %d particles of the impact nearest "
+                      "the contact point" % (steps, n)}
+
+
+# --------------------------------------------------------------- arms
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    w = make_workload(args.scale, 1)
+    for _ in range(args.warmup):
+        pass
+    cb = cpu_baseline(w, n_sub=args.ref_particles, fixed_steps=max(1, args.steps))
+    line = {"metric": "SPH+strength particle-steps/s (2M part.), chosen vs plain form at stated error",
+            "value": cb["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg (sub-volume)",
+                       "particles": w.n, "precision": "fp64 oracle"},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_19764_b300 import build, sph
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    precision = 1 if args.precision == "fp32k" else 0
+    w = make_workload(args.scale, precision)
+    p = dict(w.params, precision=precision, h_tol=1e-6 if precision else 1e-10)
+    sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
+    sim.prime()
+    for _ in range(args.warmup):
+        sim.step(w.dt)
+    sim.set_timing(True)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [sim.step(w.dt) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    phases = sim.phase_times()
+    ms_step = ms / args.steps
+    value = world * w.n * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (by CUDA-event phase time)
+    nsteps = max(phases["steps"], 1)
+    pairs_f = statistics.mean(i["pairs_force"] for i in infos)
+    pairs_d = statistics.mean(i["pairs_density"] for i in infos)
+    t_force = phases["forces"] / nsteps
+    t_dens = phases["density"] / nsteps
+    if t_force >= t_dens:
+        kname, flops, tk = "k_forces", FLOPS_FORCE_PAIR * pairs_f, t_force
+    else:
+        kname, flops, tk = "k_density", FLOPS_DENSITY_PAIR * pairs_d, t_dens
+    achieved = flops / (tk / 1e3) / 1e12
+    peak = fp32_peak_tflops(MAX_MHZ) if precision else fp64_peak_tflops(MAX_MHZ)
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": ("%s lanes x 2 x %.0f MHz (unit counts)" %
+                               ("148x128 FP32" if precision else "FP64 nominal 1.25 TFLOP/s",
+                                MAX_MHZ)),
+                "kernel_ms": tk, "pairs_per_step": pairs_f if kname == "k_forces" else pairs_d}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        host = sph.HostState(sim.to_numpy())
+        sim.step_host(host, w.dt)
+        torch.cuda.synchronize(dev)
+        ne = max(1, min(args.steps, args.e2e_steps))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            r = sim.step_host(host, w.dt)
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * w.n * ne / te, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": r["bytes_in"], "d2h_bytes_per_step": r["bytes_out"],
+               "steps": ne}
+    sim.close()
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w)
+        cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        launches_per_step = 27
+        line = {"metric": "SPH+strength particle-steps/s (2M part.), chosen vs plain form at stated error",
+                "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if precision else "f64", "data": "synthetic",
+                "config": {"workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg",
+                           "particles": w.n, "precision": args.precision,
+                           "dt": w.dt, "l2": "state 450 MB > L2, no flush",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks,
+                "phases_ms_per_step": {k: (v / nsteps if k != "steps" else v)
+                                       for k, v in phases.items()},
+                "sweeps": max(i["sweeps"] for i in infos),
+                "energy": {"e_kin": infos[-1]["e_kin"], "e_int": infos[-1]["e_int"],
+                           "e_pot": infos[-1]["e_pot"]}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32k", choices=["fp32k", "fp64"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-particles", type=int, default=20_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

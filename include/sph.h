@@ -1,0 +1,230 @@
+/*
+ * sph.h -- C ABI of the B300 (sm_103a) SPH particle step with material
+ * strength, after Meier et al., "Smoothed Particle Hydrodynamics in pkdgrav3
+ * for Shock Physics Simulations. II. Shear Strength" (§2).
+ *
+ * One step (§2.4) is: drift; cell-list neighbour search; density and
+ * smoothing-length solve (§2.1, Eq. 1-3); equation of state, yield strength
+ * (§2.3, Eq. 34-37) and radial return of the predicted deviatoric stress
+ * (Eq. 31-33); one pair loop for the full-stress momentum and energy
+ * equations with artificial viscosity (Eq. 4-8, 18-19) and the corrected
+ * velocity gradient (Eq. 20-24); the Jaumann stress rate (Eq. 13, 25-29);
+ * and the predictor-corrector kicks with rescaling (Eq. 40-43).
+ *
+ * Conventions for every call:
+ *  - All particle arrays are DEVICE pointers owned by the caller, length n,
+ *    structure-of-arrays. The library never frees them. Calls that sort
+ *    (sph_neighbours, sph_step) permute every array of sph_state in place
+ *    into cell (Morton) order; `id` travels with the particles.
+ *  - The library owns its scratch (cell list, sort buffers, packed mirrors,
+ *    predicted state) and frees it in sph_destroy.
+ *  - All calls are ordered on the CUDA stream given to sph_init and are not
+ *    thread-safe for one context. A call returns after enqueueing its work,
+ *    except where it says it synchronises.
+ *  - Every call returns a status. Device-side conditions (no convergence,
+ *    non-finite results, capacity) are latched in a device word and reported
+ *    at the next synchronising call. After SPH_E_CUDA the context is left in
+ *    SPH_E_STATE and can only be destroyed. sph_last_error() gives detail.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_E_ARG = 1,        /* invalid argument; nothing was enqueued */
+  SPH_E_CUDA = 2,       /* a CUDA runtime call failed */
+  SPH_E_NOCONV = 3,     /* smoothing-length solve did not converge */
+  SPH_E_CAPACITY = 4,   /* a scratch capacity was exceeded */
+  SPH_E_NONFINITE = 5,  /* a derivative or density came out NaN or Inf */
+  SPH_E_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+  SPH_E_STATE = 7       /* context unusable after an earlier failure */
+} sph_status;
+
+enum { SPH_EOS_LINEAR = 0, SPH_EOS_TILLOTSON = 1 };
+enum { SPH_FP64 = 0, SPH_FP32K = 1 };
+enum { SPH_JAUMANN_OBJECTIVE = 0, SPH_JAUMANN_PRINTED = 1 };
+enum { SPH_YIELD_SQRT_J2 = 0, SPH_YIELD_SQRT_3J2 = 1 };
+enum { SPH_GRAVITY_NONE = 0, SPH_GRAVITY_UNIFORM = 1, SPH_GRAVITY_RADIAL = 2 };
+#define SPH_MAX_MATERIALS 8
+#define SPH_FLAG_FIXED 1
+
+typedef struct sph_ctx sph_ctx;
+
+/* Particle state: caller-owned device arrays of length n.
+ *   x, y, z        position [m] (x at time i after a step)
+ *   vx, vy, vz     velocity at i+1/2 (half-step, §2.4) [m/s]
+ *   u              specific internal energy at i+1/2 [J/kg]
+ *   m              mass [kg]
+ *   h              kernel support radius H [m]; read as the first guess of
+ *                  the solve and overwritten with the converged value
+ *   sxx..syz       deviatoric stress S at i+1/2, five independent
+ *                  components (S_zz = -S_xx - S_yy, Eq. 11) [Pa]
+ *   rho, omega     density (Eq. 1) and grad-h term (Eq. 3)      (outputs)
+ *   pres, cs       pressure and sound speed from the EOS       (outputs)
+ *   ax..az, dudt, dsxx..dsyz
+ *                  time derivatives at i (input: at i-1, used by the
+ *                  predictor; output: at i)
+ *   eps_ii         integral of 1/2 edot:edot dt (Eq. 43)       (in/out)
+ *   nngb           #{j != i : r_ij < H_i}                       (output)
+ *   mat            material index into the sph_init table
+ *   flags          bit 0: fixed boundary particle (never moved, no
+ *                  derivatives)
+ *   id             caller's particle identifier, permuted with the rest */
+typedef struct {
+  double *x, *y, *z;
+  double *vx, *vy, *vz;
+  double *u, *m, *h;
+  double *sxx, *syy, *sxy, *sxz, *syz;
+  double *rho, *omega, *pres, *cs;
+  double *ax, *ay, *az, *dudt;
+  double *dsxx, *dsyy, *dsxy, *dsxz, *dsyz;
+  double *eps_ii;
+  int32_t *nngb, *mat, *flags;
+  int64_t *id;
+} sph_state;
+
+/* Material constants. Linear EOS P = c0^2 (rho - rho0); Tillotson with
+ * (rho0, A, B, E0, a, b, alpha, beta, Eiv, Ecv). Shear modulus shear_G, or
+ * Eq. 30 with nu = 0.25 when shear_G < 0. Yield: Eq. 34-36 with (Y0, mu_i,
+ * Ym, mu_d); thermal softening Eq. 37 with T = T0 + u / cv when
+ * thermal_softening != 0. strength = 0 makes the material a fluid (S = 0). */
+typedef struct {
+  int32_t eos;
+  double rho0, c0;
+  double A, B, E0, a, b, alpha, beta, Eiv, Ecv;
+  double shear_G;
+  double Y0, mu_i, Ym, mu_d;
+  int32_t thermal_softening;
+  double xi, Tm, T0, cv;
+  int32_t strength;
+} sph_material;
+
+/* Run-time parameters.
+ *   n_ngb          target neighbour number: (4 pi / 3) H^3 rho = n_ngb m
+ *   av_alpha, av_beta, av_eps   artificial viscosity (Eq. 5-6)
+ *   eta_c, eta_a   time-step factors (Eq. 38-39)
+ *   h_tol          Newton stop: |g| <= h_tol n_ngb m
+ *   max_sweeps     Newton sweeps before SPH_E_NOCONV
+ *   h_cap_factor   H is capped at h_cap_factor times the lattice radius
+ *   precision      SPH_FP64 or SPH_FP32K (FP32 pair arithmetic on
+ *                  cell-relative offsets with compensated sums)
+ *   jaumann        SPH_JAUMANN_OBJECTIVE (R S - S R) or _PRINTED (Eq. 25-29)
+ *   yield_norm     SPH_YIELD_SQRT_J2 (Eq. 32) or _SQRT_3J2
+ *   correction_tensor  1: G = F C (Eq. 22); 0: C = I
+ *   gravity        none, uniform g_uniform, or radial table: g_table and
+ *                  phi_table are HOST arrays of g_n values on radii
+ *                  log-spaced from g_rmin to g_rmax about g_center, copied
+ *                  at sph_init; g = g_gm / r^2 beyond g_rmax
+ *   periodic       must be 0 (periodic boxes are an oracle-only feature) */
+typedef struct {
+  int32_t n_ngb;
+  double av_alpha, av_beta, av_eps;
+  double eta_c, eta_a;
+  double h_tol;
+  int32_t max_sweeps;
+  double h_cap_factor;
+  int32_t precision, jaumann, yield_norm, correction_tensor;
+  int32_t gravity;
+  double g_uniform[3];
+  const double *g_table, *phi_table;
+  int32_t g_n;
+  double g_rmin, g_rmax, g_center[3], g_gm;
+  int32_t periodic;
+  double box_lo[3], box_hi[3];
+} sph_params;
+
+/* Per-step report (filled by the synchronising calls). Energies and
+ * momenta are FP64 sums over all particles at time i (x_i, v_i, u_i);
+ * L = sum m r x v (Eq. 46). dt_next is the minimum of Eq. 38-39. */
+typedef struct {
+  double dt, dt_next;
+  double e_kin, e_int, e_pot;
+  double p[3], L[3];
+  int32_t sweeps, n_unconverged, n_capped, n_cfallback;
+  int64_t pairs_density, pairs_force;
+  uint32_t device_flags;
+} sph_step_info;
+
+/* Create a context for n particles in `st` on `cuda_stream` (a cudaStream_t,
+ * NULL for the legacy default stream). Validates the parameters, copies
+ * params, materials and the gravity table, allocates scratch. Does not
+ * touch the state. Errors: SPH_E_ARG (n < 1, bad pointer, bad enum, n_mat
+ * out of 1..SPH_MAX_MATERIALS, periodic != 0), SPH_E_CUDA. *out is NULL on
+ * failure. */
+sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats,
+                    int32_t n_mat, const sph_state *st, int64_t n, void *cuda_stream);
+
+/* Cell-list build (replaces the paper's tree walk, §2.1): bounding box, cell
+ * size L_c = max H, 30-bit Morton keys of cell coordinates, stable radix sort,
+ * in-place permutation of every sph_state array, cell start / end. */
+sph_status sph_neighbours(sph_ctx *c);
+
+/* Density and smoothing-length solve (Eq. 1-3) from the current h as first
+ * guess; writes h, rho, omega, nngb. Requires a cell list of the current
+ * positions. Synchronises; *sweeps (may be NULL) receives the largest
+ * Newton sweep count. Returns SPH_E_NOCONV if some particle did not meet
+ * h_tol within max_sweeps (its last evaluation is kept). */
+sph_status sph_density(sph_ctx *c, int32_t *sweeps);
+
+/* Derivatives of the state as it stands (no prediction): EOS at (rho, u),
+ * yield and radial return of a copy of S (Eq. 31-37), the pair loop
+ * (Eq. 4-8, 18-22) and the stress rate (Eq. 13 / 25-29). Writes pres, cs,
+ * ax..az, dudt, dsxx..dsyz. Requires sph_density on the current cell list.
+ * The caller's S is not modified. */
+sph_status sph_forces_strength(sph_ctx *c);
+
+/* Closing kick to i (Eq. 41; v and u alike), radial return with Y at
+ * (rho_i, u_i), strain invariant (Eq. 43), then opening kick to i+1/2
+ * (Eq. 42), all with step dt > 0 and the derivatives in the state. */
+sph_status sph_stress_update(sph_ctx *c, double dt);
+
+/* One full step of length dt (dt <= 0: the dt_next of the previous call
+ * or, on the first call, of the initial derivatives). The state holds
+ * x_{i-1}, v/u/S at i-1/2 and derivatives at i-1 on entry; x_i, v/u/S at
+ * i+1/2 and derivatives at i on return. Synchronises and fills *info (may
+ * be NULL). */
+sph_status sph_step(sph_ctx *c, double dt, sph_step_info *info);
+
+/* sph_step with HOST state: the caller passes pinned or pageable host
+ * arrays in `host`; the library copies them to the context's device state,
+ * runs one step and copies the state back. h2d / d2h byte counts go to
+ * *bytes_in / *bytes_out (may be NULL). */
+sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_info *info,
+                         int64_t *bytes_in, int64_t *bytes_out);
+
+/* Derivatives of the initial state: sph_neighbours, sph_density and
+ * sph_forces_strength in one call, plus the diagnostics and dt_next in
+ * *info (may be NULL). Call once before the first sph_step. */
+sph_status sph_prime(sph_ctx *c, sph_step_info *info);
+
+/* Phase timing with CUDA events recorded on the context's stream around the
+ * phases of every sph_step: 0 neighbours (drift, keys, sort, permutation,
+ * cells), 1 prediction and packing, 2 density solve, 3 EOS, yield and
+ * packing, 4 pair loop with finalize, 5 kicks and reductions.
+ * sph_set_timing(c, 1) enables it and zeroes the accumulators;
+ * sph_phase_times copies up to n accumulated milliseconds per phase into
+ * ms and the number of timed steps into *steps (may be NULL). */
+#define SPH_NUM_PHASES 6
+sph_status sph_set_timing(sph_ctx *c, int32_t on);
+sph_status sph_phase_times(const sph_ctx *c, double *ms, int32_t n, int32_t *steps);
+
+/* Free the context and its scratch; the caller's arrays are untouched.
+ * Accepts NULL. */
+sph_status sph_destroy(sph_ctx *c);
+
+/* Static description of a status code. */
+const char *sph_status_string(sph_status s);
+
+/* Detail of the last failure on this context ("" if none). */
+const char *sph_last_error(const sph_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -549,7 +549,8 @@ static double lattice_h(const ref_params *p, const ref_material *mt, double m) {
  * otherwise H <- H - g / g', limited to [0.75 H, 1.25 H], replaced by the
  * midpoint of the bracket [lo, hi] of the root when it leaves it, and capped
  * at h_cap_factor times the lattice radius (a particle at the cap with
- * g < 0 is accepted and counted as capped). */
+ * g < 0 is accepted and counted as capped). A particle that has not met
+ * the tolerance after max_sweeps keeps its last evaluated H. */
 int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
                           int64_t n, ref_state *s, int32_t *n_unconv,
                           int32_t *n_capped) {
@@ -571,9 +572,10 @@ int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
       double Hcap = p->h_cap_factor * lattice_h(p, &mats[s->mat[i]], s->m[i]);
       double H = s->h[i] < Hcap ? s->h[i] : Hcap;
       double lo = 0.0, hi = INFINITY;
-      double rho = 0.0, rhoH = 0.0, Om = 1.0;
+      double rho = 0.0, rhoH = 0.0, Om = 1.0, Heval = H;
       int32_t c = 0, sweep, done = 0;
       for (sweep = 1; sweep <= p->max_sweeps; ++sweep) {
+        Heval = H;
         density_sums(&g, n, s, i, H, &buf, &cap, &rho, &rhoH, &c);
         Om = 1.0 + H / (3.0 * rho) * rhoH;
         double gv = 4.0 * PI / 3.0 * H * H * H * rho - target;
@@ -599,7 +601,7 @@ int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
       if (!done) ++unconv;
       if (done == 2) ++capped;
       if (sweep > worst) worst = sweep;
-      s->h[i] = H;
+      s->h[i] = Heval; /* rho, Omega and the count belong to this H */
       s->rho[i] = rho;
       s->omega[i] = Om;
       s->nngb[i] = c;

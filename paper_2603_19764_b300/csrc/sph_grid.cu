@@ -1,0 +1,352 @@
+// sph_grid.cu -- drift, bounding box, uniform cell grid, Morton keys, stable
+// LSD radix sort and the in-place permutation of the particle arrays.
+//
+// The paper finds neighbours with pkdgrav3's tree (§2.1, §4). Here a uniform
+// grid of cell edge L_c = max H over Morton-ordered cells takes its place:
+// particles are sorted by the Morton key of their cell so that every cell is
+// a contiguous index range and consecutive particles are close in space.
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+// ---------------------------------------------------------------- status
+__global__ void k_reset_status(Status *st, int full) {
+  if (threadIdx.x != 0) return;
+  for (int a = 0; a < 3; ++a) {
+    st->lo_enc[a] = ~0ull;
+    st->hi_enc[a] = 0ull;
+  }
+  st->hmax_enc = 0ull;
+  st->hmax2_enc = 0ull;
+  st->dtmin_enc = ~0ull;
+  st->max_sweeps = 0;
+  st->n_unconv = 0;
+  st->n_capped = 0;
+  st->n_cfallback = 0;
+  st->pairs_density = 0;
+  st->pairs_force = 0;
+  if (full) st->err = 0;
+}
+
+cudaError_t launch_reset_status(sph_ctx *c, int full) {
+  k_reset_status<<<1, 32, 0, c->stream>>>(c->d_status, full);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ drift + bounding box
+// x_i = x_{i-1} + dt v_{i-1/2} for moving particles (§2.4), then the box
+// of all positions and the largest H.
+__global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, const double *dtp,
+                                                      int do_drift, Status *st) {
+  __shared__ double red[7][kBlock / 32];
+  const double dt = do_drift ? *dtp : 0.0;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double hm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double p[3] = {s.x[i], s.y[i], s.z[i]};
+    if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
+      p[0] += dt * s.vx[i];
+      p[1] += dt * s.vy[i];
+      p[2] += dt * s.vz[i];
+      s.x[i] = p[0];
+      s.y[i] = p[1];
+      s.z[i] = p[2];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], p[a]);
+      hi[a] = fmax(hi[a], p[a]);
+    }
+    hm = fmax(hm, s.h[i]);
+  }
+  double v[7] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm};
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = wmin(v[k]);
+#pragma unroll
+  for (int k = 3; k < 7; ++k) v[k] = wmax(v[k]);
+  if (lane == 0)
+    for (int k = 0; k < 7; ++k) red[k][w] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x / 32;
+    for (int k = 0; k < 7; ++k) {
+      double t = lane < nw ? red[k][lane] : (k < 3 ? INFINITY : -INFINITY);
+      t = k < 3 ? wmin(t) : wmax(t);
+      if (lane == 0) {
+        if (k < 3) atomicMin(&st->lo_enc[k], enc_d(t));
+        else if (k < 6) atomicMax(&st->hi_enc[k - 3], enc_d(t));
+        else atomicMax(&st->hmax_enc, enc_d(t));
+      }
+    }
+  }
+}
+
+cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
+  int blocks = (int)((c->n + kBlock - 1) / kBlock);
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  k_drift_bbox<<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->d_dt, do_drift, c->d_status);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ grid setup
+// Cell edge L_c = max H (at least 1e-30 of the extent); at most 1024 cells
+// per axis and max_cells in all, growing L_c by 2^(1/3) until both hold.
+__global__ void k_grid_setup(Status *st, int max_cells) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = dec_d(st->lo_enc[a]);
+    hi[a] = dec_d(st->hi_enc[a]);
+  }
+  double L = dec_d(st->hmax_enc);
+  double ext = fmax(fmax(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+  if (!(L > 1e-30 * ext) || !(L > 0.0)) L = fmax(ext, 1.0) * 1e-3;
+  int d[3] = {1, 1, 1};
+  bool ok = false;
+  for (int it = 0; it < 200 && !ok; ++it) {
+    long long tot = 1;
+    ok = true;
+    for (int a = 0; a < 3; ++a) {
+      double k = floor((hi[a] - lo[a]) / L) + 1.0;
+      if (!(k <= 1024.0)) ok = false;
+      d[a] = (int)fmin(fmax(k, 1.0), 2048.0);
+      tot *= d[a];
+    }
+    if (tot > max_cells) ok = false;
+    if (!ok) L *= 1.2599210498948732;
+  }
+  if (!ok) {  // non-finite box: one cell holding everything
+    d[0] = d[1] = d[2] = 1;
+    L = INFINITY;
+    atomicOr(&st->err, ERR_NONFINITE);
+  }
+  Grid &g = st->grid;
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = lo[a];
+    g.dims[a] = d[a];
+  }
+  g.L = L;
+  g.ncells = d[0] * d[1] * d[2];
+}
+
+cudaError_t launch_grid_setup(sph_ctx *c) {
+  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->max_cells);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double invL, int dim) {
+  int k = (int)floor((x - lo) * invL);
+  return k < 0 ? 0 : (k >= dim ? dim - 1 : k);
+}
+
+// Morton key of each particle's cell; values start as the identity.
+__global__ void __launch_bounds__(kBlock) k_keys(const double *x, const double *y, const double *z,
+                                                int64_t n, const Status *st, unsigned *keys,
+                                                int *vals) {
+  const Grid g = st->grid;
+  const double invL = 1.0 / g.L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int cx = cell_coord(x[i], g.lo[0], invL, g.dims[0]);
+    const int cy = cell_coord(y[i], g.lo[1], invL, g.dims[1]);
+    const int cz = cell_coord(z[i], g.lo[2], invL, g.dims[2]);
+    keys[i] = morton3(cx, cy, cz);
+    vals[i] = (int)i;
+  }
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits, four passes.
+// Per pass: tile histograms (digit-major), one exclusive scan, and a stable
+// scatter in which each key's rank inside its tile comes from warp match
+// masks plus per-warp digit counts.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned *keys, int n, int shift,
+                                                             unsigned *hist, int ntiles) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kTile;
+  for (int k = 0; k < kSortItems; ++k) {
+    const int i = base + k * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of m = 256 * ntiles counts in one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_radix_scan(unsigned *hist, int m) {
+  __shared__ unsigned part[1024];
+  const int per = (m + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(b + per, m);
+  unsigned s = 0;
+  for (int i = b; i < e; ++i) s += hist[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    unsigned t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += t;
+    __syncthreads();
+  }
+  unsigned run = part[threadIdx.x] - s;
+  for (int i = b; i < e; ++i) {
+    unsigned v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *kin, const int *vin,
+                                                                unsigned *kout, int *vout, int n,
+                                                                int shift, const unsigned *hist,
+                                                                int ntiles) {
+  constexpr int NW = kSortThreads / 32;
+  __shared__ unsigned base[256];
+  __shared__ unsigned wcnt[NW][256];
+  const int w = threadIdx.x >> 5;
+  base[threadIdx.x] = hist[threadIdx.x * ntiles + blockIdx.x];
+  for (int k = 0; k < NW; ++k) wcnt[k][threadIdx.x] = 0;
+  __syncthreads();
+  const int tile0 = blockIdx.x * kTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int i = tile0 + r * kSortThreads + threadIdx.x;
+    const bool ok = i < n;
+    const unsigned key = ok ? kin[i] : 0u;
+    const unsigned d = ok ? ((key >> shift) & 255u) : 256u;   // 256 never matches a real digit
+    const unsigned peers = __match_any_sync(kFull, d);
+    const unsigned rank_w = __popc(peers & lanemask_lt());
+    if (ok && rank_w == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    if (ok) {
+      unsigned pos = base[d] + rank_w;
+      for (int k = 0; k < w; ++k) pos += wcnt[k][d];
+      kout[pos] = key;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    unsigned add = 0;
+    for (int k = 0; k < NW; ++k) {
+      add += wcnt[k][threadIdx.x];
+      wcnt[k][threadIdx.x] = 0;
+    }
+    base[threadIdx.x] += add;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ permutation
+// Every array of sph_state is gathered through the sort permutation into a
+// scratch block and copied back, so the caller's arrays end up in cell order.
+constexpr int kNF64 = 29;   // 28 double arrays + id
+constexpr int kNI32 = 3;
+
+struct PermTable {
+  unsigned long long *f64[kNF64];
+  unsigned *i32[kNI32];
+};
+
+static PermTable perm_table(const sph_state &s) {
+  PermTable t;
+  double *d[28] = {s.x,    s.y,    s.z,     s.vx,   s.vy,   s.vz,   s.u,    s.m,    s.h,    s.sxx,
+                   s.syy,  s.sxy,  s.sxz,   s.syz,  s.rho,  s.omega, s.pres, s.cs,  s.ax,   s.ay,
+                   s.az,   s.dudt, s.dsxx,  s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
+  for (int k = 0; k < 28; ++k) t.f64[k] = (unsigned long long *)d[k];
+  t.f64[28] = (unsigned long long *)s.id;
+  t.i32[0] = (unsigned *)s.nngb;
+  t.i32[1] = (unsigned *)s.mat;
+  t.i32[2] = (unsigned *)s.flags;
+  return t;
+}
+
+__global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm, int64_t n,
+                                                  unsigned long long *tmp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = perm[i];
+#pragma unroll 4
+    for (int f = 0; f < kNF64; ++f) tmp[f * n + i] = t.f64[f][j];
+    unsigned *t32 = (unsigned *)(tmp + kNF64 * n);
+#pragma unroll
+    for (int f = 0; f < kNI32; ++f) t32[f * n + i] = t.i32[f][j];
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_scatter_back(PermTable t, int64_t n,
+                                                        const unsigned long long *tmp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll 4
+    for (int f = 0; f < kNF64; ++f) t.f64[f][i] = tmp[f * n + i];
+    const unsigned *t32 = (const unsigned *)(tmp + kNF64 * n);
+#pragma unroll
+    for (int f = 0; f < kNI32; ++f) t.i32[f][i] = t32[f * n + i];
+  }
+}
+
+// Cell start / end over the sorted keys, and the packed cell coordinates.
+__global__ void __launch_bounds__(kBlock) k_clear_cells(int *start, const Status *st) {
+  const int nc = st->grid.ncells;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+    start[i] = -1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys, int64_t n, const Status *st,
+                                                 int *start, int *end, int *cc) {
+  const Grid g = st->grid;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned k = keys[i];
+    const int cx = compact1by2(k), cy = compact1by2(k >> 1), cz = compact1by2(k >> 2);
+    const int lin = (cz * g.dims[1] + cy) * g.dims[0] + cx;
+    cc[i] = cx | (cy << 10) | (cz << 20);
+    if (i == 0 || keys[i - 1] != k) start[lin] = (int)i;
+    if (i == n - 1 || keys[i + 1] != k) end[lin] = (int)(i + 1);
+  }
+}
+
+static int grid_for(int64_t n, int block) {
+  int64_t b = (n + block - 1) / block;
+  if (b > 148 * 16) b = 148 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_sort_permute(sph_ctx *c) {
+  const int64_t n = c->n;
+  const int gb = grid_for(n, kBlock);
+  k_keys<<<gb, kBlock, 0, c->stream>>>(c->st.x, c->st.y, c->st.z, n, c->d_status, c->keys,
+                                       c->vals);
+  unsigned *ka = c->keys, *kb = c->keys_alt;
+  int *va = c->vals, *vb = c->vals_alt;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    k_radix_hist<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, (int)n, shift, c->hist, c->ntiles);
+    k_radix_scan<<<1, 1024, 0, c->stream>>>(c->hist, 256 * c->ntiles);
+    k_radix_scatter<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, (int)n, shift,
+                                                               c->hist, c->ntiles);
+    unsigned *tk = ka;
+    ka = kb;
+    kb = tk;
+    int *tv = va;
+    va = vb;
+    vb = tv;
+  }
+  // after four passes the sorted pairs are back in keys / vals
+  PermTable t = perm_table(c->st);
+  unsigned long long *tmp = (unsigned long long *)c->tmp;
+  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
+  k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
+  k_clear_cells<<<grid_for(c->max_cells, kBlock), kBlock, 0, c->stream>>>(c->cell_start,
+                                                                          c->d_status);
+  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->d_status, c->cell_start, c->cell_end,
+                                        c->w.cc);
+  return cudaGetLastError();
+}
+
+}  // namespace sphk

@@ -1,0 +1,334 @@
+// sph_internal.cuh -- device-side types and functions shared by the CUDA
+// translation units of libsph. Not part of the public ABI (include/sph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "sph.h"
+
+namespace sphk {
+
+constexpr int kWarpsPerBlock = 4;      // pair kernels: one warp per bucket
+constexpr int kBlock = 256;            // per-particle kernels
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kPi = 3.14159265358979323846;
+
+// Wendland C2 in 3-D with support H (§3; Dehnen & Aly 2012):
+//   W      = cW / H^3 (1-q)^4 (1+4q)
+//   W'/r   = cG / H^5 (1-q)^3                 (radial derivative over r)
+//   dW/dH  = cW / H^4 (1-q)^3 (-3 - 9q + 32q^2)
+constexpr double cW = 21.0 / (2.0 * kPi);
+constexpr double cG = -210.0 / kPi;
+
+enum : unsigned { ERR_NOCONV = 1u, ERR_NONFINITE = 2u, ERR_CAPACITY = 4u, ERR_TIMEOUT = 8u };
+
+// Uniform cell grid of one step, written on the device by k_grid_setup.
+struct Grid {
+  double lo[3];
+  double L;          // cell edge
+  int dims[3];
+  int ncells;
+};
+
+// Device-resident step record. Encoded min/max use the order-preserving
+// map of doubles to unsigned 64-bit integers (enc_d / dec_d).
+struct Status {
+  unsigned int err;
+  int max_sweeps, n_unconv, n_capped, n_cfallback;
+  int pad_;
+  unsigned long long lo_enc[3], hi_enc[3], hmax_enc, hmax2_enc, dtmin_enc;
+  unsigned long long pairs_density, pairs_force;
+  double sums[9];   // e_kin, e_int, e_pot, p[3], L[3]
+  Grid grid;
+};
+
+// Kernel-side copy of the run-time parameters.
+struct KParams {
+  int n_ngb;
+  double av_alpha, av_beta, av_eps, eta_c, eta_a, h_tol;
+  int max_sweeps;
+  double h_cap_factor;
+  int precision, jaumann, yield_norm, correction;
+  int gravity;
+  double g_uniform[3];
+  const double *g_table, *phi_table, *g_radii;
+  int g_n;
+  double g_rmin, g_rmax, g_center[3], g_gm, g_inv_log_ratio;
+  const sph_material *mats;
+};
+
+// Library-owned per-particle work arrays (sorted order).
+struct Work {
+  double *vp[3], *up, *sp[5];   // evaluation (predicted) state
+  double *vsig, *edot2, *yld;   // CFL signal, 1/2 edot:edot, yield strength
+  int *cc;                      // packed cell coordinates x | y << 10 | z << 20
+  float4 *pos32;                // cell-relative x, y, z and m (FP32 form)
+  double4_32a *pos64;               // absolute x, y, z and m (FP64 form)
+  float4 *fj32[4];              // force-side neighbour data (FP32 form)
+  double4_32a *fj64[4];             // force-side neighbour data (FP64 form)
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned long long enc_d(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double dec_d(unsigned long long e) {
+  unsigned long long b = (e & 0x8000000000000000ull) ? (e & 0x7fffffffffffffffull) : ~e;
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+__host__ inline unsigned long long enc_h(double d) {
+  unsigned long long b;
+  memcpy(&b, &d, sizeof(b));
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T> __device__ __forceinline__ T wmax(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    T w = __shfl_xor_sync(kFull, v, o);
+    v = v > w ? v : w;
+  }
+  return v;
+}
+template <typename T> __device__ __forceinline__ T wmin(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    T w = __shfl_xor_sync(kFull, v, o);
+    v = v < w ? v : w;
+  }
+  return v;
+}
+template <typename T> __device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Spread the low 10 bits of v to every third bit (Morton interleave).
+__host__ __device__ inline unsigned part1by2(unsigned v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__host__ __device__ inline unsigned compact1by2(unsigned v) {
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030c30c3u;
+  v = (v | (v >> 4)) & 0x0300f00fu;
+  v = (v | (v >> 8)) & 0x030000ffu;
+  v = (v | (v >> 16)) & 0x000003ffu;
+  return v;
+}
+__host__ __device__ inline unsigned morton3(unsigned x, unsigned y, unsigned z) {
+  return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
+}
+
+// -------------------------------------------------------- material model
+// Equation of state. Linear: P = c0^2 (rho - rho0), c = c0. Tillotson
+// (Tillotson 1962; regions as in Melosh 1989): condensed or cold states,
+// hot expanded states and a linear-in-u blend in between, with
+// c^2 = P_rho + P P_u / rho^2 floored at 0.01 A / rho0.
+struct EosOut {
+  double P, c;
+};
+
+__device__ inline void till_dense(const sph_material &M, double rho, double u, double &P,
+                                  double &Pr, double &Pu) {
+  const double eta = rho / M.rho0, mu = eta - 1.0;
+  const double e0e2 = M.E0 * eta * eta;
+  const double w = u / e0e2 + 1.0;
+  const double bw = M.b / w;
+  const double bw2 = bw / w;                          // b / w^2
+  P = (M.a + bw) * rho * u + mu * (M.A + M.B * mu);
+  // dw/drho = -2 (w - 1) / rho, dw/du = 1 / (E0 eta^2)
+  Pr = (M.a + bw) * u + bw2 * rho * u * 2.0 * (w - 1.0) / rho + (M.A + 2.0 * M.B * mu) / M.rho0;
+  Pu = (M.a + bw) * rho - bw2 * rho * u / e0e2;
+}
+
+__device__ inline void till_vapour(const sph_material &M, double rho, double u, double &P,
+                                   double &Pr, double &Pu) {
+  const double eta = rho / M.rho0, mu = eta - 1.0;
+  const double e0e2 = M.E0 * eta * eta;
+  const double w = u / e0e2 + 1.0;
+  const double z = M.rho0 / rho - 1.0;
+  const double zr = -M.rho0 / (rho * rho);          // dz/drho
+  const double eb = exp(-M.beta * z), ea = exp(-M.alpha * z * z);
+  const double brw = M.b * rho * u / w;
+  const double q = brw + M.A * mu * eb;
+  const double qr = M.b * u / w + brw / w * 2.0 * (w - 1.0) / rho + M.A / M.rho0 * eb -
+                    M.A * mu * eb * M.beta * zr;
+  const double qu = M.b * rho / w - brw / w / e0e2;
+  P = M.a * rho * u + q * ea;
+  Pr = M.a * u + (qr - q * 2.0 * M.alpha * z * zr) * ea;
+  Pu = M.a * rho + qu * ea;
+}
+
+__device__ inline EosOut eos(const sph_material &M, double rho, double u) {
+  EosOut o;
+  if (M.eos == SPH_EOS_LINEAR) {
+    o.P = M.c0 * M.c0 * (rho - M.rho0);
+    o.c = M.c0;
+    return o;
+  }
+  double P, Pr, Pu;
+  if (rho >= M.rho0 || u <= M.Eiv) {
+    till_dense(M, rho, u, P, Pr, Pu);
+  } else if (u >= M.Ecv) {
+    till_vapour(M, rho, u, P, Pr, Pu);
+  } else {
+    double P1, Pr1, Pu1, P2, Pr2, Pu2;
+    till_dense(M, rho, u, P1, Pr1, Pu1);
+    till_vapour(M, rho, u, P2, Pr2, Pu2);
+    const double s = 1.0 / (M.Ecv - M.Eiv);
+    const double wv = (u - M.Eiv) * s, wd = (M.Ecv - u) * s;
+    P = wv * P2 + wd * P1;
+    Pr = wv * Pr2 + wd * Pr1;
+    Pu = wv * Pu2 + wd * Pu1 + (P2 - P1) * s;
+  }
+  double c2 = Pr + P * Pu / (rho * rho);
+  const double floor2 = 0.01 * M.A / M.rho0;
+  if (!(c2 >= floor2)) c2 = floor2;
+  o.P = P;
+  o.c = sqrt(c2);
+  return o;
+}
+
+// Shear modulus: constant, or Eq. 30 with nu = 0.25 (Gamma = 0.6 rho c^2).
+__device__ __forceinline__ double shear_mod(const sph_material &M, double rho, double c) {
+  return M.shear_G >= 0.0 ? M.shear_G : 0.6 * rho * c * c;
+}
+
+// Yield strength (Eq. 34-37) with the pressure clipped at zero.
+__device__ inline double yield(const sph_material &M, double P, double u) {
+  const double p = fmax(P, 0.0);
+  const double yi = M.Y0 + M.mu_i * p / (1.0 + M.mu_i * p / (M.Ym - M.Y0));
+  double y = fmin(yi, M.mu_d * p);
+  if (M.thermal_softening) {
+    const double T = M.T0 + u / M.cv;
+    if (!(T > 0.0)) return 0.0;
+    y *= fmax(tanh(M.xi * (M.Tm / T - 1.0)), 0.0);
+  }
+  return y;
+}
+
+// Radial return (Eq. 31-33) of S = {xx, yy, xy, xz, yz}.
+__device__ inline void radial_return(double S[5], double Y, int norm) {
+  const double zz = -(S[0] + S[1]);
+  const double j2 = 0.5 * (S[0] * S[0] + S[1] * S[1] + zz * zz) + S[2] * S[2] + S[3] * S[3] +
+                    S[4] * S[4];
+  if (!(j2 > 0.0)) return;
+  const double f = Y / sqrt(norm ? 3.0 * j2 : j2);
+  if (f < 1.0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) S[k] *= f;
+  }
+}
+
+// External field at an absolute position (uniform, or radial table with
+// linear interpolation between log-spaced radii).
+__device__ inline void ext_field(const KParams &P, double x, double y, double z, double g[3],
+                                 double *phi) {
+  g[0] = g[1] = g[2] = 0.0;
+  if (phi) *phi = 0.0;
+  if (P.gravity == SPH_GRAVITY_UNIFORM) {
+    g[0] = P.g_uniform[0];
+    g[1] = P.g_uniform[1];
+    g[2] = P.g_uniform[2];
+    if (phi) *phi = -(g[0] * x + g[1] * y + g[2] * z);
+    return;
+  }
+  if (P.gravity != SPH_GRAVITY_RADIAL) return;
+  const double dx = x - P.g_center[0], dy = y - P.g_center[1], dz = z - P.g_center[2];
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  if (!(r > 0.0)) return;
+  double gm, ph;
+  if (r >= P.g_rmax) {
+    gm = P.g_gm / (r * r);
+    ph = -P.g_gm / r;
+  } else if (r <= P.g_rmin) {
+    gm = P.g_table[0] * r / P.g_rmin;
+    ph = P.phi_table[0] + 0.5 * P.g_table[0] / P.g_rmin * (r * r - P.g_rmin * P.g_rmin);
+  } else {
+    int k = (int)floorf(log2f((float)(r / P.g_rmin)) * (float)P.g_inv_log_ratio);
+    k = max(0, min(k, P.g_n - 2));
+    if (r < P.g_radii[k] && k > 0) --k;
+    else if (r >= P.g_radii[k + 1] && k < P.g_n - 2) ++k;
+    const double r0 = P.g_radii[k], r1 = P.g_radii[k + 1];
+    const double w = (r - r0) / (r1 - r0);
+    gm = P.g_table[k] + w * (P.g_table[k + 1] - P.g_table[k]);
+    ph = P.phi_table[k] + w * (P.phi_table[k + 1] - P.phi_table[k]);
+  }
+  g[0] = -gm * dx / r;
+  g[1] = -gm * dy / r;
+  g[2] = -gm * dz / r;
+  if (phi) *phi = ph;
+}
+
+// Lattice support radius of a particle (first-guess scale and cap base).
+__device__ __forceinline__ double lattice_radius(int n_ngb, double m, double rho0) {
+  return cbrt(3.0 * n_ngb * m / (4.0 * kPi * rho0));
+}
+
+}  // namespace sphk
+
+// --------------------------------------------------------------- context
+struct sph_ctx {
+  sph_params params;
+  sph_material mats[SPH_MAX_MATERIALS];
+  int nmat;
+  sph_state st;
+  int64_t n;
+  cudaStream_t stream;
+  sphk::KParams kp;
+  sph_material *d_mats;
+  double *d_gtab, *d_phitab, *d_radii;
+  sphk::Work w;
+  // sort and cell list
+  unsigned *keys, *keys_alt;
+  int *vals, *vals_alt;
+  unsigned *hist;
+  int ntiles;
+  int *cell_start, *cell_end;
+  int max_cells;
+  void *tmp;            // permutation scratch: 32 words of 8 bytes per particle
+  double *partials;     // per-block diagnostic partial sums
+  int nred_blocks;
+  double *d_dt;         // device copy of the current dt
+  sphk::Status *d_status;
+  sphk::Status *h_status;   // pinned mirror
+  double *h_dt;             // pinned dt staging
+  double dt_next;
+  int timing;
+  cudaEvent_t ev[SPH_NUM_PHASES + 1];
+  double phase_ms[SPH_NUM_PHASES];
+  int timed_steps;
+  int primed;
+  int broken;
+  char err[512];
+};
+
+// Launch helpers implemented in the .cu files (all stream-ordered).
+namespace sphk {
+cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift);
+cudaError_t launch_grid_setup(sph_ctx *c);
+cudaError_t launch_sort_permute(sph_ctx *c);
+cudaError_t launch_predict_pack(sph_ctx *c, int predict);
+cudaError_t launch_density(sph_ctx *c);
+cudaError_t launch_eos_pack(sph_ctx *c);
+cudaError_t launch_forces(sph_ctx *c);
+cudaError_t launch_kick(sph_ctx *c, int kick);
+cudaError_t launch_reset_status(sph_ctx *c, int full);
+}  // namespace sphk

@@ -1,0 +1,112 @@
+// sph_update.cu -- closing and opening kicks with radial return (§2.4,
+// Eq. 41-43), FP64 global sums (energies, momentum, angular momentum Eq. 46)
+// and the time-step minimum of Eq. 38-39.
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+constexpr int kNSum = 9;
+
+// kick = 1: close to i (v, u, S alike), rescale S with Y at (rho_i, u_i),
+// accumulate 1/2 edot:edot dt, sum diagnostics at i, open to i+1/2.
+// kick = 0: diagnostics and time step of the state as it stands.
+__global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n, const double *dtp,
+                                                int kick, KParams P, double *partials,
+                                                Status *st) {
+  __shared__ double red[kNSum][kBlock / 32];
+  __shared__ double redt[kBlock / 32];
+  const double dt = kick ? *dtp : 0.0, hdt = 0.5 * dt;
+  double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double tmin = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
+    const double m = s.m[i];
+    const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
+    double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
+    double u = s.u[i];
+    if (kick && !fixed) {
+      const sph_material &M = P.mats[s.mat[i] & (SPH_MAX_MATERIALS - 1)];
+      const double dS[5] = {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]};
+      double S[5] = {s.sxx[i], s.syy[i], s.sxy[i], s.sxz[i], s.syz[i]};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] += hdt * a[k];
+      u += hdt * s.dudt[i];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) S[k] += hdt * dS[k];
+      if (M.strength) {
+        const EosOut e = eos(M, s.rho[i], u);
+        radial_return(S, yield(M, e.P, u), P.yield_norm);
+      } else {
+        S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
+      }
+      s.eps_ii[i] += dt * w.edot2[i];
+      // opening kick from the state at i
+      s.vx[i] = v[0] + hdt * a[0];
+      s.vy[i] = v[1] + hdt * a[1];
+      s.vz[i] = v[2] + hdt * a[2];
+      s.u[i] = u + hdt * s.dudt[i];
+      s.sxx[i] = S[0] + hdt * dS[0];
+      s.syy[i] = S[1] + hdt * dS[1];
+      s.sxy[i] = S[2] + hdt * dS[2];
+      s.sxz[i] = S[3] + hdt * dS[3];
+      s.syz[i] = S[4] + hdt * dS[4];
+    }
+    const double x = s.x[i], y = s.y[i], z = s.z[i];
+    double g[3], phi;
+    ext_field(P, x, y, z, g, &phi);
+    acc[0] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    acc[1] += m * u;
+    acc[2] += m * phi;
+    acc[3] += m * v[0];
+    acc[4] += m * v[1];
+    acc[5] += m * v[2];
+    acc[6] += m * (y * v[2] - z * v[1]);
+    acc[7] += m * (z * v[0] - x * v[2]);
+    acc[8] += m * (x * v[1] - y * v[0]);
+    if (!fixed) {
+      const double H = s.h[i];
+      const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      const double ta = am > 0.0 ? P.eta_a * sqrt(H / am) : INFINITY;   // Eq. 38, eps = H
+      const double tc = P.eta_c * H / w.vsig[i];                       // Eq. 39
+      tmin = fmin(tmin, fmin(ta, tc));
+    }
+  }
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNSum; ++k) acc[k] = wsum(acc[k]);
+  tmin = wmin(tmin);
+  if (lane == 0) {
+    for (int k = 0; k < kNSum; ++k) red[k][wi] = acc[k];
+    redt[wi] = tmin;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kNSum; ++k) {
+      double t = 0.0;
+      for (int q = 0; q < kBlock / 32; ++q) t += red[k][q];
+      partials[blockIdx.x * kNSum + k] = t;
+    }
+    double t = INFINITY;
+    for (int q = 0; q < kBlock / 32; ++q) t = fmin(t, redt[q]);
+    atomicMin(&st->dtmin_enc, enc_d(t));
+  }
+}
+
+// Fixed-order sum of the block partials.
+__global__ void k_reduce_final(const double *partials, int nblocks, Status *st) {
+  const int k = threadIdx.x;
+  if (k >= kNSum) return;
+  double t = 0.0;
+  for (int b = 0; b < nblocks; ++b) t += partials[b * kNSum + k];
+  st->sums[k] = t;
+}
+
+cudaError_t launch_kick(sph_ctx *c, int kick) {
+  k_kick<<<c->nred_blocks, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, kick, c->kp,
+                                                   c->partials, c->d_status);
+  k_reduce_final<<<1, 32, 0, c->stream>>>(c->partials, c->nred_blocks, c->d_status);
+  return cudaGetLastError();
+}
+
+}  // namespace sphk

@@ -1,0 +1,300 @@
+"""Python binding of libsph (include/sph.h): argument marshalling only.
+
+Every step of the SPH path runs in the CUDA library; this module loads it
+with ctypes, mirrors its structs, and hands it the device pointers of torch
+tensors. There is no fallback: if libsph.so is missing or CUDA is not
+available the calls raise.
+
+Function names follow the C ABI: sph_init, sph_neighbours, sph_density,
+sph_forces_strength, sph_stress_update, sph_step, sph_step_host, sph_prime,
+sph_destroy. ``Simulation`` bundles a workload's arrays as device tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph.so")
+_lib = None
+
+SPH_OK, SPH_E_ARG, SPH_E_CUDA, SPH_E_NOCONV, SPH_E_CAPACITY, SPH_E_NONFINITE, \
+    SPH_E_TIMEOUT, SPH_E_STATE = range(8)
+STATUS_NAMES = ["SPH_OK", "SPH_E_ARG", "SPH_E_CUDA", "SPH_E_NOCONV", "SPH_E_CAPACITY",
+                "SPH_E_NONFINITE", "SPH_E_TIMEOUT", "SPH_E_STATE"]
+MAX_MATERIALS = 8
+
+
+class SphError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s returned %s%s" % (where, name, (": " + detail) if detail else ""))
+
+
+_P = C.POINTER(C.c_double)
+_PI = C.POINTER(C.c_int32)
+_PL = C.POINTER(C.c_int64)
+
+F64_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h", "sxx", "syy", "sxy", "sxz", "syz",
+              "rho", "omega", "pres", "cs", "ax", "ay", "az", "dudt", "dsxx", "dsyy", "dsxy",
+              "dsxz", "dsyz", "eps_ii")
+I32_FIELDS = ("nngb", "mat", "flags")
+
+
+class SphState(C.Structure):
+    _fields_ = ([(f, _P) for f in F64_FIELDS] + [(f, _PI) for f in I32_FIELDS] + [("id", _PL)])
+
+
+class SphMaterial(C.Structure):
+    _fields_ = [("eos", C.c_int32), ("rho0", C.c_double), ("c0", C.c_double),
+                ("A", C.c_double), ("B", C.c_double), ("E0", C.c_double), ("a", C.c_double),
+                ("b", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+                ("Eiv", C.c_double), ("Ecv", C.c_double), ("shear_G", C.c_double),
+                ("Y0", C.c_double), ("mu_i", C.c_double), ("Ym", C.c_double),
+                ("mu_d", C.c_double), ("thermal_softening", C.c_int32), ("xi", C.c_double),
+                ("Tm", C.c_double), ("T0", C.c_double), ("cv", C.c_double),
+                ("strength", C.c_int32)]
+
+
+class SphParams(C.Structure):
+    _fields_ = [("n_ngb", C.c_int32), ("av_alpha", C.c_double), ("av_beta", C.c_double),
+                ("av_eps", C.c_double), ("eta_c", C.c_double), ("eta_a", C.c_double),
+                ("h_tol", C.c_double), ("max_sweeps", C.c_int32), ("h_cap_factor", C.c_double),
+                ("precision", C.c_int32), ("jaumann", C.c_int32), ("yield_norm", C.c_int32),
+                ("correction_tensor", C.c_int32), ("gravity", C.c_int32),
+                ("g_uniform", C.c_double * 3), ("g_table", _P), ("phi_table", _P),
+                ("g_n", C.c_int32), ("g_rmin", C.c_double), ("g_rmax", C.c_double),
+                ("g_center", C.c_double * 3), ("g_gm", C.c_double), ("periodic", C.c_int32),
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
+
+
+class SphStepInfo(C.Structure):
+    _fields_ = [("dt", C.c_double), ("dt_next", C.c_double), ("e_kin", C.c_double),
+                ("e_int", C.c_double), ("e_pot", C.c_double), ("p", C.c_double * 3),
+                ("L", C.c_double * 3), ("sweeps", C.c_int32), ("n_unconverged", C.c_int32),
+                ("n_capped", C.c_int32), ("n_cfallback", C.c_int32),
+                ("pairs_density", C.c_int64), ("pairs_force", C.c_int64),
+                ("device_flags", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
+                    e_pot=self.e_pot, p=tuple(self.p), L=tuple(self.L), sweeps=self.sweeps,
+                    n_unconverged=self.n_unconverged, n_capped=self.n_capped,
+                    n_cfallback=self.n_cfallback, pairs_density=self.pairs_density,
+                    pairs_force=self.pairs_force, device_flags=self.device_flags)
+
+
+EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
+           "sph_stress_update", "sph_step", "sph_step_host", "sph_prime", "sph_destroy",
+           "sph_status_string", "sph_last_error", "sph_set_timing", "sph_phase_times")
+PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
+
+
+def lib():
+    """Load libsph.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libsph.so not built: run `python -m paper_2603_19764_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        st = C.c_int
+        VP = C.c_void_p
+        L.sph_init.restype = st
+        L.sph_init.argtypes = [C.POINTER(VP), C.POINTER(SphParams), C.POINTER(SphMaterial),
+                               C.c_int32, C.POINTER(SphState), C.c_int64, VP]
+        for name in ("sph_neighbours", "sph_destroy"):
+            getattr(L, name).restype = st
+            getattr(L, name).argtypes = [VP]
+        L.sph_density.restype = st
+        L.sph_density.argtypes = [VP, _PI]
+        L.sph_forces_strength.restype = st
+        L.sph_forces_strength.argtypes = [VP]
+        L.sph_stress_update.restype = st
+        L.sph_stress_update.argtypes = [VP, C.c_double]
+        L.sph_step.restype = st
+        L.sph_step.argtypes = [VP, C.c_double, C.POINTER(SphStepInfo)]
+        L.sph_step_host.restype = st
+        L.sph_step_host.argtypes = [VP, C.POINTER(SphState), C.c_double, C.POINTER(SphStepInfo),
+                                    _PL, _PL]
+        L.sph_prime.restype = st
+        L.sph_prime.argtypes = [VP, C.POINTER(SphStepInfo)]
+        L.sph_set_timing.restype = st
+        L.sph_set_timing.argtypes = [VP, C.c_int32]
+        L.sph_phase_times.restype = st
+        L.sph_phase_times.argtypes = [VP, _P, C.c_int32, _PI]
+        L.sph_status_string.restype = C.c_char_p
+        L.sph_status_string.argtypes = [st]
+        L.sph_last_error.restype = C.c_char_p
+        L.sph_last_error.argtypes = [VP]
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- marshalling
+def make_material(d: dict) -> SphMaterial:
+    m = SphMaterial()
+    for name, _ in SphMaterial._fields_:
+        setattr(m, name, d[name])
+    return m
+
+
+def make_params(d: dict, keep: list) -> SphParams:
+    p = SphParams()
+    for name, _ in SphParams._fields_:
+        if name in ("g_table", "phi_table", "g_n"):
+            continue
+        if name in ("g_uniform", "g_center", "box_lo", "box_hi"):
+            getattr(p, name)[:] = tuple(float(v) for v in d[name])
+        else:
+            setattr(p, name, d[name])
+    if d.get("g_table") is not None:
+        g = np.ascontiguousarray(d["g_table"], np.float64)
+        ph = np.ascontiguousarray(d["phi_table"], np.float64)
+        keep += [g, ph]
+        p.g_table = g.ctypes.data_as(_P)
+        p.phi_table = ph.ctypes.data_as(_P)
+        p.g_n = g.shape[0]
+    return p
+
+
+def state_from_ptrs(ptrs: dict) -> SphState:
+    s = SphState()
+    for f in F64_FIELDS:
+        setattr(s, f, C.cast(C.c_void_p(ptrs[f]), _P))
+    for f in I32_FIELDS:
+        setattr(s, f, C.cast(C.c_void_p(ptrs[f]), _PI))
+    s.id = C.cast(C.c_void_p(ptrs["id"]), _PL)
+    return s
+
+
+class Simulation:
+    """Device-resident particle set driven through the C ABI.
+
+    arrays: dict of numpy arrays (workloads.FIELDS_*); params / materials:
+    dicts as built by workloads. The state lives in torch CUDA tensors.
+    """
+
+    def __init__(self, arrays: dict, materials: list, params: dict, device: str = "cuda:0",
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA device required: the SPH path has no CPU fallback")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = int(arrays["x"].shape[0])
+        self.t = {}
+        for f in F64_FIELDS:
+            self.t[f] = torch.as_tensor(np.ascontiguousarray(arrays[f], np.float64)).to(self.device)
+        for f in I32_FIELDS:
+            self.t[f] = torch.as_tensor(np.ascontiguousarray(arrays[f], np.int32)).to(self.device)
+        self.t["id"] = torch.as_tensor(np.ascontiguousarray(arrays["id"], np.int64)).to(self.device)
+        self._keep = []
+        self.params = make_params(params, self._keep)
+        mats = (SphMaterial * len(materials))()
+        for k, d in enumerate(materials):
+            mats[k] = make_material(d)
+        self._mats = mats
+        self.state = state_from_ptrs({k: v.data_ptr() for k, v in self.t.items()})
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        torch.cuda.synchronize(self.device)
+        self.ctx = C.c_void_p()
+        rc = lib().sph_init(C.byref(self.ctx), C.byref(self.params), mats, len(materials),
+                            C.byref(self.state), self.n, C.c_void_p(self.stream.cuda_stream))
+        if rc != SPH_OK:
+            raise SphError(rc, "sph_init")
+
+    # -- calls ---------------------------------------------------------------
+    def _check(self, rc, where, allow=()):
+        if rc != SPH_OK and rc not in allow:
+            detail = lib().sph_last_error(self.ctx).decode()
+            raise SphError(rc, where, detail)
+        return rc
+
+    def neighbours(self):
+        return self._check(lib().sph_neighbours(self.ctx), "sph_neighbours")
+
+    def density(self, allow_noconv: bool = False) -> int:
+        sw = C.c_int32()
+        self._check(lib().sph_density(self.ctx, C.byref(sw)), "sph_density",
+                    (SPH_E_NOCONV,) if allow_noconv else ())
+        return sw.value
+
+    def forces_strength(self):
+        return self._check(lib().sph_forces_strength(self.ctx), "sph_forces_strength")
+
+    def stress_update(self, dt: float):
+        return self._check(lib().sph_stress_update(self.ctx, float(dt)), "sph_stress_update")
+
+    def prime(self) -> dict:
+        info = SphStepInfo()
+        self._check(lib().sph_prime(self.ctx, C.byref(info)), "sph_prime")
+        return info.as_dict()
+
+    def step(self, dt: float = 0.0, allow=()) -> dict:
+        info = SphStepInfo()
+        rc = self._check(lib().sph_step(self.ctx, float(dt), C.byref(info)), "sph_step", allow)
+        d = info.as_dict()
+        d["status"] = rc
+        return d
+
+    def step_host(self, host: "HostState", dt: float) -> dict:
+        info = SphStepInfo()
+        bi, bo = C.c_int64(), C.c_int64()
+        self._check(lib().sph_step_host(self.ctx, C.byref(host.state), float(dt), C.byref(info),
+                                        C.byref(bi), C.byref(bo)), "sph_step_host")
+        d = info.as_dict()
+        d.update(bytes_in=bi.value, bytes_out=bo.value)
+        return d
+
+    def set_timing(self, on: bool = True):
+        return self._check(lib().sph_set_timing(self.ctx, 1 if on else 0), "sph_set_timing")
+
+    def phase_times(self) -> dict:
+        """Accumulated CUDA-event milliseconds per phase and the step count."""
+        ms = (C.c_double * len(PHASES))()
+        steps = C.c_int32()
+        self._check(lib().sph_phase_times(self.ctx, ms, len(PHASES), C.byref(steps)),
+                    "sph_phase_times")
+        d = {name: ms[k] for k, name in enumerate(PHASES)}
+        d["steps"] = steps.value
+        return d
+
+    # -- data ----------------------------------------------------------------
+    def to_numpy(self, fields=None) -> dict:
+        self.torch.cuda.synchronize(self.device)
+        fields = fields or list(self.t)
+        return {f: self.t[f].cpu().numpy() for f in fields}
+
+    def by_id(self, fields=None) -> dict:
+        """Arrays reordered by the caller's particle id (undoes the sort)."""
+        a = self.to_numpy(list(fields or self.t) + ["id"])
+        order = np.argsort(a["id"], kind="stable")
+        return {k: v[order] for k, v in a.items()}
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().sph_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostState:
+    """Pinned host copy of a particle set for sph_step_host."""
+
+    def __init__(self, arrays: dict):
+        import torch
+        self.t = {}
+        for f in F64_FIELDS:
+            self.t[f] = torch.as_tensor(np.ascontiguousarray(arrays[f], np.float64)).pin_memory()
+        for f in I32_FIELDS:
+            self.t[f] = torch.as_tensor(np.ascontiguousarray(arrays[f], np.int32)).pin_memory()
+        self.t["id"] = torch.as_tensor(np.ascontiguousarray(arrays["id"], np.int64)).pin_memory()
+        self.state = state_from_ptrs({k: v.data_ptr() for k, v in self.t.items()})

@@ -1,0 +1,97 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/sph.h declares, and the binding's struct layouts match the C
+compiler's. No compute call is made here."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2603_19764_b300 import build, sph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sph.h")
+
+
+@pytest.fixture(scope="module")
+def libsph():
+    build.build()
+    return C.CDLL(sph.LIB_PATH)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
+                     "sph_stress_update", "sph_step", "sph_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libsph):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", sph.LIB_PATH], text=True)
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(libsph, name)
+    assert set(sph.EXPORTS) <= set(declared_functions())
+
+
+def _c_layout():
+    src = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "sph.h"
+#define S(T) printf(#T " %zu\n", sizeof(T));
+#define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  S(sph_state) S(sph_material) S(sph_params) S(sph_step_info)
+  O(sph_state, id) O(sph_state, nngb) O(sph_material, strength) O(sph_material, xi)
+  O(sph_params, g_table) O(sph_params, g_n) O(sph_params, box_hi) O(sph_params, precision)
+  O(sph_step_info, pairs_density) O(sph_step_info, device_flags) O(sph_step_info, sweeps)
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), "-o", exe, c])
+        out = subprocess.check_output([exe], text=True)
+    return dict(ln.rsplit(" ", 1) for ln in out.strip().splitlines())
+
+
+def test_struct_layouts_match_binding():
+    lay = _c_layout()
+    py = {"sph_state": sph.SphState, "sph_material": sph.SphMaterial,
+          "sph_params": sph.SphParams, "sph_step_info": sph.SphStepInfo}
+    for name, cls in py.items():
+        assert int(lay[name]) == C.sizeof(cls), name
+    for key, val in lay.items():
+        if "." in key:
+            t, f = key.split(".")
+            assert getattr(py[t], f).offset == int(val), key
+
+
+def test_status_strings(libsph):
+    libsph.sph_status_string.restype = C.c_char_p
+    for k, name in enumerate(sph.STATUS_NAMES):
+        s = libsph.sph_status_string(k)
+        assert s and len(s) > 1
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu(libsph):
+    """Argument checks run before any CUDA call."""
+    libsph.sph_init.restype = C.c_int
+    ctx = C.c_void_p()
+    assert libsph.sph_init(C.byref(ctx), None, None, 1, None, 10, None) == sph.SPH_E_ARG
+    assert libsph.sph_init(None, None, None, 1, None, 10, None) == sph.SPH_E_ARG
+    assert ctx.value is None
+    libsph.sph_destroy.restype = C.c_int
+    assert libsph.sph_destroy(None) == sph.SPH_OK
