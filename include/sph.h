@@ -93,7 +93,10 @@ typedef struct {
  * (rho0, A, B, E0, a, b, alpha, beta, Eiv, Ecv). Shear modulus shear_G, or
  * Eq. 30 with nu = 0.25 when shear_G < 0. Yield: Eq. 34-36 with (Y0, mu_i,
  * Ym, mu_d); thermal softening Eq. 37 with T = T0 + u / cv when
- * thermal_softening != 0. strength = 0 makes the material a fluid (S = 0). */
+ * thermal_softening != 0. strength = 0 makes the material a fluid (S = 0).
+ * p_min floors the pressure the EOS returns (-INFINITY: no floor; 0 for a
+ * cohesionless medium that carries no tension); the sound speed is that of
+ * the unfloored EOS. */
 typedef struct {
   int32_t eos;
   double rho0, c0;
@@ -103,6 +106,7 @@ typedef struct {
   int32_t thermal_softening;
   double xi, Tm, T0, cv;
   int32_t strength;
+  double p_min;
 } sph_material;
 
 /* Run-time parameters.
@@ -141,7 +145,10 @@ typedef struct {
 
 /* Per-step report (filled by the synchronising calls). Energies and
  * momenta are FP64 sums over all particles at time i (x_i, v_i, u_i);
- * L = sum m r x v (Eq. 46). dt_next is the minimum of Eq. 38-39. */
+ * L = sum m r x v (Eq. 46). dt_next is the minimum of Eq. 38-39.
+ * pairs_density counts the in-range pairs evaluated over all Newton sweeps,
+ * pairs_force the pairs of the force loop; cand_* count the candidates the
+ * two pair kernels staged (work done to find those pairs). */
 typedef struct {
   double dt, dt_next;
   double e_kin, e_int, e_pot;
@@ -149,6 +156,7 @@ typedef struct {
   int32_t sweeps, n_unconverged, n_capped, n_cfallback;
   int64_t pairs_density, pairs_force;
   uint32_t device_flags;
+  int64_t cand_density, cand_force;
 } sph_step_info;
 
 /* Create a context for n particles in `st` on `cuda_stream` (a cudaStream_t,

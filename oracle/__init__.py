@@ -44,7 +44,7 @@ class RefMaterial(C.Structure):
                 ("Y0", C.c_double), ("mu_i", C.c_double), ("Ym", C.c_double),
                 ("mu_d", C.c_double), ("thermal_softening", C.c_int32), ("xi", C.c_double),
                 ("Tm", C.c_double), ("T0", C.c_double), ("cv", C.c_double),
-                ("strength", C.c_int32)]
+                ("strength", C.c_int32), ("p_min", C.c_double)]
 
 
 _P = C.POINTER(C.c_double)

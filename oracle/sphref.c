@@ -98,9 +98,13 @@ static void till_expanded(const ref_material *mt, double rho, double u,
   *dPdu = mt->a * rho + dinner_du * ez;
 }
 
+/* Reading: a material may floor its pressure (p_min; a cohesionless
+ * granular medium carries no tension, p_min = 0). The floor applies to P
+ * only; the sound speed is that of the unfloored EOS. */
 void ref_eos(const ref_material *mt, double rho, double u, double *P, double *cs) {
   if (mt->eos == REF_EOS_LINEAR) {
-    *P = mt->c0 * mt->c0 * (rho - mt->rho0);
+    double pl = mt->c0 * mt->c0 * (rho - mt->rho0);
+    *P = pl < mt->p_min ? mt->p_min : pl;
     *cs = mt->c0;
     return;
   }
@@ -120,7 +124,7 @@ void ref_eos(const ref_material *mt, double rho, double u, double *P, double *cs
   double c2 = pr + p / (rho * rho) * pu;
   double c2min = 0.01 * mt->A / mt->rho0;
   if (!(c2 >= c2min)) c2 = c2min;
-  *P = p;
+  *P = p < mt->p_min ? mt->p_min : p;
   *cs = sqrt(c2);
 }
 

@@ -33,6 +33,7 @@ typedef struct {
   int32_t thermal_softening; /* Eq. 37 on/off */
   double xi, Tm, T0, cv;  /* Eq. 37 and T = T0 + u / cv */
   int32_t strength;       /* 0: fluid, S stays zero */
+  double p_min;           /* pressure floor of the EOS (-inf: none) */
 } ref_material;
 
 /* Run-time parameters. */

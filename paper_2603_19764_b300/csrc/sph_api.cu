@@ -66,9 +66,10 @@ void free_all(sph_ctx *c) {
                  c->w.vp[2], c->w.up, c->w.sp[0], c->w.sp[1], c->w.sp[2], c->w.sp[3],
                  c->w.sp[4], c->w.vsig, c->w.edot2, c->w.yld, c->w.cc, c->w.pos32, c->w.pos64,
                  c->w.fj32[0], c->w.fj32[1], c->w.fj32[2], c->w.fj32[3], c->w.fj64[0],
-                 c->w.fj64[1], c->w.fj64[2], c->w.fj64[3], c->keys, c->keys_alt, c->vals,
-                 c->vals_alt, c->hist, c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt,
-                 c->d_status};
+                 c->w.fj64[1], c->w.fj64[2], c->w.fj64[3], c->w.posh32, c->w.posh64,
+                 c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
+                 c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
+                 c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -107,6 +108,8 @@ sph_status sync_status(sph_ctx *c, sph_step_info *info, double dt) {
     info->n_cfallback = h.n_cfallback;
     info->pairs_density = (int64_t)h.pairs_density;
     info->pairs_force = (int64_t)h.pairs_force;
+    info->cand_density = (int64_t)h.cand_density;
+    info->cand_force = (int64_t)h.cand_force;
     info->device_flags = h.err;
   }
   return status_from_flags(c, h.err);
@@ -273,10 +276,14 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
   CKI(dalloc(&w.cc, n));
   if (fp32) {
     CKI(dalloc(&w.pos32, n));
+    CKI(dalloc(&w.posh32, n));
     for (int k = 0; k < 4; ++k) CKI(dalloc(&w.fj32[k], n));
+    for (int k = 0; k < 3; ++k) CKI(dalloc(&w.fs32[k], n));
   } else {
     CKI(dalloc(&w.pos64, n));
+    CKI(dalloc(&w.posh64, n));
     for (int k = 0; k < 4; ++k) CKI(dalloc(&w.fj64[k], n));
+    for (int k = 0; k < 3; ++k) CKI(dalloc(&w.fs64[k], n));
   }
   CKI(dalloc(&c->keys, n));
   CKI(dalloc(&c->keys_alt, n));
@@ -284,6 +291,7 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
   CKI(dalloc(&c->vals_alt, n));
   c->ntiles = (int)((n + 2047) / 2048);
   CKI(dalloc(&c->hist, (size_t)256 * c->ntiles));
+  CKI(dalloc(&c->scan_tot, (size_t)(256 * c->ntiles + 1023) / 1024 + 1));
   int64_t mc = 2 * n;
   if (mc < 4096) mc = 4096;
   if (mc > (1 << 24)) mc = 1 << 24;

@@ -2,22 +2,21 @@
 // smoothing-length solve (§2.1, Eq. 1-3).
 //
 // One warp owns a bucket of 32 consecutive (cell-sorted) particles, one
-// particle per lane. Lanes whose cells lie within two cells of the first
-// unfinished lane form a group; the group's candidate neighbours (particles
-// of the cells within ceil(R / L_c) of the group's cells, R the largest H in
-// the group) are staged through a per-warp shared-memory list after a
-// bounding-box filter, and every lane evaluates the list against its own
-// particle. Each particle's Newton iteration on its own H runs inside the
-// kernel: the density of particle i depends only on H_i, so no global sweep
-// synchronisation is needed.
+// particle per lane, processed group by group (sph_pair.cuh). A group stages
+// every particle within 1.05 R of its bounding box (R the largest H of its
+// unconverged lanes) into shared memory once; each lane then marks, in a
+// private bit mask, the staged particles within 1.05 H_i of itself and walks
+// only those, testing r < H_i exactly. Newton sweeps reuse the staged list
+// and the masks until some H outgrows them. The density of particle i
+// depends on H_i alone, so every particle's iteration runs inside the kernel
+// without global synchronisation.
 //
 // FP64 form: absolute positions, canonical predicate r^2 = (dx dx + dy dy) +
 // dz dz without fused multiply-add. FP32 form: positions relative to the
-// group's reference cell; pairs with |r^2 - H^2| < 1e-5 H^2 are re-decided
-// with the FP64 predicate so that neighbour counts stay exact.
-#include <type_traits>
-
-#include "sph_internal.cuh"
+// group's reference cell, FP32 sums and Newton arithmetic (H itself is kept
+// in FP64); pairs with |r^2 - H^2| < 1e-5 H^2 are re-decided with the FP64
+// predicate so that neighbour counts stay exact.
+#include "sph_pair.cuh"
 
 namespace sphk {
 
@@ -64,21 +63,6 @@ cudaError_t launch_predict_pack(sph_ctx *c, int predict) {
 }
 
 // ---------------------------------------------------------------- density
-template <typename T> struct Vec4;
-template <> struct Vec4<float> {
-  using type = float4;
-  static __device__ __forceinline__ float4 load(const Work &w, int64_t i) { return __ldg(w.pos32 + i); }
-};
-template <> struct Vec4<double> {
-  using type = double4_32a;
-  static __device__ __forceinline__ double4_32a load(const Work &w, int64_t i) { return w.pos64[i]; }
-};
-
-template <typename T, int CAP> struct DList {
-  T x[CAP], y[CAP], z[CAP], m[CAP];
-  int idx[CAP];
-};
-
 struct DensArgs {
   sph_state s;
   Work w;
@@ -88,173 +72,223 @@ struct DensArgs {
   Status *st;
 };
 
+template <typename T> struct PosPtr;
+template <> struct PosPtr<float> {
+  static __device__ __forceinline__ const float4 *get(const Work &w) { return w.pos32; }
+};
+template <> struct PosPtr<double> {
+  static __device__ __forceinline__ const double4_32a *get(const Work &w) { return w.pos64; }
+};
+
 // Canonical FP64 squared distance (no contraction).
 __device__ __forceinline__ double r2_canon(double dx, double dy, double dz) {
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// Per-lane bit masks over the staged list: bit k set when r_k^2 < R2.
+// Lanes with store = false compute but keep their previous words.
+template <typename T, typename V4>
+__device__ __forceinline__ void build_masks(const V4 *Lp, unsigned (*Lm)[32], int nl, T xi, T yi,
+                                            T zi, T R2, bool store, int lane) {
+  const int nw = (nl + 31) >> 5;
+  for (int wd = 0; wd < nw; ++wd) {
+    const int kb = wd << 5;
+    const int kend = min(32, nl - kb);
+    unsigned mk = 0;
+#pragma unroll 4
+    for (int b = 0; b < kend; ++b) {
+      const V4 q = Lp[kb + b];
+      const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      mk |= (r2 < R2 ? 1u : 0u) << b;
+    }
+    if (store) Lm[wd][lane] = mk;
+  }
+}
+
+// Walk one lane's marked candidates: exact membership r < H_i, then the
+// kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
+template <typename T, typename V4, bool REL>
+__device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsigned (*Lm)[32],
+                                             int nl, int lane, T xi, T yi, T zi, T Ht, T H2,
+                                             double H2c, double xi64, double yi64, double zi64,
+                                             const sph_state &s, int self, T &rs, T &rhs,
+                                             int &cnt) {
+  const int nw = (nl + 31) >> 5;
+  for (int wd = 0; wd < nw; ++wd) {
+    unsigned mk = Lm[wd][lane];
+    while (mk) {
+      const int k = (wd << 5) + __ffs(mk) - 1;
+      mk &= mk - 1u;
+      const V4 q = Lp[k];
+      const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+      T r2;
+      bool in;
+      if (REL) {
+        r2 = dx * dx + dy * dy + dz * dz;
+        in = r2 < H2;
+        if (fabs(r2 - H2) < T(1e-5) * H2) {
+          const int j = Li[k];
+          in = r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]) < H2c;
+        }
+      } else {
+        r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
+        in = r2 < H2;
+      }
+      if (in) {
+        const T r = r2 > T(0) ? sqrt(r2) : T(0);
+        const T qq = r / Ht;
+        const T t = qq < T(1) ? T(1) - qq : T(0);
+        const T mW = q.w * t * t * t;
+        rs += mW * t * (T(1) + T(4) * qq);
+        rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
+        cnt += (Li[k] != self);
+      }
+    }
+  }
+}
+
 template <typename T, int CAP>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
-  using V4 = typename Vec4<T>::type;
-  __shared__ DList<T, CAP> lists[kWarpsPerBlock];
+  using V = V4T<T>;
+  using V4 = typename V::type;
+  __shared__ V4 s_pos[kWarpsPerBlock][CAP];
+  __shared__ int s_idx[kWarpsPerBlock][CAP];
+  __shared__ unsigned s_mask[kWarpsPerBlock][CAP / 32][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  DList<T, CAP> &Ls = lists[wib];
+  V4 *Lp = s_pos[wib];
+  int *Li = s_idx[wib];
+  unsigned(*Lm)[32] = s_mask[wib];
   const int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + wib) * 32;
   if (base >= A.n) return;
   const int64_t i = base + lane;
   const bool valid = i < A.n;
   const int64_t ic = valid ? i : base;
+  const V4 *pos = PosPtr<T>::get(A.w);
 
   const Grid g = A.st->grid;
   const T Lt = (T)g.L;
-  const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
-  const V4 p = Vec4<T>::load(A.w, ic);
-  const double mi = A.s.m[ic];
+  const V4 p = V::ld(pos, ic);
+  const T mi = p.w;
   const sph_material &M = A.p.mats[A.s.mat[ic] & (SPH_MAX_MATERIALS - 1)];
-  const double target = A.p.n_ngb * mi;
-  const double Hcap = A.p.h_cap_factor * lattice_radius(A.p.n_ngb, mi, M.rho0);
+  const T target = (T)A.p.n_ngb * mi;
+  const T tol = (T)A.p.h_tol;
+  const double Hcap =
+      A.p.h_cap_factor * (double)cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
   double H = fmin(A.s.h[ic], Hcap);
-  double xi64 = 0.0, yi64 = 0.0, zi64 = 0.0;
-  if (REL) {
-    xi64 = A.s.x[ic];
-    yi64 = A.s.y[ic];
-    zi64 = A.s.z[ic];
-  }
+  const double xi64 = A.s.x[ic], yi64 = A.s.y[ic], zi64 = A.s.z[ic];
   // Newton state: 0 running, 1 converged, 2 capped, 3 gave up, 4 idle lane
   int state = valid ? 0 : 4;
-  double lo = 0.0, hi = INFINITY;
-  double rho_o = 0.0, om_o = 1.0, H_o = H;
+  double lo = 0.0, hi = INFINITY, H_o = H;
+  T rho_o = T(0), om_o = T(1);
   int cnt_o = 0, sweeps_o = 0;
-  long long pairs = 0;
+  long long pairs = 0, cand = 0;
 
   unsigned todo = __ballot_sync(kFull, valid);
   while (todo) {
-    const int ref = __ffs(todo) - 1;
-    const int rx = __shfl_sync(kFull, cx, ref), ry = __shfl_sync(kFull, cy, ref),
-              rz = __shfl_sync(kFull, cz, ref);
-    const bool member = ((todo >> lane) & 1u) && abs(cx - rx) <= 2 && abs(cy - ry) <= 2 &&
-                        abs(cz - rz) <= 2;
-    todo &= ~__ballot_sync(kFull, member);
-    const T xi = REL ? p.x + (T)(cx - rx) * Lt : p.x;
-    const T yi = REL ? p.y + (T)(cy - ry) * Lt : p.y;
-    const T zi = REL ? p.z + (T)(cz - rz) * Lt : p.z;
+    const Group G = next_group(todo, cx, cy, cz);
+    const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
+    const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
+    const T zi = REL ? p.z + (T)(cz - G.rz) * Lt : p.z;
+    bool complete = false;   // the list holds every particle within Rl of the box
+    T Rl = T(0), Hm = T(0);  // list radius; this lane's mask radius
+    int nl = 0;
 
     for (int sweep = 1; sweep <= A.p.max_sweeps; ++sweep) {
-      const bool act = member && state == 0;
+      const bool act = G.member && state == 0;
       if (!__any_sync(kFull, act)) break;
       const T Ht = (T)H;
       const double H2c = __dmul_rn(H, H);
       const T H2 = REL ? Ht * Ht : (T)H2c;
-      const T invH = (T)(1.0 / H);
-      const T R = wmax(act ? Ht : T(0));
-      const T bx0 = wmin(act ? xi : T(1e30)), bx1 = wmax(act ? xi : T(-1e30));
-      const T by0 = wmin(act ? yi : T(1e30)), by1 = wmax(act ? yi : T(-1e30));
-      const T bz0 = wmin(act ? zi : T(1e30)), bz1 = wmax(act ? zi : T(-1e30));
-      const int x0 = wmin(act ? cx : 1 << 20), x1 = wmax(act ? cx : -1);
-      const int y0 = wmin(act ? cy : 1 << 20), y1 = wmax(act ? cy : -1);
-      const int z0 = wmin(act ? cz : 1 << 20), z1 = wmax(act ? cz : -1);
-      const int span = max(1, (int)ceil((double)R / g.L));
-      T rs = 0, rhs = 0;
+      const T Rneed = wmax(act ? Ht : T(0));
+      T rs = T(0), rhs = T(0);
       int cnt = 0;
-      int nl = 0;
-
-      auto evaluate = [&](int nlist) {
-        for (int k = 0; k < nlist; ++k) {
-          const T dx = xi - Ls.x[k], dy = yi - Ls.y[k], dz = zi - Ls.z[k];
-          T r2;
-          bool in;
-          if (REL) {
-            r2 = dx * dx + dy * dy + dz * dz;
-            in = r2 < H2;
-            if (act && fabs(r2 - H2) < T(1e-5) * H2) {
-              const int j = Ls.idx[k];
-              in = r2_canon(xi64 - A.s.x[j], yi64 - A.s.y[j], zi64 - A.s.z[j]) < H2c;
+      const bool resident = complete && Rneed <= Rl;
+      if (!resident) {
+        Rl = Rneed * T(1.05);
+        const Box<T> bx = group_box(act, xi, yi, zi);
+        Stager<T> sg = make_stager<T, REL>(bx, Rl, g, G.rx, G.ry, G.rz);
+        Hm = T(0);
+        complete = false;
+        for (int seg = 0;; ++seg) {
+          nl = 0;
+          while (nl <= CAP - 32) {
+            if (sg.jb >= sg.je &&
+                !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, G.rx, G.ry, G.rz, Lt))
+              break;
+            const int j = sg.jb + lane;
+            const bool ok = j < sg.je;
+            const V4 q = ok ? V::ld(pos, j) : V::make(0, 0, 0, 0);
+            const T xj = q.x + sg.ox, yj = q.y + sg.oy, zj = q.z + sg.oz;
+            const bool keep =
+                ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < Rl * Rl;
+            const unsigned bal = __ballot_sync(kFull, keep);
+            if (keep) {
+              const int at = nl + __popc(bal & lanemask_lt());
+              Lp[at] = V::make(xj, yj, zj, q.w);
+              Li[at] = j;
             }
-          } else {
-            r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
-            in = r2 < H2;
+            nl += __popc(bal);
+            sg.jb += 32;
           }
-          if (act && in) {
-            const T r = r2 > T(0) ? sqrt(r2) : T(0);
-            const T q = r * invH;
-            const T t = q < T(1) ? T(1) - q : T(0);
-            const T t3 = t * t * t;
-            const T mW = Ls.m[k] * t3;
-            rs += mW * t * (T(1) + T(4) * q);
-            rhs += mW * (T(-3) + q * (T(-9) + T(32) * q));
-            cnt += (Ls.idx[k] != (int)i);
+          cand += nl;
+          if (seg == 0 && sg.done) {
+            complete = true;
+            break;
           }
+          // list longer than the buffer: evaluate this segment exactly
+          __syncwarp();
+          build_masks<T, V4>(Lp, Lm, nl, xi, yi, zi, H2 * T(1.0001), act, lane);
+          __syncwarp();
+          if (act)
+            density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, Ht, H2, H2c, xi64, yi64,
+                                     zi64, A.s, (int)i, rs, rhs, cnt);
+          __syncwarp();
+          if (sg.done) break;
         }
-      };
-
-      for (int z = max(z0 - span, 0); z <= min(z1 + span, nz - 1); ++z)
-        for (int y = max(y0 - span, 0); y <= min(y1 + span, ny - 1); ++y)
-          for (int x = max(x0 - span, 0); x <= min(x1 + span, nx - 1); ++x) {
-            const int c = (z * ny + y) * nx + x;
-            const int s0 = A.cell_start[c];
-            if (s0 < 0) continue;
-            const int s1 = A.cell_end[c];
-            const T ox = REL ? (T)(x - rx) * Lt : T(0);
-            const T oy = REL ? (T)(y - ry) * Lt : T(0);
-            const T oz = REL ? (T)(z - rz) * Lt : T(0);
-            for (int jb = s0; jb < s1; jb += 32) {
-              const int j = jb + lane;
-              const bool ok = j < s1;
-              V4 q;
-              if (ok) q = Vec4<T>::load(A.w, j);
-              else q.x = q.y = q.z = q.w = T(0);
-              const T xj = q.x + ox, yj = q.y + oy, zj = q.z + oz;
-              const T ex = fmax(bx0 - xj, fmax(T(0), xj - bx1));
-              const T ey = fmax(by0 - yj, fmax(T(0), yj - by1));
-              const T ez = fmax(bz0 - zj, fmax(T(0), zj - bz1));
-              const bool keep = ok && (ex * ex + ey * ey + ez * ez < R * R * T(1.0001));
-              const unsigned bal = __ballot_sync(kFull, keep);
-              if (keep) {
-                const int at = nl + __popc(bal & lanemask_lt());
-                Ls.x[at] = xj;
-                Ls.y[at] = yj;
-                Ls.z[at] = zj;
-                Ls.m[at] = q.w;
-                Ls.idx[at] = j;
-              }
-              nl += __popc(bal);
-              if (nl > CAP - 32) {
-                __syncwarp();
-                evaluate(nl);
-                __syncwarp();
-                nl = 0;
-              }
-            }
-          }
-      __syncwarp();
-      evaluate(nl);
-      __syncwarp();
+      }
+      if (complete) {
+        // resident list: refresh the masks of lanes whose H outgrew them
+        const bool rebuild = act && !(Hm >= Ht * T(1.0001));
+        if (__any_sync(kFull, rebuild)) {
+          const T Hn = rebuild ? Ht * T(1.05) : Hm;
+          __syncwarp();
+          build_masks<T, V4>(Lp, Lm, nl, xi, yi, zi, Hn * Hn, rebuild, lane);
+          __syncwarp();
+          Hm = Hn;
+        }
+        if (act)
+          density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, Ht, H2, H2c, xi64, yi64, zi64,
+                                   A.s, (int)i, rs, rhs, cnt);
+      }
 
       if (act) {
-        // Eq. 1 and Eq. 3 with the kernel constants applied once
-        const double ih = 1.0 / H;
-        const double rho = cW * ih * ih * ih * (double)rs;
-        const double rhoH = cW * ih * ih * ih * ih * (double)rhs;
-        const double om = 1.0 + H / (3.0 * rho) * rhoH;
-        const double gv = 4.0 * kPi / 3.0 * H * H * H * rho - target;
+        // Eq. 1 and Eq. 3 with the kernel constants applied once; the
+        // residual is relative to the target kernel mass n_ngb m_i
+        const T ih = T(1) / Ht;
+        const T ih3 = ih * ih * ih;
+        const T rho = T(cW) * ih3 * rs;
+        const T rhoH = T(cW) * ih3 * ih * rhs;
+        const T om = T(1) + Ht / (T(3) * rho) * rhoH;
+        const T gq = T(4.0 * kPi / 3.0) * Ht * Ht * Ht * rho / target - T(1);
         rho_o = rho;
         om_o = om;
         cnt_o = cnt;
         H_o = H;
         sweeps_o = sweep;
         pairs += cnt;
-        if (fabs(gv) <= A.p.h_tol * target) {
+        if (fabs(gq) <= tol) {
           state = 1;
-        } else if (gv < 0.0 && H >= Hcap) {
+        } else if (gq < T(0) && H >= Hcap) {
           state = 2;
         } else {
-          if (gv < 0.0) lo = H;
+          if (gq < T(0)) lo = H;
           else hi = H;
-          const double gp = 4.0 * kPi * H * H * rho * om;
-          double Hn = gp > 0.0 ? H - gv / gp : (gv < 0.0 ? 1.25 * H : 0.75 * H);
+          const T gp = T(4.0 * kPi) * Ht * Ht * rho * om / target;
+          double Hn = gp > T(0) ? H - (double)(gq / gp) : (gq < T(0) ? 1.25 * H : 0.75 * H);
           if (!(Hn >= 0.75 * H)) Hn = 0.75 * H;
           if (!(Hn <= 1.25 * H)) Hn = 1.25 * H;
           if (hi < INFINITY && (Hn <= lo || Hn >= hi)) Hn = 0.5 * (lo + hi);
@@ -263,20 +297,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
         }
       }
     }
-    if (member && state == 0) state = 3;
+    if (G.member && state == 0) state = 3;
   }
 
   if (valid) {
     A.s.h[i] = H_o;
-    A.s.rho[i] = rho_o;
-    A.s.omega[i] = om_o;
+    A.s.rho[i] = (double)rho_o;
+    A.s.omega[i] = (double)om_o;
     A.s.nngb[i] = cnt_o;
   }
-  // step record: one atomic of each kind per warp
   const int sw = wmax(valid ? sweeps_o : 0);
   const int nu = __popc(__ballot_sync(kFull, state == 3));
   const int ncap = __popc(__ballot_sync(kFull, state == 2));
-  const bool bad = valid && !(isfinite(rho_o) && isfinite(om_o) && rho_o > 0.0);
+  const bool bad = valid && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0));
   const unsigned nbad = __ballot_sync(kFull, bad);
   const double hm = wmax(valid ? H_o : 0.0);
   const long long pw = wsum(pairs);
@@ -290,6 +323,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
     if (nbad) atomicOr(&A.st->err, ERR_NONFINITE);
     atomicMax(&A.st->hmax2_enc, enc_d(hm));
     atomicAdd(&A.st->pairs_density, (unsigned long long)pw);
+    atomicAdd(&A.st->cand_density, (unsigned long long)cand);
   }
 }
 
@@ -305,7 +339,7 @@ cudaError_t launch_density(sph_ctx *c) {
   const int64_t buckets = (c->n + 31) / 32;
   const int blocks = (int)((buckets + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (c->kp.precision == SPH_FP32K)
-    k_density<float, 256><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    k_density<float, 512><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
   else
     k_density<double, 256><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
   return cudaGetLastError();

@@ -3,14 +3,14 @@
 // finalize (§2.1-§2.3: Eq. 4-8, 13, 18-37).
 //
 // Pair loop layout: one warp per bucket of 32 cell-sorted particles (one per
-// lane), grouped as in the density kernel. Candidates j (cells within
-// ceil(max(H_bucket, H_max) / L_c), bounding-box filtered against
-// max(H_bucket, H_j)) are staged in a per-warp shared-memory list. Each lane
-// first tests the whole list against its particle (broadcast reads, one bit
-// per candidate: r < max(H_i, H_j), j != i), then walks its own set bits
-// independently, so the heavy pair body runs only for real neighbours. The
-// neighbour data (velocity, mass, m sigma / (Omega rho^2), m / (Omega rho),
-// c, rho, 1/H, kernel constant) come from packed 16-byte vectors.
+// lane), grouped as in the density kernel (sph_pair.cuh). Candidates j from
+// the cells overlapping the group's box grown by max(H_group, H_max) are
+// kept when within max(H_group, H_j) of the box and staged in shared memory
+// as (x, y, z, H^2). Each lane marks the candidates with
+// 0 < r^2 < max(H_i, H_j)^2 (broadcast reads, one bit per candidate), then
+// walks its own set bits independently, so the heavy pair body runs only
+// for real neighbours. A pair at r = 0 contributes nothing to any sum below
+// (every term carries x_ij), so excluding it is exact.
 //
 // The per-pair sums use the algebraically equal contracted forms
 //   a_i   += m_j W'_i/r sig~_i x_ij + W'_j/r (m sig~)_j x_ij      (Eq. 4, 18)
@@ -19,83 +19,94 @@
 // with sig~ = (-P I + S) / (Omega rho^2), W'/r the radial kernel derivative
 // over r and g_ij = -1/2 (m_j W'_i/r / (Omega_i rho_i) + W'_j/r m_j /
 // (Omega_j rho_j)), since every kernel gradient points along x_ij. In the
-// FP32 form the energy and the F, C^-1 sums are Kahan-compensated.
-#include <type_traits>
-
-#include "sph_internal.cuh"
+// FP32 form the energy and the F, C^-1 sums are Kahan-compensated, and the
+// per-particle finalize runs in FP32 as well: FP64 stays in positions,
+// integration and global sums.
+#include "sph_pair.cuh"
 
 namespace sphk {
 
 // ------------------------------------------------------------ EOS + pack
-__global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_t n, KParams P,
-                                                    int fp32) {
+template <typename T> struct Packed;
+template <> struct Packed<float> {
+  using V4 = float4;
+  static __device__ __forceinline__ const float4 *pos(const Work &w) { return w.pos32; }
+  static __device__ __forceinline__ float4 *posh(const Work &w) { return w.posh32; }
+  static __device__ __forceinline__ float4 *fj(const Work &w, int k) { return w.fj32[k]; }
+  static __device__ __forceinline__ float4 *fs(const Work &w, int k) { return w.fs32[k]; }
+};
+template <> struct Packed<double> {
+  using V4 = double4_32a;
+  static __device__ __forceinline__ const double4_32a *pos(const Work &w) { return w.pos64; }
+  static __device__ __forceinline__ double4_32a *posh(const Work &w) { return w.posh64; }
+  static __device__ __forceinline__ double4_32a *fj(const Work &w, int k) { return w.fj64[k]; }
+  static __device__ __forceinline__ double4_32a *fs(const Work &w, int k) { return w.fs64[k]; }
+};
+
+// Per particle: EOS at (rho, u_eval), yield, radial return of the
+// evaluation stress, and the packed neighbour / own data of the pair loop:
+//   posh = (x, y, z, H)                  fj0 = (v, m)
+//   fj1 = m/(Omega rho^2) (sxx, syy, szz, sxy)   with s = -P I + S
+//   fj2 = (m sxz', m syz', m/(Omega rho), c)     fj3 = (rho, 1/H, cG/H^5, H)
+//   fs0 = (Sxx, Syy, Sxy, Sxz)   fs1 = (Syz, Gamma, c_L, 0)   fs2 = (g, 0)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_t n, KParams P) {
+  using V = V4T<T>;
+  const typename V::type *pos = Packed<T>::pos(w);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const sph_material &M = P.mats[s.mat[i] & (SPH_MAX_MATERIALS - 1)];
-    const double rho = s.rho[i], u = w.up[i], om = s.omega[i], m = s.m[i], H = s.h[i];
-    const EosOut e = eos(M, rho, u);
-    s.pres[i] = e.P;
-    s.cs[i] = e.c;
-    const double Y = yield(M, e.P, u);
-    w.yld[i] = Y;
-    double S[5] = {w.sp[0][i], w.sp[1][i], w.sp[2][i], w.sp[3][i], w.sp[4][i]};
+    const double rhod = s.rho[i];
+    const EosT<T> e = eos_t<T>(M, rhod, w.up[i]);
+    s.pres[i] = (double)e.P;
+    s.cs[i] = (double)e.c;
+    const T Y = yield_t<T>(M, e.P, (T)w.up[i]);
+    T S[5] = {(T)w.sp[0][i], (T)w.sp[1][i], (T)w.sp[2][i], (T)w.sp[3][i], (T)w.sp[4][i]};
     if (!M.strength) {
-      S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
+      S[0] = S[1] = S[2] = S[3] = S[4] = T(0);
     } else {
-      radial_return(S, Y, P.yield_norm);
-    }
+      const T f = radial_factor_t<T>(S, Y, P.yield_norm);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) w.sp[k][i] = S[k];
-    const double inv = m / (om * rho * rho);
-    const double sxx = (S[0] - e.P) * inv, syy = (S[1] - e.P) * inv;
-    const double szz = (-S[0] - S[1] - e.P) * inv;
-    const double ih = 1.0 / H;
-    const double K = cG * ih * ih * ih * ih * ih;
-    if (fp32) {
-      w.fj32[0][i] = make_float4((float)w.vp[0][i], (float)w.vp[1][i], (float)w.vp[2][i], (float)m);
-      w.fj32[1][i] = make_float4((float)sxx, (float)syy, (float)szz, (float)(S[2] * inv));
-      w.fj32[2][i] = make_float4((float)(S[3] * inv), (float)(S[4] * inv), (float)(m / (om * rho)),
-                                 (float)e.c);
-      w.fj32[3][i] = make_float4((float)rho, (float)ih, (float)K, (float)H);
-    } else {
-      w.fj64[0][i] = make_double4_32a(w.vp[0][i], w.vp[1][i], w.vp[2][i], m);
-      w.fj64[1][i] = make_double4_32a(sxx, syy, szz, S[2] * inv);
-      w.fj64[2][i] = make_double4_32a(S[3] * inv, S[4] * inv, m / (om * rho), e.c);
-      w.fj64[3][i] = make_double4_32a(rho, ih, K, H);
+      for (int k = 0; k < 5; ++k) S[k] *= f;
     }
+    const typename V::type pp = pos[i];
+    const T rho = (T)rhod, om = (T)s.omega[i], m = (T)s.m[i], H = (T)s.h[i];
+    const T inv = m / (om * rho * rho);
+    const T ih = T(1) / H;
+    const T ih2 = ih * ih;
+    const T K = T(cG) * ih2 * ih2 * ih;
+    const T Gam = M.strength ? (T)shear_mod(M, rhod, (double)e.c) : T(0);
+    const T cl = M.strength ? sqrt(e.c * e.c + T(4.0 / 3.0) * Gam / rho) : e.c;
+    T gx[3];
+    ext_field_t<T>(P, s.x[i], s.y[i], s.z[i], gx, nullptr);
+    Packed<T>::posh(w)[i] = V::make(pp.x, pp.y, pp.z, H);
+    Packed<T>::fj(w, 0)[i] = V::make((T)w.vp[0][i], (T)w.vp[1][i], (T)w.vp[2][i], m);
+    Packed<T>::fj(w, 1)[i] =
+        V::make((S[0] - e.P) * inv, (S[1] - e.P) * inv, (-S[0] - S[1] - e.P) * inv, S[2] * inv);
+    Packed<T>::fj(w, 2)[i] = V::make(S[3] * inv, S[4] * inv, m / (om * rho), e.c);
+    Packed<T>::fj(w, 3)[i] = V::make(rho, ih, K, H);
+    Packed<T>::fs(w, 0)[i] = V::make(S[0], S[1], S[2], S[3]);
+    Packed<T>::fs(w, 1)[i] = V::make(S[4], Gam, cl, T(0));
+    Packed<T>::fs(w, 2)[i] = V::make(gx[0], gx[1], gx[2], T(0));
   }
 }
 
 cudaError_t launch_eos_pack(sph_ctx *c) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
-  k_eos_pack<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp,
-                                              c->kp.precision == SPH_FP32K);
+  if (c->kp.precision == SPH_FP32K)
+    k_eos_pack<float><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+  else
+    k_eos_pack<double><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- pair loop
-template <typename T> struct FVec;
-template <> struct FVec<float> {
-  using type = float4;
-  static __device__ __forceinline__ float4 pos(const Work &w, int64_t i) { return __ldg(w.pos32 + i); }
-  static __device__ __forceinline__ float4 fj(const Work &w, int k, int64_t i) {
-    return __ldg(w.fj32[k] + i);
-  }
-};
-template <> struct FVec<double> {
-  using type = double4_32a;
-  static __device__ __forceinline__ double4_32a pos(const Work &w, int64_t i) { return w.pos64[i]; }
-  static __device__ __forceinline__ double4_32a fj(const Work &w, int k, int64_t i) {
-    return w.fj64[k][i];
-  }
-};
-
 // Running sum: plain in FP64, Kahan-compensated in FP32.
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
-  __device__ __forceinline__ double get() const { return (double)s; }
+  __device__ __forceinline__ T get() const { return s; }
 };
 template <> struct Acc<float> {
   float s = 0.f, c = 0.f;
@@ -105,13 +116,7 @@ template <> struct Acc<float> {
     c = (t - s) - y;
     s = t;
   }
-  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
-};
-
-template <typename T, int CAP> struct FList {
-  T x[CAP], y[CAP], z[CAP], h[CAP];
-  int idx[CAP];
-  unsigned mask[CAP / 32][32];
+  __device__ __forceinline__ float get() const { return s - c; }
 };
 
 struct ForceArgs {
@@ -126,211 +131,174 @@ struct ForceArgs {
 template <typename T, int CAP>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
-  using V4 = typename FVec<T>::type;
-  __shared__ FList<T, CAP> lists[kWarpsPerBlock];
+  using V = V4T<T>;
+  using V4 = typename V::type;
+  using PK = Packed<T>;
+  __shared__ V4 s_rec[kWarpsPerBlock][CAP];
+  __shared__ int s_idx[kWarpsPerBlock][CAP];
+  __shared__ unsigned s_mask[kWarpsPerBlock][CAP / 32][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  FList<T, CAP> &Ls = lists[wib];
+  V4 *Lr = s_rec[wib];
+  int *Li = s_idx[wib];
+  unsigned(*Lm)[32] = s_mask[wib];
   const int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + wib) * 32;
   if (base >= A.n) return;
   const int64_t i = base + lane;
   const bool valid = i < A.n;
   const int64_t ic = valid ? i : base;
+  const V4 *posh = PK::posh(A.w);
+  const V4 *fj0 = PK::fj(A.w, 0), *fj1 = PK::fj(A.w, 1), *fj2 = PK::fj(A.w, 2),
+           *fj3 = PK::fj(A.w, 3);
 
   const Grid g = A.st->grid;
   const T Lt = (T)g.L;
-  const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
-  const double hmax_all = dec_d(A.st->hmax2_enc);
+  const T hmax_all = (T)dec_d(A.st->hmax2_enc);
 
-  // particle i, evaluation state
-  const V4 p = FVec<T>::pos(A.w, ic);
-  const double Hd = A.s.h[ic], rhod = A.s.rho[ic], omd = A.s.omega[ic], Pd = A.s.pres[ic];
-  const double cd = A.s.cs[ic];
-  double Sd[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) Sd[k] = A.w.sp[k][ic];
-  const double inv = 1.0 / (omd * rhod * rhod);
-  const T sxx = (T)((Sd[0] - Pd) * inv), syy = (T)((Sd[1] - Pd) * inv);
-  const T szz = (T)((-Sd[0] - Sd[1] - Pd) * inv);
-  const T sxy = (T)(Sd[2] * inv), sxz = (T)(Sd[3] * inv), syz = (T)(Sd[4] * inv);
-  const T iOr = (T)(1.0 / (omd * rhod));
-  const T Hi = (T)Hd, invHi = (T)(1.0 / Hd);
-  const T Ki = (T)(cG / (Hd * Hd * Hd * Hd * Hd));
-  const T vix = (T)A.w.vp[0][ic], viy = (T)A.w.vp[1][ic], viz = (T)A.w.vp[2][ic];
-  const T ci = (T)cd, rhoi = (T)rhod;
+  // particle i (evaluation state, packed)
+  const V4 p = V::ld(posh, ic);
+  const V4 a0 = V::ld(fj0, ic), a1 = V::ld(fj1, ic), a2 = V::ld(fj2, ic), a3 = V::ld(fj3, ic);
+  const T im = T(1) / a0.w;
+  const T sxx = a1.x * im, syy = a1.y * im, szz = a1.z * im, sxy = a1.w * im;
+  const T sxz = a2.x * im, syz = a2.y * im, iOr = a2.z * im;
+  const T Hi = p.w, Hi2 = p.w * p.w, invHi = a3.y, Ki = a3.z;
+  const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi = a3.x;
   const T al = (T)A.p.av_alpha, be = (T)A.p.av_beta, ep = (T)A.p.av_eps;
 
   T ax = 0, ay = 0, az = 0, mumax = 0;
-  Acc<T> du, F[9], Ci[6];
+  Acc<T> du, F0, F1, F2, F3, F4, F5, F6, F7, F8, C0, C1, C2, C3, C4, C5;
   int npairs = 0;
+  long long cand = 0;
 
   unsigned todo = __ballot_sync(kFull, valid);
   while (todo) {
-    const int ref = __ffs(todo) - 1;
-    const int rx = __shfl_sync(kFull, cx, ref), ry = __shfl_sync(kFull, cy, ref),
-              rz = __shfl_sync(kFull, cz, ref);
-    const bool act = ((todo >> lane) & 1u) && abs(cx - rx) <= 2 && abs(cy - ry) <= 2 &&
-                     abs(cz - rz) <= 2;
-    todo &= ~__ballot_sync(kFull, act);
-    const T xi = REL ? p.x + (T)(cx - rx) * Lt : p.x;
-    const T yi = REL ? p.y + (T)(cy - ry) * Lt : p.y;
-    const T zi = REL ? p.z + (T)(cz - rz) * Lt : p.z;
+    const Group G = next_group(todo, cx, cy, cz);
+    const bool act = G.member;
+    const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
+    const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
+    const T zi = REL ? p.z + (T)(cz - G.rz) * Lt : p.z;
     const T Rb = wmax(act ? Hi : T(0));
-    const double Rf = fmax((double)Rb, hmax_all);
-    const T bx0 = wmin(act ? xi : T(1e30)), bx1 = wmax(act ? xi : T(-1e30));
-    const T by0 = wmin(act ? yi : T(1e30)), by1 = wmax(act ? yi : T(-1e30));
-    const T bz0 = wmin(act ? zi : T(1e30)), bz1 = wmax(act ? zi : T(-1e30));
-    const int x0 = wmin(act ? cx : 1 << 20), x1 = wmax(act ? cx : -1);
-    const int y0 = wmin(act ? cy : 1 << 20), y1 = wmax(act ? cy : -1);
-    const int z0 = wmin(act ? cz : 1 << 20), z1 = wmax(act ? cz : -1);
-    const int span = max(1, (int)ceil(Rf / g.L));
-    int nl = 0;
-
-    auto process = [&](int nlist) {
-      const int nw = (nlist + 31) >> 5;
-      // 1) membership bits, broadcast reads of the list
+    const T Rf = tmax(Rb, hmax_all);
+    const Box<T> bx = group_box(act, xi, yi, zi);
+    Stager<T> sg = make_stager<T, REL>(bx, Rf, g, G.rx, G.ry, G.rz);
+    for (;;) {
+      // stage candidates
+      int nl = 0;
+      while (nl <= CAP - 32) {
+        if (sg.jb >= sg.je &&
+            !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, G.rx, G.ry, G.rz, Lt))
+          break;
+        const int j = sg.jb + lane;
+        const bool ok = j < sg.je;
+        const V4 q = ok ? V::ld(posh, j) : V::make(0, 0, 0, 0);
+        const T xj = q.x + sg.ox, yj = q.y + sg.oy, zj = q.z + sg.oz;
+        const T R = tmax(Rb, q.w);
+        const bool keep =
+            ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R;
+        const unsigned bal = __ballot_sync(kFull, keep);
+        if (keep) {
+          const int at = nl + __popc(bal & lanemask_lt());
+          Lr[at] = V::make(xj, yj, zj, q.w * q.w);
+          Li[at] = j;
+        }
+        nl += __popc(bal);
+        sg.jb += 32;
+      }
+      cand += nl;
+      __syncwarp();
+      // membership bits: 0 < r^2 < max(H_i, H_j)^2
+      const int nw = (nl + 31) >> 5;
       for (int wd = 0; wd < nw; ++wd) {
+        const int kb = wd << 5;
+        const int kend = min(32, nl - kb);
         unsigned mk = 0;
-        const int kend = min(32, nlist - (wd << 5));
+#pragma unroll 4
         for (int b = 0; b < kend; ++b) {
-          const int k = (wd << 5) + b;
-          const T dx = xi - Ls.x[k], dy = yi - Ls.y[k], dz = zi - Ls.z[k];
+          const V4 q = Lr[kb + b];
+          const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
-          const T Rk = Hi > Ls.h[k] ? Hi : Ls.h[k];
-          const bool in = act && r2 < Rk * Rk && Ls.idx[k] != (int)i;
-          mk |= (unsigned)in << b;
+          mk |= ((r2 > T(0)) & (r2 < tmax(Hi2, q.w)) ? 1u : 0u) << b;
         }
-        Ls.mask[wd][lane] = mk;
+        Lm[wd][lane] = act ? mk : 0u;
       }
       __syncwarp();
-      // 2) each lane walks its own neighbours
-      int wd = 0;
-      unsigned mk = nw > 0 ? Ls.mask[0][lane] : 0u;
-      for (;;) {
-        while (mk == 0u && wd + 1 < nw) mk = Ls.mask[++wd][lane];
-        if (mk == 0u) break;
-        const int k = (wd << 5) + __ffs(mk) - 1;
-        mk &= mk - 1u;
-        const int j = Ls.idx[k];
-        const T dx = xi - Ls.x[k], dy = yi - Ls.y[k], dz = zi - Ls.z[k];
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        const T r = r2 > T(0) ? sqrt(r2) : T(0);
-        const V4 f0 = FVec<T>::fj(A.w, 0, j);
-        const V4 f1 = FVec<T>::fj(A.w, 1, j);
-        const V4 f2 = FVec<T>::fj(A.w, 2, j);
-        const V4 f3 = FVec<T>::fj(A.w, 3, j);
-        T ti = T(1) - r * invHi;
-        ti = ti > T(0) ? ti : T(0);
-        T tj = T(1) - r * f3.y;
-        tj = tj > T(0) ? tj : T(0);
-        const T Wi = Ki * ti * ti * ti;          // W'(r, H_i) / r
-        const T Wj = f3.z * tj * tj * tj;        // W'(r, H_j) / r
-        const T mj = f0.w;
-        const T vx = vix - f0.x, vy = viy - f0.y, vz = viz - f0.z;
-        // sig~_i x_ij and (m sig~)_j x_ij
-        const T yix = sxx * dx + sxy * dy + sxz * dz;
-        const T yiy = sxy * dx + syy * dy + syz * dz;
-        const T yiz = sxz * dx + syz * dy + szz * dz;
-        const T yjx = f1.x * dx + f1.w * dy + f2.x * dz;
-        const T yjy = f1.w * dx + f1.y * dy + f2.y * dz;
-        const T yjz = f2.x * dx + f2.y * dy + f1.z * dz;
-        const T mWi = mj * Wi;
-        ax += mWi * yix + Wj * yjx;
-        ay += mWi * yiy + Wj * yjy;
-        az += mWi * yiz + Wj * yjz;
-        T dsum = -mWi * (vx * yix + vy * yiy + vz * yiz);
-        const T vr = vx * dx + vy * dy + vz * dz;
-        if (vr < T(0)) {                        // Eq. 5-8
-          const T hb = T(0.5) * (Hi + Ls.h[k]);
-          const T mu = hb * vr / (r2 + ep * hb * hb);
-          const T Pi = (-al * T(0.5) * (ci + f2.w) * mu + be * mu * mu) / (T(0.5) * (rhoi + f3.x));
-          const T t = mj * Pi * T(0.5) * (Wi + Wj);
-          ax -= t * dx;
-          ay -= t * dy;
-          az -= t * dz;
-          dsum += T(0.5) * t * vr;
-          mumax = -mu > mumax ? -mu : mumax;
-        }
-        du.add(dsum);
-        const T gs = T(-0.5) * (mWi * iOr + Wj * f2.z);   // Eq. 20-21 weight
-        const T gvx = gs * vx, gvy = gs * vy, gvz = gs * vz;
-        F[0].add(gvx * dx); F[1].add(gvx * dy); F[2].add(gvx * dz);
-        F[3].add(gvy * dx); F[4].add(gvy * dy); F[5].add(gvy * dz);
-        F[6].add(gvz * dx); F[7].add(gvz * dy); F[8].add(gvz * dz);
-        const T gx = gs * dx, gy = gs * dy;
-        Ci[0].add(gx * dx); Ci[1].add(gx * dy); Ci[2].add(gx * dz);
-        Ci[3].add(gy * dy); Ci[4].add(gy * dz); Ci[5].add(gs * dz * dz);
-        ++npairs;
-      }
-      __syncwarp();
-    };
-
-    for (int z = max(z0 - span, 0); z <= min(z1 + span, nz - 1); ++z)
-      for (int y = max(y0 - span, 0); y <= min(y1 + span, ny - 1); ++y)
-        for (int x = max(x0 - span, 0); x <= min(x1 + span, nx - 1); ++x) {
-          const int c = (z * ny + y) * nx + x;
-          const int s0 = A.cell_start[c];
-          if (s0 < 0) continue;
-          const int s1 = A.cell_end[c];
-          const T ox = REL ? (T)(x - rx) * Lt : T(0);
-          const T oy = REL ? (T)(y - ry) * Lt : T(0);
-          const T oz = REL ? (T)(z - rz) * Lt : T(0);
-          for (int jb = s0; jb < s1; jb += 32) {
-            const int j = jb + lane;
-            const bool ok = j < s1;
-            V4 q, f3;
-            if (ok) {
-              q = FVec<T>::pos(A.w, j);
-              f3 = FVec<T>::fj(A.w, 3, j);
-            } else {
-              q.x = q.y = q.z = q.w = T(0);
-              f3.x = f3.y = f3.z = f3.w = T(0);
-            }
-            const T xj = q.x + ox, yj = q.y + oy, zj = q.z + oz;
-            const T ex = fmax(bx0 - xj, fmax(T(0), xj - bx1));
-            const T ey = fmax(by0 - yj, fmax(T(0), yj - by1));
-            const T ez = fmax(bz0 - zj, fmax(T(0), zj - bz1));
-            const T R = Rb > f3.w ? Rb : f3.w;
-            const bool keep = ok && (ex * ex + ey * ey + ez * ez < R * R * T(1.0001));
-            const unsigned bal = __ballot_sync(kFull, keep);
-            if (keep) {
-              const int at = nl + __popc(bal & lanemask_lt());
-              Ls.x[at] = xj;
-              Ls.y[at] = yj;
-              Ls.z[at] = zj;
-              Ls.h[at] = f3.w;
-              Ls.idx[at] = j;
-            }
-            nl += __popc(bal);
-            if (nl > CAP - 32) {
-              __syncwarp();
-              process(nl);
-              nl = 0;
-            }
+      // each lane walks its own neighbours
+      for (int wd = 0; wd < nw; ++wd) {
+        unsigned mk = Lm[wd][lane];
+        while (mk) {
+          const int k = (wd << 5) + __ffs(mk) - 1;
+          mk &= mk - 1u;
+          const int j = Li[k];
+          const V4 q = Lr[k];
+          const V4 f0 = V::ld(fj0, j), f1 = V::ld(fj1, j), f2 = V::ld(fj2, j), f3 = V::ld(fj3, j);
+          const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          const T r = sqrt(r2);
+          const T ti = tmax(T(1) - r * invHi, T(0));
+          const T tj = tmax(T(1) - r * f3.y, T(0));
+          const T Wi = Ki * ti * ti * ti;   // W'(r, H_i) / r
+          const T Wj = f3.z * tj * tj * tj; // W'(r, H_j) / r
+          const T mj = f0.w;
+          const T vx = vix - f0.x, vy = viy - f0.y, vz = viz - f0.z;
+          const T yix = sxx * dx + sxy * dy + sxz * dz;
+          const T yiy = sxy * dx + syy * dy + syz * dz;
+          const T yiz = sxz * dx + syz * dy + szz * dz;
+          const T yjx = f1.x * dx + f1.w * dy + f2.x * dz;
+          const T yjy = f1.w * dx + f1.y * dy + f2.y * dz;
+          const T yjz = f2.x * dx + f2.y * dy + f1.z * dz;
+          const T mWi = mj * Wi;
+          ax += mWi * yix + Wj * yjx;
+          ay += mWi * yiy + Wj * yjy;
+          az += mWi * yiz + Wj * yjz;
+          T dsum = -mWi * (vx * yix + vy * yiy + vz * yiz);
+          const T vr = vx * dx + vy * dy + vz * dz;
+          if (vr < T(0)) {  // Eq. 5-8
+            const T hb = T(0.5) * (Hi + f3.w);
+            const T mu = hb * vr / (r2 + ep * hb * hb);
+            const T Pi = (be * mu - al * T(0.5) * (ci + f2.w)) * mu / (T(0.5) * (rhoi + f3.x));
+            const T t = T(0.5) * mj * Pi * (Wi + Wj);
+            ax -= t * dx;
+            ay -= t * dy;
+            az -= t * dz;
+            dsum += T(0.5) * t * vr;
+            mumax = tmax(mumax, -mu);
           }
+          du.add(dsum);
+          const T gs = T(-0.5) * (mWi * iOr + Wj * f2.z);  // Eq. 20-21 weight
+          const T gvx = gs * vx, gvy = gs * vy, gvz = gs * vz;
+          F0.add(gvx * dx); F1.add(gvx * dy); F2.add(gvx * dz);
+          F3.add(gvy * dx); F4.add(gvy * dy); F5.add(gvy * dz);
+          F6.add(gvz * dx); F7.add(gvz * dy); F8.add(gvz * dz);
+          const T gx = gs * dx, gy = gs * dy;
+          C0.add(gx * dx); C1.add(gx * dy); C2.add(gx * dz);
+          C3.add(gy * dy); C4.add(gy * dz); C5.add(gs * dz * dz);
+          ++npairs;
         }
-    __syncwarp();
-    process(nl);
+      }
+      __syncwarp();
+      if (sg.done) break;
+    }
   }
 
-  // ------------------------------------------------ finalize (FP64)
+  // ---------------------------------------- finalize (Eq. 21-29, 38-39)
   int fallback = 0;
   if (valid) {
-    const sph_material &M = A.p.mats[A.s.mat[i] & (SPH_MAX_MATERIALS - 1)];
+    const V4 s0 = V::ld(PK::fs(A.w, 0), i), s1 = V::ld(PK::fs(A.w, 1), i),
+             s2 = V::ld(PK::fs(A.w, 2), i);
     const bool fixed = A.s.flags[i] & SPH_FLAG_FIXED;
-    double Fm[9], Cm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Fm[k] = F[k].get();
-    const double c00 = Ci[0].get(), c01 = Ci[1].get(), c02 = Ci[2].get();
-    const double c11 = Ci[3].get(), c12 = Ci[4].get(), c22 = Ci[5].get();
+    const T F[9] = {F0.get(), F1.get(), F2.get(), F3.get(), F4.get(),
+                    F5.get(), F6.get(), F7.get(), F8.get()};
+    const T c00 = C0.get(), c01 = C1.get(), c02 = C2.get();
+    const T c11 = C3.get(), c12 = C4.get(), c22 = C5.get();
+    T Cm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     if (A.p.correction) {
       // inverse of the symmetric C^-1 by cofactors (Eq. 21-22)
-      const double k00 = c11 * c22 - c12 * c12, k01 = c02 * c12 - c01 * c22,
-                   k02 = c01 * c12 - c02 * c11;
-      const double det = c00 * k00 + c01 * k01 + c02 * k02;
-      if (A.s.nngb[i] >= 8 && fabs(det) >= 1e-3) {
-        const double id = 1.0 / det;
+      const T k00 = c11 * c22 - c12 * c12, k01 = c02 * c12 - c01 * c22,
+              k02 = c01 * c12 - c02 * c11;
+      const T det = c00 * k00 + c01 * k01 + c02 * k02;
+      if (A.s.nngb[i] >= 8 && fabs(det) >= T(1e-3)) {
+        const T id = T(1) / det;
         Cm[0] = k00 * id;
         Cm[1] = Cm[3] = k01 * id;
         Cm[2] = Cm[6] = k02 * id;
@@ -341,57 +309,52 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
         fallback = 1;
       }
     }
-    double G[9];
+    T G[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b)
-        G[3 * a + b] = Fm[3 * a] * Cm[b] + Fm[3 * a + 1] * Cm[3 + b] + Fm[3 * a + 2] * Cm[6 + b];
-    // strain rate and rotation rate (Eq. 23-24)
-    double E[9], R[9];
+        G[3 * a + b] = F[3 * a] * Cm[b] + F[3 * a + 1] * Cm[3 + b] + F[3 * a + 2] * Cm[6 + b];
+    T E[9], R[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        E[3 * a + b] = 0.5 * (G[3 * a + b] + G[3 * b + a]);
-        R[3 * a + b] = 0.5 * (G[3 * a + b] - G[3 * b + a]);
+        E[3 * a + b] = T(0.5) * (G[3 * a + b] + G[3 * b + a]);
+        R[3 * a + b] = T(0.5) * (G[3 * a + b] - G[3 * b + a]);
       }
-    double e2 = 0.0;
+    T e2 = 0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) e2 += E[k] * E[k];
-    const double Gam = shear_mod(M, rhod, cd);
-    double dS[5] = {0, 0, 0, 0, 0};
-    if (M.strength) {
-      const double Sm[9] = {Sd[0], Sd[2], Sd[3], Sd[2], Sd[1], Sd[4], Sd[3], Sd[4], -Sd[0] - Sd[1]};
-      const double tr3 = (E[0] + E[4] + E[8]) / 3.0;
-      const double sg = A.p.jaumann == SPH_JAUMANN_PRINTED ? -1.0 : 1.0;
-      const int ia[5] = {0, 1, 0, 0, 1}, ib[5] = {0, 1, 1, 2, 2};
+    // Eq. 13 with R S - S R (objective) or S R - R S (Eq. 25-29 as printed)
+    const T Gam = s1.y;
+    const T Sm[9] = {s0.x, s0.z, s0.w, s0.z, s0.y, s1.x, s0.w, s1.x, -s0.x - s0.y};
+    const T tr3 = (E[0] + E[4] + E[8]) / T(3);
+    const T sg = A.p.jaumann == SPH_JAUMANN_PRINTED ? T(-1) : T(1);
+    T dS[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const int a = ia[q], b = ib[q];
-        double rot = 0.0;
+    for (int q = 0; q < 5; ++q) {
+      const int a = q == 1 || q == 4 ? 1 : 0;
+      const int b = q == 0 ? 0 : (q == 1 || q == 2 ? 1 : 2);
+      T rot = 0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) rot += R[3 * a + k] * Sm[3 * k + b] - Sm[3 * a + k] * R[3 * k + b];
-        dS[q] = 2.0 * Gam * (E[3 * a + b] - (a == b ? tr3 : 0.0)) + sg * rot;
-      }
+      for (int k = 0; k < 3; ++k) rot += R[3 * a + k] * Sm[3 * k + b] - Sm[3 * a + k] * R[3 * k + b];
+      dS[q] = T(2) * Gam * (E[3 * a + b] - (a == b ? tr3 : T(0))) + sg * rot;
     }
-    double gx[3];
-    ext_field(A.p, A.s.x[i], A.s.y[i], A.s.z[i], gx, nullptr);
-    const double cl = M.strength ? sqrt(cd * cd + 4.0 / 3.0 * Gam / rhod) : cd;
-    A.w.vsig[i] = (1.0 + 0.6 * A.p.av_alpha) * cl + 0.6 * A.p.av_beta * (double)mumax;
-    A.w.edot2[i] = 0.5 * e2;
-    const double axd = (double)ax + gx[0], ayd = (double)ay + gx[1], azd = (double)az + gx[2];
-    const double dud = du.get();
-    A.s.ax[i] = fixed ? 0.0 : axd;
-    A.s.ay[i] = fixed ? 0.0 : ayd;
-    A.s.az[i] = fixed ? 0.0 : azd;
-    A.s.dudt[i] = fixed ? 0.0 : dud;
-    A.s.dsxx[i] = fixed ? 0.0 : dS[0];
-    A.s.dsyy[i] = fixed ? 0.0 : dS[1];
-    A.s.dsxy[i] = fixed ? 0.0 : dS[2];
-    A.s.dsxz[i] = fixed ? 0.0 : dS[3];
-    A.s.dsyz[i] = fixed ? 0.0 : dS[4];
-    bool fin = isfinite(axd) && isfinite(ayd) && isfinite(azd) && isfinite(dud);
+    A.w.vsig[i] = (double)(T(1.0 + 0.6 * A.p.av_alpha) * s1.z + T(0.6 * A.p.av_beta) * mumax);
+    A.w.edot2[i] = (double)(T(0.5) * e2);
+    const T axt = ax + s2.x, ayt = ay + s2.y, azt = az + s2.z;
+    const T dud = du.get();
+    A.s.ax[i] = fixed ? 0.0 : (double)axt;
+    A.s.ay[i] = fixed ? 0.0 : (double)ayt;
+    A.s.az[i] = fixed ? 0.0 : (double)azt;
+    A.s.dudt[i] = fixed ? 0.0 : (double)dud;
+    A.s.dsxx[i] = fixed ? 0.0 : (double)dS[0];
+    A.s.dsyy[i] = fixed ? 0.0 : (double)dS[1];
+    A.s.dsxy[i] = fixed ? 0.0 : (double)dS[2];
+    A.s.dsxz[i] = fixed ? 0.0 : (double)dS[3];
+    A.s.dsyz[i] = fixed ? 0.0 : (double)dS[4];
+    bool fin = isfinite(axt) && isfinite(ayt) && isfinite(azt) && isfinite(dud);
 #pragma unroll
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(dS[k]);
     if (!fin) atomicOr(&A.st->err, ERR_NONFINITE);
@@ -401,6 +364,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
   if (lane == 0) {
     if (nfb) atomicAdd(&A.st->n_cfallback, nfb);
     atomicAdd(&A.st->pairs_force, (unsigned long long)pw);
+    atomicAdd(&A.st->cand_force, (unsigned long long)cand);
   }
 }
 
@@ -416,7 +380,7 @@ cudaError_t launch_forces(sph_ctx *c) {
   const int64_t buckets = (c->n + 31) / 32;
   const int blocks = (int)((buckets + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (c->kp.precision == SPH_FP32K)
-    k_forces<float, 256><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    k_forces<float, 512><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
   else
     k_forces<double, 256><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
   return cudaGetLastError();

@@ -25,6 +25,8 @@ __global__ void k_reset_status(Status *st, int full) {
   st->n_cfallback = 0;
   st->pairs_density = 0;
   st->pairs_force = 0;
+  st->cand_density = 0;
+  st->cand_force = 0;
   if (full) st->err = 0;
 }
 
@@ -180,27 +182,68 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned *key
   hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of m = 256 * ntiles counts in one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_radix_scan(unsigned *hist, int m) {
-  __shared__ unsigned part[1024];
-  const int per = (m + 1023) / 1024;
-  const int b = threadIdx.x * per, e = min(b + per, m);
-  unsigned s = 0;
-  for (int i = b; i < e; ++i) s += hist[i];
-  part[threadIdx.x] = s;
+// Exclusive scan of the m = 256 * ntiles tile counts (digit-major) in three
+// kernels: per-segment totals, a scan of the totals, per-segment scans.
+constexpr int kScanSeg = 1024;
+
+__device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned *sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) sh[w] = v;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    unsigned t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+  if (w == 0) {
+    unsigned s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += t;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  const unsigned add = w > 0 ? sh[w - 1] : 0u;
+  __syncthreads();
+  return v + add;
+}
+
+__global__ void __launch_bounds__(kScanSeg) k_scan_totals(const unsigned *hist, int m,
+                                                          unsigned *tot) {
+  __shared__ unsigned sh[32];
+  const int i = blockIdx.x * kScanSeg + threadIdx.x;
+  unsigned v = i < m ? hist[i] : 0u;
+  v = block_scan_incl(v, sh);
+  if (threadIdx.x == kScanSeg - 1) tot[blockIdx.x] = v;
+}
+
+// One block, chunks of kScanSeg totals with a running carry.
+__global__ void __launch_bounds__(kScanSeg) k_scan_of_totals(unsigned *tot, int nseg) {
+  __shared__ unsigned sh[32];
+  __shared__ unsigned carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int b = 0; b < nseg; b += kScanSeg) {
+    const int i = b + threadIdx.x;
+    const unsigned v = i < nseg ? tot[i] : 0u;
+    const unsigned inc = block_scan_incl(v, sh);
+    const unsigned c0 = carry;
+    if (i < nseg) tot[i] = c0 + inc - v;   // exclusive
     __syncthreads();
-    part[threadIdx.x] += t;
+    if (threadIdx.x == kScanSeg - 1) carry = c0 + inc;
     __syncthreads();
   }
-  unsigned run = part[threadIdx.x] - s;
-  for (int i = b; i < e; ++i) {
-    unsigned v = hist[i];
-    hist[i] = run;
-    run += v;
-  }
+}
+
+__global__ void __launch_bounds__(kScanSeg) k_scan_apply(unsigned *hist, int m,
+                                                         const unsigned *tot) {
+  __shared__ unsigned sh[32];
+  const int i = blockIdx.x * kScanSeg + threadIdx.x;
+  const unsigned v = i < m ? hist[i] : 0u;
+  const unsigned inc = block_scan_incl(v, sh);
+  if (i < m) hist[i] = tot[blockIdx.x] + inc - v;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *kin, const int *vin,
@@ -327,7 +370,10 @@ cudaError_t launch_sort_permute(sph_ctx *c) {
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 8 * pass;
     k_radix_hist<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, (int)n, shift, c->hist, c->ntiles);
-    k_radix_scan<<<1, 1024, 0, c->stream>>>(c->hist, 256 * c->ntiles);
+    const int m = 256 * c->ntiles, nseg = (m + kScanSeg - 1) / kScanSeg;
+    k_scan_totals<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot);
+    k_scan_of_totals<<<1, kScanSeg, 0, c->stream>>>(c->scan_tot, nseg);
+    k_scan_apply<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot);
     k_radix_scatter<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, (int)n, shift,
                                                                c->hist, c->ntiles);
     unsigned *tk = ka;

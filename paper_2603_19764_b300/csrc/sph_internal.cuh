@@ -40,6 +40,7 @@ struct Status {
   int pad_;
   unsigned long long lo_enc[3], hi_enc[3], hmax_enc, hmax2_enc, dtmin_enc;
   unsigned long long pairs_density, pairs_force;
+  unsigned long long cand_density, cand_force;   // staged candidates
   double sums[9];   // e_kin, e_int, e_pot, p[3], L[3]
   Grid grid;
 };
@@ -65,9 +66,13 @@ struct Work {
   double *vsig, *edot2, *yld;   // CFL signal, 1/2 edot:edot, yield strength
   int *cc;                      // packed cell coordinates x | y << 10 | z << 20
   float4 *pos32;                // cell-relative x, y, z and m (FP32 form)
-  double4_32a *pos64;               // absolute x, y, z and m (FP64 form)
+  double4_32a *pos64;           // absolute x, y, z and m (FP64 form)
+  float4 *posh32;               // positions with H (force pass)
+  double4_32a *posh64;
   float4 *fj32[4];              // force-side neighbour data (FP32 form)
-  double4_32a *fj64[4];             // force-side neighbour data (FP64 form)
+  double4_32a *fj64[4];         // force-side neighbour data (FP64 form)
+  float4 *fs32[3];              // own stress, shear modulus, c_L, external g
+  double4_32a *fs64[3];
 };
 
 // ---------------------------------------------------------------- helpers
@@ -115,6 +120,9 @@ template <typename T> __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
+template <typename T> __device__ __forceinline__ T tmax_(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T tmin_(T a, T b) { return a < b ? a : b; }
+
 // Spread the low 10 bits of v to every third bit (Morton interleave).
 __host__ __device__ inline unsigned part1by2(unsigned v) {
   v &= 0x3ffu;
@@ -137,71 +145,79 @@ __host__ __device__ inline unsigned morton3(unsigned x, unsigned y, unsigned z) 
 }
 
 // -------------------------------------------------------- material model
-// Equation of state. Linear: P = c0^2 (rho - rho0), c = c0. Tillotson
-// (Tillotson 1962; regions as in Melosh 1989): condensed or cold states,
-// hot expanded states and a linear-in-u blend in between, with
-// c^2 = P_rho + P P_u / rho^2 floored at 0.01 A / rho0.
-struct EosOut {
-  double P, c;
+// Equation of state, evaluated in T (FP64 form: double; FP32 form: float).
+// Linear: P = c0^2 (rho - rho0), c = c0. Tillotson (Tillotson 1962; regions
+// as in Melosh 1989): condensed or cold states, hot expanded states and a
+// linear-in-u blend in between, with c^2 = P_rho + P P_u / rho^2 floored at
+// 0.01 A / rho0. mu = rho / rho0 - 1 is formed from an FP64 difference so
+// that the FP32 form keeps its relative accuracy near rho0. The returned P
+// is floored at the material's p_min; c is that of the unfloored EOS.
+template <typename T> struct EosT {
+  T P, c;
 };
 
-__device__ inline void till_dense(const sph_material &M, double rho, double u, double &P,
-                                  double &Pr, double &Pu) {
-  const double eta = rho / M.rho0, mu = eta - 1.0;
-  const double e0e2 = M.E0 * eta * eta;
-  const double w = u / e0e2 + 1.0;
-  const double bw = M.b / w;
-  const double bw2 = bw / w;                          // b / w^2
-  P = (M.a + bw) * rho * u + mu * (M.A + M.B * mu);
+template <typename T>
+__device__ inline void till_dense_t(const sph_material &M, T eta, T mu, T rho, T u, T &P, T &Pr,
+                                    T &Pu) {
+  const T A = (T)M.A, B = (T)M.B, a = (T)M.a, b = (T)M.b;
+  const T e0e2 = (T)M.E0 * eta * eta;
+  const T w = u / e0e2 + T(1);
+  const T bw = b / w, bw2 = bw / w;            // b / w, b / w^2
+  P = (a + bw) * rho * u + mu * (A + B * mu);
   // dw/drho = -2 (w - 1) / rho, dw/du = 1 / (E0 eta^2)
-  Pr = (M.a + bw) * u + bw2 * rho * u * 2.0 * (w - 1.0) / rho + (M.A + 2.0 * M.B * mu) / M.rho0;
-  Pu = (M.a + bw) * rho - bw2 * rho * u / e0e2;
+  Pr = (a + bw) * u + bw2 * u * T(2) * (w - T(1)) + (A + T(2) * B * mu) / (T)M.rho0;
+  Pu = (a + bw) * rho - bw2 * rho * u / e0e2;
 }
 
-__device__ inline void till_vapour(const sph_material &M, double rho, double u, double &P,
-                                   double &Pr, double &Pu) {
-  const double eta = rho / M.rho0, mu = eta - 1.0;
-  const double e0e2 = M.E0 * eta * eta;
-  const double w = u / e0e2 + 1.0;
-  const double z = M.rho0 / rho - 1.0;
-  const double zr = -M.rho0 / (rho * rho);          // dz/drho
-  const double eb = exp(-M.beta * z), ea = exp(-M.alpha * z * z);
-  const double brw = M.b * rho * u / w;
-  const double q = brw + M.A * mu * eb;
-  const double qr = M.b * u / w + brw / w * 2.0 * (w - 1.0) / rho + M.A / M.rho0 * eb -
-                    M.A * mu * eb * M.beta * zr;
-  const double qu = M.b * rho / w - brw / w / e0e2;
-  P = M.a * rho * u + q * ea;
-  Pr = M.a * u + (qr - q * 2.0 * M.alpha * z * zr) * ea;
-  Pu = M.a * rho + qu * ea;
+template <typename T>
+__device__ inline void till_vapour_t(const sph_material &M, T eta, T mu, T rho, T u, T &P, T &Pr,
+                                     T &Pu) {
+  const T A = (T)M.A, a = (T)M.a, b = (T)M.b, al = (T)M.alpha, be = (T)M.beta;
+  const T e0e2 = (T)M.E0 * eta * eta;
+  const T w = u / e0e2 + T(1);
+  const T z = -mu / eta;                       // rho0 / rho - 1
+  const T zr = T(-1) / (eta * rho);            // dz / drho
+  const T eb = exp(-be * z), ea = exp(-al * z * z);
+  const T brw = b * rho * u / w;
+  const T q = brw + A * mu * eb;
+  const T qr = b * u / w + brw / w * T(2) * (w - T(1)) / rho + A / (T)M.rho0 * eb -
+               A * mu * eb * be * zr;
+  const T qu = b * rho / w - brw / w / e0e2;
+  P = a * rho * u + q * ea;
+  Pr = a * u + (qr - q * T(2) * al * z * zr) * ea;
+  Pu = a * rho + qu * ea;
 }
 
-__device__ inline EosOut eos(const sph_material &M, double rho, double u) {
-  EosOut o;
+template <typename T>
+__device__ inline EosT<T> eos_t(const sph_material &M, double rhod, double ud) {
+  EosT<T> o;
   if (M.eos == SPH_EOS_LINEAR) {
-    o.P = M.c0 * M.c0 * (rho - M.rho0);
-    o.c = M.c0;
+    o.P = (T)fmax(M.c0 * M.c0 * (rhod - M.rho0), M.p_min);
+    o.c = (T)M.c0;
     return o;
   }
-  double P, Pr, Pu;
-  if (rho >= M.rho0 || u <= M.Eiv) {
-    till_dense(M, rho, u, P, Pr, Pu);
-  } else if (u >= M.Ecv) {
-    till_vapour(M, rho, u, P, Pr, Pu);
+  const T u = (T)ud, rho = (T)rhod;
+  const T mu = (T)(rhod - M.rho0) / (T)M.rho0;
+  const T eta = T(1) + mu;
+  T P, Pr, Pu;
+  if (rhod >= M.rho0 || ud <= M.Eiv) {
+    till_dense_t<T>(M, eta, mu, rho, u, P, Pr, Pu);
+  } else if (ud >= M.Ecv) {
+    till_vapour_t<T>(M, eta, mu, rho, u, P, Pr, Pu);
   } else {
-    double P1, Pr1, Pu1, P2, Pr2, Pu2;
-    till_dense(M, rho, u, P1, Pr1, Pu1);
-    till_vapour(M, rho, u, P2, Pr2, Pu2);
-    const double s = 1.0 / (M.Ecv - M.Eiv);
-    const double wv = (u - M.Eiv) * s, wd = (M.Ecv - u) * s;
+    T P1, Pr1, Pu1, P2, Pr2, Pu2;
+    till_dense_t<T>(M, eta, mu, rho, u, P1, Pr1, Pu1);
+    till_vapour_t<T>(M, eta, mu, rho, u, P2, Pr2, Pu2);
+    const T s = T(1) / (T)(M.Ecv - M.Eiv);
+    const T wv = (T)(ud - M.Eiv) * s, wd = (T)(M.Ecv - ud) * s;
     P = wv * P2 + wd * P1;
     Pr = wv * Pr2 + wd * Pr1;
     Pu = wv * Pu2 + wd * Pu1 + (P2 - P1) * s;
   }
-  double c2 = Pr + P * Pu / (rho * rho);
-  const double floor2 = 0.01 * M.A / M.rho0;
+  T c2 = Pr + P * Pu / (rho * rho);
+  const T floor2 = (T)(0.01 * M.A / M.rho0);
   if (!(c2 >= floor2)) c2 = floor2;
-  o.P = P;
+  o.P = tmax_(P, (T)M.p_min);
   o.c = sqrt(c2);
   return o;
 }
@@ -212,64 +228,67 @@ __device__ __forceinline__ double shear_mod(const sph_material &M, double rho, d
 }
 
 // Yield strength (Eq. 34-37) with the pressure clipped at zero.
-__device__ inline double yield(const sph_material &M, double P, double u) {
-  const double p = fmax(P, 0.0);
-  const double yi = M.Y0 + M.mu_i * p / (1.0 + M.mu_i * p / (M.Ym - M.Y0));
-  double y = fmin(yi, M.mu_d * p);
+template <typename T> __device__ inline T yield_t(const sph_material &M, T P, T u) {
+  const T p = tmax_(P, T(0));
+  const T Y0 = (T)M.Y0, mi = (T)M.mu_i;
+  const T yi = Y0 + mi * p / (T(1) + mi * p / ((T)M.Ym - Y0));
+  T y = tmin_(yi, (T)M.mu_d * p);
   if (M.thermal_softening) {
-    const double T = M.T0 + u / M.cv;
-    if (!(T > 0.0)) return 0.0;
-    y *= fmax(tanh(M.xi * (M.Tm / T - 1.0)), 0.0);
+    const T Tk = (T)M.T0 + u / (T)M.cv;
+    if (!(Tk > T(0))) return T(0);
+    y *= tmax_(tanh((T)M.xi * ((T)M.Tm / Tk - T(1))), T(0));
   }
   return y;
 }
 
-// Radial return (Eq. 31-33) of S = {xx, yy, xy, xz, yz}.
-__device__ inline void radial_return(double S[5], double Y, int norm) {
-  const double zz = -(S[0] + S[1]);
-  const double j2 = 0.5 * (S[0] * S[0] + S[1] * S[1] + zz * zz) + S[2] * S[2] + S[3] * S[3] +
-                    S[4] * S[4];
-  if (!(j2 > 0.0)) return;
-  const double f = Y / sqrt(norm ? 3.0 * j2 : j2);
-  if (f < 1.0) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) S[k] *= f;
-  }
+// Radial-return factor (Eq. 31-33) of S = {xx, yy, xy, xz, yz}.
+template <typename T> __device__ inline T radial_factor_t(const T S[5], T Y, int norm) {
+  const T zz = -(S[0] + S[1]);
+  const T j2 = T(0.5) * (S[0] * S[0] + S[1] * S[1] + zz * zz) + S[2] * S[2] + S[3] * S[3] +
+               S[4] * S[4];
+  if (!(j2 > T(0))) return T(1);
+  const T f = Y / sqrt(norm ? T(3) * j2 : j2);
+  return f < T(1) ? f : T(1);
 }
 
 // External field at an absolute position (uniform, or radial table with
-// linear interpolation between log-spaced radii).
-__device__ inline void ext_field(const KParams &P, double x, double y, double z, double g[3],
-                                 double *phi) {
-  g[0] = g[1] = g[2] = 0.0;
-  if (phi) *phi = 0.0;
+// linear interpolation between log-spaced radii). The offset from the
+// centre is formed in FP64.
+template <typename T>
+__device__ inline void ext_field_t(const KParams &P, double x, double y, double z, T g[3], T *phi) {
+  g[0] = g[1] = g[2] = T(0);
+  if (phi) *phi = T(0);
   if (P.gravity == SPH_GRAVITY_UNIFORM) {
-    g[0] = P.g_uniform[0];
-    g[1] = P.g_uniform[1];
-    g[2] = P.g_uniform[2];
-    if (phi) *phi = -(g[0] * x + g[1] * y + g[2] * z);
+    g[0] = (T)P.g_uniform[0];
+    g[1] = (T)P.g_uniform[1];
+    g[2] = (T)P.g_uniform[2];
+    if (phi) *phi = (T)(-(P.g_uniform[0] * x + P.g_uniform[1] * y + P.g_uniform[2] * z));
     return;
   }
   if (P.gravity != SPH_GRAVITY_RADIAL) return;
-  const double dx = x - P.g_center[0], dy = y - P.g_center[1], dz = z - P.g_center[2];
-  const double r = sqrt(dx * dx + dy * dy + dz * dz);
-  if (!(r > 0.0)) return;
-  double gm, ph;
-  if (r >= P.g_rmax) {
-    gm = P.g_gm / (r * r);
-    ph = -P.g_gm / r;
-  } else if (r <= P.g_rmin) {
-    gm = P.g_table[0] * r / P.g_rmin;
-    ph = P.phi_table[0] + 0.5 * P.g_table[0] / P.g_rmin * (r * r - P.g_rmin * P.g_rmin);
+  const T dx = (T)(x - P.g_center[0]), dy = (T)(y - P.g_center[1]), dz = (T)(z - P.g_center[2]);
+  const T r = sqrt(dx * dx + dy * dy + dz * dz);
+  if (!(r > T(0))) return;
+  const T rmin = (T)P.g_rmin, rmax = (T)P.g_rmax;
+  T gm, ph;
+  if (r >= rmax) {
+    gm = (T)P.g_gm / (r * r);
+    ph = -(T)P.g_gm / r;
+  } else if (r <= rmin) {
+    const T g0 = (T)P.g_table[0];
+    gm = g0 * r / rmin;
+    ph = (T)P.phi_table[0] + T(0.5) * g0 / rmin * (r * r - rmin * rmin);
   } else {
-    int k = (int)floorf(log2f((float)(r / P.g_rmin)) * (float)P.g_inv_log_ratio);
+    int k = (int)floorf(log2f((float)(r / rmin)) * (float)P.g_inv_log_ratio);
     k = max(0, min(k, P.g_n - 2));
-    if (r < P.g_radii[k] && k > 0) --k;
-    else if (r >= P.g_radii[k + 1] && k < P.g_n - 2) ++k;
-    const double r0 = P.g_radii[k], r1 = P.g_radii[k + 1];
-    const double w = (r - r0) / (r1 - r0);
-    gm = P.g_table[k] + w * (P.g_table[k + 1] - P.g_table[k]);
-    ph = P.phi_table[k] + w * (P.phi_table[k + 1] - P.phi_table[k]);
+    if (r < (T)P.g_radii[k] && k > 0) --k;
+    else if (r >= (T)P.g_radii[k + 1] && k < P.g_n - 2) ++k;
+    const T r0 = (T)P.g_radii[k], r1 = (T)P.g_radii[k + 1];
+    const T w = (r - r0) / (r1 - r0);
+    const T ga = (T)P.g_table[k], gb = (T)P.g_table[k + 1];
+    gm = ga + w * (gb - ga);
+    const T pa = (T)P.phi_table[k], pb = (T)P.phi_table[k + 1];
+    ph = pa + w * (pb - pa);
   }
   g[0] = -gm * dx / r;
   g[1] = -gm * dy / r;
@@ -299,7 +318,7 @@ struct sph_ctx {
   // sort and cell list
   unsigned *keys, *keys_alt;
   int *vals, *vals_alt;
-  unsigned *hist;
+  unsigned *hist, *scan_tot;
   int ntiles;
   int *cell_start, *cell_end;
   int max_cells;

@@ -1,0 +1,159 @@
+// sph_pair.cuh -- warp-per-bucket machinery shared by the two pair kernels
+// (density solve and force loop).
+//
+// A bucket is 32 consecutive cell-sorted particles, one per lane. Lanes whose
+// cells lie within two cells of the first unfinished lane form a group; a
+// group stages its candidate neighbours, particles of the cells that overlap
+// the group's bounding box grown by a search radius, into a per-warp
+// shared-memory list after a bounding-box distance filter. The staging is
+// resumable so that a list longer than the buffer is processed in segments.
+#pragma once
+
+#include <type_traits>
+
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+template <typename T> struct V4T;
+template <> struct V4T<float> {
+  using type = float4;
+  static __device__ __forceinline__ float4 ld(const float4 *p, int64_t i) { return __ldg(p + i); }
+  static __device__ __forceinline__ float4 make(float x, float y, float z, float w) {
+    return make_float4(x, y, z, w);
+  }
+};
+template <> struct V4T<double> {
+  using type = double4_32a;
+  static __device__ __forceinline__ double4_32a ld(const double4_32a *p, int64_t i) { return p[i]; }
+  static __device__ __forceinline__ double4_32a make(double x, double y, double z, double w) {
+    return make_double4_32a(x, y, z, w);
+  }
+};
+
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+
+// Squared distance of a point to an axis-aligned box (0 inside).
+template <typename T>
+__device__ __forceinline__ T box_d2(T x, T y, T z, T x0, T x1, T y0, T y1, T z0, T z1) {
+  const T ex = tmax(x0 - x, tmax(T(0), x - x1));
+  const T ey = tmax(y0 - y, tmax(T(0), y - y1));
+  const T ez = tmax(z0 - z, tmax(T(0), z - z1));
+  return ex * ex + ey * ey + ez * ez;
+}
+
+// Group of lanes around the first lane still in `todo`.
+struct Group {
+  int rx, ry, rz;   // reference cell
+  bool member;
+};
+__device__ __forceinline__ Group next_group(unsigned &todo, int cx, int cy, int cz) {
+  const int lane = threadIdx.x & 31;
+  Group g;
+  const int ref = __ffs(todo) - 1;
+  g.rx = __shfl_sync(kFull, cx, ref);
+  g.ry = __shfl_sync(kFull, cy, ref);
+  g.rz = __shfl_sync(kFull, cz, ref);
+  g.member = ((todo >> lane) & 1u) && abs(cx - g.rx) <= 2 && abs(cy - g.ry) <= 2 &&
+             abs(cz - g.rz) <= 2;
+  todo &= ~__ballot_sync(kFull, g.member);
+  return g;
+}
+
+// Bounding box of the active lanes (warp-uniform result).
+template <typename T> struct Box {
+  T x0, x1, y0, y1, z0, z1;
+};
+template <typename T>
+__device__ __forceinline__ Box<T> group_box(bool act, T x, T y, T z) {
+  Box<T> b;
+  b.x0 = wmin(act ? x : T(1e30));
+  b.x1 = wmax(act ? x : T(-1e30));
+  b.y0 = wmin(act ? y : T(1e30));
+  b.y1 = wmax(act ? y : T(-1e30));
+  b.z0 = wmin(act ? z : T(1e30));
+  b.z1 = wmax(act ? z : T(-1e30));
+  return b;
+}
+
+// Resumable walk over the particles of the cells overlapping box +- R.
+// Coordinates are relative to the origin of the reference cell (FP32 form)
+// or absolute (FP64 form); `off` converts a cell index into the coordinate
+// frame of the staged positions.
+template <typename T> struct Stager {
+  int kx0, kx1, ky0, ky1, kz0, kz1;  // cell range
+  int nxr, nyr, ncr;                 // range extents, number of cells
+  int ci;                            // next cell (linear in the range)
+  int jb, je;                        // current chunk start, cell end
+  T ox, oy, oz;                      // coordinate offset of the current cell
+  bool done;
+};
+
+template <typename T>
+__device__ __forceinline__ int cell_floor(T v, double invL) {
+  return (int)floor((double)v * invL);
+}
+
+// Set up a stager for box +- R. REL: coordinates relative to cell (rx, ry, rz).
+template <typename T, bool REL>
+__device__ __forceinline__ Stager<T> make_stager(const Box<T> &b, T R, const Grid &g, int rx,
+                                                 int ry, int rz) {
+  Stager<T> s;
+  const double invL = 1.0 / g.L;
+  if (REL) {
+    s.kx0 = rx + (int)floorf((float)(b.x0 - R) * (float)invL);
+    s.kx1 = rx + (int)floorf((float)(b.x1 + R) * (float)invL);
+    s.ky0 = ry + (int)floorf((float)(b.y0 - R) * (float)invL);
+    s.ky1 = ry + (int)floorf((float)(b.y1 + R) * (float)invL);
+    s.kz0 = rz + (int)floorf((float)(b.z0 - R) * (float)invL);
+    s.kz1 = rz + (int)floorf((float)(b.z1 + R) * (float)invL);
+  } else {
+    s.kx0 = (int)floor(((double)b.x0 - (double)R - g.lo[0]) * invL);
+    s.kx1 = (int)floor(((double)b.x1 + (double)R - g.lo[0]) * invL);
+    s.ky0 = (int)floor(((double)b.y0 - (double)R - g.lo[1]) * invL);
+    s.ky1 = (int)floor(((double)b.y1 + (double)R - g.lo[1]) * invL);
+    s.kz0 = (int)floor(((double)b.z0 - (double)R - g.lo[2]) * invL);
+    s.kz1 = (int)floor(((double)b.z1 + (double)R - g.lo[2]) * invL);
+  }
+  s.kx0 = max(s.kx0, 0);
+  s.ky0 = max(s.ky0, 0);
+  s.kz0 = max(s.kz0, 0);
+  s.kx1 = min(s.kx1, g.dims[0] - 1);
+  s.ky1 = min(s.ky1, g.dims[1] - 1);
+  s.kz1 = min(s.kz1, g.dims[2] - 1);
+  s.nxr = max(0, s.kx1 - s.kx0 + 1);
+  s.nyr = max(0, s.ky1 - s.ky0 + 1);
+  s.ncr = s.nxr * s.nyr * max(0, s.kz1 - s.kz0 + 1);
+  s.ci = 0;
+  s.jb = 0;
+  s.je = 0;
+  s.ox = s.oy = s.oz = T(0);
+  s.done = s.ncr == 0;
+  return s;
+}
+
+// Advance to the next non-empty cell; false when the range is exhausted.
+template <typename T, bool REL>
+__device__ __forceinline__ bool stager_next_cell(Stager<T> &s, const Grid &g, const int *cstart,
+                                                 const int *cend, int rx, int ry, int rz, T Lt) {
+  while (s.ci < s.ncr) {
+    const int q = s.ci++;
+    const int x = s.kx0 + q % s.nxr;
+    const int y = s.ky0 + (q / s.nxr) % s.nyr;
+    const int z = s.kz0 + q / (s.nxr * s.nyr);
+    const int c = (z * g.dims[1] + y) * g.dims[0] + x;
+    const int s0 = cstart[c];
+    if (s0 < 0) continue;
+    s.jb = s0;
+    s.je = cend[c];
+    s.ox = REL ? (T)(x - rx) * Lt : T(0);
+    s.oy = REL ? (T)(y - ry) * Lt : T(0);
+    s.oz = REL ? (T)(z - rz) * Lt : T(0);
+    return true;
+  }
+  s.done = true;
+  return false;
+}
+
+}  // namespace sphk

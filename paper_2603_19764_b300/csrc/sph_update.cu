@@ -9,7 +9,10 @@ constexpr int kNSum = 9;
 
 // kick = 1: close to i (v, u, S alike), rescale S with Y at (rho_i, u_i),
 // accumulate 1/2 edot:edot dt, sum diagnostics at i, open to i+1/2.
-// kick = 0: diagnostics and time step of the state as it stands.
+// kick = 0: diagnostics and time step of the state as it stands. The
+// integration and the sums are FP64; the EOS, yield and time-step criteria
+// are evaluated in T.
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n, const double *dtp,
                                                 int kick, KParams P, double *partials,
                                                 Status *st) {
@@ -17,7 +20,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n,
   __shared__ double redt[kBlock / 32];
   const double dt = kick ? *dtp : 0.0, hdt = 0.5 * dt;
   double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double tmin = INFINITY;
+  T tmin = T(INFINITY);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
@@ -35,8 +38,11 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n,
 #pragma unroll
       for (int k = 0; k < 5; ++k) S[k] += hdt * dS[k];
       if (M.strength) {
-        const EosOut e = eos(M, s.rho[i], u);
-        radial_return(S, yield(M, e.P, u), P.yield_norm);
+        const EosT<T> e = eos_t<T>(M, s.rho[i], u);
+        const T St[5] = {(T)S[0], (T)S[1], (T)S[2], (T)S[3], (T)S[4]};
+        const double f = (double)radial_factor_t<T>(St, yield_t<T>(M, e.P, (T)u), P.yield_norm);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) S[k] *= f;
       } else {
         S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
       }
@@ -53,11 +59,11 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n,
       s.syz[i] = S[4] + hdt * dS[4];
     }
     const double x = s.x[i], y = s.y[i], z = s.z[i];
-    double g[3], phi;
-    ext_field(P, x, y, z, g, &phi);
+    T g[3], phi;
+    ext_field_t<T>(P, x, y, z, g, &phi);
     acc[0] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     acc[1] += m * u;
-    acc[2] += m * phi;
+    acc[2] += m * (double)phi;
     acc[3] += m * v[0];
     acc[4] += m * v[1];
     acc[5] += m * v[2];
@@ -65,20 +71,21 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n,
     acc[7] += m * (z * v[0] - x * v[2]);
     acc[8] += m * (x * v[1] - y * v[0]);
     if (!fixed) {
-      const double H = s.h[i];
-      const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-      const double ta = am > 0.0 ? P.eta_a * sqrt(H / am) : INFINITY;   // Eq. 38, eps = H
-      const double tc = P.eta_c * H / w.vsig[i];                       // Eq. 39
-      tmin = fmin(tmin, fmin(ta, tc));
+      const T H = (T)s.h[i];
+      const T ax = (T)a[0], ay = (T)a[1], az = (T)a[2];
+      const T am = sqrt(ax * ax + ay * ay + az * az);
+      const T ta = am > T(0) ? (T)P.eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
+      const T tc = (T)P.eta_c * H / (T)w.vsig[i];                          // Eq. 39
+      tmin = tmin_(tmin, tmin_(ta, tc));
     }
   }
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kNSum; ++k) acc[k] = wsum(acc[k]);
-  tmin = wmin(tmin);
+  double tm = wmin((double)tmin);
   if (lane == 0) {
     for (int k = 0; k < kNSum; ++k) red[k][wi] = acc[k];
-    redt[wi] = tmin;
+    redt[wi] = tm;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -93,19 +100,34 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n,
   }
 }
 
-// Fixed-order sum of the block partials.
-__global__ void k_reduce_final(const double *partials, int nblocks, Status *st) {
-  const int k = threadIdx.x;
-  if (k >= kNSum) return;
-  double t = 0.0;
-  for (int b = 0; b < nblocks; ++b) t += partials[b * kNSum + k];
-  st->sums[k] = t;
+// Fixed-order sum of the block partials: strided per-thread sums, then a
+// tree over the block (deterministic for a fixed block count).
+__global__ void __launch_bounds__(kBlock) k_reduce_final(const double *partials, int nblocks,
+                                                        Status *st) {
+  __shared__ double red[kBlock / 32];
+  for (int k = 0; k < kNSum; ++k) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) t += partials[b * kNSum + k];
+    t = wsum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int q = 0; q < kBlock / 32; ++q) s += red[q];
+      st->sums[k] = s;
+    }
+    __syncthreads();
+  }
 }
 
 cudaError_t launch_kick(sph_ctx *c, int kick) {
-  k_kick<<<c->nred_blocks, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, kick, c->kp,
-                                                   c->partials, c->d_status);
-  k_reduce_final<<<1, 32, 0, c->stream>>>(c->partials, c->nred_blocks, c->d_status);
+  if (c->kp.precision == SPH_FP32K)
+    k_kick<float><<<c->nred_blocks, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, kick,
+                                                            c->kp, c->partials, c->d_status);
+  else
+    k_kick<double><<<c->nred_blocks, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, kick,
+                                                             c->kp, c->partials, c->d_status);
+  k_reduce_final<<<1, kBlock, 0, c->stream>>>(c->partials, c->nred_blocks, c->d_status);
   return cudaGetLastError();
 }
 

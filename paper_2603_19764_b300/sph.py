@@ -56,7 +56,7 @@ class SphMaterial(C.Structure):
                 ("Y0", C.c_double), ("mu_i", C.c_double), ("Ym", C.c_double),
                 ("mu_d", C.c_double), ("thermal_softening", C.c_int32), ("xi", C.c_double),
                 ("Tm", C.c_double), ("T0", C.c_double), ("cv", C.c_double),
-                ("strength", C.c_int32)]
+                ("strength", C.c_int32), ("p_min", C.c_double)]
 
 
 class SphParams(C.Structure):
@@ -77,14 +77,16 @@ class SphStepInfo(C.Structure):
                 ("L", C.c_double * 3), ("sweeps", C.c_int32), ("n_unconverged", C.c_int32),
                 ("n_capped", C.c_int32), ("n_cfallback", C.c_int32),
                 ("pairs_density", C.c_int64), ("pairs_force", C.c_int64),
-                ("device_flags", C.c_uint32)]
+                ("device_flags", C.c_uint32), ("cand_density", C.c_int64),
+                ("cand_force", C.c_int64)]
 
     def as_dict(self) -> dict:
         return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
                     e_pot=self.e_pot, p=tuple(self.p), L=tuple(self.L), sweeps=self.sweeps,
                     n_unconverged=self.n_unconverged, n_capped=self.n_capped,
                     n_cfallback=self.n_cfallback, pairs_density=self.pairs_density,
-                    pairs_force=self.pairs_force, device_flags=self.device_flags)
+                    pairs_force=self.pairs_force, device_flags=self.device_flags,
+                    cand_density=self.cand_density, cand_force=self.cand_force)
 
 
 EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",

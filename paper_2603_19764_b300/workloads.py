@@ -78,12 +78,13 @@ EOS_TILLOTSON = 1
 
 
 def granular_material() -> dict:
-    """Cohesionless granular medium: linear EOS, Y = tan(30 deg) P."""
+    """Cohesionless granular medium: linear EOS without tension, Y = tan(30 deg) P."""
     mu = math.tan(math.radians(30.0))
     return dict(eos=EOS_LINEAR, rho0=1600.0, c0=100.0, A=1600.0 * 100.0 ** 2, B=0.0,
                 E0=1.0, a=0.0, b=0.0, alpha=0.0, beta=0.0, Eiv=0.0, Ecv=1.0,
                 shear_G=5.0e6, Y0=0.0, mu_i=mu, Ym=math.inf, mu_d=mu,
-                thermal_softening=0, xi=0.0, Tm=0.0, T0=293.0, cv=790.0, strength=1)
+                thermal_softening=0, xi=0.0, Tm=0.0, T0=293.0, cv=790.0, strength=1,
+                p_min=0.0)
 
 
 def basalt_material() -> dict:
@@ -91,7 +92,8 @@ def basalt_material() -> dict:
     return dict(eos=EOS_TILLOTSON, rho0=2700.0, c0=0.0, A=26.7e9, B=26.7e9,
                 E0=487.0e6, a=0.5, b=1.5, alpha=5.0, beta=5.0, Eiv=4.72e6, Ecv=18.2e6,
                 shear_G=22.7e9, Y0=10.0e6, mu_i=1.5, Ym=3.5e9, mu_d=0.6,
-                thermal_softening=1, xi=1.2, Tm=1373.0, T0=293.0, cv=790.0, strength=1)
+                thermal_softening=1, xi=1.2, Tm=1373.0, T0=293.0, cv=790.0, strength=1,
+                p_min=-math.inf)
 
 
 def default_params(precision: int = 0) -> dict:
@@ -216,8 +218,7 @@ def granular_column(seed: int = BASE_SEED + 1, nx: int = 16, ny: int = 8, nz: in
     a["flags"][col.shape[0]:] = 1
     p = default_params(precision)
     p.update(gravity=1, g_uniform=(0.0, 0.0, -9.81))
-    dt = 0.3 * float(a["h"][0]) / longitudinal_speed(mat)
-    return Workload("granular_column_%d" % n, a, [mat], p, dt)
+    return Workload("granular_column_%d" % n, a, [mat], p, _dt_for(mat, float(a["h"][0]), 0.0))
 
 
 def _body(rng: SplitMix64, n: int, spacing: float, mat: dict, v_sigma: float,
@@ -243,6 +244,7 @@ def _concat(parts: list) -> dict:
 
 
 def _dt_for(mat: dict, h: float, v_bulk: float) -> float:
+    """Fixed step under the CFL form of Eq. 39 (eta_C = 0.3, alpha = 1, beta = 2)."""
     return 0.3 * h / (1.6 * longitudinal_speed(mat) + 1.2 * v_bulk)
 
 
@@ -341,7 +343,7 @@ def periodic_wave_box(nx: int = 64, ny: int = 8, nz: int = 8, spacing: float = 1
     mat = dict(eos=EOS_LINEAR, rho0=1000.0, c0=100.0, A=1000.0 * 100.0 ** 2, B=0.0, E0=1.0,
                a=0.0, b=0.0, alpha=0.0, beta=0.0, Eiv=0.0, Ecv=1.0, shear_G=3.0e6, Y0=1e30,
                mu_i=0.0, Ym=math.inf, mu_d=1e30, thermal_softening=0, xi=0.0, Tm=0.0,
-               T0=293.0, cv=790.0, strength=1)
+               T0=293.0, cv=790.0, strength=1, p_min=-math.inf)
     ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
     n = nx * ny * nz
     a = _empty_arrays(n)

@@ -93,8 +93,10 @@ def test_forces_given_density(name, precision):
     g = sim.by_id()
     st = dict(w.arrays, h=g["h"], rho=g["rho"], omega=g["omega"], nngb=g["nngb"])
     st, S = oracle.eos_yield(p, w.materials, st)
-    assert np.allclose(g["pres"], st["pres"], rtol=1e-12, atol=1e-6)
-    assert np.allclose(g["cs"], st["cs"], rtol=1e-12)
+    # the FP32 form evaluates the EOS in FP32 (mu from an FP64 difference)
+    eos_tol = 1e-12 if precision == 0 else 2e-6
+    assert _maxnorm_err(g["pres"], st["pres"]) < eos_tol
+    assert np.allclose(g["cs"], st["cs"], rtol=eos_tol)
     out, _ = oracle.forces(p, w.materials, st, S=S)
     for f in DERIVS:
         e = _maxnorm_err(g[f], out[f])
@@ -116,6 +118,7 @@ def test_full_steps_granular_column(precision):
     assert pinfo["dt_next"] == pytest.approx(rinfo["dt_next"], rel=1e-5)
     nsteps = 20
     ref_state = ref
+    x0 = np.stack([w.arrays[f] for f in ("x", "y", "z")])
     for k in range(nsteps):
         ref_state, ri = oracle.step(p, w.materials, ref_state, w.dt)
         gi = sim.step(w.dt)
@@ -126,8 +129,12 @@ def test_full_steps_granular_column(precision):
             for f in DERIVS:
                 e = _maxnorm_err(g[f], ref_state[f])
                 assert e < max(DERIV_TOL[precision], 1e-6) * (1 if k == 0 else 10), (k, f, e)
-            for f in ("x", "y", "z"):
-                assert np.max(np.abs(g[f] - ref_state[f])) < 1e-9
+            xg = np.stack([g[f] for f in ("x", "y", "z")])
+            xr = np.stack([ref_state[f] for f in ("x", "y", "z")])
+            disp = np.max(np.abs(xr - x0))
+            # positions: FP64 to round-off, FP32 to 1e-3 of the displacement
+            tol = 1e-12 + (1e-9 if precision == 0 else 1e-3) * disp
+            assert np.max(np.abs(xg - xr)) < tol, (k, np.max(np.abs(xg - xr)), disp)
             assert gi["e_kin"] == pytest.approx(ri[0]["e_kin"], rel=1e-4)
     sim.close()
 

@@ -59,10 +59,21 @@ def test_kernel_scaling_identity():
 
 # ------------------------------------------------------------------- EOS ---
 def test_linear_eos():
-    m = wl.granular_material()
+    m = dict(wl.granular_material(), p_min=-math.inf)
     P, c = oracle.eos(m, np.array([1600.0, 1700.0, 1500.0]), np.zeros(3))
     assert np.allclose(P, [0.0, 100.0 ** 2 * 100, -100.0 ** 2 * 100], rtol=0, atol=1e-9)
     assert np.all(c == 100.0)
+    # the granular medium carries no tension: P floored at zero, c unchanged
+    P, c = oracle.eos(wl.granular_material(), np.array([1500.0, 1700.0]), np.zeros(2))
+    assert np.array_equal(P, [0.0, 100.0 ** 2 * 100]) and np.all(c == 100.0)
+
+
+def test_pressure_floor_tillotson():
+    m = wl.basalt_material()
+    P0, c0 = oracle.eos(m, 0.9 * m["rho0"], 0.0)
+    assert P0 < 0
+    P1, c1 = oracle.eos(dict(m, p_min=-1e6), 0.9 * m["rho0"], 0.0)
+    assert P1 == -1e6 and c1 == c0
 
 
 def test_tillotson_reference_state():
