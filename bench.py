@@ -273,6 +273,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "phases_ms_per_step": {k: (v / nsteps if k != "steps" else v)
                                        for k, v in phases.items()},
                 "sweeps": max(i["sweeps"] for i in infos),
+                "pairs_per_step": {"density": pairs_d, "force": pairs_f},
+                "candidates_per_step": {
+                    "density": statistics.mean(i["cand_density"] for i in infos),
+                    "force": statistics.mean(i["cand_force"] for i in infos)},
                 "energy": {"e_kin": infos[-1]["e_kin"], "e_int": infos[-1]["e_int"],
                            "e_pot": infos[-1]["e_pot"]}}
         print(json.dumps(line), flush=True)

@@ -110,14 +110,19 @@ __device__ __forceinline__ void build_masks(const V4 *Lp, unsigned (*Lm)[32], in
 // kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
 template <typename T, typename V4, bool REL>
 __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsigned (*Lm)[32],
-                                             int nl, int lane, T xi, T yi, T zi, T Ht, T H2,
+                                             int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              double H2c, double xi64, double yi64, double zi64,
                                              const sph_state &s, int self, T &rs, T &rhs,
                                              int &cnt) {
+  // every lane advances through its own words: lanes do not wait for each
+  // other at word boundaries
   const int nw = (nl + 31) >> 5;
-  for (int wd = 0; wd < nw; ++wd) {
-    unsigned mk = Lm[wd][lane];
-    while (mk) {
+  int wd = 0;
+  unsigned mk = nw > 0 ? Lm[0][lane] : 0u;
+  for (;;) {
+    while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
+    if (mk == 0u) break;
+    {
       const int k = (wd << 5) + __ffs(mk) - 1;
       mk &= mk - 1u;
       const V4 q = Lp[k];
@@ -136,8 +141,7 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
         in = r2 < H2;
       }
       if (in) {
-        const T r = r2 > T(0) ? sqrt(r2) : T(0);
-        const T qq = r / Ht;
+        const T qq = root(r2) * invH;
         const T t = qq < T(1) ? T(1) - qq : T(0);
         const T mW = q.w * t * t * t;
         rs += mW * t * (T(1) + T(4) * qq);
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
   const V4 *pos = PosPtr<T>::get(A.w);
 
   const Grid g = A.st->grid;
-  const T Lt = (T)g.L;
+  const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
   const V4 p = V::ld(pos, ic);
@@ -201,6 +205,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
       const bool act = G.member && state == 0;
       if (!__any_sync(kFull, act)) break;
       const T Ht = (T)H;
+      const T invHt = T(1) / Ht;
       const double H2c = __dmul_rn(H, H);
       const T H2 = REL ? Ht * Ht : (T)H2c;
       const T Rneed = wmax(act ? Ht : T(0));
@@ -210,14 +215,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
       if (!resident) {
         Rl = Rneed * T(1.05);
         const Box<T> bx = group_box(act, xi, yi, zi);
-        Stager<T> sg = make_stager<T, REL>(bx, Rl, g, G.rx, G.ry, G.rz);
+        Stager<T> sg = make_stager<T, REL>(bx, Rl, g, invL, G.rx, G.ry, G.rz);
         Hm = T(0);
         complete = false;
         for (int seg = 0;; ++seg) {
           nl = 0;
           while (nl <= CAP - 32) {
             if (sg.jb >= sg.je &&
-                !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, G.rx, G.ry, G.rz, Lt))
+                !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, Lt))
               break;
             const int j = sg.jb + lane;
             const bool ok = j < sg.je;
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
             sg.jb += 32;
           }
           cand += nl;
-          if (seg == 0 && sg.done) {
+          if (seg == 0 && stager_finished(sg)) {
             complete = true;
             break;
           }
@@ -244,10 +249,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
           build_masks<T, V4>(Lp, Lm, nl, xi, yi, zi, H2 * T(1.0001), act, lane);
           __syncwarp();
           if (act)
-            density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, Ht, H2, H2c, xi64, yi64,
+            density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
                                      zi64, A.s, (int)i, rs, rhs, cnt);
           __syncwarp();
-          if (sg.done) break;
+          if (stager_finished(sg)) break;
         }
       }
       if (complete) {
@@ -261,14 +266,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
           Hm = Hn;
         }
         if (act)
-          density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, Ht, H2, H2c, xi64, yi64, zi64,
+          density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64, zi64,
                                    A.s, (int)i, rs, rhs, cnt);
       }
 
       if (act) {
         // Eq. 1 and Eq. 3 with the kernel constants applied once; the
         // residual is relative to the target kernel mass n_ngb m_i
-        const T ih = T(1) / Ht;
+        const T ih = invHt;
         const T ih3 = ih * ih * ih;
         const T rho = T(cW) * ih3 * rs;
         const T rhoH = T(cW) * ih3 * ih * rhs;

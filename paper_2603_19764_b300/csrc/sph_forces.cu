@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
            *fj3 = PK::fj(A.w, 3);
 
   const Grid g = A.st->grid;
-  const T Lt = (T)g.L;
+  const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
   const T hmax_all = (T)dec_d(A.st->hmax2_enc);
@@ -181,13 +181,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
     const T Rb = wmax(act ? Hi : T(0));
     const T Rf = tmax(Rb, hmax_all);
     const Box<T> bx = group_box(act, xi, yi, zi);
-    Stager<T> sg = make_stager<T, REL>(bx, Rf, g, G.rx, G.ry, G.rz);
+    Stager<T> sg = make_stager<T, REL>(bx, Rf, g, invL, G.rx, G.ry, G.rz);
     for (;;) {
       // stage candidates
       int nl = 0;
       while (nl <= CAP - 32) {
         if (sg.jb >= sg.je &&
-            !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, G.rx, G.ry, G.rz, Lt))
+            !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, Lt))
           break;
         const int j = sg.jb + lane;
         const bool ok = j < sg.je;
@@ -223,10 +223,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
         Lm[wd][lane] = act ? mk : 0u;
       }
       __syncwarp();
-      // each lane walks its own neighbours
-      for (int wd = 0; wd < nw; ++wd) {
-        unsigned mk = Lm[wd][lane];
-        while (mk) {
+      // each lane walks its own neighbours, independently of the others
+      int wd = 0;
+      unsigned mk = nw > 0 ? Lm[0][lane] : 0u;
+      for (;;) {
+        while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
+        if (mk == 0u) break;
+        {
           const int k = (wd << 5) + __ffs(mk) - 1;
           mk &= mk - 1u;
           const int j = Li[k];
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
           const V4 f0 = V::ld(fj0, j), f1 = V::ld(fj1, j), f2 = V::ld(fj2, j), f3 = V::ld(fj3, j);
           const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
-          const T r = sqrt(r2);
+          const T r = root(r2);
           const T ti = tmax(T(1) - r * invHi, T(0));
           const T tj = tmax(T(1) - r * f3.y, T(0));
           const T Wi = Ki * ti * ti * ti;   // W'(r, H_i) / r
@@ -255,8 +258,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
           const T vr = vx * dx + vy * dy + vz * dz;
           if (vr < T(0)) {  // Eq. 5-8
             const T hb = T(0.5) * (Hi + f3.w);
-            const T mu = hb * vr / (r2 + ep * hb * hb);
-            const T Pi = (be * mu - al * T(0.5) * (ci + f2.w)) * mu / (T(0.5) * (rhoi + f3.x));
+            const T mu = quot(hb * vr, r2 + ep * hb * hb);
+            const T Pi = quot((be * mu - al * T(0.5) * (ci + f2.w)) * mu, T(0.5) * (rhoi + f3.x));
             const T t = T(0.5) * mj * Pi * (Wi + Wj);
             ax -= t * dx;
             ay -= t * dy;
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
         }
       }
       __syncwarp();
-      if (sg.done) break;
+      if (stager_finished(sg)) break;
     }
   }
 

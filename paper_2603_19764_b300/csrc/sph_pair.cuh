@@ -34,6 +34,20 @@ template <> struct V4T<double> {
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
+// Square root of x >= 0 and a quotient: correctly rounded in FP64; in FP32
+// through the hardware reciprocal square root and the fast divide (a few
+// ulp), which the FP32 form's tolerances absorb.
+template <typename T> __device__ __forceinline__ T root(T x);
+template <> __device__ __forceinline__ float root<float>(float x) {
+  return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+template <> __device__ __forceinline__ double root<double>(double x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T quot(T a, T b);
+template <> __device__ __forceinline__ float quot<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
+
 // Squared distance of a point to an axis-aligned box (0 inside).
 template <typename T>
 __device__ __forceinline__ T box_d2(T x, T y, T z, T x0, T x1, T y0, T y1, T z0, T z1) {
@@ -79,42 +93,42 @@ __device__ __forceinline__ Box<T> group_box(bool act, T x, T y, T z) {
 
 // Resumable walk over the particles of the cells overlapping box +- R.
 // Coordinates are relative to the origin of the reference cell (FP32 form)
-// or absolute (FP64 form); `off` converts a cell index into the coordinate
-// frame of the staged positions.
+// or absolute (FP64 form); (ox, oy, oz) converts the staged cell's packed
+// positions into that frame. The cell counters advance without integer
+// division, and the FP32 offsets are kept as exact integer-valued floats.
 template <typename T> struct Stager {
   int kx0, kx1, ky0, ky1, kz0, kz1;  // cell range
-  int nxr, nyr, ncr;                 // range extents, number of cells
-  int ci;                            // next cell (linear in the range)
+  int x, y, z;                       // next cell
+  T fx0, fy0, fx, fy, fz;            // (cell - reference) as exact floats
   int jb, je;                        // current chunk start, cell end
   T ox, oy, oz;                      // coordinate offset of the current cell
-  bool done;
+  bool done;                         // no further cell to fetch
 };
 
-template <typename T>
-__device__ __forceinline__ int cell_floor(T v, double invL) {
-  return (int)floor((double)v * invL);
+// All staged: no further cell and the current one consumed.
+template <typename T> __device__ __forceinline__ bool stager_finished(const Stager<T> &s) {
+  return s.done && s.jb >= s.je;
 }
 
 // Set up a stager for box +- R. REL: coordinates relative to cell (rx, ry, rz).
 template <typename T, bool REL>
-__device__ __forceinline__ Stager<T> make_stager(const Box<T> &b, T R, const Grid &g, int rx,
-                                                 int ry, int rz) {
+__device__ __forceinline__ Stager<T> make_stager(const Box<T> &b, T R, const Grid &g, T invL,
+                                                 int rx, int ry, int rz) {
   Stager<T> s;
-  const double invL = 1.0 / g.L;
   if (REL) {
-    s.kx0 = rx + (int)floorf((float)(b.x0 - R) * (float)invL);
-    s.kx1 = rx + (int)floorf((float)(b.x1 + R) * (float)invL);
-    s.ky0 = ry + (int)floorf((float)(b.y0 - R) * (float)invL);
-    s.ky1 = ry + (int)floorf((float)(b.y1 + R) * (float)invL);
-    s.kz0 = rz + (int)floorf((float)(b.z0 - R) * (float)invL);
-    s.kz1 = rz + (int)floorf((float)(b.z1 + R) * (float)invL);
+    s.kx0 = rx + (int)floorf((float)((b.x0 - R) * invL));
+    s.kx1 = rx + (int)floorf((float)((b.x1 + R) * invL));
+    s.ky0 = ry + (int)floorf((float)((b.y0 - R) * invL));
+    s.ky1 = ry + (int)floorf((float)((b.y1 + R) * invL));
+    s.kz0 = rz + (int)floorf((float)((b.z0 - R) * invL));
+    s.kz1 = rz + (int)floorf((float)((b.z1 + R) * invL));
   } else {
-    s.kx0 = (int)floor(((double)b.x0 - (double)R - g.lo[0]) * invL);
-    s.kx1 = (int)floor(((double)b.x1 + (double)R - g.lo[0]) * invL);
-    s.ky0 = (int)floor(((double)b.y0 - (double)R - g.lo[1]) * invL);
-    s.ky1 = (int)floor(((double)b.y1 + (double)R - g.lo[1]) * invL);
-    s.kz0 = (int)floor(((double)b.z0 - (double)R - g.lo[2]) * invL);
-    s.kz1 = (int)floor(((double)b.z1 + (double)R - g.lo[2]) * invL);
+    s.kx0 = (int)floor(((double)b.x0 - (double)R - g.lo[0]) * (double)invL);
+    s.kx1 = (int)floor(((double)b.x1 + (double)R - g.lo[0]) * (double)invL);
+    s.ky0 = (int)floor(((double)b.y0 - (double)R - g.lo[1]) * (double)invL);
+    s.ky1 = (int)floor(((double)b.y1 + (double)R - g.lo[1]) * (double)invL);
+    s.kz0 = (int)floor(((double)b.z0 - (double)R - g.lo[2]) * (double)invL);
+    s.kz1 = (int)floor(((double)b.z1 + (double)R - g.lo[2]) * (double)invL);
   }
   s.kx0 = max(s.kx0, 0);
   s.ky0 = max(s.ky0, 0);
@@ -122,37 +136,58 @@ __device__ __forceinline__ Stager<T> make_stager(const Box<T> &b, T R, const Gri
   s.kx1 = min(s.kx1, g.dims[0] - 1);
   s.ky1 = min(s.ky1, g.dims[1] - 1);
   s.kz1 = min(s.kz1, g.dims[2] - 1);
-  s.nxr = max(0, s.kx1 - s.kx0 + 1);
-  s.nyr = max(0, s.ky1 - s.ky0 + 1);
-  s.ncr = s.nxr * s.nyr * max(0, s.kz1 - s.kz0 + 1);
-  s.ci = 0;
+  s.x = s.kx0;
+  s.y = s.ky0;
+  s.z = s.kz0;
+  s.fx0 = (T)(s.kx0 - rx);
+  s.fx = s.fx0;
+  s.fy0 = (T)(s.ky0 - ry);
+  s.fy = s.fy0;
+  s.fz = (T)(s.kz0 - rz);
   s.jb = 0;
   s.je = 0;
   s.ox = s.oy = s.oz = T(0);
-  s.done = s.ncr == 0;
+  s.done = s.kx0 > s.kx1 || s.ky0 > s.ky1 || s.kz0 > s.kz1;
   return s;
 }
 
 // Advance to the next non-empty cell; false when the range is exhausted.
 template <typename T, bool REL>
 __device__ __forceinline__ bool stager_next_cell(Stager<T> &s, const Grid &g, const int *cstart,
-                                                 const int *cend, int rx, int ry, int rz, T Lt) {
-  while (s.ci < s.ncr) {
-    const int q = s.ci++;
-    const int x = s.kx0 + q % s.nxr;
-    const int y = s.ky0 + (q / s.nxr) % s.nyr;
-    const int z = s.kz0 + q / (s.nxr * s.nyr);
-    const int c = (z * g.dims[1] + y) * g.dims[0] + x;
+                                                 const int *cend, T Lt) {
+  while (!s.done) {
+    const int c = (s.z * g.dims[1] + s.y) * g.dims[0] + s.x;
+    const T fx = s.fx, fy = s.fy, fz = s.fz;
+    // step to the following cell of the range
+    if (s.x < s.kx1) {
+      ++s.x;
+      s.fx += T(1);
+    } else {
+      s.x = s.kx0;
+      s.fx = s.fx0;
+      if (s.y < s.ky1) {
+        ++s.y;
+        s.fy += T(1);
+      } else {
+        s.y = s.ky0;
+        s.fy = s.fy0;
+        if (s.z < s.kz1) {
+          ++s.z;
+          s.fz += T(1);
+        } else {
+          s.done = true;
+        }
+      }
+    }
     const int s0 = cstart[c];
     if (s0 < 0) continue;
     s.jb = s0;
     s.je = cend[c];
-    s.ox = REL ? (T)(x - rx) * Lt : T(0);
-    s.oy = REL ? (T)(y - ry) * Lt : T(0);
-    s.oz = REL ? (T)(z - rz) * Lt : T(0);
+    s.ox = REL ? fx * Lt : T(0);
+    s.oy = REL ? fy * Lt : T(0);
+    s.oz = REL ? fz * Lt : T(0);
     return true;
   }
-  s.done = true;
   return false;
 }
 

@@ -93,10 +93,11 @@ def test_forces_given_density(name, precision):
     g = sim.by_id()
     st = dict(w.arrays, h=g["h"], rho=g["rho"], omega=g["omega"], nngb=g["nngb"])
     st, S = oracle.eos_yield(p, w.materials, st)
-    # the FP32 form evaluates the EOS in FP32 (mu from an FP64 difference)
-    eos_tol = 1e-12 if precision == 0 else 2e-6
-    assert _maxnorm_err(g["pres"], st["pres"]) < eos_tol
-    assert np.allclose(g["cs"], st["cs"], rtol=eos_tol)
+    # the FP32 form evaluates the EOS in FP32 (mu from an FP64 difference);
+    # c^2 = P_rho + P P_u / rho^2 loses relative precision where A + 2 B mu
+    # cancels (rho near 0.75 rho0 for basalt), up to a few 1e-6
+    assert _maxnorm_err(g["pres"], st["pres"]) < (1e-12 if precision == 0 else 2e-6)
+    assert np.allclose(g["cs"], st["cs"], rtol=1e-12 if precision == 0 else 2e-5)
     out, _ = oracle.forces(p, w.materials, st, S=S)
     for f in DERIVS:
         e = _maxnorm_err(g[f], out[f])
