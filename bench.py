@@ -277,6 +277,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "candidates_per_step": {
                     "density": statistics.mean(i["cand_density"] for i in infos),
                     "force": statistics.mean(i["cand_force"] for i in infos)},
+                "groups_per_bucket": {
+                    "density": statistics.mean(i["groups_density"] for i in infos) / ((w.n + 31) // 32),
+                    "force": statistics.mean(i["groups_force"] for i in infos) / ((w.n + 31) // 32)},
                 "energy": {"e_kin": infos[-1]["e_kin"], "e_int": infos[-1]["e_int"],
                            "e_pot": infos[-1]["e_pot"]}}
         print(json.dumps(line), flush=True)

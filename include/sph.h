@@ -157,6 +157,7 @@ typedef struct {
   int64_t pairs_density, pairs_force;
   uint32_t device_flags;
   int64_t cand_density, cand_force;
+  int64_t groups_density, groups_force;  /* lane groups the pair kernels formed */
 } sph_step_info;
 
 /* Create a context for n particles in `st` on `cuda_stream` (a cudaStream_t,

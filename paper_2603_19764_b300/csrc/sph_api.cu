@@ -110,6 +110,8 @@ sph_status sync_status(sph_ctx *c, sph_step_info *info, double dt) {
     info->pairs_force = (int64_t)h.pairs_force;
     info->cand_density = (int64_t)h.cand_density;
     info->cand_force = (int64_t)h.cand_force;
+    info->groups_density = (int64_t)h.groups_density;
+    info->groups_force = (int64_t)h.groups_force;
     info->device_flags = h.err;
   }
   return status_from_flags(c, h.err);
@@ -209,6 +211,15 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
   c->n = n;
   c->stream = (cudaStream_t)cuda_stream;
   const bool fp32 = p->precision == SPH_FP32K;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        c->num_sms < 1) {
+      free(c);
+      return SPH_E_CUDA;
+    }
+  }
 
 #define CKI(call)                          \
   do {                                     \

@@ -153,7 +153,7 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
 }
 
 template <typename T, int CAP>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
   using V4 = typename V::type;
@@ -164,8 +164,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
   V4 *Lp = s_pos[wib];
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
-  const int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + wib) * 32;
-  if (base >= A.n) return;
+  // persistent warps: each takes the next bucket of 32 particles
+  const int64_t nbuckets = (A.n + 31) / 32;
+  long long w_pairs = 0, w_cand = 0;
+  int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0;
+  unsigned w_bad = 0;
+  double w_hm = 0.0;
+  for (;;) {
+  unsigned bk = 0;
+  if (lane == 0) bk = atomicAdd(&A.st->next_bucket[0], 1u);
+  bk = __shfl_sync(kFull, bk, 0);
+  if ((int64_t)bk >= nbuckets) break;
+  const int64_t base = (int64_t)bk * 32;
   const int64_t i = base + lane;
   const bool valid = i < A.n;
   const int64_t ic = valid ? i : base;
@@ -194,6 +204,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
   unsigned todo = __ballot_sync(kFull, valid);
   while (todo) {
     const Group G = next_group(todo, cx, cy, cz);
+    ++w_groups;
     const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
     const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
     const T zi = REL ? p.z + (T)(cz - G.rz) * Lt : p.z;
@@ -311,13 +322,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
     A.s.omega[i] = (double)om_o;
     A.s.nngb[i] = cnt_o;
   }
-  const int sw = wmax(valid ? sweeps_o : 0);
-  const int nu = __popc(__ballot_sync(kFull, state == 3));
-  const int ncap = __popc(__ballot_sync(kFull, state == 2));
-  const bool bad = valid && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0));
-  const unsigned nbad = __ballot_sync(kFull, bad);
-  const double hm = wmax(valid ? H_o : 0.0);
-  const long long pw = wsum(pairs);
+  w_sw = max(w_sw, valid ? sweeps_o : 0);
+  w_nu += state == 3;
+  w_ncap += state == 2;
+  w_bad |= (valid && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0))) ? 1u
+                                                                                           : 0u;
+  w_hm = fmax(w_hm, valid ? H_o : 0.0);
+  w_pairs += pairs;
+  w_cand += cand;
+  }  // bucket loop
+  const int sw = wmax(w_sw);
+  const int nu = wsum(w_nu);
+  const int ncap = wsum(w_ncap);
+  const unsigned nbad = __ballot_sync(kFull, w_bad != 0u);
+  const double hm = wmax(w_hm);
+  const long long pw = wsum(w_pairs);
   if (lane == 0) {
     atomicMax(&A.st->max_sweeps, sw);
     if (nu) {
@@ -328,7 +347,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_density(DensArgs A) {
     if (nbad) atomicOr(&A.st->err, ERR_NONFINITE);
     atomicMax(&A.st->hmax2_enc, enc_d(hm));
     atomicAdd(&A.st->pairs_density, (unsigned long long)pw);
-    atomicAdd(&A.st->cand_density, (unsigned long long)cand);
+    atomicAdd(&A.st->cand_density, (unsigned long long)w_cand);
+    atomicAdd(&A.st->groups_density, (unsigned long long)w_groups);
   }
 }
 
@@ -341,12 +361,14 @@ cudaError_t launch_density(sph_ctx *c) {
   a.cell_end = c->cell_end;
   a.p = c->kp;
   a.st = c->d_status;
-  const int64_t buckets = (c->n + 31) / 32;
-  const int blocks = (int)((buckets + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K)
-    k_density<float, 512><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    k_density<float, 512><<<resident_grid(c, k_density<float, 512>), 32 * kWarpsPerBlock, 0,
+                            c->stream>>>(a);
   else
-    k_density<double, 256><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    k_density<double, 256><<<resident_grid(c, k_density<double, 256>), 32 * kWarpsPerBlock, 0,
+                             c->stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -129,7 +129,7 @@ struct ForceArgs {
 };
 
 template <typename T, int CAP>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
   using V4 = typename V::type;
@@ -141,8 +141,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
   V4 *Lr = s_rec[wib];
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
-  const int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + wib) * 32;
-  if (base >= A.n) return;
+  // persistent warps: each takes the next bucket of 32 particles
+  const int64_t nbuckets = (A.n + 31) / 32;
+  long long w_pairs = 0, w_cand = 0;
+  int w_fb = 0, w_groups = 0;
+  for (;;) {
+  unsigned bk = 0;
+  if (lane == 0) bk = atomicAdd(&A.st->next_bucket[1], 1u);
+  bk = __shfl_sync(kFull, bk, 0);
+  if ((int64_t)bk >= nbuckets) break;
+  const int64_t base = (int64_t)bk * 32;
   const int64_t i = base + lane;
   const bool valid = i < A.n;
   const int64_t ic = valid ? i : base;
@@ -174,6 +182,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
   unsigned todo = __ballot_sync(kFull, valid);
   while (todo) {
     const Group G = next_group(todo, cx, cy, cz);
+    ++w_groups;
     const bool act = G.member;
     const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
     const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
@@ -362,12 +371,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_forces(ForceArgs A) {
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(dS[k]);
     if (!fin) atomicOr(&A.st->err, ERR_NONFINITE);
   }
-  const int nfb = __popc(__ballot_sync(kFull, fallback != 0));
-  const long long pw = wsum((long long)npairs);
+  w_fb += fallback;
+  w_pairs += npairs;
+  w_cand += cand;
+  }  // bucket loop
+  const int nfb = wsum(w_fb);
+  const long long pw = wsum(w_pairs);
   if (lane == 0) {
     if (nfb) atomicAdd(&A.st->n_cfallback, nfb);
     atomicAdd(&A.st->pairs_force, (unsigned long long)pw);
-    atomicAdd(&A.st->cand_force, (unsigned long long)cand);
+    atomicAdd(&A.st->cand_force, (unsigned long long)w_cand);
+    atomicAdd(&A.st->groups_force, (unsigned long long)w_groups);
   }
 }
 
@@ -380,12 +394,14 @@ cudaError_t launch_forces(sph_ctx *c) {
   a.cell_end = c->cell_end;
   a.p = c->kp;
   a.st = c->d_status;
-  const int64_t buckets = (c->n + 31) / 32;
-  const int blocks = (int)((buckets + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[1], 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K)
-    k_forces<float, 512><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    k_forces<float, 512><<<resident_grid(c, k_forces<float, 512>), 32 * kWarpsPerBlock, 0,
+                           c->stream>>>(a);
   else
-    k_forces<double, 256><<<blocks, 32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    k_forces<double, 256><<<resident_grid(c, k_forces<double, 256>), 32 * kWarpsPerBlock, 0,
+                            c->stream>>>(a);
   return cudaGetLastError();
 }
 

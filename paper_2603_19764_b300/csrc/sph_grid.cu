@@ -27,6 +27,8 @@ __global__ void k_reset_status(Status *st, int full) {
   st->pairs_force = 0;
   st->cand_density = 0;
   st->cand_force = 0;
+  st->groups_density = 0;
+  st->groups_force = 0;
   if (full) st->err = 0;
 }
 

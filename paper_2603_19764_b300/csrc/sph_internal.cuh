@@ -41,6 +41,8 @@ struct Status {
   unsigned long long lo_enc[3], hi_enc[3], hmax_enc, hmax2_enc, dtmin_enc;
   unsigned long long pairs_density, pairs_force;
   unsigned long long cand_density, cand_force;   // staged candidates
+  unsigned long long groups_density, groups_force;
+  unsigned next_bucket[2];                      // persistent-warp work counters
   double sums[9];   // e_kin, e_int, e_pot, p[3], L[3]
   Grid grid;
 };
@@ -330,6 +332,7 @@ struct sph_ctx {
   sphk::Status *h_status;   // pinned mirror
   double *h_dt;             // pinned dt staging
   double dt_next;
+  int num_sms;
   int timing;
   cudaEvent_t ev[SPH_NUM_PHASES + 1];
   double phase_ms[SPH_NUM_PHASES];
@@ -338,6 +341,19 @@ struct sph_ctx {
   int broken;
   char err[512];
 };
+
+// Grid of a persistent pair kernel: as many blocks as stay resident, at
+// most one warp per bucket of 32 particles.
+template <typename K> inline int resident_grid(const sph_ctx *c, K kernel) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * sphk::kWarpsPerBlock,
+                                                    0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int64_t buckets = (c->n + 31) / 32;
+  const int64_t need = (buckets + sphk::kWarpsPerBlock - 1) / sphk::kWarpsPerBlock;
+  const int64_t have = (int64_t)per_sm * c->num_sms;
+  return (int)(need < have ? need : have);
+}
 
 // Launch helpers implemented in the .cu files (all stream-ordered).
 namespace sphk {

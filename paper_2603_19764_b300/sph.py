@@ -78,7 +78,8 @@ class SphStepInfo(C.Structure):
                 ("n_capped", C.c_int32), ("n_cfallback", C.c_int32),
                 ("pairs_density", C.c_int64), ("pairs_force", C.c_int64),
                 ("device_flags", C.c_uint32), ("cand_density", C.c_int64),
-                ("cand_force", C.c_int64)]
+                ("cand_force", C.c_int64), ("groups_density", C.c_int64),
+                ("groups_force", C.c_int64)]
 
     def as_dict(self) -> dict:
         return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
@@ -86,7 +87,8 @@ class SphStepInfo(C.Structure):
                     n_unconverged=self.n_unconverged, n_capped=self.n_capped,
                     n_cfallback=self.n_cfallback, pairs_density=self.pairs_density,
                     pairs_force=self.pairs_force, device_flags=self.device_flags,
-                    cand_density=self.cand_density, cand_force=self.cand_force)
+                    cand_density=self.cand_density, cand_force=self.cand_force,
+                    groups_density=self.groups_density, groups_force=self.groups_force)
 
 
 EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
