@@ -223,6 +223,27 @@ sph_status sph_prime(sph_ctx *c, sph_step_info *info);
 sph_status sph_set_timing(sph_ctx *c, int32_t on);
 sph_status sph_phase_times(const sph_ctx *c, double *ms, int32_t n, int32_t *steps);
 
+/* Global sums of a particle state with no allocation of any kind. The
+ * paper has no counterpart; this is a library service for callers that may
+ * not allocate device memory: a host application that has committed the
+ * whole device heap to its own allocator or a fixed budget, or a monitoring
+ * hook that must leave the device's allocation state untouched between
+ * steps. Needs no context: reads x, y, z, vx, vy, vz, u, m of `st` (DEVICE
+ * arrays of length n, other pointers may be NULL) and writes 8 doubles to
+ * the caller-owned DEVICE array `sums`: kinetic energy, internal energy,
+ * linear momentum (3) and angular momentum L = sum m r x v (3), each an
+ * FP64 sum over all particles. Its scratch is a fixed array compiled into
+ * the library (partial sums of at most 1184 blocks, 75,776 bytes, held by
+ * every GPU that loads the library until the process exits). The first
+ * call on each device looks up that array's device address; make it before
+ * any stream capture. Every call on a device shares the array, so calls
+ * that overlap on the GPU (different streams, no ordering) race. Ordered on
+ * `cuda_stream`; returns after enqueueing. Errors: SPH_E_ARG (NULL
+ * pointer, n < 1 or n > SPH_NOALLOC_MAX_N), SPH_E_CUDA. */
+#define SPH_NOALLOC_MAX_N ((int64_t)1 << 31)
+sph_status sph_diagnostics_noalloc(const sph_state *st, int64_t n, double *sums,
+                                   void *cuda_stream);
+
 /* Free the context and its scratch; the caller's arrays are untouched.
  * Accepts NULL. */
 sph_status sph_destroy(sph_ctx *c);

@@ -93,7 +93,8 @@ class SphStepInfo(C.Structure):
 
 EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_stress_update", "sph_step", "sph_step_host", "sph_prime", "sph_destroy",
-           "sph_status_string", "sph_last_error", "sph_set_timing", "sph_phase_times")
+           "sph_status_string", "sph_last_error", "sph_set_timing", "sph_phase_times",
+           "sph_diagnostics_noalloc")
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
 
 
@@ -129,6 +130,8 @@ def lib():
         L.sph_set_timing.argtypes = [VP, C.c_int32]
         L.sph_phase_times.restype = st
         L.sph_phase_times.argtypes = [VP, _P, C.c_int32, _PI]
+        L.sph_diagnostics_noalloc.restype = st
+        L.sph_diagnostics_noalloc.argtypes = [C.POINTER(SphState), C.c_int64, VP, VP]
         L.sph_status_string.restype = C.c_char_p
         L.sph_status_string.argtypes = [st]
         L.sph_last_error.restype = C.c_char_p
