@@ -50,6 +50,32 @@ FLOPS_FORCE_PAIR = 151
 N_SM, FP32_LANES, MAX_MHZ = 148, 128, 2032.0
 FP64_NOMINAL_TFLOPS = 1.25
 
+# DRAM bytes (read + write) per particle per launch of the FP32 pair kernels,
+# from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` on the
+# 600k-particle impact (bench.py --scale 0.3; profiles/ has the command) and
+# scaled by particles. Keyed by a hash of the kernel's sources: once the
+# kernel changes the figure no longer applies and traffic is reported null.
+KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh"),
+                  "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (188.17, "08f335af3979"),
+                        "k_density": (56.63, "323d4567f0c4")}
+
+
+def source_hash(kernel: str) -> str:
+    import hashlib
+    m = hashlib.sha1()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2603_19764_b300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return m.hexdigest()[:12]
+
+
+def traffic_per_launch(kernel: str, n: int, precision: int):
+    if precision != 1 or kernel not in TRAFFIC_PER_PARTICLE:
+        return None
+    per, h = TRAFFIC_PER_PARTICLE[kernel]
+    return per * n if source_hash(kernel) == h else None
+
 
 def fp32_peak_tflops(mhz: float) -> float:
     return N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -225,7 +251,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     achieved = flops / (tk / 1e3) / 1e12
     peak = fp32_peak_tflops(MAX_MHZ) if precision else fp64_peak_tflops(MAX_MHZ)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_per_launch(kname, w.n, precision), "traffic_unit": "bytes",
                 "peak_basis": ("%s lanes x 2 x %.0f MHz (unit counts)" %
                                ("148x128 FP32" if precision else "FP64 nominal 1.25 TFLOP/s",
                                 MAX_MHZ)),
