@@ -154,6 +154,26 @@ def contact_subvolume(w, n_sub: int) -> dict:
     return sub
 
 
+def sampled_error(sim, w, p, precision: int, nsample: int = 1000, seed: int = 7) -> dict:
+    """Oracle comparison on nsample particles of the current GPU state."""
+    import oracle
+    sim.forces_strength()
+    g = sim.to_numpy()
+    idx = np.sort(np.random.default_rng(seed).choice(w.n, nsample, replace=False))
+    rho, _, cnt = oracle.density_given_h(p, g, idx=idx)
+    st, S = oracle.eos_yield(p, w.materials, g)
+    out, _ = oracle.forces(p, w.materials, st, S=S, idx=idx)
+    derr = 0.0
+    for f in ("ax", "ay", "az", "dudt", "dsxx", "dsyy", "dsxy", "dsxz", "dsyz"):
+        scale = float(np.max(np.abs(g[f]))) or 1.0
+        derr = max(derr, float(np.max(np.abs(g[f][idx] - out[f][idx]))) / scale)
+    return {"sample": nsample, "rho_rel_max": float(np.max(np.abs(g["rho"][idx] / rho - 1))),
+            "counts_exact": bool(np.array_equal(cnt, g["nngb"][idx])),
+            "deriv_maxnorm_rel": derr,
+            "tolerance": {"rho_rel": 1e-5 if precision else 1e-6,
+                          "deriv_maxnorm_rel": 1e-4 if precision else 1e-9}}
+
+
 def cpu_baseline(w, n_sub: int = 100_000, budget_s: float = 12.0, max_steps: int = 20,
                  fixed_steps: int | None = None) -> dict:
     """The FP64 C oracle, as it stands, on a bounded sub-volume."""
@@ -276,6 +296,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         e2e = {"value": world * w.n * ne / te, "unit": "particle-steps/s",
                "h2d_bytes_per_step": r["bytes_in"], "d2h_bytes_per_step": r["bytes_out"],
                "steps": ne}
+    # error of this form against the FP64 oracle on a seeded sample, on the
+    # state the timed steps produced (derivatives recomputed as it stands)
+    err = None
+    if rank == 0 and not args.no_error:
+        err = sampled_error(sim, w, p, precision)
     sim.close()
 
     cb = None
@@ -294,7 +319,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                            "particles": w.n, "precision": args.precision,
                            "dt": w.dt, "l2": "state 450 MB > L2, no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "error": err,
                 "gpu_launches": launches_per_step * args.steps,
                 "clocks": clocks,
                 "phases_ms_per_step": {k: (v / nsteps if k != "steps" else v)
@@ -324,6 +349,7 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
