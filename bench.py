@@ -180,10 +180,11 @@ def cpu_baseline(w, n_sub: int = 100_000, budget_s: float = 12.0, max_steps: int
     import oracle
     sub = contact_subvolume(w, min(n_sub, w.n))
     p = dict(w.params, h_tol=1e-10)
-    st, _ = oracle.derivatives(p, w.materials, sub)
+    st, info = oracle.derivatives(p, w.materials, sub)
     steps, t0 = 0, time.perf_counter()
     while True:
-        st, _ = oracle.step(p, w.materials, st, w.dt)
+        st, infos = oracle.step(p, w.materials, st, info["dt_next"])
+        info = infos[-1]
         steps += 1
         el = time.perf_counter() - t0
         if fixed_steps is not None:
@@ -219,6 +220,29 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def time_plain(w, dev, steps: int = 3, warmup: int = 3) -> dict:
+    """The plain FP64 form on workload w: particle-steps/s over `steps`."""
+    import torch
+    from paper_2603_19764_b300 import sph
+    p = dict(w.params, precision=0, h_tol=1e-10)
+    sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
+    sim.prime()
+    for _ in range(warmup):
+        sim.step(0.0)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(0.0)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    sim.close()
+    return {"value": w.n * steps / (ms / 1e3), "unit": "particle-steps/s",
+            "ms_per_step": ms / steps, "steps": steps, "precision": "fp64"}
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
     import torch.distributed as dist
@@ -233,7 +257,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
     sim.prime()
     for _ in range(args.warmup):
-        sim.step(w.dt)
+        sim.step(0.0)
     sim.set_timing(True)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if world > 1:
@@ -244,7 +268,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    infos = [sim.step(w.dt) for _ in range(args.steps)]
+    infos = [sim.step(0.0) for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
@@ -282,12 +306,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     e2e = None
     if not args.no_e2e:
         host = sph.HostState(sim.to_numpy())
-        sim.step_host(host, w.dt)
+        sim.step_host(host, 0.0)
         torch.cuda.synchronize(dev)
         ne = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
         for _ in range(ne):
-            r = sim.step_host(host, w.dt)
+            r = sim.step_host(host, 0.0)
         te = time.perf_counter() - t0
         if world > 1:
             tt = torch.tensor([te], dtype=torch.float64, device=dev)
@@ -308,8 +332,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         cb = cpu_baseline(w)
         cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
+    # the plain FP64 form on the same impact, a few steps, for the chosen-vs-plain ratio
+    plain = None
+    if rank == 0 and args.precision == "fp32k" and not args.no_plain:
+        plain = time_plain(w, dev, steps=args.plain_steps)
+
     if rank == 0:
-        launches_per_step = 27
         line = {"metric": "SPH+strength particle-steps/s (2M part.), chosen vs plain form at stated error",
                 "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -317,10 +345,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "dtype": "f32+f64" if precision else "f64", "data": "synthetic",
                 "config": {"workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg",
                            "particles": w.n, "precision": args.precision,
-                           "dt": w.dt, "l2": "state 450 MB > L2, no flush",
+                           "dt": "adaptive, Eq. 38-39 (dt_next of the previous step)",
+                           "dt_mean": statistics.mean(i["dt"] for i in infos),
+                           "l2": "state 450 MB > L2, no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "error": err,
-                "gpu_launches": launches_per_step * args.steps,
+                "gpu_launches": sum(i["kernel_launches"] for i in infos),
+                "plain_fp64": plain,
                 "clocks": clocks,
                 "phases_ms_per_step": {k: (v / nsteps if k != "steps" else v)
                                        for k, v in phases.items()},
@@ -337,6 +368,113 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank: int, world: int, local_rank: int):
+    """The batched form on the 64-impact sweep, against the same 64 impacts
+    stepped one after another by their own contexts (sequential launches).
+
+    Every system steps with its own adaptive dt (its dt_next). Arms: batched FP32 form under
+    a CUDA graph with tuned group spans (the chosen form), batched FP64,
+    sequential FP32 form, sequential plain FP64. Each arm's value is
+    particles x steps / device time of its timed steps.
+    """
+    import torch
+    import torch.distributed as dist
+    from paper_2603_19764_b300 import build, sph
+    from paper_2603_19764_b300 import workloads as wl
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = wl.impact_batch(64, precision=1, scale=args.batch_scale)
+    zeros = np.zeros(len(w.systems))   # every system at its own dt_next
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        out = [fn() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), out
+
+    def batched(precision, steps, tune, graph, sampler=None):
+        p = dict(w.params, precision=precision, h_tol=1e-6 if precision else 1e-10)
+        sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev), systems=w.systems)
+        sim.prime()
+        sim.set_graph(graph)
+        if tune:
+            sim.autotune(tune)
+            for _ in range(3 * tune):
+                sim.step_batch(zeros)
+        for _ in range(args.warmup):
+            sim.step_batch(zeros)
+        if world > 1:
+            dist.barrier()
+        if sampler:
+            sampler.start()
+        ms, infos = timed(lambda: sim.step_batch(zeros), steps)
+        clocks = sampler.stop() if sampler else None
+        rep = sim.tune_info()
+        err = sampled_error(sim, w, p, precision) if (rank == 0 and not args.no_error) else None
+        sim.close()
+        return ms, infos, rep, err, clocks
+
+    def sequential(precision, steps):
+        p = dict(w.params, precision=precision, h_tol=1e-6 if precision else 1e-10)
+        sims = []
+        for k in range(len(w.systems)):
+            ws = w.system(k)
+            sims.append(sph.Simulation(ws.arrays, ws.materials, p, device=str(dev)))
+        for sim in sims:
+            sim.prime()
+            sim.step(0.0)
+
+        def one():
+            return [sim.step(0.0) for sim in sims]
+        ms, infos = timed(one, steps)
+        for sim in sims:
+            sim.close()
+        return ms, sum(i["kernel_launches"] for step in infos for i in step)
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    ms_c, infos, rep, err, clocks = batched(1, args.steps, 2, True, sampler)
+    if world > 1:
+        t = torch.tensor([ms_c], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_c = float(t.item())
+    value = world * w.n * args.steps / (ms_c / 1e3)
+    ks = max(1, min(args.steps, args.plain_steps))
+    arms = {}
+    if rank == 0:
+        ms_b64, _, rep64, err64, _ = batched(0, ks, 2, True)
+        arms["batched_fp64"] = {"value": w.n * ks / (ms_b64 / 1e3), "ms_per_step": ms_b64 / ks,
+                                "steps": ks, "spans": [rep64["span_density"], rep64["span_forces"]],
+                                "error": err64}
+        for name, prec in (("sequential_fp32k", 1), ("sequential_fp64_plain", 0)):
+            ms_s, nl = sequential(prec, ks)
+            arms[name] = {"value": w.n * ks / (ms_s / 1e3), "ms_per_step": ms_s / ks,
+                          "steps": ks, "gpu_launches": nl}
+        sizes = [c for _, c in w.systems]
+        line = {"metric": "SPH+strength particle-steps/s, 64-impact batch, batched vs sequential",
+                "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_c / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "64 basalt impacts, targets log-uniform 2k-200k, "
+                                       "gamma 0.01-0.5, 1-20 km/s, 0-60 deg, one seed",
+                           "particles": w.n, "systems": len(sizes), "smallest": min(sizes),
+                           "largest": max(sizes), "precision": "fp32k", "graph": True,
+                           "dt": "adaptive per system, Eq. 38-39",
+                           "l2": "state > L2, no flush"},
+                "tuner": rep, "error": err, "clocks": clocks,
+                "gpu_launches": sum(i["kernel_launches"] for i in infos),
+                "arms": arms,
+                "speedup_vs_sequential_plain": value / arms["sequential_fp64_plain"]["value"],
+                "speedup_vs_sequential_same_form": value / arms["sequential_fp32k"]["value"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,6 +488,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--workload", default="impact", choices=["impact", "batch64"])
+    ap.add_argument("--batch-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -365,7 +507,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "batch64":
+            run_batch(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -52,6 +52,7 @@ enum { SPH_JAUMANN_OBJECTIVE = 0, SPH_JAUMANN_PRINTED = 1 };
 enum { SPH_YIELD_SQRT_J2 = 0, SPH_YIELD_SQRT_3J2 = 1 };
 enum { SPH_GRAVITY_NONE = 0, SPH_GRAVITY_UNIFORM = 1, SPH_GRAVITY_RADIAL = 2 };
 #define SPH_MAX_MATERIALS 8
+#define SPH_MAX_SYSTEMS 1024
 #define SPH_FLAG_FIXED 1
 
 typedef struct sph_ctx sph_ctx;
@@ -158,7 +159,20 @@ typedef struct {
   uint32_t device_flags;
   int64_t cand_density, cand_force;
   int64_t groups_density, groups_force;  /* lane groups the pair kernels formed */
+  int32_t kernel_launches;               /* kernels the call launched */
 } sph_step_info;
+
+/* Report of the group-span tuner (sph_autotune). The pair kernels give
+ * each warp a bucket of 32 sorted particles; lanes whose cells lie within
+ * `span` cells of one another share one staged candidate list. */
+typedef struct {
+  int32_t span_density, span_forces;   /* spans in use */
+  int32_t steps_left;                  /* tuning steps still to run */
+  int32_t n_cand;                      /* candidates (SPH_TUNE_MAX at most) */
+  int32_t cand[4];                     /* candidate spans */
+  int32_t timed[4];                    /* steps timed per candidate */
+  double ms_density[4], ms_forces[4];  /* summed kernel milliseconds */
+} sph_tune_report;
 
 /* Create a context for n particles in `st` on `cuda_stream` (a cudaStream_t,
  * NULL for the legacy default stream). Validates the parameters, copies
@@ -168,6 +182,20 @@ typedef struct {
  * failure. */
 sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats,
                     int32_t n_mat, const sph_state *st, int64_t n, void *cuda_stream);
+
+/* A batch of n_sys independent systems in one context (the many uneven
+ * impacts of a Q_RD* series, §3.2): system k is the particles with ids in
+ * [sys_first[k], sys_first[k+1]) (HOST array of n_sys + 1 values, first 0,
+ * last n, increasing; ids must be 0..n-1). Systems never interact: each has
+ * its own bounding box, cell grid, time step and sums, and work is split
+ * into 32-particle buckets that never straddle two systems, so a system's
+ * arithmetic does not depend on the batch around it. One launch of each
+ * kernel covers all systems. Radial-table gravity needs n_sys = 1. Errors
+ * as sph_init, plus SPH_E_ARG for bad system bounds or n_sys out of
+ * 1..SPH_MAX_SYSTEMS. sph_init is this call with one system. */
+sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material *mats,
+                          int32_t n_mat, const sph_state *st, int64_t n, int32_t n_sys,
+                          const int64_t *sys_first, void *cuda_stream);
 
 /* Cell-list build (replaces the paper's tree walk, §2.1): bounding box, cell
  * size L_c = max H, 30-bit Morton keys of cell coordinates, stable radix sort,
@@ -199,6 +227,41 @@ sph_status sph_stress_update(sph_ctx *c, double dt);
  * i+1/2 and derivatives at i on return. Synchronises and fills *info (may
  * be NULL). */
 sph_status sph_step(sph_ctx *c, double dt, sph_step_info *info);
+
+/* One step of every system of a batch, system k with step dt[k] (HOST
+ * array of n_sys; dt[k] <= 0: that system's dt_next). *info (may be NULL)
+ * receives batch totals: sums over systems, the smallest dt_next, dt of
+ * system 0. Synchronises. */
+sph_status sph_step_batch(sph_ctx *c, const double *dt, sph_step_info *info);
+
+/* Per-system reports of the last synchronising call, systems 0..n-1. */
+sph_status sph_batch_info(const sph_ctx *c, sph_step_info *info, int32_t n);
+
+/* Replay every following sph_step / sph_step_batch from one CUDA graph
+ * (on = 1) captured at the first such step on a stream the library owns and
+ * ordered after the caller's stream. The graph records the pointers and
+ * parameters of sph_init; it is dropped by sph_set_graph and
+ * sph_set_timing. on = 0 returns to direct launches. */
+sph_status sph_set_graph(sph_ctx *c, int32_t on);
+
+/* Tune the group span of the two pair kernels (the cell extent that shares
+ * one staged candidate list; candidates 1, 2 and 3 cells) over the next
+ * `rounds` x 3 calls of sph_step / sph_step_batch: each such step runs with
+ * one candidate and times both kernels with CUDA events; after the last,
+ * each kernel keeps its fastest span and any captured graph is dropped so
+ * that the next step captures the tuned launch. Tuning steps are ordinary
+ * steps: in the FP64 form their results are bit-identical whatever the
+ * span; in the FP32 form the span moves the cell-relative frame, within the
+ * form's tolerances. rounds = 0 stops tuning and keeps the current spans.
+ * Returns SPH_E_ARG for rounds outside 0..64. */
+sph_status sph_autotune(sph_ctx *c, int32_t rounds);
+
+/* Set the group spans by hand (1..3 cells each; SPH_E_ARG otherwise) and
+ * stop any tuning in progress. Drops a captured graph. */
+sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces);
+
+/* The tuner's state and timings. */
+sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out);
 
 /* sph_step with HOST state: the caller passes pinned or pageable host
  * arrays in `host`; the library copies them to the context's device state,

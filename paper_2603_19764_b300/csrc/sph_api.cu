@@ -1,6 +1,8 @@
 // sph_api.cu -- the extern "C" entry points of include/sph.h: context
 // set-up, validation, scratch ownership, the call sequences of one step
-// (§2.4) and status reporting.
+// (§2.4), batches of independent systems, CUDA-graph replay of the step and
+// status reporting.
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -34,6 +36,7 @@ sph_status fail_cuda(sph_ctx *c, cudaError_t e, const char *what) {
   do {                                                                           \
     if (!(c)) return SPH_E_ARG;                                                  \
     if ((c)->broken) return fail(c, SPH_E_STATE, "context unusable after a CUDA error"); \
+    (c)->nlaunch = 0;                                                            \
   } while (0)
 
 template <typename T> cudaError_t dalloc(T **p, size_t count) {
@@ -51,12 +54,13 @@ bool state_complete(const sph_state *s) {
 }
 
 // Validation of the device state at set-up: material index in range,
-// positive mass and H, finite positions.
-__global__ void k_validate(sph_state s, int64_t n, int nmat, unsigned *bad) {
+// positive mass and H, finite positions; in a batch, ids in 0..n-1.
+__global__ void k_validate(sph_state s, int64_t n, int nmat, int check_id, unsigned *bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool ok = s.mat[i] >= 0 && s.mat[i] < nmat && s.m[i] > 0.0 && s.h[i] > 0.0 &&
-                    isfinite(s.x[i]) && isfinite(s.y[i]) && isfinite(s.z[i]) && isfinite(s.h[i]);
+    bool ok = s.mat[i] >= 0 && s.mat[i] < nmat && s.m[i] > 0.0 && s.h[i] > 0.0 &&
+              isfinite(s.x[i]) && isfinite(s.y[i]) && isfinite(s.z[i]) && isfinite(s.h[i]);
+    if (check_id) ok = ok && s.id[i] >= 0 && s.id[i] < n;
     if (!ok) atomicOr(bad, 1u);
   }
 }
@@ -69,11 +73,15 @@ void free_all(sph_ctx *c) {
                  c->w.fj64[1], c->w.fj64[2], c->w.fj64[3], c->w.posh32, c->w.posh64,
                  c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
-                 c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status};
+                 c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
+                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_sys) cudaFreeHost(c->h_sys);
   if (c->h_dt) cudaFreeHost(c->h_dt);
+  free(c->sys_first);
+  free(c->dt_next);
 }
 
 sph_status status_from_flags(sph_ctx *c, unsigned flags) {
@@ -84,42 +92,71 @@ sph_status status_from_flags(sph_ctx *c, unsigned flags) {
   return SPH_OK;
 }
 
-// Copy the device record to the host, wait, clear the latched error word.
-sph_status sync_status(sph_ctx *c, sph_step_info *info, double dt) {
+// Enqueue the copies of the device records to their pinned mirrors and the
+// clearing of the latched error word.
+sph_status enqueue_status_readback(sph_ctx *c) {
   CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_sys, c->d_sys, sizeof(SysRec) * c->nsys, cudaMemcpyDeviceToHost,
+                     c->stream));
   CK(cudaMemsetAsync(&c->d_status->err, 0, sizeof(unsigned), c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  const Status &h = *c->h_status;
-  const double dtn = dec_d(h.dtmin_enc);
-  if (h.dtmin_enc != ~0ull && dtn > 0.0) c->dt_next = dtn;
-  if (info) {
-    info->dt = dt;
-    info->dt_next = c->dt_next;
-    info->e_kin = h.sums[0];
-    info->e_int = h.sums[1];
-    info->e_pot = h.sums[2];
-    for (int k = 0; k < 3; ++k) {
-      info->p[k] = h.sums[3 + k];
-      info->L[k] = h.sums[6 + k];
-    }
-    info->sweeps = h.max_sweeps;
-    info->n_unconverged = h.n_unconv;
-    info->n_capped = h.n_capped;
-    info->n_cfallback = h.n_cfallback;
-    info->pairs_density = (int64_t)h.pairs_density;
-    info->pairs_force = (int64_t)h.pairs_force;
-    info->cand_density = (int64_t)h.cand_density;
-    info->cand_force = (int64_t)h.cand_force;
-    info->groups_density = (int64_t)h.groups_density;
-    info->groups_force = (int64_t)h.groups_force;
-    info->device_flags = h.err;
-  }
-  return status_from_flags(c, h.err);
+  return SPH_OK;
 }
 
-sph_status set_dt(sph_ctx *c, double dt) {
-  *c->h_dt = dt;
-  CK(cudaMemcpyAsync(c->d_dt, c->h_dt, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+// Report of system `sys` (sys < 0: totals over the batch).
+void fill_info(const sph_ctx *c, int sys, sph_step_info *info) {
+  const Status &h = *c->h_status;
+  memset(info, 0, sizeof(*info));
+  const int k0 = sys < 0 ? 0 : sys, k1 = sys < 0 ? c->nsys : sys + 1;
+  info->dt = c->h_dt[k0];
+  info->dt_next = INFINITY;
+  for (int k = k0; k < k1; ++k) {
+    const SysRec &r = c->h_sys[k];
+    info->e_kin += r.sums[0];
+    info->e_int += r.sums[1];
+    info->e_pot += r.sums[2];
+    for (int a = 0; a < 3; ++a) {
+      info->p[a] += r.sums[3 + a];
+      info->L[a] += r.sums[6 + a];
+    }
+    if (c->dt_next[k] < info->dt_next) info->dt_next = c->dt_next[k];
+  }
+  // counters are kept for the whole batch only
+  info->sweeps = h.max_sweeps;
+  info->n_unconverged = h.n_unconv;
+  info->n_capped = h.n_capped;
+  info->n_cfallback = h.n_cfallback;
+  info->pairs_density = (int64_t)h.pairs_density;
+  info->pairs_force = (int64_t)h.pairs_force;
+  info->device_flags = h.err;
+  info->cand_density = (int64_t)h.cand_density;
+  info->cand_force = (int64_t)h.cand_force;
+  info->groups_density = (int64_t)h.groups_density;
+  info->groups_force = (int64_t)h.groups_force;
+  info->kernel_launches = c->nlaunch;
+}
+
+// After a synchronisation: per-system dt_next from the mirrors, the report,
+// the status.
+sph_status finish_sync(sph_ctx *c, sph_step_info *info) {
+  for (int k = 0; k < c->nsys; ++k) {
+    const unsigned long long e = c->h_sys[k].dtmin_enc;
+    const double dtn = dec_d(e);
+    if (e != ~0ull && dtn > 0.0) c->dt_next[k] = dtn;
+  }
+  if (info) fill_info(c, -1, info);
+  return status_from_flags(c, c->h_status->err);
+}
+
+sph_status sync_status(sph_ctx *c, sph_step_info *info) {
+  sph_status s = enqueue_status_readback(c);
+  if (s != SPH_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return finish_sync(c, info);
+}
+
+sph_status upload_dt(sph_ctx *c) {
+  CK(cudaMemcpyAsync(c->d_dt, c->h_dt, sizeof(double) * c->nsys, cudaMemcpyHostToDevice,
+                     c->stream));
   return SPH_OK;
 }
 
@@ -138,16 +175,36 @@ sph_status run_neighbours(sph_ctx *c, int drift) {
   return SPH_OK;
 }
 
+// Tuner marker k (density start / end, forces start / end) on tuning steps.
+cudaError_t tmark(sph_ctx *c, int k) {
+  return c->tune_now ? cudaEventRecord(c->tev[k], c->stream) : cudaSuccess;
+}
+
 sph_status run_derivatives(sph_ctx *c, int predict) {
   CK(launch_predict_pack(c, predict));
   CK(mark(c, 2));
+  CK(tmark(c, 0));
   CK(launch_density(c));
+  CK(tmark(c, 1));
   CK(mark(c, 3));
   CK(launch_eos_pack(c));
   CK(mark(c, 4));
+  CK(tmark(c, 2));
   CK(launch_forces(c));
+  CK(tmark(c, 3));
   CK(mark(c, 5));
   return SPH_OK;
+}
+
+// Everything one step enqueues, from the dt upload to the status readback.
+sph_status enqueue_step(sph_ctx *c) {
+  sph_status s = upload_dt(c);
+  if (s == SPH_OK) s = run_neighbours(c, 1);
+  if (s == SPH_OK) s = run_derivatives(c, 1);
+  if (s != SPH_OK) return s;
+  CK(launch_kick(c, 1));
+  CK(mark(c, 6));
+  return enqueue_status_readback(c);
 }
 
 // Accumulate the phase times of the step just synchronised.
@@ -159,6 +216,104 @@ sph_status collect_times(sph_ctx *c) {
     c->phase_ms[k] += ms;
   }
   c->timed_steps += 1;
+  return SPH_OK;
+}
+
+void drop_graph(sph_ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+}
+
+// Start of a step: while tuning, the candidate span this step runs with.
+void tune_begin(sph_ctx *c) {
+  c->tune_now = c->tune_left > 0;
+  if (c->tune_now) {
+    const int span = kSpans[c->tune_idx % kNumSpans];
+    c->kp.span_d = span;
+    c->kp.span_f = span;
+  }
+}
+
+// End of a synchronised tuning step: book its kernel times; after the last
+// one, keep each kernel's fastest span.
+sph_status tune_end(sph_ctx *c) {
+  if (!c->tune_now) return SPH_OK;
+  c->tune_now = 0;
+  float md = 0.f, mf = 0.f;
+  CK(cudaEventElapsedTime(&md, c->tev[0], c->tev[1]));
+  CK(cudaEventElapsedTime(&mf, c->tev[2], c->tev[3]));
+  const int k = c->tune_idx % kNumSpans;
+  c->tune_ms_d[k] += md;
+  c->tune_ms_f[k] += mf;
+  c->tune_n[k] += 1;
+  c->tune_idx += 1;
+  c->tune_left -= 1;
+  if (c->tune_left == 0) {
+    int bd = 0, bf = 0;
+    for (int q = 1; q < kNumSpans; ++q) {
+      if (c->tune_ms_d[q] / c->tune_n[q] < c->tune_ms_d[bd] / c->tune_n[bd]) bd = q;
+      if (c->tune_ms_f[q] / c->tune_n[q] < c->tune_ms_f[bf] / c->tune_n[bf]) bf = q;
+    }
+    c->kp.span_d = kSpans[bd];
+    c->kp.span_f = kSpans[bf];
+    drop_graph(c);
+  }
+  return SPH_OK;
+}
+
+// One step, enqueued directly or replayed from a CUDA graph captured on the
+// library's own stream (the caller's stream may be the legacy default
+// stream, which cannot be captured). Tuning steps are always direct.
+// Synchronises.
+sph_status run_step(sph_ctx *c, sph_step_info *info) {
+  tune_begin(c);
+  if (!c->use_graph || c->tune_now) {
+    sph_status s = enqueue_step(c);
+    if (s != SPH_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    cudaStream_t caller = c->stream;
+    CK(cudaEventRecord(c->fence, caller));
+    CK(cudaStreamWaitEvent(c->gstream, c->fence, 0));
+    if (!c->graph_exec) {
+      c->stream = c->gstream;
+      const cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+      sph_status s = e == cudaSuccess ? enqueue_step(c) : fail_cuda(c, e, "cudaStreamBeginCapture");
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+      c->stream = caller;
+      if (s != SPH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e2 != cudaSuccess) return fail_cuda(c, e2, "cudaStreamEndCapture");
+      const cudaError_t e3 = cudaGraphInstantiate(&c->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e3 != cudaSuccess) return fail_cuda(c, e3, "cudaGraphInstantiate");
+      c->graph_nlaunch = c->nlaunch;
+    }
+    c->nlaunch = c->graph_nlaunch;
+    CK(cudaGraphLaunch(c->graph_exec, c->gstream));
+    CK(cudaStreamSynchronize(c->gstream));
+  }
+  const sph_status s = finish_sync(c, info);
+  sph_status t = collect_times(c);
+  if (t == SPH_OK) t = tune_end(c);
+  return s != SPH_OK ? s : t;
+}
+
+// Stage the dt of every system: dt[k] > 0 as given, otherwise that
+// system's dt_next.
+sph_status stage_dt(sph_ctx *c, const double *dt, double all) {
+  for (int k = 0; k < c->nsys; ++k) {
+    double d = dt ? dt[k] : all;
+    if (!(d > 0.0)) {
+      if (!c->primed || !(c->dt_next[k] > 0.0))
+        return fail(c, SPH_E_STATE, "dt <= 0 needs a dt_next from sph_prime or an earlier step");
+      d = c->dt_next[k];
+    }
+    c->h_dt[k] = d;
+  }
   return SPH_OK;
 }
 
@@ -182,16 +337,22 @@ const char *sph_status_string(sph_status s) {
 
 const char *sph_last_error(const sph_ctx *c) { return c ? c->err : "no context"; }
 
-sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats, int32_t n_mat,
-                    const sph_state *st, int64_t n, void *cuda_stream) {
+sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material *mats,
+                          int32_t n_mat, const sph_state *st, int64_t n, int32_t n_sys,
+                          const int64_t *sys_first, void *cuda_stream) {
   if (!out) return SPH_E_ARG;
   *out = nullptr;
   if (!p || !mats || !st || n < 1 || n > (int64_t)1 << 30) return SPH_E_ARG;
   if (n_mat < 1 || n_mat > SPH_MAX_MATERIALS || !state_complete(st)) return SPH_E_ARG;
+  if (n_sys < 1 || n_sys > SPH_MAX_SYSTEMS || !sys_first) return SPH_E_ARG;
+  if (sys_first[0] != 0 || sys_first[n_sys] != n) return SPH_E_ARG;
+  for (int k = 0; k < n_sys; ++k)
+    if (sys_first[k + 1] <= sys_first[k]) return SPH_E_ARG;
   if (p->precision != SPH_FP64 && p->precision != SPH_FP32K) return SPH_E_ARG;
   if (p->jaumann != SPH_JAUMANN_OBJECTIVE && p->jaumann != SPH_JAUMANN_PRINTED) return SPH_E_ARG;
   if (p->yield_norm != SPH_YIELD_SQRT_J2 && p->yield_norm != SPH_YIELD_SQRT_3J2) return SPH_E_ARG;
   if (p->gravity < SPH_GRAVITY_NONE || p->gravity > SPH_GRAVITY_RADIAL) return SPH_E_ARG;
+  if (p->gravity == SPH_GRAVITY_RADIAL && n_sys > 1) return SPH_E_ARG;
   if (p->periodic != 0) return SPH_E_ARG;
   if (!(p->n_ngb >= 1) || !(p->h_tol > 0.0) || p->max_sweeps < 1 || !(p->h_cap_factor > 0.0))
     return SPH_E_ARG;
@@ -210,6 +371,7 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
   c->st = *st;
   c->n = n;
   c->stream = (cudaStream_t)cuda_stream;
+  c->nsys = n_sys;
   const bool fp32 = p->precision == SPH_FP32K;
   {
     int dev = 0;
@@ -231,9 +393,76 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
     }                                      \
   } while (0)
 
+  // Systems: particle ranges, 32-particle buckets and reduction chunks that
+  // never straddle two systems, a cell budget of twice the particle count
+  // (at least 4096, at most 2^24) each.
+  c->sys_first = (int64_t *)malloc(sizeof(int64_t) * (n_sys + 1));
+  c->dt_next = (double *)calloc(n_sys, sizeof(double));
+  SysRec *rec = (SysRec *)calloc(n_sys, sizeof(SysRec));
+  int *bnd = (int *)malloc(sizeof(int) * 3 * (n_sys + 1));
+  if (!c->sys_first || !c->dt_next || !rec || !bnd) {
+    free(rec);
+    free(bnd);
+    free_all(c);
+    free(c);
+    return SPH_E_ARG;
+  }
+  int *bb = bnd, *bk = bnd + (n_sys + 1), *bc = bnd + 2 * (n_sys + 1);
+  int64_t buckets = 0, chunks = 0, cells = 0;
+  for (int k = 0; k <= n_sys; ++k) {
+    c->sys_first[k] = sys_first[k];
+    bb[k] = (int)sys_first[k];
+    bk[k] = (int)buckets;
+    bc[k] = (int)chunks;
+    if (k == n_sys) break;
+    const int64_t cnt = sys_first[k + 1] - sys_first[k];
+    rec[k].begin = (int)sys_first[k];
+    rec[k].end = (int)sys_first[k + 1];
+    rec[k].bucket_off = (int)buckets;
+    rec[k].chunk_off = (int)chunks;
+    int64_t cap = 2 * cnt;
+    if (cap < 4096) cap = 4096;
+    if (cap > (1 << 24)) cap = 1 << 24;
+    rec[k].cell_cap = (int)cap;
+    buckets += (cnt + 31) / 32;
+    chunks += (cnt + kChunk - 1) / kChunk;
+    cells += cap;
+  }
+  // 32-bit sort keys: the system index above a Morton code of 3 * axis_bits
+  int sys_bits = 0;
+  while ((1 << sys_bits) < n_sys) ++sys_bits;
+  int axis_bits = (32 - sys_bits) / 3;
+  if (axis_bits > 10) axis_bits = 10;
+  c->nchunks = (int)chunks;
+  c->max_cells = (int)cells;
+  KParams &kp = c->kp;
+  kp.nsys = n_sys;
+  kp.axis_bits = axis_bits;
+  kp.nbuckets = (int)buckets;
+  kp.nchunks = (int)chunks;
+  kp.span_d = 2;
+  kp.span_f = 2;
+  cudaError_t es = dalloc(&c->d_sys, n_sys);
+  if (es == cudaSuccess) es = cudaMemcpy(c->d_sys, rec, sizeof(SysRec) * n_sys, cudaMemcpyHostToDevice);
+  if (es == cudaSuccess) es = dalloc(&c->d_sys_begin, n_sys + 1);
+  if (es == cudaSuccess) es = dalloc(&c->d_sys_bucket, n_sys + 1);
+  if (es == cudaSuccess) es = dalloc(&c->d_sys_chunk, n_sys + 1);
+  if (es == cudaSuccess)
+    es = cudaMemcpy(c->d_sys_begin, bb, sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice);
+  if (es == cudaSuccess)
+    es = cudaMemcpy(c->d_sys_bucket, bk, sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice);
+  if (es == cudaSuccess)
+    es = cudaMemcpy(c->d_sys_chunk, bc, sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice);
+  free(rec);
+  free(bnd);
+  CKI(es);
+  kp.sys = c->d_sys;
+  kp.sys_begin = c->d_sys_begin;
+  kp.sys_bucket = c->d_sys_bucket;
+  kp.sys_chunk = c->d_sys_chunk;
+
   CKI(dalloc(&c->d_mats, SPH_MAX_MATERIALS));
   CKI(cudaMemcpy(c->d_mats, c->mats, sizeof(c->mats), cudaMemcpyHostToDevice));
-  KParams &kp = c->kp;
   kp.n_ngb = p->n_ngb;
   kp.av_alpha = p->av_alpha;
   kp.av_beta = p->av_beta;
@@ -303,27 +532,25 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
   c->ntiles = (int)((n + 2047) / 2048);
   CKI(dalloc(&c->hist, (size_t)256 * c->ntiles));
   CKI(dalloc(&c->scan_tot, (size_t)(256 * c->ntiles + 1023) / 1024 + 1));
-  int64_t mc = 2 * n;
-  if (mc < 4096) mc = 4096;
-  if (mc > (1 << 24)) mc = 1 << 24;
-  c->max_cells = (int)mc;
-  CKI(dalloc(&c->cell_start, mc));
-  CKI(dalloc(&c->cell_end, mc));
+  CKI(dalloc(&c->cell_start, c->max_cells));
+  CKI(dalloc(&c->cell_end, c->max_cells));
   CKI(cudaMalloc(&c->tmp, (size_t)n * 32 * 8));
-  int64_t rb = (n + kBlock - 1) / kBlock;
-  if (rb > 148 * 8) rb = 148 * 8;
-  c->nred_blocks = (int)rb;
-  CKI(dalloc(&c->partials, (size_t)rb * 9));
-  CKI(dalloc(&c->d_dt, 1));
+  CKI(dalloc(&c->partials, (size_t)c->nchunks * 9));
+  CKI(dalloc(&c->d_dt, n_sys));
+  kp.dt = c->d_dt;
   CKI(dalloc(&c->d_status, 1));
   CKI(cudaMemset(c->d_status, 0, sizeof(Status)));
   CKI(cudaMallocHost((void **)&c->h_status, sizeof(Status)));
-  CKI(cudaMallocHost((void **)&c->h_dt, sizeof(double)));
+  CKI(cudaMallocHost((void **)&c->h_sys, sizeof(SysRec) * n_sys));
+  CKI(cudaMallocHost((void **)&c->h_dt, sizeof(double) * n_sys));
+  memset(c->h_status, 0, sizeof(Status));
+  memset(c->h_sys, 0, sizeof(SysRec) * n_sys);
+  memset(c->h_dt, 0, sizeof(double) * n_sys);
   // validate the caller's state once
   unsigned *bad = nullptr;
   CKI(dalloc(&bad, 1));
   CKI(cudaMemset(bad, 0, sizeof(unsigned)));
-  k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, n_mat, bad);
+  k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, n_mat, n_sys > 1, bad);
   unsigned hbad = 0;
   CKI(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   CKI(cudaStreamSynchronize(c->stream));
@@ -338,13 +565,20 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
 #undef CKI
 }
 
+sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats, int32_t n_mat,
+                    const sph_state *st, int64_t n, void *cuda_stream) {
+  const int64_t first[2] = {0, n};
+  return sph_init_batch(out, p, mats, n_mat, st, n, 1, first, cuda_stream);
+}
+
 sph_status sph_set_timing(sph_ctx *c, int32_t on) {
   ENTER(c);
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);  // a captured graph holds the phase events of its capture
   if (on && !c->timing) {
     for (int k = 0; k <= SPH_NUM_PHASES; ++k) CK(cudaEventCreate(&c->ev[k]));
   }
   if (!on && c->timing) {
-    CK(cudaStreamSynchronize(c->stream));
     for (int k = 0; k <= SPH_NUM_PHASES; ++k) cudaEventDestroy(c->ev[k]);
   }
   c->timing = on ? 1 : 0;
@@ -360,14 +594,74 @@ sph_status sph_phase_times(const sph_ctx *c, double *ms, int32_t n, int32_t *ste
   return SPH_OK;
 }
 
+sph_status sph_set_graph(sph_ctx *c, int32_t on) {
+  ENTER(c);
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  if (on && !c->gstream) {
+    CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->fence, cudaEventDisableTiming));
+  }
+  c->use_graph = on ? 1 : 0;
+  return SPH_OK;
+}
+
 sph_status sph_destroy(sph_ctx *c) {
   if (!c) return SPH_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  if (c->gstream) cudaStreamSynchronize(c->gstream);
+  drop_graph(c);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->fence) cudaEventDestroy(c->fence);
   if (c->timing)
     for (int k = 0; k <= SPH_NUM_PHASES; ++k) cudaEventDestroy(c->ev[k]);
+  if (c->tev[0])
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(c->tev[k]);
   free_all(c);
   free(c);
+  return SPH_OK;
+}
+
+sph_status sph_autotune(sph_ctx *c, int32_t rounds) {
+  ENTER(c);
+  if (rounds < 0 || rounds > 64) return fail(c, SPH_E_ARG, "rounds must be in 0..64");
+  if (rounds > 0 && !c->tev[0])
+    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&c->tev[k]));
+  c->tune_left = rounds * kNumSpans;
+  c->tune_idx = 0;
+  for (int k = 0; k < kNumSpans; ++k) {
+    c->tune_ms_d[k] = c->tune_ms_f[k] = 0.0;
+    c->tune_n[k] = 0;
+  }
+  return SPH_OK;
+}
+
+sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces) {
+  ENTER(c);
+  if (span_density < kSpans[0] || span_density > kSpans[kNumSpans - 1] ||
+      span_forces < kSpans[0] || span_forces > kSpans[kNumSpans - 1])
+    return fail(c, SPH_E_ARG, "span out of range");
+  c->tune_left = 0;
+  c->kp.span_d = span_density;
+  c->kp.span_f = span_forces;
+  drop_graph(c);
+  return SPH_OK;
+}
+
+sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out) {
+  if (!c || !out) return SPH_E_ARG;
+  memset(out, 0, sizeof(*out));
+  out->span_density = c->kp.span_d;
+  out->span_forces = c->kp.span_f;
+  out->steps_left = c->tune_left;
+  out->n_cand = kNumSpans;
+  for (int k = 0; k < kNumSpans; ++k) {
+    out->cand[k] = kSpans[k];
+    out->timed[k] = c->tune_n[k];
+    out->ms_density[k] = c->tune_ms_d[k];
+    out->ms_forces[k] = c->tune_ms_f[k];
+  }
   return SPH_OK;
 }
 
@@ -381,7 +675,7 @@ sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
   CK(launch_predict_pack(c, 0));
   CK(launch_density(c));
   sph_step_info info;
-  const sph_status s = sync_status(c, &info, 0.0);
+  const sph_status s = sync_status(c, &info);
   if (sweeps) *sweeps = info.sweeps;
   return s;
 }
@@ -397,42 +691,44 @@ sph_status sph_forces_strength(sph_ctx *c) {
 sph_status sph_stress_update(sph_ctx *c, double dt) {
   ENTER(c);
   if (!(dt > 0.0)) return fail(c, SPH_E_ARG, "dt must be positive");
-  sph_status s = set_dt(c, dt);
+  for (int k = 0; k < c->nsys; ++k) c->h_dt[k] = dt;
+  sph_status s = upload_dt(c);
   if (s != SPH_OK) return s;
   CK(launch_kick(c, 1));
+  CK(cudaStreamSynchronize(c->stream));  // the staging buffer is reused by the next call
   return SPH_OK;
 }
 
 sph_status sph_prime(sph_ctx *c, sph_step_info *info) {
   ENTER(c);
+  for (int k = 0; k < c->nsys; ++k) c->h_dt[k] = 0.0;
   sph_status s = run_neighbours(c, 0);
   if (s != SPH_OK) return s;
   s = run_derivatives(c, 0);
   if (s != SPH_OK) return s;
   CK(launch_kick(c, 0));
-  s = sync_status(c, info, 0.0);
+  s = sync_status(c, info);
   if (s == SPH_OK || s == SPH_E_NOCONV) c->primed = 1;
   return s;
 }
 
 sph_status sph_step(sph_ctx *c, double dt, sph_step_info *info) {
   ENTER(c);
-  if (!(dt > 0.0)) {
-    if (!c->primed || !(c->dt_next > 0.0))
-      return fail(c, SPH_E_STATE, "dt <= 0 needs a dt_next from sph_prime or an earlier step");
-    dt = c->dt_next;
-  }
-  sph_status s = set_dt(c, dt);
-  if (s != SPH_OK) return s;
-  s = run_neighbours(c, 1);
-  if (s != SPH_OK) return s;
-  s = run_derivatives(c, 1);
-  if (s != SPH_OK) return s;
-  CK(launch_kick(c, 1));
-  CK(mark(c, 6));
-  s = sync_status(c, info, dt);
-  const sph_status t = collect_times(c);
-  return s != SPH_OK ? s : t;
+  const sph_status s = stage_dt(c, nullptr, dt);
+  return s != SPH_OK ? s : run_step(c, info);
+}
+
+sph_status sph_step_batch(sph_ctx *c, const double *dt, sph_step_info *info) {
+  ENTER(c);
+  if (!dt) return fail(c, SPH_E_ARG, "dt array is NULL");
+  const sph_status s = stage_dt(c, dt, 0.0);
+  return s != SPH_OK ? s : run_step(c, info);
+}
+
+sph_status sph_batch_info(const sph_ctx *c, sph_step_info *info, int32_t n) {
+  if (!c || !info || n < 1 || n > c->nsys) return SPH_E_ARG;
+  for (int k = 0; k < n; ++k) fill_info(c, k, &info[k]);
+  return SPH_OK;
 }
 
 sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_info *info,

@@ -23,15 +23,14 @@ namespace sphk {
 // Evaluation state and position packing. predict = 1: v, u, S at i from
 // the half-step values and the derivatives at i-1 (Eq. 40); predict = 0:
 // the state as it stands.
-__global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, int64_t n,
-                                                        const double *dtp, int predict,
-                                                        const Status *st, int fp32) {
-  const Grid g = st->grid;
-  const double hdt = predict ? 0.5 * (*dtp) : 0.0;
+__global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, int64_t n, KParams P,
+                                                        int predict, int fp32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
+    const Grid &g = P.sys[sy].grid;
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
-    const double k = fixed ? 0.0 : hdt;
+    const double k = (fixed || !predict) ? 0.0 : 0.5 * P.dt[sy];
     w.vp[0][i] = s.vx[i] + k * s.ax[i];
     w.vp[1][i] = s.vy[i] + k * s.ay[i];
     w.vp[2][i] = s.vz[i] + k * s.az[i];
@@ -57,8 +56,9 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
 cudaError_t launch_predict_pack(sph_ctx *c, int predict) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
-  k_predict_pack<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, predict,
-                                                  c->d_status, c->kp.precision == SPH_FP32K);
+  k_predict_pack<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp, predict,
+                                                  c->kp.precision == SPH_FP32K);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -165,23 +165,25 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
   // persistent warps: each takes the next bucket of 32 particles
-  const int64_t nbuckets = (A.n + 31) / 32;
+  const int nbuckets = A.p.nbuckets;
   long long w_pairs = 0, w_cand = 0;
   int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0;
   unsigned w_bad = 0;
-  double w_hm = 0.0;
   for (;;) {
   unsigned bk = 0;
   if (lane == 0) bk = atomicAdd(&A.st->next_bucket[0], 1u);
   bk = __shfl_sync(kFull, bk, 0);
-  if ((int64_t)bk >= nbuckets) break;
-  const int64_t base = (int64_t)bk * 32;
+  if ((int)bk >= nbuckets) break;
+  // the bucket's system and its sorted range
+  const int sy = A.p.nsys > 1 ? sys_lookup(A.p.sys_bucket, A.p.nsys, bk) : 0;
+  const SysRec &R = A.p.sys[sy];
+  const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
   const int64_t i = base + lane;
-  const bool valid = i < A.n;
+  const bool valid = i < R.end;
   const int64_t ic = valid ? i : base;
   const V4 *pos = PosPtr<T>::get(A.w);
 
-  const Grid g = A.st->grid;
+  const Grid g = R.grid;
   const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
 
   unsigned todo = __ballot_sync(kFull, valid);
   while (todo) {
-    const Group G = next_group(todo, cx, cy, cz);
+    const Group G = next_group(todo, cx, cy, cz, A.p.span_d);
     ++w_groups;
     const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
     const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
@@ -327,7 +329,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   w_ncap += state == 2;
   w_bad |= (valid && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0))) ? 1u
                                                                                            : 0u;
-  w_hm = fmax(w_hm, valid ? H_o : 0.0);
+  {
+    const double hb = wmax(valid ? H_o : 0.0);
+    if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, enc_d(hb));
+  }
   w_pairs += pairs;
   w_cand += cand;
   }  // bucket loop
@@ -335,7 +340,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const int nu = wsum(w_nu);
   const int ncap = wsum(w_ncap);
   const unsigned nbad = __ballot_sync(kFull, w_bad != 0u);
-  const double hm = wmax(w_hm);
   const long long pw = wsum(w_pairs);
   if (lane == 0) {
     atomicMax(&A.st->max_sweeps, sw);
@@ -345,7 +349,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
     }
     if (ncap) atomicAdd(&A.st->n_capped, ncap);
     if (nbad) atomicOr(&A.st->err, ERR_NONFINITE);
-    atomicMax(&A.st->hmax2_enc, enc_d(hm));
     atomicAdd(&A.st->pairs_density, (unsigned long long)pw);
     atomicAdd(&A.st->cand_density, (unsigned long long)w_cand);
     atomicAdd(&A.st->groups_density, (unsigned long long)w_groups);
@@ -369,6 +372,7 @@ cudaError_t launch_density(sph_ctx *c) {
   else
     k_density<double, 256><<<resident_grid(c, k_density<double, 256>), 32 * kWarpsPerBlock, 0,
                              c->stream>>>(a);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -98,6 +98,7 @@ cudaError_t launch_eos_pack(sph_ctx *c) {
     k_eos_pack<float><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
   else
     k_eos_pack<double><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -142,27 +143,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
   // persistent warps: each takes the next bucket of 32 particles
-  const int64_t nbuckets = (A.n + 31) / 32;
+  const int nbuckets = A.p.nbuckets;
   long long w_pairs = 0, w_cand = 0;
   int w_fb = 0, w_groups = 0;
   for (;;) {
   unsigned bk = 0;
   if (lane == 0) bk = atomicAdd(&A.st->next_bucket[1], 1u);
   bk = __shfl_sync(kFull, bk, 0);
-  if ((int64_t)bk >= nbuckets) break;
-  const int64_t base = (int64_t)bk * 32;
+  if ((int)bk >= nbuckets) break;
+  // the bucket's system and its sorted range
+  const int sy = A.p.nsys > 1 ? sys_lookup(A.p.sys_bucket, A.p.nsys, bk) : 0;
+  const SysRec &R = A.p.sys[sy];
+  const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
   const int64_t i = base + lane;
-  const bool valid = i < A.n;
+  const bool valid = i < R.end;
   const int64_t ic = valid ? i : base;
   const V4 *posh = PK::posh(A.w);
   const V4 *fj0 = PK::fj(A.w, 0), *fj1 = PK::fj(A.w, 1), *fj2 = PK::fj(A.w, 2),
            *fj3 = PK::fj(A.w, 3);
 
-  const Grid g = A.st->grid;
+  const Grid g = R.grid;
   const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
-  const T hmax_all = (T)dec_d(A.st->hmax2_enc);
+  const T hmax_all = (T)dec_d(R.hmax2_enc);
 
   // particle i (evaluation state, packed)
   const V4 p = V::ld(posh, ic);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
 
   unsigned todo = __ballot_sync(kFull, valid);
   while (todo) {
-    const Group G = next_group(todo, cx, cy, cz);
+    const Group G = next_group(todo, cx, cy, cz, A.p.span_f);
     ++w_groups;
     const bool act = G.member;
     const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
@@ -402,6 +406,7 @@ cudaError_t launch_forces(sph_ctx *c) {
   else
     k_forces<double, 256><<<resident_grid(c, k_forces<double, 256>), 32 * kWarpsPerBlock, 0,
                             c->stream>>>(a);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -10,79 +10,93 @@
 namespace sphk {
 
 // ---------------------------------------------------------------- status
-__global__ void k_reset_status(Status *st, int full) {
-  if (threadIdx.x != 0) return;
-  for (int a = 0; a < 3; ++a) {
-    st->lo_enc[a] = ~0ull;
-    st->hi_enc[a] = 0ull;
+__global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full) {
+  if (threadIdx.x == 0) {
+    st->max_sweeps = 0;
+    st->n_unconv = 0;
+    st->n_capped = 0;
+    st->n_cfallback = 0;
+    st->pairs_density = 0;
+    st->pairs_force = 0;
+    st->cand_density = 0;
+    st->cand_force = 0;
+    st->groups_density = 0;
+    st->groups_force = 0;
+    if (full) st->err = 0;
   }
-  st->hmax_enc = 0ull;
-  st->hmax2_enc = 0ull;
-  st->dtmin_enc = ~0ull;
-  st->max_sweeps = 0;
-  st->n_unconv = 0;
-  st->n_capped = 0;
-  st->n_cfallback = 0;
-  st->pairs_density = 0;
-  st->pairs_force = 0;
-  st->cand_density = 0;
-  st->cand_force = 0;
-  st->groups_density = 0;
-  st->groups_force = 0;
-  if (full) st->err = 0;
+  for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
+    SysRec &r = sys[k];
+    for (int a = 0; a < 3; ++a) {
+      r.lo_enc[a] = ~0ull;
+      r.hi_enc[a] = 0ull;
+    }
+    r.hmax_enc = 0ull;
+    r.hmax2_enc = 0ull;
+    r.dtmin_enc = ~0ull;
+  }
 }
 
 cudaError_t launch_reset_status(sph_ctx *c, int full) {
-  k_reset_status<<<1, 32, 0, c->stream>>>(c->d_status, full);
+  k_reset_status<<<1, 256, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, full);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------ drift + bounding box
-// x_i = x_{i-1} + dt v_{i-1/2} for moving particles (§2.4), then the box
-// of all positions and the largest H.
-__global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, const double *dtp,
-                                                      int do_drift, Status *st) {
-  __shared__ double red[7][kBlock / 32];
-  const double dt = do_drift ? *dtp : 0.0;
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  double hm = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double p[3] = {s.x[i], s.y[i], s.z[i]};
-    if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
-      p[0] += dt * s.vx[i];
-      p[1] += dt * s.vy[i];
-      p[2] += dt * s.vz[i];
-      s.x[i] = p[0];
-      s.y[i] = p[1];
-      s.z[i] = p[2];
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = fmin(lo[a], p[a]);
-      hi[a] = fmax(hi[a], p[a]);
-    }
-    hm = fmax(hm, s.h[i]);
-  }
-  double v[7] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm};
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) v[k] = wmin(v[k]);
-#pragma unroll
-  for (int k = 3; k < 7; ++k) v[k] = wmax(v[k]);
-  if (lane == 0)
-    for (int k = 0; k < 7; ++k) red[k][w] = v[k];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x / 32;
-    for (int k = 0; k < 7; ++k) {
-      double t = lane < nw ? red[k][lane] : (k < 3 ? INFINITY : -INFINITY);
-      t = k < 3 ? wmin(t) : wmax(t);
-      if (lane == 0) {
-        if (k < 3) atomicMin(&st->lo_enc[k], enc_d(t));
-        else if (k < 6) atomicMax(&st->hi_enc[k - 3], enc_d(t));
-        else atomicMax(&st->hmax_enc, enc_d(t));
+// x_i = x_{i-1} + dt v_{i-1/2} for moving particles (§2.4), then the box of
+// every system's positions and its largest H. Runs before the sort, so a
+// particle's system comes from its id. A warp whose particles share one
+// system reduces before its atomics.
+__global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, KParams P,
+                                                      int do_drift) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += stride) {
+    const int64_t i = base + lane;
+    const bool ok = i < n;
+    int sy = 0;
+    double p[3] = {0, 0, 0}, h = 0.0;
+    if (ok) {
+      sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
+      p[0] = s.x[i];
+      p[1] = s.y[i];
+      p[2] = s.z[i];
+      if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
+        const double dt = P.dt[sy];
+        p[0] += dt * s.vx[i];
+        p[1] += dt * s.vy[i];
+        p[2] += dt * s.vz[i];
+        s.x[i] = p[0];
+        s.y[i] = p[1];
+        s.z[i] = p[2];
       }
+      h = s.h[i];
+    }
+    const int s0 = __shfl_sync(kFull, sy, 0);
+    if (__all_sync(kFull, !ok || sy == s0)) {
+      double lo[3], hi[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = wmin(ok ? p[a] : INFINITY);
+        hi[a] = wmax(ok ? p[a] : -INFINITY);
+      }
+      const double hm = wmax(ok ? h : 0.0);
+      if (lane == 0) {
+        SysRec &r = P.sys[s0];
+        for (int a = 0; a < 3; ++a) {
+          atomicMin(&r.lo_enc[a], enc_d(lo[a]));
+          atomicMax(&r.hi_enc[a], enc_d(hi[a]));
+        }
+        atomicMax(&r.hmax_enc, enc_d(hm));
+      }
+    } else if (ok) {
+      SysRec &r = P.sys[sy];
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&r.lo_enc[a], enc_d(p[a]));
+        atomicMax(&r.hi_enc[a], enc_d(p[a]));
+      }
+      atomicMax(&r.hmax_enc, enc_d(h));
     }
   }
 }
@@ -90,53 +104,64 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, c
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
   int blocks = (int)((c->n + kBlock - 1) / kBlock);
   if (blocks > 148 * 8) blocks = 148 * 8;
-  k_drift_bbox<<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->d_dt, do_drift, c->d_status);
+  k_drift_bbox<<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ grid setup
-// Cell edge L_c = max H (at least 1e-30 of the extent); at most 1024 cells
-// per axis and max_cells in all, growing L_c by 2^(1/3) until both hold.
-__global__ void k_grid_setup(Status *st, int max_cells) {
+// Per system: cell edge L_c = max H; at most 2^axis_bits cells per axis and
+// the system's cell capacity in all, growing L_c by 2^(1/3) until both hold.
+// Then the systems' cell ranges are laid out one after the other.
+__global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double lo[3], hi[3];
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = dec_d(st->lo_enc[a]);
-    hi[a] = dec_d(st->hi_enc[a]);
-  }
-  double L = dec_d(st->hmax_enc);
-  double ext = fmax(fmax(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
-  if (!(L > 1e-30 * ext) || !(L > 0.0)) L = fmax(ext, 1.0) * 1e-3;
-  int d[3] = {1, 1, 1};
-  bool ok = false;
-  for (int it = 0; it < 200 && !ok; ++it) {
-    long long tot = 1;
-    ok = true;
+  const double max_axis = (double)(1 << axis_bits);
+  int off = 0;
+  for (int k = 0; k < nsys; ++k) {
+    SysRec &r = sys[k];
+    double lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-      double k = floor((hi[a] - lo[a]) / L) + 1.0;
-      if (!(k <= 1024.0)) ok = false;
-      d[a] = (int)fmin(fmax(k, 1.0), 2048.0);
-      tot *= d[a];
+      lo[a] = dec_d(r.lo_enc[a]);
+      hi[a] = dec_d(r.hi_enc[a]);
     }
-    if (tot > max_cells) ok = false;
-    if (!ok) L *= 1.2599210498948732;
+    double L = dec_d(r.hmax_enc);
+    const double ext = fmax(fmax(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+    if (!(L > 1e-30 * ext) || !(L > 0.0)) L = fmax(ext, 1.0) * 1e-3;
+    int d[3] = {1, 1, 1};
+    bool ok = false;
+    for (int it = 0; it < 200 && !ok; ++it) {
+      long long tot = 1;
+      ok = true;
+      for (int a = 0; a < 3; ++a) {
+        const double kk = floor((hi[a] - lo[a]) / L) + 1.0;
+        if (!(kk <= max_axis)) ok = false;
+        d[a] = (int)fmin(fmax(kk, 1.0), 2.0 * max_axis);
+        tot *= d[a];
+      }
+      if (tot > r.cell_cap) ok = false;
+      if (!ok) L *= 1.2599210498948732;
+    }
+    if (!ok) {  // non-finite box: one cell holding the whole system
+      d[0] = d[1] = d[2] = 1;
+      L = INFINITY;
+      atomicOr(&st->err, ERR_NONFINITE);
+    }
+    Grid &g = r.grid;
+    for (int a = 0; a < 3; ++a) {
+      g.lo[a] = lo[a];
+      g.dims[a] = d[a];
+    }
+    g.L = L;
+    g.ncells = d[0] * d[1] * d[2];
+    g.cell_off = off;
+    off += g.ncells;
   }
-  if (!ok) {  // non-finite box: one cell holding everything
-    d[0] = d[1] = d[2] = 1;
-    L = INFINITY;
-    atomicOr(&st->err, ERR_NONFINITE);
-  }
-  Grid &g = st->grid;
-  for (int a = 0; a < 3; ++a) {
-    g.lo[a] = lo[a];
-    g.dims[a] = d[a];
-  }
-  g.L = L;
-  g.ncells = d[0] * d[1] * d[2];
+  st->total_cells = off;
 }
 
 cudaError_t launch_grid_setup(sph_ctx *c) {
-  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->max_cells);
+  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, c->kp.axis_bits);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -145,18 +170,19 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double invL, int 
   return k < 0 ? 0 : (k >= dim ? dim - 1 : k);
 }
 
-// Morton key of each particle's cell; values start as the identity.
-__global__ void __launch_bounds__(kBlock) k_keys(const double *x, const double *y, const double *z,
-                                                int64_t n, const Status *st, unsigned *keys,
+// Key = system << 3 axis_bits | Morton code of the cell within the system;
+// values start as the identity.
+__global__ void __launch_bounds__(kBlock) k_keys(sph_state s, int64_t n, KParams P, unsigned *keys,
                                                 int *vals) {
-  const Grid g = st->grid;
-  const double invL = 1.0 / g.L;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int cx = cell_coord(x[i], g.lo[0], invL, g.dims[0]);
-    const int cy = cell_coord(y[i], g.lo[1], invL, g.dims[1]);
-    const int cz = cell_coord(z[i], g.lo[2], invL, g.dims[2]);
-    keys[i] = morton3(cx, cy, cz);
+    const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
+    const Grid &g = P.sys[sy].grid;
+    const double invL = 1.0 / g.L;
+    const int cx = cell_coord(s.x[i], g.lo[0], invL, g.dims[0]);
+    const int cy = cell_coord(s.y[i], g.lo[1], invL, g.dims[1]);
+    const int cz = cell_coord(s.z[i], g.lo[2], invL, g.dims[2]);
+    keys[i] = ((unsigned)sy << (3 * P.axis_bits)) | morton3(cx, cy, cz);
     vals[i] = (int)i;
   }
 }
@@ -337,19 +363,23 @@ __global__ void __launch_bounds__(kBlock) k_scatter_back(PermTable t, int64_t n,
 
 // Cell start / end over the sorted keys, and the packed cell coordinates.
 __global__ void __launch_bounds__(kBlock) k_clear_cells(int *start, const Status *st) {
-  const int nc = st->grid.ncells;
+  const int nc = st->total_cells;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
     start[i] = -1;
 }
 
-__global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys, int64_t n, const Status *st,
+__global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys, int64_t n, KParams P,
                                                  int *start, int *end, int *cc) {
-  const Grid g = st->grid;
+  const int sh = 3 * P.axis_bits;
+  const unsigned mask = sh >= 32 ? ~0u : ((1u << sh) - 1u);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const unsigned k = keys[i];
-    const int cx = compact1by2(k), cy = compact1by2(k >> 1), cz = compact1by2(k >> 2);
-    const int lin = (cz * g.dims[1] + cy) * g.dims[0] + cx;
+    const int sy = sh >= 32 ? 0 : (int)(k >> sh);
+    const unsigned mc = k & mask;
+    const Grid &g = P.sys[sy].grid;
+    const int cx = compact1by2(mc), cy = compact1by2(mc >> 1), cz = compact1by2(mc >> 2);
+    const int lin = g.cell_off + (cz * g.dims[1] + cy) * g.dims[0] + cx;
     cc[i] = cx | (cy << 10) | (cz << 20);
     if (i == 0 || keys[i - 1] != k) start[lin] = (int)i;
     if (i == n - 1 || keys[i + 1] != k) end[lin] = (int)(i + 1);
@@ -365,8 +395,7 @@ static int grid_for(int64_t n, int block) {
 cudaError_t launch_sort_permute(sph_ctx *c) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
-  k_keys<<<gb, kBlock, 0, c->stream>>>(c->st.x, c->st.y, c->st.z, n, c->d_status, c->keys,
-                                       c->vals);
+  k_keys<<<gb, kBlock, 0, c->stream>>>(c->st, n, c->kp, c->keys, c->vals);
   unsigned *ka = c->keys, *kb = c->keys_alt;
   int *va = c->vals, *vb = c->vals_alt;
   for (int pass = 0; pass < 4; ++pass) {
@@ -392,8 +421,8 @@ cudaError_t launch_sort_permute(sph_ctx *c) {
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
   k_clear_cells<<<grid_for(c->max_cells, kBlock), kBlock, 0, c->stream>>>(c->cell_start,
                                                                           c->d_status);
-  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->d_status, c->cell_start, c->cell_end,
-                                        c->w.cc);
+  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->kp, c->cell_start, c->cell_end, c->w.cc);
+  c->nlaunch += 1 + 4 * 5 + 4;   // keys, four radix passes, permutation, cells
   return cudaGetLastError();
 }
 

@@ -24,27 +24,43 @@ constexpr double cG = -210.0 / kPi;
 
 enum : unsigned { ERR_NOCONV = 1u, ERR_NONFINITE = 2u, ERR_CAPACITY = 4u, ERR_TIMEOUT = 8u };
 
-// Uniform cell grid of one step, written on the device by k_grid_setup.
+// Uniform cell grid of one system for one step, written on the device by
+// k_grid_setup. Global cell index = cell_off + (z * dims[1] + y) * dims[0] + x.
 struct Grid {
   double lo[3];
   double L;          // cell edge
   int dims[3];
   int ncells;
+  int cell_off;
 };
 
-// Device-resident step record. Encoded min/max use the order-preserving
-// map of doubles to unsigned 64-bit integers (enc_d / dec_d).
+// One independent particle system of a context (a context holds one system,
+// or a batch of them that never interact). Its particles occupy the sorted
+// positions [begin, end), which are also its range of caller ids. Encoded
+// min/max use the order-preserving map of doubles to unsigned 64-bit
+// integers (enc_d / dec_d).
+struct SysRec {
+  unsigned long long lo_enc[3], hi_enc[3], hmax_enc, hmax2_enc, dtmin_enc;
+  Grid grid;
+  int begin, end;      // sorted positions (= ids) of the system's particles
+  int bucket_off;      // first 32-particle bucket of the system
+  int chunk_off;       // first reduction chunk of the system
+  int cell_cap;        // cells the system may use
+  int pad_;
+  double sums[9];      // e_kin, e_int, e_pot, p[3], L[3]
+};
+
+// Device-resident step record shared by all systems of a context.
 struct Status {
   unsigned int err;
   int max_sweeps, n_unconv, n_capped, n_cfallback;
   int pad_;
-  unsigned long long lo_enc[3], hi_enc[3], hmax_enc, hmax2_enc, dtmin_enc;
   unsigned long long pairs_density, pairs_force;
   unsigned long long cand_density, cand_force;   // staged candidates
   unsigned long long groups_density, groups_force;
   unsigned next_bucket[2];                      // persistent-warp work counters
-  double sums[9];   // e_kin, e_int, e_pot, p[3], L[3]
-  Grid grid;
+  int total_cells;                              // cells of all systems this step
+  int pad2_;
 };
 
 // Kernel-side copy of the run-time parameters.
@@ -60,7 +76,34 @@ struct KParams {
   int g_n;
   double g_rmin, g_rmax, g_center[3], g_gm, g_inv_log_ratio;
   const sph_material *mats;
+  // systems
+  int nsys, axis_bits;         // Morton bits per axis below the system bits
+  int nbuckets, nchunks;
+  SysRec *sys;                 // nsys records (device)
+  const int *sys_begin;        // nsys + 1 sorted-position boundaries (device)
+  const int *sys_bucket;       // nsys + 1 bucket boundaries (device)
+  const int *sys_chunk;        // nsys + 1 chunk boundaries (device)
+  const double *dt;            // current step of every system (device)
+  int span_d, span_f;          // group span of the density / force kernels
 };
+
+// Group spans the tuner chooses among.
+constexpr int kNumSpans = 3;
+constexpr int kSpans[kNumSpans] = {1, 2, 3};
+
+constexpr int kChunk = 2048;   // particles per reduction chunk (8 per thread)
+
+// System owning a sorted position / an id / a bucket / a chunk: the last
+// boundary not above the value (bounds has nsys + 1 entries).
+__device__ __forceinline__ int sys_lookup(const int *bounds, int nsys, int64_t v) {
+  int lo = 0, hi = nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bounds[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 // Library-owned per-particle work arrays (sorted order).
 struct Work {
@@ -325,16 +368,35 @@ struct sph_ctx {
   int *cell_start, *cell_end;
   int max_cells;
   void *tmp;            // permutation scratch: 32 words of 8 bytes per particle
-  double *partials;     // per-block diagnostic partial sums
-  int nred_blocks;
-  double *d_dt;         // device copy of the current dt
+  double *partials;     // per-chunk diagnostic partial sums
+  int nchunks;
+  int nsys;
+  int64_t *sys_first;   // host copy of the system boundaries (nsys + 1)
+  int *d_sys_begin, *d_sys_bucket, *d_sys_chunk;
+  sphk::SysRec *d_sys;
+  sphk::SysRec *h_sys;      // pinned mirror
+  double *d_dt;             // device copy of the current dt of every system
   sphk::Status *d_status;
   sphk::Status *h_status;   // pinned mirror
-  double *h_dt;             // pinned dt staging
-  double dt_next;
+  double *h_dt;             // pinned dt staging (nsys)
+  double *dt_next;          // host, per system
+  int occ_density, occ_forces;   // resident blocks per SM of the pair kernels
   int num_sms;
   int timing;
+  int use_graph;
+  cudaStream_t gstream;         // library stream that graphs are captured on
+  cudaEvent_t fence;            // caller stream -> library stream ordering
+  cudaGraphExec_t graph_exec;   // captured step
   cudaEvent_t ev[SPH_NUM_PHASES + 1];
+  // online tuning of the group spans over the coming steps
+  int nlaunch;                  // kernels enqueued by the current call
+  int graph_nlaunch;            // kernels in the captured step
+  int tune_left;                // steps still to be timed (0: not tuning)
+  int tune_idx;                 // tuning steps taken so far
+  int tune_now;                 // the step being enqueued is timed
+  cudaEvent_t tev[4];           // density start / end, forces start / end
+  double tune_ms_d[sphk::kNumSpans], tune_ms_f[sphk::kNumSpans];
+  int tune_n[sphk::kNumSpans];
   double phase_ms[SPH_NUM_PHASES];
   int timed_steps;
   int primed;
@@ -349,8 +411,7 @@ template <typename K> inline int resident_grid(const sph_ctx *c, K kernel) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * sphk::kWarpsPerBlock,
                                                     0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
-  const int64_t buckets = (c->n + 31) / 32;
-  const int64_t need = (buckets + sphk::kWarpsPerBlock - 1) / sphk::kWarpsPerBlock;
+  const int64_t need = ((int64_t)c->kp.nbuckets + sphk::kWarpsPerBlock - 1) / sphk::kWarpsPerBlock;
   const int64_t have = (int64_t)per_sm * c->num_sms;
   return (int)(need < have ? need : have);
 }

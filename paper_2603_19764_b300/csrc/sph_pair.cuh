@@ -57,20 +57,25 @@ __device__ __forceinline__ T box_d2(T x, T y, T z, T x0, T x1, T y0, T y1, T z0,
   return ex * ex + ey * ey + ez * ez;
 }
 
-// Group of lanes around the first lane still in `todo`.
+// Group of lanes around the first lane still in `todo`: the lanes whose
+// cells lie within `span` cells of that lane's cell on every axis. A wider
+// span stages fewer, longer candidate lists per bucket. Each lane's
+// neighbours are visited in the same order whatever the span (cells in
+// z, y, x order, particles in sorted order), so the span changes only the
+// FP32 form's cell-relative frame, never the FP64 form's bits.
 struct Group {
   int rx, ry, rz;   // reference cell
   bool member;
 };
-__device__ __forceinline__ Group next_group(unsigned &todo, int cx, int cy, int cz) {
+__device__ __forceinline__ Group next_group(unsigned &todo, int cx, int cy, int cz, int span) {
   const int lane = threadIdx.x & 31;
   Group g;
   const int ref = __ffs(todo) - 1;
   g.rx = __shfl_sync(kFull, cx, ref);
   g.ry = __shfl_sync(kFull, cy, ref);
   g.rz = __shfl_sync(kFull, cz, ref);
-  g.member = ((todo >> lane) & 1u) && abs(cx - g.rx) <= 2 && abs(cy - g.ry) <= 2 &&
-             abs(cz - g.rz) <= 2;
+  g.member = ((todo >> lane) & 1u) && abs(cx - g.rx) <= span && abs(cy - g.ry) <= span &&
+             abs(cz - g.rz) <= span;
   todo &= ~__ballot_sync(kFull, g.member);
   return g;
 }
@@ -156,7 +161,7 @@ template <typename T, bool REL>
 __device__ __forceinline__ bool stager_next_cell(Stager<T> &s, const Grid &g, const int *cstart,
                                                  const int *cend, T Lt) {
   while (!s.done) {
-    const int c = (s.z * g.dims[1] + s.y) * g.dims[0] + s.x;
+    const int c = g.cell_off + (s.z * g.dims[1] + s.y) * g.dims[0] + s.x;
     const T fx = s.fx, fy = s.fy, fz = s.fz;
     // step to the following cell of the range
     if (s.x < s.kx1) {

@@ -12,17 +12,22 @@ constexpr int kNSum = 9;
 // kick = 0: diagnostics and time step of the state as it stands. The
 // integration and the sums are FP64; the EOS, yield and time-step criteria
 // are evaluated in T.
+// One block per chunk of kChunk consecutive particles of one system, so
+// that every system's sums are formed in a fixed order of its own.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n, const double *dtp,
-                                                int kick, KParams P, double *partials,
-                                                Status *st) {
+__global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, KParams P,
+                                                double *partials) {
   __shared__ double red[kNSum][kBlock / 32];
   __shared__ double redt[kBlock / 32];
-  const double dt = kick ? *dtp : 0.0, hdt = 0.5 * dt;
+  const int b = blockIdx.x;
+  const int sy = P.nsys > 1 ? sys_lookup(P.sys_chunk, P.nsys, b) : 0;
+  SysRec &R = P.sys[sy];
+  const int64_t c0 = R.begin + (int64_t)(b - R.chunk_off) * kChunk;
+  const int64_t c1 = c0 + kChunk < R.end ? c0 + kChunk : R.end;
+  const double dt = kick ? P.dt[sy] : 0.0, hdt = 0.5 * dt;
   double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T tmin = T(INFINITY);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
     const double m = s.m[i];
     const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
@@ -96,25 +101,26 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int64_t n,
     }
     double t = INFINITY;
     for (int q = 0; q < kBlock / 32; ++q) t = fmin(t, redt[q]);
-    atomicMin(&st->dtmin_enc, enc_d(t));
+    atomicMin(&R.dtmin_enc, enc_d(t));
   }
 }
 
-// Fixed-order sum of the block partials: strided per-thread sums, then a
-// tree over the block (deterministic for a fixed block count).
-__global__ void __launch_bounds__(kBlock) k_reduce_final(const double *partials, int nblocks,
-                                                        Status *st) {
+// Per system (one block each): fixed-order sum of its chunks' partials,
+// strided per thread, then a tree over the block.
+__global__ void __launch_bounds__(kBlock) k_reduce_final(const double *partials, KParams P) {
   __shared__ double red[kBlock / 32];
+  SysRec &R = P.sys[blockIdx.x];
+  const int b0 = R.chunk_off, b1 = P.sys_chunk[blockIdx.x + 1];
   for (int k = 0; k < kNSum; ++k) {
     double t = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) t += partials[b * kNSum + k];
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) t += partials[b * kNSum + k];
     t = wsum(t);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int q = 0; q < kBlock / 32; ++q) s += red[q];
-      st->sums[k] = s;
+      R.sums[k] = s;
     }
     __syncthreads();
   }
@@ -122,12 +128,11 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *partials,
 
 cudaError_t launch_kick(sph_ctx *c, int kick) {
   if (c->kp.precision == SPH_FP32K)
-    k_kick<float><<<c->nred_blocks, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, kick,
-                                                            c->kp, c->partials, c->d_status);
+    k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials);
   else
-    k_kick<double><<<c->nred_blocks, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->d_dt, kick,
-                                                             c->kp, c->partials, c->d_status);
-  k_reduce_final<<<1, kBlock, 0, c->stream>>>(c->partials, c->nred_blocks, c->d_status);
+    k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials);
+  k_reduce_final<<<c->nsys, kBlock, 0, c->stream>>>(c->partials, c->kp);
+  c->nlaunch += 2;
   return cudaGetLastError();
 }
 

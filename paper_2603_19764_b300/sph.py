@@ -25,6 +25,7 @@ SPH_OK, SPH_E_ARG, SPH_E_CUDA, SPH_E_NOCONV, SPH_E_CAPACITY, SPH_E_NONFINITE, \
 STATUS_NAMES = ["SPH_OK", "SPH_E_ARG", "SPH_E_CUDA", "SPH_E_NOCONV", "SPH_E_CAPACITY",
                 "SPH_E_NONFINITE", "SPH_E_TIMEOUT", "SPH_E_STATE"]
 MAX_MATERIALS = 8
+SPH_MAX_SYSTEMS = 1024
 
 
 class SphError(RuntimeError):
@@ -79,7 +80,7 @@ class SphStepInfo(C.Structure):
                 ("pairs_density", C.c_int64), ("pairs_force", C.c_int64),
                 ("device_flags", C.c_uint32), ("cand_density", C.c_int64),
                 ("cand_force", C.c_int64), ("groups_density", C.c_int64),
-                ("groups_force", C.c_int64)]
+                ("groups_force", C.c_int64), ("kernel_launches", C.c_int32)]
 
     def as_dict(self) -> dict:
         return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
@@ -88,13 +89,23 @@ class SphStepInfo(C.Structure):
                     n_cfallback=self.n_cfallback, pairs_density=self.pairs_density,
                     pairs_force=self.pairs_force, device_flags=self.device_flags,
                     cand_density=self.cand_density, cand_force=self.cand_force,
-                    groups_density=self.groups_density, groups_force=self.groups_force)
+                    groups_density=self.groups_density, groups_force=self.groups_force,
+                    kernel_launches=self.kernel_launches)
+
+
+class SphTuneReport(C.Structure):
+    _fields_ = [("span_density", C.c_int32), ("span_forces", C.c_int32),
+                ("steps_left", C.c_int32), ("n_cand", C.c_int32), ("cand", C.c_int32 * 4),
+                ("timed", C.c_int32 * 4), ("ms_density", C.c_double * 4),
+                ("ms_forces", C.c_double * 4)]
 
 
 EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_stress_update", "sph_step", "sph_step_host", "sph_prime", "sph_destroy",
            "sph_status_string", "sph_last_error", "sph_set_timing", "sph_phase_times",
-           "sph_diagnostics_noalloc")
+           "sph_diagnostics_noalloc", "sph_init_batch", "sph_step_batch", "sph_batch_info",
+           "sph_set_graph", "sph_autotune", "sph_tune_info",
+           "sph_set_spans")
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
 
 
@@ -130,6 +141,22 @@ def lib():
         L.sph_set_timing.argtypes = [VP, C.c_int32]
         L.sph_phase_times.restype = st
         L.sph_phase_times.argtypes = [VP, _P, C.c_int32, _PI]
+        L.sph_init_batch.restype = st
+        L.sph_init_batch.argtypes = [C.POINTER(VP), C.POINTER(SphParams), C.POINTER(SphMaterial),
+                                     C.c_int32, C.POINTER(SphState), C.c_int64, C.c_int32, _PL,
+                                     VP]
+        L.sph_step_batch.restype = st
+        L.sph_step_batch.argtypes = [VP, _P, C.POINTER(SphStepInfo)]
+        L.sph_batch_info.restype = st
+        L.sph_batch_info.argtypes = [VP, C.POINTER(SphStepInfo), C.c_int32]
+        L.sph_autotune.restype = st
+        L.sph_autotune.argtypes = [VP, C.c_int32]
+        L.sph_set_spans.restype = st
+        L.sph_set_spans.argtypes = [VP, C.c_int32, C.c_int32]
+        L.sph_tune_info.restype = st
+        L.sph_tune_info.argtypes = [VP, C.POINTER(SphTuneReport)]
+        L.sph_set_graph.restype = st
+        L.sph_set_graph.argtypes = [VP, C.c_int32]
         L.sph_diagnostics_noalloc.restype = st
         L.sph_diagnostics_noalloc.argtypes = [C.POINTER(SphState), C.c_int64, VP, VP]
         L.sph_status_string.restype = C.c_char_p
@@ -185,7 +212,7 @@ class Simulation:
     """
 
     def __init__(self, arrays: dict, materials: list, params: dict, device: str = "cuda:0",
-                 stream=None):
+                 stream=None, systems=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("CUDA device required: the SPH path has no CPU fallback")
@@ -208,8 +235,19 @@ class Simulation:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         torch.cuda.synchronize(self.device)
         self.ctx = C.c_void_p()
-        rc = lib().sph_init(C.byref(self.ctx), C.byref(self.params), mats, len(materials),
-                            C.byref(self.state), self.n, C.c_void_p(self.stream.cuda_stream))
+        if systems is None:
+            self.nsys = 1
+            rc = lib().sph_init(C.byref(self.ctx), C.byref(self.params), mats, len(materials),
+                                C.byref(self.state), self.n, C.c_void_p(self.stream.cuda_stream))
+        else:
+            first = np.array([0] + [o + c for o, c in systems], dtype=np.int64)
+            if any(int(first[k]) != int(o) for k, (o, _) in enumerate(systems)):
+                raise ValueError("systems must be contiguous (offset, count) ranges from 0")
+            self.nsys = len(systems)
+            rc = lib().sph_init_batch(C.byref(self.ctx), C.byref(self.params), mats,
+                                      len(materials), C.byref(self.state), self.n, self.nsys,
+                                      first.ctypes.data_as(_PL),
+                                      C.c_void_p(self.stream.cuda_stream))
         if rc != SPH_OK:
             raise SphError(rc, "sph_init")
 
@@ -246,6 +284,38 @@ class Simulation:
         d = info.as_dict()
         d["status"] = rc
         return d
+
+    def step_batch(self, dts) -> dict:
+        d = np.ascontiguousarray(dts, np.float64)
+        if d.shape != (self.nsys,):
+            raise ValueError("step_batch needs one dt per system (%d)" % self.nsys)
+        info = SphStepInfo()
+        self._check(lib().sph_step_batch(self.ctx, d.ctypes.data_as(_P), C.byref(info)),
+                    "sph_step_batch")
+        return info.as_dict()
+
+    def batch_info(self) -> list:
+        arr = (SphStepInfo * self.nsys)()
+        self._check(lib().sph_batch_info(self.ctx, arr, self.nsys), "sph_batch_info")
+        return [a.as_dict() for a in arr]
+
+    def autotune(self, rounds: int = 2):
+        return self._check(lib().sph_autotune(self.ctx, int(rounds)), "sph_autotune")
+
+    def set_spans(self, span_density: int, span_forces: int):
+        return self._check(lib().sph_set_spans(self.ctx, int(span_density), int(span_forces)),
+                           "sph_set_spans")
+
+    def tune_info(self) -> dict:
+        r = SphTuneReport()
+        self._check(lib().sph_tune_info(self.ctx, C.byref(r)), "sph_tune_info")
+        k = r.n_cand
+        return {"span_density": r.span_density, "span_forces": r.span_forces,
+                "steps_left": r.steps_left, "cand": list(r.cand[:k]), "timed": list(r.timed[:k]),
+                "ms_density": list(r.ms_density[:k]), "ms_forces": list(r.ms_forces[:k])}
+
+    def set_graph(self, on: bool = True):
+        return self._check(lib().sph_set_graph(self.ctx, 1 if on else 0), "sph_set_graph")
 
     def step_host(self, host: "HostState", dt: float) -> dict:
         info = SphStepInfo()

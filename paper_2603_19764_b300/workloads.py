@@ -124,6 +124,7 @@ class Workload:
     params: dict
     dt: float
     systems: list | None = None   # (offset, count) per independent system
+    dts: list | None = None       # fixed step of each system
 
     @property
     def n(self) -> int:
@@ -132,7 +133,16 @@ class Workload:
     def copy(self) -> "Workload":
         return Workload(self.name, {k: v.copy() for k, v in self.arrays.items()},
                         [dict(m) for m in self.materials], dict(self.params), self.dt,
-                        None if self.systems is None else list(self.systems))
+                        None if self.systems is None else list(self.systems),
+                        None if self.dts is None else list(self.dts))
+
+    def system(self, k: int) -> "Workload":
+        """System k of a batch on its own, ids renumbered from 0."""
+        off, cnt = self.systems[k]
+        a = {key: v[off:off + cnt].copy() for key, v in self.arrays.items()}
+        a["id"] = a["id"] - off
+        return Workload("%s_sys%d" % (self.name, k), a, [dict(m) for m in self.materials],
+                        dict(self.params), self.dts[k] if self.dts else self.dt)
 
 
 def _empty_arrays(n: int) -> dict:
@@ -303,7 +313,8 @@ def impact_batch(n_systems: int = 64, seed: int = BASE_SEED + 4, spacing: float 
     uniform in [0.01, 0.5], N_i = max(341, round(gamma N_t)), speed uniform
     in [1, 20] km/s, angle uniform in [0, 60] degrees. Systems are placed
     far apart along x so that no pair of particles from different systems
-    is ever within a kernel radius; each keeps its own radial table centre.
+    is ever within a kernel radius. Each system keeps its own fixed step
+    (dts); dt is the smallest of them.
     """
     rng = SplitMix64(seed)
     lo, hi = math.log(nt_range[0] * scale), math.log(nt_range[1] * scale)
@@ -330,7 +341,7 @@ def impact_batch(n_systems: int = 64, seed: int = BASE_SEED + 4, spacing: float 
     arr = _concat(parts)
     p = default_params(precision)
     return Workload("impact_batch_%d" % n_systems, arr, [basalt_material()], p, min(dts),
-                    systems=systems)
+                    systems=systems, dts=dts)
 
 
 def periodic_wave_box(nx: int = 64, ny: int = 8, nz: int = 8, spacing: float = 1.0,

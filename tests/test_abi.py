@@ -51,10 +51,11 @@ def _c_layout():
 #define S(T) printf(#T " %zu\n", sizeof(T));
 #define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
-  S(sph_state) S(sph_material) S(sph_params) S(sph_step_info)
+  S(sph_state) S(sph_material) S(sph_params) S(sph_step_info) S(sph_tune_report)
   O(sph_state, id) O(sph_state, nngb) O(sph_material, strength) O(sph_material, xi)
   O(sph_params, g_table) O(sph_params, g_n) O(sph_params, box_hi) O(sph_params, precision)
   O(sph_step_info, pairs_density) O(sph_step_info, device_flags) O(sph_step_info, sweeps)
+  O(sph_step_info, kernel_launches) O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
   return 0;
 }
 """
@@ -70,7 +71,8 @@ int main(void) {
 def test_struct_layouts_match_binding():
     lay = _c_layout()
     py = {"sph_state": sph.SphState, "sph_material": sph.SphMaterial,
-          "sph_params": sph.SphParams, "sph_step_info": sph.SphStepInfo}
+          "sph_params": sph.SphParams, "sph_step_info": sph.SphStepInfo,
+          "sph_tune_report": sph.SphTuneReport}
     for name, cls in py.items():
         assert int(lay[name]) == C.sizeof(cls), name
     for key, val in lay.items():
@@ -95,3 +97,34 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu(libsph):
     assert ctx.value is None
     libsph.sph_destroy.restype = C.c_int
     assert libsph.sph_destroy(None) == sph.SPH_OK
+
+
+def test_batch_init_rejects_bad_system_bounds_without_touching_the_gpu(libsph):
+    """System bounds are checked on the host before any CUDA call."""
+    from paper_2603_19764_b300 import workloads as wl
+    w = wl.impact(500, 60, seed=3)
+    keep = []
+    p = sph.make_params(dict(w.params, precision=0), keep)
+    mats = (sph.SphMaterial * 1)(sph.make_material(w.materials[0]))
+    st = sph.state_from_ptrs({f: 4096 for f in sph.F64_FIELDS + sph.I32_FIELDS + ("id",)})
+    f = libsph.sph_init_batch
+    f.restype = C.c_int
+    f.argtypes = [C.POINTER(C.c_void_p), C.POINTER(sph.SphParams), C.POINTER(sph.SphMaterial),
+                  C.c_int32, C.POINTER(sph.SphState), C.c_int64, C.c_int32,
+                  C.POINTER(C.c_int64), C.c_void_p]
+    n = 100
+    ctx = C.c_void_p()
+
+    def call(bounds, nsys=None):
+        b = (C.c_int64 * len(bounds))(*bounds)
+        k = len(bounds) - 1 if nsys is None else nsys
+        return f(C.byref(ctx), C.byref(p), mats, 1, C.byref(st), n, k, b, None)
+
+    assert call([1, 50, 100]) == sph.SPH_E_ARG          # does not start at 0
+    assert call([0, 50, 99]) == sph.SPH_E_ARG           # does not end at n
+    assert call([0, 50, 50, 100]) == sph.SPH_E_ARG      # empty system
+    assert call([0, 60, 40, 100]) == sph.SPH_E_ARG      # decreasing
+    assert call([0, 100], nsys=0) == sph.SPH_E_ARG      # no system
+    assert call([0] * 1026, nsys=sph.SPH_MAX_SYSTEMS + 1) == sph.SPH_E_ARG
+    assert f(C.byref(ctx), C.byref(p), mats, 1, C.byref(st), n, 2, None, None) == sph.SPH_E_ARG
+    assert ctx.value is None

@@ -31,9 +31,12 @@ def _built():
 
 def _check(w, precision, nsample=1500, seed=5):
     p = dict(w.params, precision=precision, h_tol=1e-10 if precision == 0 else 1e-6)
-    sim = sph.Simulation(w.arrays, w.materials, p)
+    sim = sph.Simulation(w.arrays, w.materials, p, systems=w.systems)
     sim.prime()
-    sim.step(w.dt)
+    if w.dts is not None:
+        sim.step_batch(np.zeros(len(w.dts)))   # every system at its own dt_next
+    else:
+        sim.step(w.dt)
     # evaluate the derivatives of the state as it stands, as the oracle will
     sim.forces_strength()
     g = sim.to_numpy()
@@ -71,3 +74,7 @@ def test_impact_8m_fp32():
 
 def test_batch_of_64_impacts_fp64():
     _check(wl.config(4, precision=0), 0, nsample=1000)
+
+
+def test_batch_of_64_impacts_fp32():
+    _check(wl.config(4, precision=1), 1, nsample=1000)
