@@ -392,3 +392,27 @@ def config(index: int, precision: int | None = None, scale: float = 1.0) -> Work
         return impact(int(7_200_000 * scale), int(800_000 * scale),
                       precision=1 if precision is None else precision)
     raise ValueError("config index must be 1..5")
+
+
+# --------------------------------------------------------------------------
+# Initial weights of the smoothing-length network (6-64-64-1)
+# --------------------------------------------------------------------------
+MLP_NIN, MLP_NHID = 6, 64
+MLP_NPARAM = MLP_NHID * MLP_NIN + MLP_NHID + MLP_NHID * MLP_NHID + MLP_NHID + MLP_NHID + 1
+
+
+def mlp_init(seed: int = BASE_SEED + 7) -> np.ndarray:
+    """Seeded initial parameter vector: weights uniform in +-sqrt(6 / (fan_in
+    + fan_out)) (Glorot and Bengio 2010), biases zero. Order: W1[64][6], b1,
+    W2[64][64], b2, W3[64], b3."""
+    rng = SplitMix64(seed)
+
+    def glorot(fan_out, fan_in):
+        a = math.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(fan_out * fan_in, -a, a)
+
+    nh, ni = MLP_NHID, MLP_NIN
+    theta = np.concatenate([glorot(nh, ni), np.zeros(nh), glorot(nh, nh), np.zeros(nh),
+                            glorot(1, nh), np.zeros(1)])
+    assert theta.shape[0] == MLP_NPARAM
+    return theta
