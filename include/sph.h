@@ -160,6 +160,7 @@ typedef struct {
   int64_t cand_density, cand_force;
   int64_t groups_density, groups_force;  /* lane groups the pair kernels formed */
   int32_t kernel_launches;               /* kernels the call launched */
+  int64_t sweeps_total;                  /* Newton sweeps summed over particles */
 } sph_step_info;
 
 /* Report of the group-span tuner (sph_autotune). The pair kernels give
@@ -262,6 +263,77 @@ sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces);
 
 /* The tuner's state and timings. */
 sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out);
+
+/* ---------------------------------------------------------------------
+ * Learned smoothing-length proposal. The paper's solve (§2.1, Eq. 2-3)
+ * starts Newton from the previous support radius; this form starts it from
+ * a proposal and leaves the exact solve to decide H and the count. The
+ * proposal is made per particle at the end of every step from six features
+ * of the converged state (f0 = log(H / H_bar), H_bar = (3 N_ngb m / (4 pi
+ * rho0))^(1/3); f1 = n / N_ngb - 1; f2 = log(rho / rho0); f3 = dt tr G,
+ * the trace of the corrected velocity gradient of Eq. 18-20; f4 =
+ * log(H / H_prev), the previous step's H; f5 = Omega - 1) by a 6-64-64-1
+ * network with tanh hidden units and a linear output that predicts
+ * log(H_next / H), in bf16 weights with FP32 accumulation on the tensor
+ * cores. The predicted ratio is limited to [0.8, 1.25].
+ * --------------------------------------------------------------------- */
+#define SPH_MLP_NIN 6
+#define SPH_MLP_NHID 64
+#define SPH_MLP_NPARAM 4673   /* W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3 */
+#define SPH_MLP_NNORM 14      /* x_mu[6], x_sd[6], y_mu, y_sd */
+
+enum { SPH_GUESS_PREVIOUS = 0, SPH_GUESS_CONTINUITY = 1, SPH_GUESS_NETWORK = 2 };
+
+typedef struct sph_mlp sph_mlp;   /* opaque network on one device */
+
+/* Create a network with zero parameters on `cuda_stream` (NULL: legacy
+ * default stream); every call below runs on that stream. Owns its device
+ * memory (about 1.5 MB) until sph_mlp_destroy. SPH_E_CUDA on allocation
+ * failure. */
+sph_status sph_mlp_create(sph_mlp **out, void *cuda_stream);
+sph_status sph_mlp_destroy(sph_mlp *net);
+const char *sph_mlp_last_error(const sph_mlp *net);
+
+/* Load parameters (HOST, SPH_MLP_NPARAM floats in the order above) and the
+ * normalisation (HOST, SPH_MLP_NNORM floats; standard deviations > 0,
+ * SPH_E_ARG otherwise); resets the Adam moments. Synchronises. */
+sph_status sph_mlp_set(sph_mlp *net, const float *theta, const float *norm);
+/* Copy parameters and normalisation to HOST arrays (either may be NULL). */
+sph_status sph_mlp_get(const sph_mlp *net, float *theta, float *norm);
+/* Set the normalisation to the means and standard deviations (floored at
+ * 1e-6) of m DEVICE samples X (m x 6, row-major) and y (m), skipping
+ * samples with a non-finite target. Synchronises. */
+sph_status sph_mlp_fit_norm(sph_mlp *net, const float *X, const float *y, int64_t m);
+/* Predictions log(H_next / H) of m DEVICE feature rows into DEVICE pred. */
+sph_status sph_mlp_forward(sph_mlp *net, const float *X, int64_t m, float *pred);
+/* Loss L = 1/(2 m') sum (out - (y - y_mu) / y_sd)^2 over the m' samples
+ * with finite features and target among rows idx[0..m) (DEVICE, NULL: rows
+ * 0..m), into *loss (HOST); its gradient (SPH_MLP_NPARAM floats) into
+ * DEVICE grad when not NULL. Deterministic. Synchronises. */
+sph_status sph_mlp_loss_grad(sph_mlp *net, const float *X, const float *y, const int64_t *idx,
+                             int64_t m, float *loss, float *grad);
+/* One Adam update (Kingma & Ba 2015) with DEVICE gradient grad. */
+sph_status sph_mlp_adam_step(sph_mlp *net, const float *grad, float lr, float beta1, float beta2,
+                             float eps);
+/* One epoch of minibatch Adam (beta 0.9, 0.999, eps 1e-8) over the rows in
+ * the order perm (DEVICE, m entries), `batch` rows per update (>= 16);
+ * *mean_loss (HOST) the mean of the minibatch losses. */
+sph_status sph_mlp_train_epoch(sph_mlp *net, const float *X, const float *y, const int64_t *perm,
+                               int64_t m, int32_t batch, float lr, float *mean_loss);
+
+/* Starting radius of the context's smoothing-length solves: guess =
+ * SPH_GUESS_PREVIOUS (the paper's), SPH_GUESS_CONTINUITY (H exp(-dt tr G /
+ * 3), the continuity equation's estimate) or SPH_GUESS_NETWORK (`net`,
+ * which must stay alive while in use). record = 1 keeps, after every step,
+ * one training sample per particle (sph_learn_samples). Any mode other than
+ * (PREVIOUS, 0) needs ids 0..n-1 (checked: SPH_E_ARG) and allocates about
+ * 60 bytes per particle; proposals start one step after the call. Drops a
+ * captured graph. */
+sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sph_mlp *net);
+/* The samples of the last step, by particle id: X (DEVICE, n x 6) the
+ * features of the step before, y (DEVICE, n) log(H / H_before); rows
+ * without a previous step are NaN. SPH_E_STATE unless recording. */
+sph_status sph_learn_samples(sph_ctx *c, float *X, float *y);
 
 /* sph_step with HOST state: the caller passes pinned or pageable host
  * arrays in `host`; the library copies them to the context's device state,

@@ -74,7 +74,8 @@ void free_all(sph_ctx *c) {
                  c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
-                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk};
+                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->w.divv,
+                 c->learn.hprev, c->learn.hprop, c->learn.feat, c->learn.x_out, c->learn.y_out};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -133,6 +134,7 @@ void fill_info(const sph_ctx *c, int sys, sph_step_info *info) {
   info->groups_density = (int64_t)h.groups_density;
   info->groups_force = (int64_t)h.groups_force;
   info->kernel_launches = c->nlaunch;
+  info->sweeps_total = (int64_t)h.sweeps_total;
 }
 
 // After a synchronisation: per-system dt_next from the mirrors, the report,
@@ -192,6 +194,7 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
   CK(tmark(c, 2));
   CK(launch_forces(c));
   CK(tmark(c, 3));
+  CK(launch_learn(c));
   CK(mark(c, 5));
   return SPH_OK;
 }
@@ -537,6 +540,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   CKI(cudaMalloc(&c->tmp, (size_t)n * 32 * 8));
   CKI(dalloc(&c->partials, (size_t)c->nchunks * 9));
   CKI(dalloc(&c->d_dt, n_sys));
+  CKI(cudaMemset(c->d_dt, 0, sizeof(double) * n_sys));
   kp.dt = c->d_dt;
   CKI(dalloc(&c->d_status, 1));
   CKI(cudaMemset(c->d_status, 0, sizeof(Status)));
@@ -702,7 +706,8 @@ sph_status sph_stress_update(sph_ctx *c, double dt) {
 sph_status sph_prime(sph_ctx *c, sph_step_info *info) {
   ENTER(c);
   for (int k = 0; k < c->nsys; ++k) c->h_dt[k] = 0.0;
-  sph_status s = run_neighbours(c, 0);
+  sph_status s = upload_dt(c);
+  if (s == SPH_OK) s = run_neighbours(c, 0);
   if (s != SPH_OK) return s;
   s = run_derivatives(c, 0);
   if (s != SPH_OK) return s;
@@ -723,6 +728,70 @@ sph_status sph_step_batch(sph_ctx *c, const double *dt, sph_step_info *info) {
   if (!dt) return fail(c, SPH_E_ARG, "dt array is NULL");
   const sph_status s = stage_dt(c, dt, 0.0);
   return s != SPH_OK ? s : run_step(c, info);
+}
+
+sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sph_mlp *net) {
+  ENTER(c);
+  if (guess < SPH_GUESS_PREVIOUS || guess > SPH_GUESS_NETWORK || (record != 0 && record != 1))
+    return fail(c, SPH_E_ARG, "unknown guess mode");
+  if (guess == SPH_GUESS_NETWORK && !net) return fail(c, SPH_E_ARG, "network guess needs a network");
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  LearnArgs &L = c->learn;
+  const int64_t n = c->n;
+  if (guess == SPH_GUESS_PREVIOUS && !record) {
+    void *p[] = {c->w.divv, L.hprev, L.hprop, L.feat, L.x_out, L.y_out};
+    for (void *q : p)
+      if (q) cudaFree(q);
+    memset(&L, 0, sizeof(L));
+    c->w.divv = nullptr;
+    c->kp.h_guess = nullptr;
+    c->net = nullptr;
+    return SPH_OK;
+  }
+  if (!L.hprev) {
+    unsigned *bad = nullptr;
+    CK(dalloc(&bad, 1));
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->stream));
+    k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, c->nmat, 1, bad);
+    unsigned hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(bad);
+    if (hbad) return fail(c, SPH_E_ARG, "the learned form needs ids 0..n-1");
+    CK(dalloc(&c->w.divv, n));
+    CK(dalloc(&L.hprev, n));
+    CK(dalloc(&L.hprop, n));
+    CK(dalloc(&L.feat, (size_t)n * 8));
+    CK(cudaMemsetAsync(L.hprev, 0, sizeof(double) * n, c->stream));
+    CK(cudaMemsetAsync(L.hprop, 0, sizeof(double) * n, c->stream));
+  }
+  if (record && !L.x_out) {
+    CK(dalloc(&L.x_out, (size_t)n * 6));
+    CK(dalloc(&L.y_out, n));
+    CK(cudaMemsetAsync(L.x_out, 0xff, sizeof(float) * 6 * n, c->stream));   // NaN
+    CK(cudaMemsetAsync(L.y_out, 0xff, sizeof(float) * n, c->stream));
+  }
+  L.guess = guess;
+  L.record = record;
+  L.divv = c->w.divv;
+  c->net = guess == SPH_GUESS_NETWORK ? net : nullptr;
+  // a new guess mode starts from the previous radius until it has proposed
+  CK(cudaMemsetAsync(L.hprop, 0, sizeof(double) * n, c->stream));
+  c->kp.h_guess = guess == SPH_GUESS_PREVIOUS ? nullptr : L.hprop;
+  CK(cudaStreamSynchronize(c->stream));
+  return SPH_OK;
+}
+
+sph_status sph_learn_samples(sph_ctx *c, float *X, float *y) {
+  ENTER(c);
+  if (!X || !y) return fail(c, SPH_E_ARG, "NULL sample buffer");
+  if (!c->learn.record || !c->learn.x_out) return fail(c, SPH_E_STATE, "not recording");
+  CK(cudaMemcpyAsync(X, c->learn.x_out, sizeof(float) * 6 * c->n, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(y, c->learn.y_out, sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  return SPH_OK;
 }
 
 sph_status sph_batch_info(const sph_ctx *c, sph_step_info *info, int32_t n) {

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const int nbuckets = A.p.nbuckets;
   long long w_pairs = 0, w_cand = 0;
   int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0;
+  long long w_swt = 0;
   unsigned w_bad = 0;
   for (;;) {
   unsigned bk = 0;
@@ -194,7 +195,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const T tol = (T)A.p.h_tol;
   const double Hcap =
       A.p.h_cap_factor * (double)cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
-  double H = fmin(A.s.h[ic], Hcap);
+  // starting radius: the previous H, or the proposal of the learned form
+  double H = A.s.h[ic];
+  if (A.p.h_guess) {
+    const double hg = A.p.h_guess[A.s.id[ic]];
+    if (hg > 0.0) H = hg;
+  }
+  H = fmin(H, Hcap);
   const double xi64 = A.s.x[ic], yi64 = A.s.y[ic], zi64 = A.s.z[ic];
   // Newton state: 0 running, 1 converged, 2 capped, 3 gave up, 4 idle lane
   int state = valid ? 0 : 4;
@@ -325,6 +332,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
     A.s.nngb[i] = cnt_o;
   }
   w_sw = max(w_sw, valid ? sweeps_o : 0);
+  w_swt += valid ? sweeps_o : 0;
   w_nu += state == 3;
   w_ncap += state == 2;
   w_bad |= (valid && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0))) ? 1u
@@ -341,8 +349,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const int ncap = wsum(w_ncap);
   const unsigned nbad = __ballot_sync(kFull, w_bad != 0u);
   const long long pw = wsum(w_pairs);
+  const long long swt = wsum(w_swt);
   if (lane == 0) {
     atomicMax(&A.st->max_sweeps, sw);
+    atomicAdd(&A.st->sweeps_total, (unsigned long long)swt);
     if (nu) {
       atomicAdd(&A.st->n_unconv, nu);
       atomicOr(&A.st->err, ERR_NOCONV);

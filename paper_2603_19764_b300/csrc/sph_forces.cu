@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
     }
     A.w.vsig[i] = (double)(T(1.0 + 0.6 * A.p.av_alpha) * s1.z + T(0.6 * A.p.av_beta) * mumax);
     A.w.edot2[i] = (double)(T(0.5) * e2);
+    if (A.w.divv) A.w.divv[i] = (float)(E[0] + E[4] + E[8]);
     const T axt = ax + s2.x, ayt = ay + s2.y, azt = az + s2.z;
     const T dud = du.get();
     A.s.ax[i] = fixed ? 0.0 : (double)axt;

@@ -22,6 +22,7 @@ __global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full) {
     st->cand_force = 0;
     st->groups_density = 0;
     st->groups_force = 0;
+    st->sweeps_total = 0;
     if (full) st->err = 0;
   }
   for (int k = threadIdx.x; k < nsys; k += blockDim.x) {

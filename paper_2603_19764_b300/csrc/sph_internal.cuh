@@ -58,6 +58,7 @@ struct Status {
   unsigned long long pairs_density, pairs_force;
   unsigned long long cand_density, cand_force;   // staged candidates
   unsigned long long groups_density, groups_force;
+  unsigned long long sweeps_total;              // Newton sweeps summed over particles
   unsigned next_bucket[2];                      // persistent-warp work counters
   int total_cells;                              // cells of all systems this step
   int pad2_;
@@ -85,6 +86,7 @@ struct KParams {
   const int *sys_chunk;        // nsys + 1 chunk boundaries (device)
   const double *dt;            // current step of every system (device)
   int span_d, span_f;          // group span of the density / force kernels
+  const double *h_guess;       // starting radius of the solve by particle id, or null
 };
 
 // Group spans the tuner chooses among.
@@ -118,6 +120,17 @@ struct Work {
   double4_32a *fj64[4];         // force-side neighbour data (FP64 form)
   float4 *fs32[3];              // own stress, shear modulus, c_L, external g
   double4_32a *fs64[3];
+  float *divv;                  // tr of the corrected velocity gradient (learned form)
+};
+
+// Arrays of the learned form, indexed by particle id.
+struct LearnArgs {
+  int guess, record;
+  const float *divv;            // sorted order
+  double *hprev;                // H of the last solve
+  double *hprop;                // starting radius proposed for the next solve
+  float *feat;                  // features of the last step, 8 floats per id
+  float *x_out, *y_out;         // samples of the last step (record)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -389,6 +402,8 @@ struct sph_ctx {
   cudaGraphExec_t graph_exec;   // captured step
   cudaEvent_t ev[SPH_NUM_PHASES + 1];
   // online tuning of the group spans over the coming steps
+  sphk::LearnArgs learn;        // learned form (hprev == null: off)
+  const struct sph_mlp *net;    // network of the learned guess
   int nlaunch;                  // kernels enqueued by the current call
   int graph_nlaunch;            // kernels in the captured step
   int tune_left;                // steps still to be timed (0: not tuning)
@@ -427,4 +442,5 @@ cudaError_t launch_eos_pack(sph_ctx *c);
 cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_kick(sph_ctx *c, int kick);
 cudaError_t launch_reset_status(sph_ctx *c, int full);
+cudaError_t launch_learn(sph_ctx *c);
 }  // namespace sphk

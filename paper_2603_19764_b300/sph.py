@@ -80,7 +80,8 @@ class SphStepInfo(C.Structure):
                 ("pairs_density", C.c_int64), ("pairs_force", C.c_int64),
                 ("device_flags", C.c_uint32), ("cand_density", C.c_int64),
                 ("cand_force", C.c_int64), ("groups_density", C.c_int64),
-                ("groups_force", C.c_int64), ("kernel_launches", C.c_int32)]
+                ("groups_force", C.c_int64), ("kernel_launches", C.c_int32),
+                ("sweeps_total", C.c_int64)]
 
     def as_dict(self) -> dict:
         return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
@@ -90,7 +91,7 @@ class SphStepInfo(C.Structure):
                     pairs_force=self.pairs_force, device_flags=self.device_flags,
                     cand_density=self.cand_density, cand_force=self.cand_force,
                     groups_density=self.groups_density, groups_force=self.groups_force,
-                    kernel_launches=self.kernel_launches)
+                    kernel_launches=self.kernel_launches, sweeps_total=self.sweeps_total)
 
 
 class SphTuneReport(C.Structure):
@@ -105,7 +106,12 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_status_string", "sph_last_error", "sph_set_timing", "sph_phase_times",
            "sph_diagnostics_noalloc", "sph_init_batch", "sph_step_batch", "sph_batch_info",
            "sph_set_graph", "sph_autotune", "sph_tune_info",
-           "sph_set_spans")
+           "sph_set_spans", "sph_mlp_create", "sph_mlp_destroy", "sph_mlp_last_error",
+           "sph_mlp_set", "sph_mlp_get", "sph_mlp_fit_norm", "sph_mlp_forward",
+           "sph_mlp_loss_grad", "sph_mlp_adam_step", "sph_mlp_train_epoch",
+           "sph_set_learned_h", "sph_learn_samples")
+MLP_NPARAM, MLP_NNORM = 4673, 14
+GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
 
 
@@ -149,6 +155,31 @@ def lib():
         L.sph_step_batch.argtypes = [VP, _P, C.POINTER(SphStepInfo)]
         L.sph_batch_info.restype = st
         L.sph_batch_info.argtypes = [VP, C.POINTER(SphStepInfo), C.c_int32]
+        _PF = C.POINTER(C.c_float)
+        L.sph_mlp_create.restype = st
+        L.sph_mlp_create.argtypes = [C.POINTER(VP), VP]
+        L.sph_mlp_destroy.restype = st
+        L.sph_mlp_destroy.argtypes = [VP]
+        L.sph_mlp_last_error.restype = C.c_char_p
+        L.sph_mlp_last_error.argtypes = [VP]
+        L.sph_mlp_set.restype = st
+        L.sph_mlp_set.argtypes = [VP, _PF, _PF]
+        L.sph_mlp_get.restype = st
+        L.sph_mlp_get.argtypes = [VP, _PF, _PF]
+        L.sph_mlp_fit_norm.restype = st
+        L.sph_mlp_fit_norm.argtypes = [VP, VP, VP, C.c_int64]
+        L.sph_mlp_forward.restype = st
+        L.sph_mlp_forward.argtypes = [VP, VP, C.c_int64, VP]
+        L.sph_mlp_loss_grad.restype = st
+        L.sph_mlp_loss_grad.argtypes = [VP, VP, VP, VP, C.c_int64, _PF, VP]
+        L.sph_mlp_adam_step.restype = st
+        L.sph_mlp_adam_step.argtypes = [VP, VP, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.sph_mlp_train_epoch.restype = st
+        L.sph_mlp_train_epoch.argtypes = [VP, VP, VP, VP, C.c_int64, C.c_int32, C.c_float, _PF]
+        L.sph_set_learned_h.restype = st
+        L.sph_set_learned_h.argtypes = [VP, C.c_int32, C.c_int32, VP]
+        L.sph_learn_samples.restype = st
+        L.sph_learn_samples.argtypes = [VP, VP, VP]
         L.sph_autotune.restype = st
         L.sph_autotune.argtypes = [VP, C.c_int32]
         L.sph_set_spans.restype = st
@@ -302,6 +333,22 @@ class Simulation:
     def autotune(self, rounds: int = 2):
         return self._check(lib().sph_autotune(self.ctx, int(rounds)), "sph_autotune")
 
+    def set_learned_h(self, guess: int, record: bool = False, net: "Mlp | None" = None):
+        self._net = net
+        return self._check(lib().sph_set_learned_h(self.ctx, int(guess), 1 if record else 0,
+                                                   net.ptr if net is not None else None),
+                           "sph_set_learned_h")
+
+    def learn_samples(self):
+        """(X, y) of the last step as torch tensors indexed by particle id."""
+        torch = self.torch
+        X = torch.empty((self.n, 6), dtype=torch.float32, device=self.device)
+        y = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        self._check(lib().sph_learn_samples(self.ctx, C.c_void_p(X.data_ptr()),
+                                            C.c_void_p(y.data_ptr())), "sph_learn_samples")
+        self.stream.synchronize()
+        return X, y
+
     def set_spans(self, span_density: int, span_forces: int):
         return self._check(lib().sph_set_spans(self.ctx, int(span_density), int(span_forces)),
                            "sph_set_spans")
@@ -375,3 +422,102 @@ class HostState:
             self.t[f] = torch.as_tensor(np.ascontiguousarray(arrays[f], np.int32)).pin_memory()
         self.t["id"] = torch.as_tensor(np.ascontiguousarray(arrays["id"], np.int64)).pin_memory()
         self.state = state_from_ptrs({k: v.data_ptr() for k, v in self.t.items()})
+
+
+class Mlp:
+    """The smoothing-length network on one device (torch tensors in and out)."""
+
+    def __init__(self, device: str = "cuda:0", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA device required: the network has no CPU fallback")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ptr = C.c_void_p()
+        rc = lib().sph_mlp_create(C.byref(self.ptr), C.c_void_p(self.stream.cuda_stream))
+        if rc != SPH_OK:
+            raise SphError(rc, "sph_mlp_create")
+
+    def _check(self, rc, where):
+        if rc != SPH_OK:
+            raise SphError(rc, where, lib().sph_mlp_last_error(self.ptr).decode())
+        return rc
+
+    def _dev(self, a, dtype):
+        t = self.torch
+        x = a if isinstance(a, t.Tensor) else t.as_tensor(np.asarray(a))
+        return x.to(device=self.device, dtype=dtype).contiguous()
+
+    def set(self, theta, norm):
+        th = np.ascontiguousarray(theta, np.float32)
+        nm = np.ascontiguousarray(norm, np.float32)
+        if th.shape != (MLP_NPARAM,) or nm.shape != (MLP_NNORM,):
+            raise ValueError("theta needs %d values and norm %d" % (MLP_NPARAM, MLP_NNORM))
+        _PF = C.POINTER(C.c_float)
+        return self._check(lib().sph_mlp_set(self.ptr, th.ctypes.data_as(_PF),
+                                             nm.ctypes.data_as(_PF)), "sph_mlp_set")
+
+    def get(self):
+        th = np.empty(MLP_NPARAM, np.float32)
+        nm = np.empty(MLP_NNORM, np.float32)
+        _PF = C.POINTER(C.c_float)
+        self._check(lib().sph_mlp_get(self.ptr, th.ctypes.data_as(_PF), nm.ctypes.data_as(_PF)),
+                    "sph_mlp_get")
+        return th, nm
+
+    def fit_norm(self, X, y):
+        X = self._dev(X, self.torch.float32)
+        y = self._dev(y, self.torch.float32)
+        return self._check(lib().sph_mlp_fit_norm(self.ptr, C.c_void_p(X.data_ptr()),
+                                                  C.c_void_p(y.data_ptr()), X.shape[0]),
+                           "sph_mlp_fit_norm")
+
+    def forward(self, X):
+        X = self._dev(X, self.torch.float32)
+        out = self.torch.empty(X.shape[0], dtype=self.torch.float32, device=self.device)
+        self._check(lib().sph_mlp_forward(self.ptr, C.c_void_p(X.data_ptr()), X.shape[0],
+                                          C.c_void_p(out.data_ptr())), "sph_mlp_forward")
+        self.stream.synchronize()
+        return out
+
+    def loss_grad(self, X, y, idx=None):
+        X = self._dev(X, self.torch.float32)
+        y = self._dev(y, self.torch.float32)
+        m = X.shape[0] if idx is None else len(idx)
+        ix = None if idx is None else self._dev(idx, self.torch.int64)
+        g = self.torch.empty(MLP_NPARAM, dtype=self.torch.float32, device=self.device)
+        loss = C.c_float()
+        self._check(lib().sph_mlp_loss_grad(self.ptr, C.c_void_p(X.data_ptr()),
+                                            C.c_void_p(y.data_ptr()),
+                                            C.c_void_p(ix.data_ptr()) if ix is not None else None,
+                                            m, C.byref(loss), C.c_void_p(g.data_ptr())),
+                    "sph_mlp_loss_grad")
+        return loss.value, g
+
+    def adam_step(self, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        g = self._dev(grad, self.torch.float32)
+        return self._check(lib().sph_mlp_adam_step(self.ptr, C.c_void_p(g.data_ptr()), lr, beta1,
+                                                   beta2, eps), "sph_mlp_adam_step")
+
+    def train_epoch(self, X, y, perm, batch=4096, lr=1e-3) -> float:
+        X = self._dev(X, self.torch.float32)
+        y = self._dev(y, self.torch.float32)
+        p = self._dev(perm, self.torch.int64)
+        loss = C.c_float()
+        self._check(lib().sph_mlp_train_epoch(self.ptr, C.c_void_p(X.data_ptr()),
+                                              C.c_void_p(y.data_ptr()), C.c_void_p(p.data_ptr()),
+                                              p.shape[0], int(batch), float(lr), C.byref(loss)),
+                    "sph_mlp_train_epoch")
+        return loss.value
+
+    def close(self):
+        if self.ptr:
+            lib().sph_mlp_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
