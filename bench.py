@@ -475,6 +475,160 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args, rank: int, world: int, local_rank: int):
+    """The learned smoothing-length guess on the 8M-particle impact.
+
+    Histories: `history_steps` steps of the 1M basalt sphere (plain FP64) and
+    of the 2M impact (FP32 form) with recording on, every `record_every`-th
+    step kept. The network is trained on the GPU by the library's kernels.
+    Then the 8M impact (FP32 form) runs with the previous-H guess, the
+    continuity guess and the network guess from the same primed state;
+    value = particle-steps/s of the network arm.
+    """
+    import torch
+    import torch.distributed as dist
+    from paper_2603_19764_b300 import build, sph
+    from paper_2603_19764_b300 import workloads as wl
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sc = args.learned_scale
+
+    # ---- histories
+    t_hist = time.perf_counter()
+    Xs, ys, sources = [], [], []
+    for name, w, prec in (("basalt sphere 1M, FP64", wl.config(2, scale=sc), 0),
+                          ("impact 2M, FP32 form", wl.config(3, scale=sc), 1)):
+        p = dict(w.params, precision=prec, h_tol=1e-6 if prec else 1e-10)
+        sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
+        sim.set_learned_h(sph.GUESS_PREVIOUS, record=True)
+        sim.prime()
+        kept = 0
+        for k in range(args.history_steps):
+            sim.step(0.0)
+            if (k + 1) % args.record_every == 0:
+                X, y = sim.learn_samples()
+                ok = torch.isfinite(y)
+                Xs.append(X[ok].clone())
+                ys.append(y[ok].clone())
+                kept += 1
+        sim.close()
+        sources.append({"workload": name, "particles": w.n, "steps": args.history_steps,
+                        "kept_steps": kept})
+        del w
+    X = torch.cat(Xs)
+    y = torch.cat(ys)
+    del Xs, ys
+    torch.cuda.synchronize(dev)
+    t_hist = time.perf_counter() - t_hist
+
+    # ---- training on the GPU
+    t_train = time.perf_counter()
+    net = sph.Mlp(device=str(dev))
+    net.set(wl.mlp_init(), np.ones(sph.MLP_NNORM))
+    net.fit_norm(X, y)
+    L0, _ = net.loss_grad(X, y)
+    losses = []
+    for ep in range(args.epochs):
+        perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(ep))
+        losses.append(net.train_epoch(X, y, perm, batch=16384, lr=2e-3))
+    L1, _ = net.loss_grad(X, y)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t_train
+    nsamples = int(X.shape[0])
+    del X, y
+
+    # ---- the 8M impact with each guess
+    w = wl.config(5, scale=sc)
+    p = dict(w.params, precision=1, h_tol=1e-6)
+    arms, states = {}, {}
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    clocks = None
+    for name, guess in (("previous", sph.GUESS_PREVIOUS), ("continuity", sph.GUESS_CONTINUITY),
+                        ("network", sph.GUESS_NETWORK)):
+        sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
+        sim.set_learned_h(guess, net=net if guess == sph.GUESS_NETWORK else None)
+        sim.prime()
+        first = sim.step(0.0)
+        states[name] = _by_id(sim.to_numpy(), ("id", "h", "nngb", "x", "y", "z"))
+        for _ in range(args.warmup):
+            sim.step(0.0)
+        sim.set_timing(True)
+        if world > 1:
+            dist.barrier()
+        if sampler and name == "network":
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        infos = [sim.step(0.0) for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        if sampler and name == "network":
+            clocks = sampler.stop()
+        ph = sim.phase_times()
+        err = None
+        if name == "network" and rank == 0 and not args.no_error:
+            err = sampled_error(sim, w, p, 1)
+        sim.close()
+        nst = max(ph["steps"], 1)
+        arms[name] = {"value": w.n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                      "sweeps_per_particle": statistics.mean(i["sweeps_total"] for i in infos) / w.n,
+                      "first_step_sweeps_per_particle": first["sweeps_total"] / w.n,
+                      "max_sweeps": max(i["sweeps"] for i in infos),
+                      "density_ms_per_step": ph["density"] / nst,
+                      "phases_ms_per_step": {k: v / nst for k, v in ph.items() if k != "steps"},
+                      "gpu_launches": sum(i["kernel_launches"] for i in infos)}
+        if err is not None:
+            arms[name]["error"] = err
+    # neighbour counts after the exact solve, one step from the same primed
+    # state: previous-H guess against the network guess
+    a, b = states["previous"], states["network"]
+    mism = np.nonzero(a["nngb"] != b["nngb"])[0]
+    rel_h = np.abs(b["h"] / a["h"] - 1.0)
+    detail = []
+    X3 = np.stack([a["x"], a["y"], a["z"]], 1)
+    for i in mism[:20]:
+        d = np.sqrt(((X3 - X3[i]) ** 2).sum(1))
+        q = np.abs(d[np.abs(d / a["h"][i] - 1) < 1e-3] / a["h"][i] - 1)
+        detail.append({"id": int(a["id"][i]), "counts": [int(a["nngb"][i]), int(b["nngb"][i])],
+                       "h_rel_diff": float(rel_h[i]),
+                       "closest_abs_r_over_H_minus_1": float(q.min()) if q.size else None})
+    value = arms["network"]["value"]
+    if rank == 0:
+        line = {"metric": "SPH+strength particle-steps/s (8M impact), learned vs previous-H guess",
+                "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": arms["network"]["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64, network bf16", "data": "synthetic",
+                "config": {"workload": "basalt impact 7.2M+0.8M particles, 5 km/s, 45 deg",
+                           "particles": w.n, "precision": "fp32k", "dt": "adaptive, Eq. 38-39",
+                           "l2": "state > L2, no flush"},
+                "training": {"sources": sources, "samples": nsamples, "epochs": args.epochs,
+                             "batch": 16384, "lr": 2e-3, "loss_before": L0, "loss_after": L1,
+                             "epoch_losses": losses, "history_seconds": t_hist,
+                             "train_seconds": t_train},
+                "arms": arms,
+                "sweeps_saved_per_particle": (arms["previous"]["sweeps_per_particle"] -
+                                              arms["network"]["sweeps_per_particle"]),
+                "speedup_vs_previous": value / arms["previous"]["value"],
+                "counts_after_one_step": {"mismatches": int(mism.size), "particles": w.n,
+                                          "max_h_rel_diff": float(rel_h.max()),
+                                          "detail": detail},
+                "clocks": clocks,
+                "gpu_launches": arms["network"]["gpu_launches"]}
+        print(json.dumps(line), flush=True)
+    net.close()
+
+
+def _by_id(g: dict, keys) -> dict:
+    order = np.argsort(g["id"], kind="stable")
+    return {k: g[k][order] for k in keys}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,7 +644,11 @@ def main():
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
-    ap.add_argument("--workload", default="impact", choices=["impact", "batch64"])
+    ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned"])
+    ap.add_argument("--history-steps", type=int, default=200)
+    ap.add_argument("--record-every", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--learned-scale", type=float, default=1.0)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -509,6 +667,8 @@ def main():
     try:
         if args.workload == "batch64":
             run_batch(args, rank, world, local_rank)
+        elif args.workload == "learned":
+            run_learned(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

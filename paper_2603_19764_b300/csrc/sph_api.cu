@@ -75,7 +75,8 @@ void free_all(sph_ctx *c) {
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
                  c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->w.divv,
-                 c->learn.hprev, c->learn.hprop, c->learn.feat, c->learn.x_out, c->learn.y_out};
+                 c->learn.hprev, c->learn.hprop, c->learn.feat[0], c->learn.feat[1],
+                 c->learn.feat[2], c->learn.x_out, c->learn.y_out};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -537,7 +538,8 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   CKI(dalloc(&c->scan_tot, (size_t)(256 * c->ntiles + 1023) / 1024 + 1));
   CKI(dalloc(&c->cell_start, c->max_cells));
   CKI(dalloc(&c->cell_end, c->max_cells));
-  CKI(cudaMalloc(&c->tmp, (size_t)n * 32 * 8));
+  c->tmp_words = 32;
+  CKI(cudaMalloc(&c->tmp, (size_t)n * c->tmp_words * 8));
   CKI(dalloc(&c->partials, (size_t)c->nchunks * 9));
   CKI(dalloc(&c->d_dt, n_sys));
   CKI(cudaMemset(c->d_dt, 0, sizeof(double) * n_sys));
@@ -739,8 +741,15 @@ sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sp
   drop_graph(c);
   LearnArgs &L = c->learn;
   const int64_t n = c->n;
+  if (!record) {   // recording buffers
+    void *p[] = {L.feat[0], L.feat[1], L.feat[2], L.x_out, L.y_out};
+    for (void *q : p)
+      if (q) cudaFree(q);
+    L.feat[0] = L.feat[1] = L.feat[2] = nullptr;
+    L.x_out = L.y_out = nullptr;
+  }
   if (guess == SPH_GUESS_PREVIOUS && !record) {
-    void *p[] = {c->w.divv, L.hprev, L.hprop, L.feat, L.x_out, L.y_out};
+    void *p[] = {c->w.divv, L.hprev, L.hprop};
     for (void *q : p)
       if (q) cudaFree(q);
     memset(&L, 0, sizeof(L));
@@ -750,6 +759,7 @@ sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sp
     return SPH_OK;
   }
   if (!L.hprev) {
+    // samples are written by particle id
     unsigned *bad = nullptr;
     CK(dalloc(&bad, 1));
     CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->stream));
@@ -762,21 +772,29 @@ sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sp
     CK(dalloc(&c->w.divv, n));
     CK(dalloc(&L.hprev, n));
     CK(dalloc(&L.hprop, n));
-    CK(dalloc(&L.feat, (size_t)n * 8));
-    CK(cudaMemsetAsync(L.hprev, 0, sizeof(double) * n, c->stream));
-    CK(cudaMemsetAsync(L.hprop, 0, sizeof(double) * n, c->stream));
   }
   if (record && !L.x_out) {
+    for (int k = 0; k < 3; ++k) CK(dalloc(&L.feat[k], n));
     CK(dalloc(&L.x_out, (size_t)n * 6));
     CK(dalloc(&L.y_out, n));
     CK(cudaMemsetAsync(L.x_out, 0xff, sizeof(float) * 6 * n, c->stream));   // NaN
     CK(cudaMemsetAsync(L.y_out, 0xff, sizeof(float) * n, c->stream));
   }
+  // the sort carries the learned arrays with their particles
+  const int words = 29 + 2 + (record ? 3 : 0) + 2;
+  if (c->tmp_words < words) {
+    CK(cudaFree(c->tmp));
+    c->tmp = nullptr;
+    CK(cudaMalloc(&c->tmp, (size_t)n * words * 8));
+    c->tmp_words = words;
+  }
   L.guess = guess;
   L.record = record;
   L.divv = c->w.divv;
   c->net = guess == SPH_GUESS_NETWORK ? net : nullptr;
-  // a new guess mode starts from the previous radius until it has proposed
+  // the history restarts: the first step after the call records no sample
+  // and the solve starts from the previous radius until a proposal exists
+  CK(cudaMemsetAsync(L.hprev, 0, sizeof(double) * n, c->stream));
   CK(cudaMemsetAsync(L.hprop, 0, sizeof(double) * n, c->stream));
   c->kp.h_guess = guess == SPH_GUESS_PREVIOUS ? nullptr : L.hprop;
   CK(cudaStreamSynchronize(c->stream));

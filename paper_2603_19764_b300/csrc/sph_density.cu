@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   // starting radius: the previous H, or the proposal of the learned form
   double H = A.s.h[ic];
   if (A.p.h_guess) {
-    const double hg = A.p.h_guess[A.s.id[ic]];
+    const double hg = A.p.h_guess[ic];
     if (hg > 0.0) H = hg;
   }
   H = fmin(H, Hcap);

@@ -318,13 +318,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *
 // scratch block and copied back, so the caller's arrays end up in cell order.
 constexpr int kNF64 = 29;   // 28 double arrays + id
 constexpr int kNI32 = 3;
+constexpr int kNLearn = 5;  // learned form: H_prev, H proposal, three feature pairs
 
 struct PermTable {
-  unsigned long long *f64[kNF64];
+  unsigned long long *f64[kNF64 + kNLearn];
   unsigned *i32[kNI32];
+  int nf64;   // 8-byte fields in use
 };
 
-static PermTable perm_table(const sph_state &s) {
+static PermTable perm_table(const sph_state &s, const LearnArgs &L) {
   PermTable t;
   double *d[28] = {s.x,    s.y,    s.z,     s.vx,   s.vy,   s.vz,   s.u,    s.m,    s.h,    s.sxx,
                    s.syy,  s.sxy,  s.sxz,   s.syz,  s.rho,  s.omega, s.pres, s.cs,  s.ax,   s.ay,
@@ -334,6 +336,14 @@ static PermTable perm_table(const sph_state &s) {
   t.i32[0] = (unsigned *)s.nngb;
   t.i32[1] = (unsigned *)s.mat;
   t.i32[2] = (unsigned *)s.flags;
+  t.nf64 = kNF64;
+  // the learned form's per-particle arrays follow their particles
+  if (L.hprev) {
+    t.f64[t.nf64++] = (unsigned long long *)L.hprev;
+    t.f64[t.nf64++] = (unsigned long long *)L.hprop;
+    if (L.feat[0])
+      for (int k = 0; k < 3; ++k) t.f64[t.nf64++] = (unsigned long long *)L.feat[k];
+  }
   return t;
 }
 
@@ -343,8 +353,8 @@ __global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm,
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = perm[i];
 #pragma unroll 4
-    for (int f = 0; f < kNF64; ++f) tmp[f * n + i] = t.f64[f][j];
-    unsigned *t32 = (unsigned *)(tmp + kNF64 * n);
+    for (int f = 0; f < t.nf64; ++f) tmp[f * n + i] = t.f64[f][j];
+    unsigned *t32 = (unsigned *)(tmp + t.nf64 * n);
 #pragma unroll
     for (int f = 0; f < kNI32; ++f) t32[f * n + i] = t.i32[f][j];
   }
@@ -355,8 +365,8 @@ __global__ void __launch_bounds__(kBlock) k_scatter_back(PermTable t, int64_t n,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll 4
-    for (int f = 0; f < kNF64; ++f) t.f64[f][i] = tmp[f * n + i];
-    const unsigned *t32 = (const unsigned *)(tmp + kNF64 * n);
+    for (int f = 0; f < t.nf64; ++f) t.f64[f][i] = tmp[f * n + i];
+    const unsigned *t32 = (const unsigned *)(tmp + t.nf64 * n);
 #pragma unroll
     for (int f = 0; f < kNI32; ++f) t.i32[f][i] = t32[f * n + i];
   }
@@ -416,7 +426,7 @@ cudaError_t launch_sort_permute(sph_ctx *c) {
     vb = tv;
   }
   // after four passes the sorted pairs are back in keys / vals
-  PermTable t = perm_table(c->st);
+  PermTable t = perm_table(c->st, c->learn);
   unsigned long long *tmp = (unsigned long long *)c->tmp;
   k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);

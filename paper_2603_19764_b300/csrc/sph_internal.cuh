@@ -86,7 +86,7 @@ struct KParams {
   const int *sys_chunk;        // nsys + 1 chunk boundaries (device)
   const double *dt;            // current step of every system (device)
   int span_d, span_f;          // group span of the density / force kernels
-  const double *h_guess;       // starting radius of the solve by particle id, or null
+  const double *h_guess;       // starting radius of the solve (sorted order), or null
 };
 
 // Group spans the tuner chooses among.
@@ -123,14 +123,16 @@ struct Work {
   float *divv;                  // tr of the corrected velocity gradient (learned form)
 };
 
-// Arrays of the learned form, indexed by particle id.
+// Arrays of the learned form. hprev, hprop and feat are per-particle
+// arrays in sorted order that the sort permutes with the state; the
+// recorded samples are indexed by particle id.
 struct LearnArgs {
   int guess, record;
-  const float *divv;            // sorted order
+  const float *divv;            // tr G of the last force pass
   double *hprev;                // H of the last solve
   double *hprop;                // starting radius proposed for the next solve
-  float *feat;                  // features of the last step, 8 floats per id
-  float *x_out, *y_out;         // samples of the last step (record)
+  float2 *feat[3];              // features of the last step (record)
+  float *x_out, *y_out;         // samples of the last step, by id (record)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -380,7 +382,8 @@ struct sph_ctx {
   int ntiles;
   int *cell_start, *cell_end;
   int max_cells;
-  void *tmp;            // permutation scratch: 32 words of 8 bytes per particle
+  void *tmp;            // permutation scratch: tmp_words words of 8 bytes per particle
+  int tmp_words;
   double *partials;     // per-chunk diagnostic partial sums
   int nchunks;
   int nsys;

@@ -466,7 +466,7 @@ namespace sphk {
 
 // After the force pass of a step (sorted order): the features of every
 // particle from its converged H, count, density, Omega, dt div v and the
-// H of the previous step (all arrays indexed by particle id); with
+// H of the previous step (per-particle arrays the sort permutes); with
 // recording on, the previous step's features and the target
 // log(H_now / H_prev) as a training sample; with a guess mode, the starting
 // radius of the next step's solve: H exp(-dt div v / 3) (continuity) or
@@ -488,30 +488,35 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
     const int64_t ic = valid ? i : ch * 32;
     const int64_t id = s.id[ic];
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, ic) : 0;
+    // the features are FP32 quantities: ratios, logarithms and the cube
+    // root in FP32
     const double H = s.h[ic];
     const float dtdiv = (float)P.dt[sy] * L.divv[ic];
-    const double hp = L.hprev[id];
+    const double hp = L.hprev[ic];
     const sph_material &M = P.mats[s.mat[ic] & (SPH_MAX_MATERIALS - 1)];
-    const double hbar = cbrt(3.0 * P.n_ngb * s.m[ic] / (4.0 * kPi * M.rho0));
+    // (no FP64 division: it costs tens of FP64 operations on this part)
+    const float rho0 = (float)M.rho0;
+    const float hbar = cbrtf((float)(3.0 * P.n_ngb / (4.0 * kPi)) * ((float)s.m[ic] / rho0));
+    const float lhp = hp > 0.0 ? logf((float)H / (float)hp) : 0.f;
     float f[NIN];
-    f[0] = (float)log(H / hbar);
-    f[1] = (float)((double)s.nngb[ic] / P.n_ngb - 1.0);
-    f[2] = (float)log(s.rho[ic] / M.rho0);
+    f[0] = logf((float)H / hbar);
+    f[1] = (float)s.nngb[ic] / (float)P.n_ngb - 1.f;
+    f[2] = logf((float)s.rho[ic] / rho0);
     f[3] = dtdiv;
-    f[4] = hp > 0.0 ? (float)log(H / hp) : 0.f;
+    f[4] = lhp;
     f[5] = (float)(s.omega[ic] - 1.0);
     if (valid && L.record) {
       float *xo = L.x_out + id * NIN;
-      const float *fp = L.feat + id * 8;
       const bool have = hp > 0.0;
 #pragma unroll
-      for (int k = 0; k < NIN; ++k) xo[k] = have ? fp[k] : NAN;
-      L.y_out[id] = have ? (float)log(H / hp) : NAN;
-    }
-    if (valid && L.feat) {
-      float *fp = L.feat + id * 8;
+      for (int k = 0; k < 3; ++k) {
+        const float2 fp = L.feat[k][ic];
+        xo[2 * k] = have ? fp.x : NAN;
+        xo[2 * k + 1] = have ? fp.y : NAN;
+      }
+      L.y_out[id] = have ? lhp : NAN;
 #pragma unroll
-      for (int k = 0; k < NIN; ++k) fp[k] = f[k];
+      for (int k = 0; k < 3; ++k) L.feat[k][ic] = make_float2(f[2 * k], f[2 * k + 1]);
     }
     float r = 0.f;
     if (L.guess == SPH_GUESS_CONTINUITY) r = -dtdiv / 3.f;
@@ -539,9 +544,9 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
       if (L.guess != SPH_GUESS_PREVIOUS) {
         const float lo = -0.22314355f, hi = 0.22314355f;   // log 0.8, log 1.25
         r = isfinite(r) ? fminf(fmaxf(r, lo), hi) : 0.f;
-        L.hprop[id] = H * exp((double)r);
+        L.hprop[ic] = H * (double)expf(r);
       }
-      L.hprev[id] = H;
+      L.hprev[ic] = H;
     }
   }
 }

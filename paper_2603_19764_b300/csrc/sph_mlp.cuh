@@ -78,6 +78,16 @@ __device__ __forceinline__ void load_net(Smem &S, const Net &N, bool with_transp
   }
 }
 
+// tanh x = 1 - 2 / (e^(2x) + 1), an identity of the hyperbolic functions,
+// evaluated with the hardware exponential and the fast divide: about six
+// instructions where the library tanhf takes several times more, with an
+// absolute error of a few 1e-7 (the first layer is rounded to bf16, 4e-3
+// relative, right after). Saturates to +-1 when e^(2x) overflows or
+// underflows.
+__device__ __forceinline__ float tanh_fast(float x) {
+  return 1.f - __fdividef(2.f, __expf(2.f * x) + 1.f);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // lo in the low half
   return *reinterpret_cast<uint32_t *>(&v);
@@ -144,10 +154,10 @@ __device__ __forceinline__ void forward_tile(const Smem &S, const uint32_t (&ax)
     load_b(S.w1, LD1, 8 * nt, 0, b0, b1);
     mma16816(c, ax, b0, b1);
     const int col = 8 * nt + 2 * t;
-    T.a1[nt][0] = tanhf(c[0] + S.b1[col]);
-    T.a1[nt][1] = tanhf(c[1] + S.b1[col + 1]);
-    T.a1[nt][2] = tanhf(c[2] + S.b1[col]);
-    T.a1[nt][3] = tanhf(c[3] + S.b1[col + 1]);
+    T.a1[nt][0] = tanh_fast(c[0] + S.b1[col]);
+    T.a1[nt][1] = tanh_fast(c[1] + S.b1[col + 1]);
+    T.a1[nt][2] = tanh_fast(c[2] + S.b1[col]);
+    T.a1[nt][3] = tanh_fast(c[3] + S.b1[col + 1]);
   }
   uint32_t a1f[4][4];
   to_a(T.a1, a1f);
@@ -162,10 +172,10 @@ __device__ __forceinline__ void forward_tile(const Smem &S, const uint32_t (&ax)
       mma16816(c, a1f[kt], b0, b1);
     }
     const int col = 8 * nt + 2 * t;
-    T.a2[nt][0] = tanhf(c[0] + S.b2[col]);
-    T.a2[nt][1] = tanhf(c[1] + S.b2[col + 1]);
-    T.a2[nt][2] = tanhf(c[2] + S.b2[col]);
-    T.a2[nt][3] = tanhf(c[3] + S.b2[col + 1]);
+    T.a2[nt][0] = tanh_fast(c[0] + S.b2[col]);
+    T.a2[nt][1] = tanh_fast(c[1] + S.b2[col + 1]);
+    T.a2[nt][2] = tanh_fast(c[2] + S.b2[col]);
+    T.a2[nt][3] = tanh_fast(c[3] + S.b2[col + 1]);
     p0 += T.a2[nt][0] * S.w3[col] + T.a2[nt][1] * S.w3[col + 1];
     p1 += T.a2[nt][2] * S.w3[col] + T.a2[nt][3] * S.w3[col + 1];
   }

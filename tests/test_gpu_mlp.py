@@ -138,3 +138,29 @@ def test_training_on_the_gpu_fits_a_smooth_function():
                           y.astype(np.float64), bf16=True)
     assert abs(Lo - L1) <= 1e-3 * L1 + 1e-7
     net.close()
+
+
+def test_hidden_tanh_against_numpy():
+    """One path through the network isolates the second layer's tanh, which
+    stays FP32: out = w3 tanh(beta bf16(tanh(alpha x))) + b3. The kernels'
+    tanh (from the exponential identity) must stay within 1e-6 absolute of
+    numpy's, apart from the rare first-layer value that the two round to
+    different bf16 neighbours."""
+    W1 = np.zeros((64, 6))
+    W2 = np.zeros((64, 64))
+    W3 = np.zeros(64)
+    W1[9, 0], W2[30, 9], W3[30] = 1.0, 2.5, 1.0
+    theta = mlp.pack(W1, np.zeros(64), W2, np.zeros(64), W3, 0.0)
+    norm = np.concatenate([np.zeros(6), np.ones(6), [0.0, 1.0]])
+    x = np.linspace(-6.0, 6.0, 40001).astype(np.float32)
+    X = np.zeros((x.size, 6), np.float32)
+    X[:, 0] = x
+    net = _net(theta, norm)
+    got = net.forward(X).cpu().numpy().astype(np.float64)
+    net.close()
+    xb = mlp.bf16_round(x.astype(np.float64))
+    want = np.tanh(2.5 * mlp.bf16_round(np.tanh(xb)))
+    err = np.abs(got - want)
+    assert np.quantile(err, 0.999) <= 1e-6
+    assert np.max(err) <= 2.5 * 2.0 ** -8      # one bf16 step of the first layer
+    assert np.max(np.abs(got)) <= 1.0
