@@ -351,9 +351,11 @@ sph_status sph_prime(sph_ctx *c, sph_step_info *info);
  * phases of every sph_step: 0 neighbours (drift, keys, sort, permutation,
  * cells), 1 prediction and packing, 2 density solve, 3 EOS, yield and
  * packing, 4 pair loop with finalize, 5 kicks and reductions.
- * sph_set_timing(c, 1) enables it and zeroes the accumulators;
+ * sph_set_timing(c, 1) enables it and zeroes the accumulators. Steps
+ * replayed from a graph (sph_set_graph) are not phase-timed;
  * sph_phase_times copies up to n accumulated milliseconds per phase into
- * ms and the number of timed steps into *steps (may be NULL). */
+ * ms and the number of timed steps into *steps (may be NULL). Phase 4
+ * includes the learned form's per-step kernel. */
 #define SPH_NUM_PHASES 6
 sph_status sph_set_timing(sph_ctx *c, int32_t on);
 sph_status sph_phase_times(const sph_ctx *c, double *ms, int32_t n, int32_t *steps);

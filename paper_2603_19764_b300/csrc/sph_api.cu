@@ -163,9 +163,11 @@ sph_status upload_dt(sph_ctx *c) {
   return SPH_OK;
 }
 
-// Phase marker k (0..SPH_NUM_PHASES) when timing is on.
+// Phase marker k (0..SPH_NUM_PHASES) when timing is on. Steps replayed
+// from a graph are not phase-timed (events recorded by graph nodes give no
+// elapsed times), so nothing is recorded while capturing.
 cudaError_t mark(sph_ctx *c, int k) {
-  return c->timing ? cudaEventRecord(c->ev[k], c->stream) : cudaSuccess;
+  return c->timing && !c->capturing ? cudaEventRecord(c->ev[k], c->stream) : cudaSuccess;
 }
 
 sph_status run_neighbours(sph_ctx *c, int drift) {
@@ -271,7 +273,8 @@ sph_status tune_end(sph_ctx *c) {
 // Synchronises.
 sph_status run_step(sph_ctx *c, sph_step_info *info) {
   tune_begin(c);
-  if (!c->use_graph || c->tune_now) {
+  const bool via_graph = c->use_graph && !c->tune_now;
+  if (!via_graph) {
     sph_status s = enqueue_step(c);
     if (s != SPH_OK) return s;
     CK(cudaStreamSynchronize(c->stream));
@@ -281,11 +284,13 @@ sph_status run_step(sph_ctx *c, sph_step_info *info) {
     CK(cudaStreamWaitEvent(c->gstream, c->fence, 0));
     if (!c->graph_exec) {
       c->stream = c->gstream;
+      c->capturing = 1;
       const cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
       sph_status s = e == cudaSuccess ? enqueue_step(c) : fail_cuda(c, e, "cudaStreamBeginCapture");
       cudaGraph_t g = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
       c->stream = caller;
+      c->capturing = 0;
       if (s != SPH_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
@@ -301,7 +306,7 @@ sph_status run_step(sph_ctx *c, sph_step_info *info) {
     CK(cudaStreamSynchronize(c->gstream));
   }
   const sph_status s = finish_sync(c, info);
-  sph_status t = collect_times(c);
+  sph_status t = via_graph ? SPH_OK : collect_times(c);
   if (t == SPH_OK) t = tune_end(c);
   return s != SPH_OK ? s : t;
 }
@@ -580,7 +585,7 @@ sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats
 sph_status sph_set_timing(sph_ctx *c, int32_t on) {
   ENTER(c);
   CK(cudaStreamSynchronize(c->stream));
-  drop_graph(c);  // a captured graph holds the phase events of its capture
+
   if (on && !c->timing) {
     for (int k = 0; k <= SPH_NUM_PHASES; ++k) CK(cudaEventCreate(&c->ev[k]));
   }

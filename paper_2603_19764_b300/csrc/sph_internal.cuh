@@ -400,6 +400,7 @@ struct sph_ctx {
   int num_sms;
   int timing;
   int use_graph;
+  int capturing;                // the step is being captured into a graph
   cudaStream_t gstream;         // library stream that graphs are captured on
   cudaEvent_t fence;            // caller stream -> library stream ordering
   cudaGraphExec_t graph_exec;   // captured step
