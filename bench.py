@@ -258,7 +258,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sim.prime()
     # the chosen form: group spans tuned on the first steps, then the step
     # replayed from a CUDA graph
-    if args.tune > 0:
+    if args.spans:
+        sim.set_spans(*[int(v) for v in args.spans.split(",")])
+    elif args.tune > 0:
         sim.autotune(args.tune)
         for _ in range(3 * args.tune):
             sim.step(0.0)
@@ -661,6 +663,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--tune", type=int, default=2)
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--spans", default="", help="density,forces group spans (no tuning)")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned"])
     ap.add_argument("--history-steps", type=int, default=200)

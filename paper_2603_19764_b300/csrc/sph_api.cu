@@ -479,6 +479,10 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.eta_c = p->eta_c;
   kp.eta_a = p->eta_a;
   kp.h_tol = p->h_tol;
+  kp.av_alpha_f = (float)p->av_alpha;
+  kp.av_beta_f = (float)p->av_beta;
+  kp.av_eps_f = (float)p->av_eps;
+  kp.h_tol_f = (float)p->h_tol;
   kp.max_sweeps = p->max_sweeps;
   kp.h_cap_factor = p->h_cap_factor;
   kp.precision = p->precision;

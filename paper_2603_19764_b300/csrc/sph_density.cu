@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const T mi = p.w;
   const sph_material &M = A.p.mats[A.s.mat[ic] & (SPH_MAX_MATERIALS - 1)];
   const T target = (T)A.p.n_ngb * mi;
-  const T tol = (T)A.p.h_tol;
+  const T tol = pconst<T>(A.p.h_tol, A.p.h_tol_f);
   const double Hcap =
       A.p.h_cap_factor * (double)cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
   // starting radius: the previous H, or the proposal of the learned form

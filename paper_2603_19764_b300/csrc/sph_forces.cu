@@ -103,21 +103,37 @@ cudaError_t launch_eos_pack(sph_ctx *c) {
 }
 
 // ------------------------------------------------------------- pair loop
-// Running sum: plain in FP64, Kahan-compensated in FP32.
+// Running sums of the pair loop. FP64 form: plain. FP32 form, energy and
+// velocity-gradient sums (du, F): compensated in blocks -- the terms of
+// kSumBlock consecutive pairs are added plainly, then each block sum enters
+// a Kahan sum, which bounds the error by a block's rounding (kSumBlock ulp
+// of the block's terms) at a quarter of the cost of compensating every
+// term. The correction-tensor sums C^-1 = sum g x x (Eq. 21) are added
+// plainly in both forms: their diagonal terms share one sign, and their
+// rounding error is a few ulp of the matrix norm.
+constexpr int kSumBlock = 4;
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
+  __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ T get() const { return s; }
 };
 template <> struct Acc<float> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = v - c;
+  float p = 0.f, s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) { p += v; }
+  __device__ __forceinline__ void flush() {
+    const float y = p - c;
     const float t = s + y;
     c = (t - s) - y;
     s = t;
+    p = 0.f;
   }
   __device__ __forceinline__ float get() const { return s - c; }
+};
+template <typename T> struct Plain {
+  T s = 0;
+  __device__ __forceinline__ void add(T v) { s += v; }
+  __device__ __forceinline__ T get() const { return s; }
 };
 
 struct ForceArgs {
@@ -176,11 +192,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
   const T sxz = a2.x * im, syz = a2.y * im, iOr = a2.z * im;
   const T Hi = p.w, Hi2 = p.w * p.w, invHi = a3.y, Ki = a3.z;
   const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi = a3.x;
-  const T al = (T)A.p.av_alpha, be = (T)A.p.av_beta, ep = (T)A.p.av_eps;
+  const T al = pconst<T>(A.p.av_alpha, A.p.av_alpha_f);
+  const T be = pconst<T>(A.p.av_beta, A.p.av_beta_f);
+  const T ep = pconst<T>(A.p.av_eps, A.p.av_eps_f);
 
   T ax = 0, ay = 0, az = 0, mumax = 0;
-  Acc<T> du, F0, F1, F2, F3, F4, F5, F6, F7, F8, C0, C1, C2, C3, C4, C5;
-  int npairs = 0;
+  Acc<T> du, F0, F1, F2, F3, F4, F5, F6, F7, F8;
+  Plain<T> C0, C1, C2, C3, C4, C5;
+  int npairs = 0, blk = 0;
   long long cand = 0;
 
   unsigned todo = __ballot_sync(kFull, valid);
@@ -290,6 +309,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           C0.add(gx * dx); C1.add(gx * dy); C2.add(gx * dz);
           C3.add(gy * dy); C4.add(gy * dz); C5.add(gs * dz * dz);
           ++npairs;
+          if (++blk == kSumBlock) {   // lanes stay in step: one pair per pass each
+            blk = 0;
+            du.flush(); F0.flush(); F1.flush(); F2.flush(); F3.flush();
+            F4.flush(); F5.flush(); F6.flush(); F7.flush(); F8.flush();
+          }
         }
       }
       __syncwarp();
@@ -297,6 +321,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
     }
   }
 
+  du.flush(); F0.flush(); F1.flush(); F2.flush(); F3.flush();
+  F4.flush(); F5.flush(); F6.flush(); F7.flush(); F8.flush();
   // ---------------------------------------- finalize (Eq. 21-29, 38-39)
   int fallback = 0;
   if (valid) {

@@ -86,8 +86,16 @@ struct KParams {
   const int *sys_chunk;        // nsys + 1 chunk boundaries (device)
   const double *dt;            // current step of every system (device)
   int span_d, span_f;          // group span of the density / force kernels
+  // FP32 copies of the constants the FP32 pair loops use, so that a
+  // constant the compiler reloads inside a loop needs no FP64 conversion
+  float av_alpha_f, av_beta_f, av_eps_f, h_tol_f;
   const double *h_guess;       // starting radius of the solve (sorted order), or null
 };
+
+// A run-time constant in the pair loops' arithmetic type.
+template <typename T> __device__ __forceinline__ T pconst(double d, float f);
+template <> __device__ __forceinline__ float pconst<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pconst<double>(double d, float) { return d; }
 
 // Group spans the tuner chooses among.
 constexpr int kNumSpans = 3;
