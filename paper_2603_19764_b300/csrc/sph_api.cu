@@ -69,8 +69,7 @@ void free_all(sph_ctx *c) {
   void *dev[] = {c->d_mats, c->d_gtab, c->d_phitab, c->d_radii, c->w.vp[0], c->w.vp[1],
                  c->w.vp[2], c->w.up, c->w.sp[0], c->w.sp[1], c->w.sp[2], c->w.sp[3],
                  c->w.sp[4], c->w.vsig, c->w.edot2, c->w.yld, c->w.cc, c->w.pos32, c->w.pos64,
-                 c->w.fj32[0], c->w.fj32[1], c->w.fj32[2], c->w.fj32[3], c->w.fj64[0],
-                 c->w.fj64[1], c->w.fj64[2], c->w.fj64[3], c->w.posh32, c->w.posh64,
+                 c->w.fj32, c->w.fj64, c->w.posh32, c->w.posh64,
                  c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
@@ -530,12 +529,12 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   if (fp32) {
     CKI(dalloc(&w.pos32, n));
     CKI(dalloc(&w.posh32, n));
-    for (int k = 0; k < 4; ++k) CKI(dalloc(&w.fj32[k], n));
+    CKI(dalloc(&w.fj32, (size_t)4 * n));
     for (int k = 0; k < 3; ++k) CKI(dalloc(&w.fs32[k], n));
   } else {
     CKI(dalloc(&w.pos64, n));
     CKI(dalloc(&w.posh64, n));
-    for (int k = 0; k < 4; ++k) CKI(dalloc(&w.fj64[k], n));
+    CKI(dalloc(&w.fj64, (size_t)4 * n));
     for (int k = 0; k < 3; ++k) CKI(dalloc(&w.fs64[k], n));
   }
   CKI(dalloc(&c->keys, n));

@@ -32,22 +32,22 @@ template <> struct Packed<float> {
   using V4 = float4;
   static __device__ __forceinline__ const float4 *pos(const Work &w) { return w.pos32; }
   static __device__ __forceinline__ float4 *posh(const Work &w) { return w.posh32; }
-  static __device__ __forceinline__ float4 *fj(const Work &w, int k) { return w.fj32[k]; }
+  static __device__ __forceinline__ float4 *rec(const Work &w) { return w.fj32; }
   static __device__ __forceinline__ float4 *fs(const Work &w, int k) { return w.fs32[k]; }
 };
 template <> struct Packed<double> {
   using V4 = double4_32a;
   static __device__ __forceinline__ const double4_32a *pos(const Work &w) { return w.pos64; }
   static __device__ __forceinline__ double4_32a *posh(const Work &w) { return w.posh64; }
-  static __device__ __forceinline__ double4_32a *fj(const Work &w, int k) { return w.fj64[k]; }
+  static __device__ __forceinline__ double4_32a *rec(const Work &w) { return w.fj64; }
   static __device__ __forceinline__ double4_32a *fs(const Work &w, int k) { return w.fs64[k]; }
 };
 
 // Per particle: EOS at (rho, u_eval), yield, radial return of the
 // evaluation stress, and the packed neighbour / own data of the pair loop:
-//   posh = (x, y, z, H)                  fj0 = (v, m)
-//   fj1 = m/(Omega rho^2) (sxx, syy, szz, sxy)   with s = -P I + S
-//   fj2 = (m sxz', m syz', m/(Omega rho), c)     fj3 = (rho, 1/H, cG/H^5, H)
+//   posh = (x, y, z, H), and the neighbour record of 4 consecutive vectors
+//   rec0 = (v, m)   rec1 = m/(Omega rho^2) (sxx, syy, szz, sxy), s = -P I + S
+//   rec2 = (m sxz', m syz', m/(Omega rho), c)   rec3 = (rho, 1/H, cG/H^5, H)
 //   fs0 = (Sxx, Syy, Sxy, Sxz)   fs1 = (Syz, Gamma, c_L, 0)   fs2 = (g, 0)
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_t n, KParams P) {
@@ -80,11 +80,12 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
     T gx[3];
     ext_field_t<T>(P, s.x[i], s.y[i], s.z[i], gx, nullptr);
     Packed<T>::posh(w)[i] = V::make(pp.x, pp.y, pp.z, H);
-    Packed<T>::fj(w, 0)[i] = V::make((T)w.vp[0][i], (T)w.vp[1][i], (T)w.vp[2][i], m);
-    Packed<T>::fj(w, 1)[i] =
+    typename V::type *rec = Packed<T>::rec(w) + 4 * i;
+    rec[0] = V::make((T)w.vp[0][i], (T)w.vp[1][i], (T)w.vp[2][i], m);
+    rec[1] =
         V::make((S[0] - e.P) * inv, (S[1] - e.P) * inv, (-S[0] - S[1] - e.P) * inv, S[2] * inv);
-    Packed<T>::fj(w, 2)[i] = V::make(S[3] * inv, S[4] * inv, m / (om * rho), e.c);
-    Packed<T>::fj(w, 3)[i] = V::make(rho, ih, K, H);
+    rec[2] = V::make(S[3] * inv, S[4] * inv, m / (om * rho), e.c);
+    rec[3] = V::make(rho, ih, K, H);
     Packed<T>::fs(w, 0)[i] = V::make(S[0], S[1], S[2], S[3]);
     Packed<T>::fs(w, 1)[i] = V::make(S[4], Gam, cl, T(0));
     Packed<T>::fs(w, 2)[i] = V::make(gx[0], gx[1], gx[2], T(0));
@@ -175,8 +176,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
   const bool valid = i < R.end;
   const int64_t ic = valid ? i : base;
   const V4 *posh = PK::posh(A.w);
-  const V4 *fj0 = PK::fj(A.w, 0), *fj1 = PK::fj(A.w, 1), *fj2 = PK::fj(A.w, 2),
-           *fj3 = PK::fj(A.w, 3);
+  const V4 *rec = PK::rec(A.w);   // 4 consecutive vectors per particle
 
   const Grid g = R.grid;
   const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
 
   // particle i (evaluation state, packed)
   const V4 p = V::ld(posh, ic);
-  const V4 a0 = V::ld(fj0, ic), a1 = V::ld(fj1, ic), a2 = V::ld(fj2, ic), a3 = V::ld(fj3, ic);
+  const V4 a0 = V::ld(rec, 4 * ic), a1 = V::ld(rec, 4 * ic + 1), a2 = V::ld(rec, 4 * ic + 2),
+           a3 = V::ld(rec, 4 * ic + 3);
   const T im = T(1) / a0.w;
   const T sxx = a1.x * im, syy = a1.y * im, szz = a1.z * im, sxy = a1.w * im;
   const T sxz = a2.x * im, syz = a2.y * im, iOr = a2.z * im;
@@ -266,7 +267,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           mk &= mk - 1u;
           const int j = Li[k];
           const V4 q = Lr[k];
-          const V4 f0 = V::ld(fj0, j), f1 = V::ld(fj1, j), f2 = V::ld(fj2, j), f3 = V::ld(fj3, j);
+          const V4 *rj = rec + 4 * j;
+          const V4 f0 = V::ld(rj, 0), f1 = V::ld(rj, 1), f2 = V::ld(rj, 2), f3 = V::ld(rj, 3);
           const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
           const T r = root(r2);

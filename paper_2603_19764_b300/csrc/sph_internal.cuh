@@ -124,8 +124,8 @@ struct Work {
   double4_32a *pos64;           // absolute x, y, z and m (FP64 form)
   float4 *posh32;               // positions with H (force pass)
   double4_32a *posh64;
-  float4 *fj32[4];              // force-side neighbour data (FP32 form)
-  double4_32a *fj64[4];         // force-side neighbour data (FP64 form)
+  float4 *fj32;                 // force-side neighbour records, 4 vectors per
+  double4_32a *fj64;            // particle, contiguous (FP32 / FP64 form)
   float4 *fs32[3];              // own stress, shear modulus, c_L, external g
   double4_32a *fs64[3];
   float *divv;                  // tr of the corrected velocity gradient (learned form)
