@@ -214,18 +214,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
     const T Rb = wmax(act ? Hi : T(0));
     const T Rf = tmax(Rb, hmax_all);
     const Box<T> bx = group_box(act, xi, yi, zi);
-    Stager<T> sg = make_stager<T, REL>(bx, Rf, g, invL, G.rx, G.ry, G.rz);
+    Stager sg = make_stager<T, REL>(bx, Rf, g, invL, G.rx, G.ry, G.rz);
     for (;;) {
       // stage candidates
       int nl = 0;
       while (nl <= CAP - 32) {
-        if (sg.jb >= sg.je &&
-            !stager_next_cell<T, REL>(sg, g, A.cell_start, A.cell_end, Lt))
+        int j;
+        bool ok;
+        T ox, oy, oz;
+        if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, G.rx, G.ry, G.rz, j, ok,
+                                  ox, oy, oz))
           break;
-        const int j = sg.jb + lane;
-        const bool ok = j < sg.je;
         const V4 q = ok ? V::ld(posh, j) : V::make(0, 0, 0, 0);
-        const T xj = q.x + sg.ox, yj = q.y + sg.oy, zj = q.z + sg.oz;
+        const T xj = q.x + ox, yj = q.y + oy, zj = q.z + oz;
         const T R = tmax(Rb, q.w);
         const bool keep =
             ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R;
@@ -236,7 +237,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           Li[at] = j;
         }
         nl += __popc(bal);
-        sg.jb += 32;
       }
       cand += nl;
       __syncwarp();

@@ -96,104 +96,128 @@ __device__ __forceinline__ Box<T> group_box(bool act, T x, T y, T z) {
   return b;
 }
 
-// Resumable walk over the particles of the cells overlapping box +- R.
-// Coordinates are relative to the origin of the reference cell (FP32 form)
-// or absolute (FP64 form); (ox, oy, oz) converts the staged cell's packed
-// positions into that frame. The cell counters advance without integer
-// division, and the FP32 offsets are kept as exact integer-valued floats.
-template <typename T> struct Stager {
-  int kx0, kx1, ky0, ky1, kz0, kz1;  // cell range
-  int x, y, z;                       // next cell
-  T fx0, fy0, fx, fy, fz;            // (cell - reference) as exact floats
-  int jb, je;                        // current chunk start, cell end
-  T ox, oy, oz;                      // coordinate offset of the current cell
-  bool done;                         // no further cell to fetch
+// Resumable stream of the particles of the cells overlapping box +- R, in
+// cell order (z, then y, then x) and sorted order within a cell. The cell
+// ranges are read 32 cells at a time, one cell per lane, so their loads
+// overlap instead of forming a chain; a prefix sum over the lanes then maps
+// stream positions to (cell, particle), and every chunk of 32 positions
+// fills all lanes whatever the cell sizes. Coordinates are relative to the
+// origin of the reference cell (FP32 form) or absolute (FP64 form): a
+// particle's offset is (its cell - reference cell) * L, formed from exact
+// integer-valued floats.
+struct Stager {
+  int kx0, ky0, kz0;       // first cell of the range
+  int nx, ny, ncell;       // range extents in x and y, cells in the range
+  int c0;                  // first cell of the next batch
+  int s0, pre, off;        // this lane's cell of the batch: start, exclusive
+                           // prefix of the counts, packed offset to the
+                           // reference cell (10 bits per axis, biased 512)
+  int total, pos;          // particles in the batch, next stream position
 };
 
-// All staged: no further cell and the current one consumed.
-template <typename T> __device__ __forceinline__ bool stager_finished(const Stager<T> &s) {
-  return s.done && s.jb >= s.je;
+// All staged: no cell left and the batch consumed.
+__device__ __forceinline__ bool stager_finished(const Stager &s) {
+  return s.c0 >= s.ncell && s.pos >= s.total;
 }
 
-// Set up a stager for box +- R. REL: coordinates relative to cell (rx, ry, rz).
+// Set up a stager for box +- R. REL: box in coordinates relative to cell
+// (rx, ry, rz).
 template <typename T, bool REL>
-__device__ __forceinline__ Stager<T> make_stager(const Box<T> &b, T R, const Grid &g, T invL,
-                                                 int rx, int ry, int rz) {
-  Stager<T> s;
+__device__ __forceinline__ Stager make_stager(const Box<T> &b, T R, const Grid &g, T invL,
+                                              int rx, int ry, int rz) {
+  int kx0, kx1, ky0, ky1, kz0, kz1;
   if (REL) {
-    s.kx0 = rx + (int)floorf((float)((b.x0 - R) * invL));
-    s.kx1 = rx + (int)floorf((float)((b.x1 + R) * invL));
-    s.ky0 = ry + (int)floorf((float)((b.y0 - R) * invL));
-    s.ky1 = ry + (int)floorf((float)((b.y1 + R) * invL));
-    s.kz0 = rz + (int)floorf((float)((b.z0 - R) * invL));
-    s.kz1 = rz + (int)floorf((float)((b.z1 + R) * invL));
+    kx0 = rx + (int)floorf((float)((b.x0 - R) * invL));
+    kx1 = rx + (int)floorf((float)((b.x1 + R) * invL));
+    ky0 = ry + (int)floorf((float)((b.y0 - R) * invL));
+    ky1 = ry + (int)floorf((float)((b.y1 + R) * invL));
+    kz0 = rz + (int)floorf((float)((b.z0 - R) * invL));
+    kz1 = rz + (int)floorf((float)((b.z1 + R) * invL));
   } else {
-    s.kx0 = (int)floor(((double)b.x0 - (double)R - g.lo[0]) * (double)invL);
-    s.kx1 = (int)floor(((double)b.x1 + (double)R - g.lo[0]) * (double)invL);
-    s.ky0 = (int)floor(((double)b.y0 - (double)R - g.lo[1]) * (double)invL);
-    s.ky1 = (int)floor(((double)b.y1 + (double)R - g.lo[1]) * (double)invL);
-    s.kz0 = (int)floor(((double)b.z0 - (double)R - g.lo[2]) * (double)invL);
-    s.kz1 = (int)floor(((double)b.z1 + (double)R - g.lo[2]) * (double)invL);
+    kx0 = (int)floor(((double)b.x0 - (double)R - g.lo[0]) * (double)invL);
+    kx1 = (int)floor(((double)b.x1 + (double)R - g.lo[0]) * (double)invL);
+    ky0 = (int)floor(((double)b.y0 - (double)R - g.lo[1]) * (double)invL);
+    ky1 = (int)floor(((double)b.y1 + (double)R - g.lo[1]) * (double)invL);
+    kz0 = (int)floor(((double)b.z0 - (double)R - g.lo[2]) * (double)invL);
+    kz1 = (int)floor(((double)b.z1 + (double)R - g.lo[2]) * (double)invL);
   }
-  s.kx0 = max(s.kx0, 0);
-  s.ky0 = max(s.ky0, 0);
-  s.kz0 = max(s.kz0, 0);
-  s.kx1 = min(s.kx1, g.dims[0] - 1);
-  s.ky1 = min(s.ky1, g.dims[1] - 1);
-  s.kz1 = min(s.kz1, g.dims[2] - 1);
-  s.x = s.kx0;
-  s.y = s.ky0;
-  s.z = s.kz0;
-  s.fx0 = (T)(s.kx0 - rx);
-  s.fx = s.fx0;
-  s.fy0 = (T)(s.ky0 - ry);
-  s.fy = s.fy0;
-  s.fz = (T)(s.kz0 - rz);
-  s.jb = 0;
-  s.je = 0;
-  s.ox = s.oy = s.oz = T(0);
-  s.done = s.kx0 > s.kx1 || s.ky0 > s.ky1 || s.kz0 > s.kz1;
+  Stager s;
+  s.kx0 = max(kx0, 0);
+  s.ky0 = max(ky0, 0);
+  s.kz0 = max(kz0, 0);
+  s.nx = min(kx1, g.dims[0] - 1) - s.kx0 + 1;
+  s.ny = min(ky1, g.dims[1] - 1) - s.ky0 + 1;
+  const int nz = min(kz1, g.dims[2] - 1) - s.kz0 + 1;
+  s.ncell = (s.nx > 0 && s.ny > 0 && nz > 0) ? s.nx * s.ny * nz : 0;
+  s.c0 = 0;
+  s.s0 = 0;
+  s.pre = 0;
+  s.off = 0;
+  s.total = 0;
+  s.pos = 0;
+  (void)rx;
+  (void)ry;
+  (void)rz;
   return s;
 }
 
-// Advance to the next non-empty cell; false when the range is exhausted.
+// The next 32 stream positions, one per lane: particle index j (valid when
+// ok) and its coordinate offset. false when the stream is exhausted
+// (warp-uniform).
 template <typename T, bool REL>
-__device__ __forceinline__ bool stager_next_cell(Stager<T> &s, const Grid &g, const int *cstart,
-                                                 const int *cend, T Lt) {
-  while (!s.done) {
-    const int c = g.cell_off + (s.z * g.dims[1] + s.y) * g.dims[0] + s.x;
-    const T fx = s.fx, fy = s.fy, fz = s.fz;
-    // step to the following cell of the range
-    if (s.x < s.kx1) {
-      ++s.x;
-      s.fx += T(1);
-    } else {
-      s.x = s.kx0;
-      s.fx = s.fx0;
-      if (s.y < s.ky1) {
-        ++s.y;
-        s.fy += T(1);
-      } else {
-        s.y = s.ky0;
-        s.fy = s.fy0;
-        if (s.z < s.kz1) {
-          ++s.z;
-          s.fz += T(1);
-        } else {
-          s.done = true;
-        }
-      }
+__device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int *cstart,
+                                             const int *cend, T Lt, int rx, int ry, int rz,
+                                             int &j, bool &ok, T &ox, T &oy, T &oz) {
+  const int lane = threadIdx.x & 31;
+  while (s.pos >= s.total) {
+    if (s.c0 >= s.ncell) return false;
+    // the next 32 cells of the range, one per lane
+    const int c = s.c0 + lane;
+    int cnt = 0, st = 0, off = 0;
+    if (c < s.ncell) {
+      const int x = c % s.nx, t = c / s.nx;
+      const int y = t % s.ny, z = t / s.ny;
+      const int gx = s.kx0 + x, gy = s.ky0 + y, gz = s.kz0 + z;
+      const int cell = g.cell_off + (gz * g.dims[1] + gy) * g.dims[0] + gx;
+      st = cstart[cell];
+      if (st >= 0) cnt = cend[cell] - st;
+      off = (gx - rx + 512) | ((gy - ry + 512) << 10) | ((gz - rz + 512) << 20);
     }
-    const int s0 = cstart[c];
-    if (s0 < 0) continue;
-    s.jb = s0;
-    s.je = cend[c];
-    s.ox = REL ? fx * Lt : T(0);
-    s.oy = REL ? fy * Lt : T(0);
-    s.oz = REL ? fz * Lt : T(0);
-    return true;
+    int inc = cnt;   // inclusive prefix over the lanes
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += v;
+    }
+    s.s0 = st;
+    s.pre = inc - cnt;
+    s.off = off;
+    s.total = __shfl_sync(kFull, inc, 31);
+    s.pos = 0;
+    s.c0 += 32;
   }
-  return false;
+  const int k = s.pos + lane;
+  ok = k < s.total;
+  // the lane whose cell holds stream position k: the last one with pre <= k
+  int own = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = own + step;
+    const int pc = __shfl_sync(kFull, s.pre, cand & 31);
+    if (cand < 32 && pc <= k) own = cand;
+  }
+  const int p0 = __shfl_sync(kFull, s.pre, own);
+  j = __shfl_sync(kFull, s.s0, own) + (k - p0);
+  const int off = __shfl_sync(kFull, s.off, own);
+  if (REL) {
+    ox = (T)((off & 1023) - 512) * Lt;
+    oy = (T)(((off >> 10) & 1023) - 512) * Lt;
+    oz = (T)(((off >> 20) & 1023) - 512) * Lt;
+  } else {
+    ox = oy = oz = T(0);
+  }
+  s.pos += 32;
+  return true;
 }
 
 }  // namespace sphk
