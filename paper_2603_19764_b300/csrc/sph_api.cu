@@ -75,7 +75,7 @@ void free_all(sph_ctx *c) {
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
                  c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->w.divv,
                  c->learn.hprev, c->learn.hprop, c->learn.feat[0], c->learn.feat[1],
-                 c->learn.feat[2], c->learn.x_out, c->learn.y_out};
+                 c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -548,6 +548,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   CKI(dalloc(&c->cell_end, c->max_cells));
   c->tmp_words = 32;
   CKI(cudaMalloc(&c->tmp, (size_t)n * c->tmp_words * 8));
+  CKI(alloc_density_spill(c));
   CKI(dalloc(&c->partials, (size_t)c->nchunks * 9));
   CKI(dalloc(&c->d_dt, n_sys));
   CKI(cudaMemset(c->d_dt, 0, sizeof(double) * n_sys));

@@ -70,7 +70,30 @@ struct DensArgs {
   const int *cell_start, *cell_end;
   KParams p;
   Status *st;
+  void *spill;      // per-warp overflow of the candidate lists (kSpill entries)
 };
+
+// Candidates beyond the shared-memory list of a warp continue in a private
+// global-memory region of kSpill entries (positions, indices, mask words),
+// so that a list of up to CAP + kSpill candidates stays resident across the
+// Newton sweeps instead of being staged again for every sweep.
+constexpr int kSpill = 1024;
+
+template <typename V4> struct SpillView {
+  V4 *p;
+  int *i;
+  unsigned (*m)[32];
+};
+template <typename V4>
+__device__ __forceinline__ SpillView<V4> spill_view(void *base, int warp) {
+  const size_t per = (size_t)kSpill * (sizeof(V4) + 2 * sizeof(int));
+  char *b = (char *)base + per * warp;
+  SpillView<V4> v;
+  v.p = (V4 *)b;
+  v.i = (int *)(b + (size_t)kSpill * sizeof(V4));
+  v.m = (unsigned(*)[32])(b + (size_t)kSpill * (sizeof(V4) + sizeof(int)));
+  return v;
+}
 
 template <typename T> struct PosPtr;
 template <> struct PosPtr<float> {
@@ -129,6 +152,8 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
       const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
       T r2;
       bool in;
+      // (Lp, Li, Lm: the shared-memory list or its global overflow; neither
+      // is read through the read-only path, the kernel writes both)
       if (REL) {
         r2 = dx * dx + dy * dy + dz * dz;
         in = r2 < H2;
@@ -164,6 +189,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   V4 *Lp = s_pos[wib];
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
+  const SpillView<V4> Sv = spill_view<V4>(A.spill, blockIdx.x * kWarpsPerBlock + wib);
+  constexpr int TCAP = CAP + kSpill;
   // persistent warps: each takes the next bucket of 32 particles
   const int nbuckets = A.p.nbuckets;
   long long w_pairs = 0, w_cand = 0;
@@ -240,7 +267,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         complete = false;
         for (int seg = 0;; ++seg) {
           nl = 0;
-          while (nl <= CAP - 32) {
+          while (nl <= TCAP - 32) {
             int j;
             bool ok;
             T ox, oy, oz;
@@ -254,8 +281,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
             const unsigned bal = __ballot_sync(kFull, keep);
             if (keep) {
               const int at = nl + __popc(bal & lanemask_lt());
-              Lp[at] = V::make(xj, yj, zj, q.w);
-              Li[at] = j;
+              if (at < CAP) {
+                Lp[at] = V::make(xj, yj, zj, q.w);
+                Li[at] = j;
+              } else {
+                Sv.p[at - CAP] = V::make(xj, yj, zj, q.w);
+                Sv.i[at - CAP] = j;
+              }
             }
             nl += __popc(bal);
           }
@@ -264,13 +296,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
             complete = true;
             break;
           }
-          // list longer than the buffer: evaluate this segment exactly
+          // list longer than both buffers: evaluate this segment exactly
+          const int n1 = min(nl, CAP), n2 = nl - n1;
           __syncwarp();
-          build_masks<T, V4>(Lp, Lm, nl, xi, yi, zi, H2 * T(1.0001), act, lane);
+          build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, H2 * T(1.0001), act, lane);
+          build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, H2 * T(1.0001), act, lane);
           __syncwarp();
-          if (act)
-            density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
+          if (act) {
+            density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
                                      zi64, A.s, (int)i, rs, rhs, cnt);
+            density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, H2c, xi64,
+                                     yi64, zi64, A.s, (int)i, rs, rhs, cnt);
+          }
           __syncwarp();
           if (stager_finished(sg)) break;
         }
@@ -278,16 +315,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       if (complete) {
         // resident list: refresh the masks of lanes whose H outgrew them
         const bool rebuild = act && !(Hm >= Ht * T(1.0001));
+        const int n1 = min(nl, CAP), n2 = nl - n1;
         if (__any_sync(kFull, rebuild)) {
           const T Hn = rebuild ? Ht * T(1.05) : Hm;
           __syncwarp();
-          build_masks<T, V4>(Lp, Lm, nl, xi, yi, zi, Hn * Hn, rebuild, lane);
+          build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
+          build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
           __syncwarp();
           Hm = Hn;
         }
-        if (act)
-          density_walk<T, V4, REL>(Lp, Li, Lm, nl, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64, zi64,
-                                   A.s, (int)i, rs, rhs, cnt);
+        if (act) {
+          density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
+                                   zi64, A.s, (int)i, rs, rhs, cnt);
+          density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, H2c, xi64,
+                                   yi64, zi64, A.s, (int)i, rs, rhs, cnt);
+        }
       }
 
       if (act) {
@@ -374,6 +416,7 @@ cudaError_t launch_density(sph_ctx *c) {
   a.cell_end = c->cell_end;
   a.p = c->kp;
   a.st = c->d_status;
+  a.spill = c->dens_spill;
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K)
@@ -384,6 +427,29 @@ cudaError_t launch_density(sph_ctx *c) {
                              c->stream>>>(a);
   c->nlaunch += 1;
   return cudaGetLastError();
+}
+
+}  // namespace sphk
+
+namespace sphk {
+
+// Overflow region of the density lists: one kSpill-entry region per warp
+// that can be resident, at most one warp per bucket.
+cudaError_t alloc_density_spill(sph_ctx *c) {
+  int per_sm = 0;
+  cudaError_t e = c->kp.precision == SPH_FP32K
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, k_density<float, 512>, 32 * kWarpsPerBlock, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, k_density<double, 256>, 32 * kWarpsPerBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = ((int64_t)c->kp.nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int64_t blocks = (int64_t)per_sm * c->num_sms;
+  if (blocks > need) blocks = need;
+  const size_t v4 = c->kp.precision == SPH_FP32K ? sizeof(float4) : sizeof(double4_32a);
+  const size_t per = (size_t)kSpill * (v4 + 2 * sizeof(int));
+  return cudaMalloc(&c->dens_spill, per * (size_t)(blocks * kWarpsPerBlock));
 }
 
 }  // namespace sphk

@@ -405,6 +405,7 @@ struct sph_ctx {
   double *h_dt;             // pinned dt staging (nsys)
   double *dt_next;          // host, per system
   int occ_density, occ_forces;   // resident blocks per SM of the pair kernels
+  void *dens_spill;              // overflow of the density kernel's candidate lists
   int num_sms;
   int timing;
   int use_graph;
@@ -455,4 +456,5 @@ cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_kick(sph_ctx *c, int kick);
 cudaError_t launch_reset_status(sph_ctx *c, int full);
 cudaError_t launch_learn(sph_ctx *c);
+cudaError_t alloc_density_spill(sph_ctx *c);
 }  // namespace sphk
