@@ -171,7 +171,8 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
         const T mW = q.w * t * t * t;
         rs += mW * t * (T(1) + T(4) * qq);
         rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
-        cnt += (Li[k] != self);
+        // only a pair at r = 0 can be the particle itself
+        cnt += r2 > T(0) ? 1 : (Li[k] != self);
       }
     }
   }
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         const bool rebuild = act && !(Hm >= Ht * T(1.0001));
         const int n1 = min(nl, CAP), n2 = nl - n1;
         if (__any_sync(kFull, rebuild)) {
-          const T Hn = rebuild ? Ht * T(1.05) : Hm;
+          const T Hn = rebuild ? Ht * T(1.02) : Hm;
           __syncwarp();
           build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
           build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
