@@ -46,58 +46,99 @@ cudaError_t launch_reset_status(sph_ctx *c, int full) {
 // ------------------------------------------------------ drift + bounding box
 // x_i = x_{i-1} + dt v_{i-1/2} for moving particles (§2.4), then the box of
 // every system's positions and its largest H. Runs before the sort, so a
-// particle's system comes from its id. A warp whose particles share one
-// system reduces before its atomics.
+// particle's system comes from its id. Each thread keeps running extrema
+// for the system of its current particle and flushes them with atomics
+// only when the system changes; at the end the block combines the threads
+// that share one system (the common case) before a single set of atomics.
+__device__ __forceinline__ void flush_box(SysRec &r, const double (&lo)[3], const double (&hi)[3],
+                                          double hm) {
+  for (int a = 0; a < 3; ++a) {
+    atomicMin(&r.lo_enc[a], enc_d(lo[a]));
+    atomicMax(&r.hi_enc[a], enc_d(hi[a]));
+  }
+  atomicMax(&r.hmax_enc, enc_d(hm));
+}
+
 __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, KParams P,
                                                       int do_drift) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
-       base += stride) {
-    const int64_t i = base + lane;
-    const bool ok = i < n;
-    int sy = 0;
-    double p[3] = {0, 0, 0}, h = 0.0;
-    if (ok) {
-      sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
-      p[0] = s.x[i];
-      p[1] = s.y[i];
-      p[2] = s.z[i];
-      if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
-        const double dt = P.dt[sy];
-        p[0] += dt * s.vx[i];
-        p[1] += dt * s.vy[i];
-        p[2] += dt * s.vz[i];
-        s.x[i] = p[0];
-        s.y[i] = p[1];
-        s.z[i] = p[2];
-      }
-      h = s.h[i];
+  __shared__ double red[7][kBlock / 32];
+  __shared__ int wsys[kBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double hm = 0.0;
+  int cur = -1;   // system of the running extrema (-1: none)
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
+    double p[3] = {s.x[i], s.y[i], s.z[i]};
+    if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
+      const double dt = P.dt[sy];
+      p[0] += dt * s.vx[i];
+      p[1] += dt * s.vy[i];
+      p[2] += dt * s.vz[i];
+      s.x[i] = p[0];
+      s.y[i] = p[1];
+      s.z[i] = p[2];
     }
-    const int s0 = __shfl_sync(kFull, sy, 0);
-    if (__all_sync(kFull, !ok || sy == s0)) {
-      double lo[3], hi[3];
-#pragma unroll
+    if (sy != cur) {
+      if (cur >= 0) flush_box(P.sys[cur], lo, hi, hm);
+      cur = sy;
       for (int a = 0; a < 3; ++a) {
-        lo[a] = wmin(ok ? p[a] : INFINITY);
-        hi[a] = wmax(ok ? p[a] : -INFINITY);
+        lo[a] = INFINITY;
+        hi[a] = -INFINITY;
       }
-      const double hm = wmax(ok ? h : 0.0);
-      if (lane == 0) {
-        SysRec &r = P.sys[s0];
-        for (int a = 0; a < 3; ++a) {
-          atomicMin(&r.lo_enc[a], enc_d(lo[a]));
-          atomicMax(&r.hi_enc[a], enc_d(hi[a]));
-        }
-        atomicMax(&r.hmax_enc, enc_d(hm));
+      hm = 0.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], p[a]);
+      hi[a] = fmax(hi[a], p[a]);
+    }
+    hm = fmax(hm, s.h[i]);
+  }
+  // threads of a warp with one common system reduce by shuffles, warps of
+  // a block with one common system through shared memory
+  int any = -1;   // a system held by some lane of the warp (lane 0 first)
+  {
+    const unsigned has = __ballot_sync(kFull, cur >= 0);
+    if (has) any = __shfl_sync(kFull, cur, __ffs(has) - 1);
+  }
+  const bool warp_uniform = __all_sync(kFull, cur < 0 || cur == any);
+  double v[7] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm};
+  if (warp_uniform) {
+    for (int k = 0; k < 3; ++k) v[k] = wmin(v[k]);
+    for (int k = 3; k < 7; ++k) v[k] = wmax(v[k]);
+  } else if (cur >= 0) {
+    flush_box(P.sys[cur], lo, hi, hm);   // mixed warp: every lane on its own
+  }
+  if (lane == 0) {
+    wsys[w] = warp_uniform ? any : -2;   // -1: no particle, -2: flushed
+    for (int k = 0; k < 7; ++k) red[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sb = -1;
+    bool one = true;
+    for (int q = 0; q < kBlock / 32; ++q) {
+      if (wsys[q] == -1) continue;
+      if (wsys[q] == -2 || (sb >= 0 && wsys[q] != sb)) one = false;
+      else sb = wsys[q];
+    }
+    if (one && sb >= 0) {
+      double b[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+      for (int q = 0; q < kBlock / 32; ++q) {
+        if (wsys[q] < 0) continue;
+        for (int k = 0; k < 3; ++k) b[k] = fmin(b[k], red[k][q]);
+        for (int k = 3; k < 7; ++k) b[k] = fmax(b[k], red[k][q]);
       }
-    } else if (ok) {
-      SysRec &r = P.sys[sy];
-      for (int a = 0; a < 3; ++a) {
-        atomicMin(&r.lo_enc[a], enc_d(p[a]));
-        atomicMax(&r.hi_enc[a], enc_d(p[a]));
+      const double bl[3] = {b[0], b[1], b[2]}, bh[3] = {b[3], b[4], b[5]};
+      flush_box(P.sys[sb], bl, bh, b[6]);
+    } else {
+      for (int q = 0; q < kBlock / 32; ++q) {
+        if (wsys[q] < 0) continue;
+        const double bl[3] = {red[0][q], red[1][q], red[2][q]};
+        const double bh[3] = {red[3][q], red[4][q], red[5][q]};
+        flush_box(P.sys[wsys[q]], bl, bh, red[6][q]);
       }
-      atomicMax(&r.hmax_enc, enc_d(h));
     }
   }
 }
