@@ -52,13 +52,13 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per particle per launch of the FP32 pair kernels,
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` on the
-# 600k-particle impact (bench.py --scale 0.3; profiles/ has the command) and
-# scaled by particles. Keyed by a hash of the kernel's sources: once the
+# 600k-particle impact (bench.py --scale 0.3 --spans 1,1; profiles/ has the
+# command) and scaled by particles. Keyed by a hash of the kernel's sources: once the
 # kernel changes the figure no longer applies and traffic is reported null.
 KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (188.17, "08f335af3979"),
-                        "k_density": (56.63, "323d4567f0c4")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (186.11, "3f41d3c94132"),
+                        "k_density": (60.49, "944a0b23900e")}
 
 
 def source_hash(kernel: str) -> str:
