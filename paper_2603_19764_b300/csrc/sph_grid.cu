@@ -46,10 +46,13 @@ cudaError_t launch_reset_status(sph_ctx *c, int full) {
 // ------------------------------------------------------ drift + bounding box
 // x_i = x_{i-1} + dt v_{i-1/2} for moving particles (§2.4), then the box of
 // every system's positions and its largest H. Runs before the sort, so a
-// particle's system comes from its id. Each thread keeps running extrema
-// for the system of its current particle and flushes them with atomics
-// only when the system changes; at the end the block combines the threads
-// that share one system (the common case) before a single set of atomics.
+// particle's system comes from its id. A block covers kDriftChunk
+// consecutive particles, which belong to one system except near system
+// boundaries (systems stay contiguous through every sort). Each thread
+// keeps running extrema for the system of its current particle and flushes
+// them with atomics only when the system changes; at the end the block
+// combines the threads that share one system (the common case) before a
+// single set of atomics.
 __device__ __forceinline__ void flush_box(SysRec &r, const double (&lo)[3], const double (&hi)[3],
                                           double hm) {
   for (int a = 0; a < 3; ++a) {
@@ -59,6 +62,8 @@ __device__ __forceinline__ void flush_box(SysRec &r, const double (&lo)[3], cons
   atomicMax(&r.hmax_enc, enc_d(hm));
 }
 
+constexpr int kDriftChunk = 8 * kBlock;
+
 __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, KParams P,
                                                       int do_drift) {
   __shared__ double red[7][kBlock / 32];
@@ -67,8 +72,9 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   double hm = 0.0;
   int cur = -1;   // system of the running extrema (-1: none)
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t c0 = (int64_t)blockIdx.x * kDriftChunk;
+  const int64_t c1 = c0 + kDriftChunk < n ? c0 + kDriftChunk : n;
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
     double p[3] = {s.x[i], s.y[i], s.z[i]};
     if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
@@ -144,8 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
 }
 
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
-  int blocks = (int)((c->n + kBlock - 1) / kBlock);
-  if (blocks > 148 * 8) blocks = 148 * 8;
+  const int blocks = (int)((c->n + kDriftChunk - 1) / kDriftChunk);
   k_drift_bbox<<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
   c->nlaunch += 1;
   return cudaGetLastError();
