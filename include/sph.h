@@ -264,6 +264,16 @@ sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces);
 /* The tuner's state and timings. */
 sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out);
 
+/* Self-check of the library's own FP64 <-> FP32 conversions (the
+ * per-particle kernels convert on the integer pipe, since the conversion
+ * instructions run on the FP64 unit): for each of the n DEVICE values, the
+ * library's double -> float against the hardware round-to-nearest
+ * conversion, and float -> double back, bit for bit. *mismatches (HOST)
+ * receives the number of values that differ. Synchronises; allocates 8
+ * bytes. */
+sph_status sph_check_conversions(const double *in, int64_t n, int64_t *mismatches,
+                                 void *cuda_stream);
+
 /* ---------------------------------------------------------------------
  * Learned smoothing-length proposal. The paper's solve (§2.1, Eq. 2-3)
  * starts Newton from the previous support radius; this form starts it from

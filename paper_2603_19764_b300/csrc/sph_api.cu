@@ -43,6 +43,44 @@ template <typename T> cudaError_t dalloc(T **p, size_t count) {
   return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
 }
 
+// A material's parameters and derived constants in the type of a form.
+template <typename T> MatT<T> mat_copy(const sph_material &m) {
+  MatT<T> o;
+  memset(&o, 0, sizeof(o));
+  o.eos = m.eos;
+  o.strength = m.strength;
+  o.thermal_softening = m.thermal_softening;
+  o.rho0_d = m.rho0;
+  o.Eiv_d = m.Eiv;
+  o.Ecv_d = m.Ecv;
+  o.c0sq_d = m.c0 * m.c0;
+  o.p_min_d = m.p_min;
+  o.rho0 = (T)m.rho0;
+  o.inv_rho0 = (T)(1.0 / m.rho0);
+  o.c0 = (T)m.c0;
+  o.c0sq = (T)(m.c0 * m.c0);
+  o.A = (T)m.A;
+  o.B = (T)m.B;
+  o.E0 = (T)m.E0;
+  o.a = (T)m.a;
+  o.b = (T)m.b;
+  o.alpha = (T)m.alpha;
+  o.beta = (T)m.beta;
+  o.inv_dE = m.Ecv > m.Eiv ? (T)(1.0 / (m.Ecv - m.Eiv)) : (T)0;
+  o.floor2 = (T)(0.01 * m.A / m.rho0);
+  o.shear_G = (T)m.shear_G;
+  o.Y0 = (T)m.Y0;
+  o.mu_i = (T)m.mu_i;
+  o.Ym = (T)m.Ym;
+  o.mu_d = (T)m.mu_d;
+  o.xi = (T)m.xi;
+  o.Tm = (T)m.Tm;
+  o.T0 = (T)m.T0;
+  o.inv_cv = (T)(1.0 / m.cv);
+  o.p_min = (T)m.p_min;
+  return o;
+}
+
 bool state_complete(const sph_state *s) {
   const void *p[] = {s->x,    s->y,    s->z,    s->vx,    s->vy,     s->vz,   s->u,    s->m,
                      s->h,    s->sxx,  s->syy,  s->sxy,   s->sxz,    s->syz,  s->rho,  s->omega,
@@ -66,7 +104,7 @@ __global__ void k_validate(sph_state s, int64_t n, int nmat, int check_id, unsig
 }
 
 void free_all(sph_ctx *c) {
-  void *dev[] = {c->d_mats, c->d_gtab, c->d_phitab, c->d_radii, c->w.vp[0], c->w.vp[1],
+  void *dev[] = {c->d_mats, c->d_matf, c->d_matd, c->d_gtab, c->d_phitab, c->d_radii, c->w.vp[0], c->w.vp[1],
                  c->w.vp[2], c->w.up, c->w.sp[0], c->w.sp[1], c->w.sp[2], c->w.sp[3],
                  c->w.sp[4], c->w.vsig, c->w.edot2, c->w.yld, c->w.cc, c->w.pos32, c->w.pos64,
                  c->w.fj32, c->w.fj64, c->w.posh32, c->w.posh64,
@@ -471,6 +509,18 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
 
   CKI(dalloc(&c->d_mats, SPH_MAX_MATERIALS));
   CKI(cudaMemcpy(c->d_mats, c->mats, sizeof(c->mats), cudaMemcpyHostToDevice));
+  {
+    MatT<float> mf[SPH_MAX_MATERIALS];
+    MatT<double> md[SPH_MAX_MATERIALS];
+    for (int k = 0; k < SPH_MAX_MATERIALS; ++k) {
+      mf[k] = mat_copy<float>(c->mats[k]);
+      md[k] = mat_copy<double>(c->mats[k]);
+    }
+    CKI(dalloc(&c->d_matf, SPH_MAX_MATERIALS));
+    CKI(dalloc(&c->d_matd, SPH_MAX_MATERIALS));
+    CKI(cudaMemcpy(c->d_matf, mf, sizeof(mf), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(c->d_matd, md, sizeof(md), cudaMemcpyHostToDevice));
+  }
   kp.n_ngb = p->n_ngb;
   kp.av_alpha = p->av_alpha;
   kp.av_beta = p->av_beta;
@@ -494,6 +544,8 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     kp.g_center[a] = p->g_center[a];
   }
   kp.mats = c->d_mats;
+  kp.matf = c->d_matf;
+  kp.matd = c->d_matd;
   if (p->gravity == SPH_GRAVITY_RADIAL) {
     const int gn = p->g_n;
     double *radii = (double *)malloc(sizeof(double) * gn);

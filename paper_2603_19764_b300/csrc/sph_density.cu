@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
       const double ox = g.lo[0] + (c & 1023) * g.L;
       const double oy = g.lo[1] + ((c >> 10) & 1023) * g.L;
       const double oz = g.lo[2] + ((c >> 20) & 1023) * g.L;
-      w.pos32[i] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), (float)m);
+      w.pos32[i] = make_float4(d2f(x - ox), d2f(y - oy), d2f(z - oz), d2f(m));
     } else {
       w.pos64[i] = make_double4_32a(x, y, z, m);
     }
@@ -370,8 +370,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
 
   if (valid) {
     A.s.h[i] = H_o;
-    A.s.rho[i] = (double)rho_o;
-    A.s.omega[i] = (double)om_o;
+    A.s.rho[i] = from_t(rho_o);
+    A.s.omega[i] = from_t(om_o);
     A.s.nngb[i] = cnt_o;
   }
   w_sw = max(w_sw, valid ? sweeps_o : 0);

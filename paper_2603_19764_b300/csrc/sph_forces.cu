@@ -55,13 +55,14 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
   const typename V::type *pos = Packed<T>::pos(w);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const sph_material &M = P.mats[s.mat[i] & (SPH_MAX_MATERIALS - 1)];
-    const double rhod = s.rho[i];
-    const EosT<T> e = eos_t<T>(M, rhod, w.up[i]);
-    s.pres[i] = (double)e.P;
-    s.cs[i] = (double)e.c;
-    const T Y = yield_t<T>(M, e.P, (T)w.up[i]);
-    T S[5] = {(T)w.sp[0][i], (T)w.sp[1][i], (T)w.sp[2][i], (T)w.sp[3][i], (T)w.sp[4][i]};
+    const MatT<T> &M = mat_t<T>(P, s.mat[i]);
+    const double rhod = s.rho[i], ud = w.up[i];
+    const EosT<T> e = eos_t<T>(M, rhod, ud);
+    s.pres[i] = from_t(e.P);
+    s.cs[i] = from_t(e.c);
+    const T Y = yield_t<T>(M, e.P, to_t<T>(ud));
+    T S[5] = {to_t<T>(w.sp[0][i]), to_t<T>(w.sp[1][i]), to_t<T>(w.sp[2][i]), to_t<T>(w.sp[3][i]),
+              to_t<T>(w.sp[4][i])};
     if (!M.strength) {
       S[0] = S[1] = S[2] = S[3] = S[4] = T(0);
     } else {
@@ -70,18 +71,19 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
       for (int k = 0; k < 5; ++k) S[k] *= f;
     }
     const typename V::type pp = pos[i];
-    const T rho = (T)rhod, om = (T)s.omega[i], m = (T)s.m[i], H = (T)s.h[i];
+    const T rho = to_t<T>(rhod), om = to_t<T>(s.omega[i]), m = to_t<T>(s.m[i]),
+            H = to_t<T>(s.h[i]);
     const T inv = m / (om * rho * rho);
     const T ih = T(1) / H;
     const T ih2 = ih * ih;
     const T K = T(cG) * ih2 * ih2 * ih;
-    const T Gam = M.strength ? (T)shear_mod(M, rhod, (double)e.c) : T(0);
+    const T Gam = M.strength ? shear_mod_t<T>(M, rho, e.c) : T(0);
     const T cl = M.strength ? sqrt(e.c * e.c + T(4.0 / 3.0) * Gam / rho) : e.c;
     T gx[3];
     ext_field_t<T>(P, s.x[i], s.y[i], s.z[i], gx, nullptr);
     Packed<T>::posh(w)[i] = V::make(pp.x, pp.y, pp.z, H);
     typename V::type *rec = Packed<T>::rec(w) + 4 * i;
-    rec[0] = V::make((T)w.vp[0][i], (T)w.vp[1][i], (T)w.vp[2][i], m);
+    rec[0] = V::make(to_t<T>(w.vp[0][i]), to_t<T>(w.vp[1][i]), to_t<T>(w.vp[2][i]), m);
     rec[1] =
         V::make((S[0] - e.P) * inv, (S[1] - e.P) * inv, (-S[0] - S[1] - e.P) * inv, S[2] * inv);
     rec[2] = V::make(S[3] * inv, S[4] * inv, m / (om * rho), e.c);
@@ -385,20 +387,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
       for (int k = 0; k < 3; ++k) rot += R[3 * a + k] * Sm[3 * k + b] - Sm[3 * a + k] * R[3 * k + b];
       dS[q] = T(2) * Gam * (E[3 * a + b] - (a == b ? tr3 : T(0))) + sg * rot;
     }
-    A.w.vsig[i] = (double)(T(1.0 + 0.6 * A.p.av_alpha) * s1.z + T(0.6 * A.p.av_beta) * mumax);
-    A.w.edot2[i] = (double)(T(0.5) * e2);
+    A.w.vsig[i] = from_t((T(1) + T(0.6) * al) * s1.z + T(0.6) * be * mumax);
+    A.w.edot2[i] = from_t(T(0.5) * e2);
     if (A.w.divv) A.w.divv[i] = (float)(E[0] + E[4] + E[8]);
     const T axt = ax + s2.x, ayt = ay + s2.y, azt = az + s2.z;
     const T dud = du.get();
-    A.s.ax[i] = fixed ? 0.0 : (double)axt;
-    A.s.ay[i] = fixed ? 0.0 : (double)ayt;
-    A.s.az[i] = fixed ? 0.0 : (double)azt;
-    A.s.dudt[i] = fixed ? 0.0 : (double)dud;
-    A.s.dsxx[i] = fixed ? 0.0 : (double)dS[0];
-    A.s.dsyy[i] = fixed ? 0.0 : (double)dS[1];
-    A.s.dsxy[i] = fixed ? 0.0 : (double)dS[2];
-    A.s.dsxz[i] = fixed ? 0.0 : (double)dS[3];
-    A.s.dsyz[i] = fixed ? 0.0 : (double)dS[4];
+    A.s.ax[i] = fixed ? 0.0 : from_t(axt);
+    A.s.ay[i] = fixed ? 0.0 : from_t(ayt);
+    A.s.az[i] = fixed ? 0.0 : from_t(azt);
+    A.s.dudt[i] = fixed ? 0.0 : from_t(dud);
+    A.s.dsxx[i] = fixed ? 0.0 : from_t(dS[0]);
+    A.s.dsyy[i] = fixed ? 0.0 : from_t(dS[1]);
+    A.s.dsxy[i] = fixed ? 0.0 : from_t(dS[2]);
+    A.s.dsxz[i] = fixed ? 0.0 : from_t(dS[3]);
+    A.s.dsyz[i] = fixed ? 0.0 : from_t(dS[4]);
     bool fin = isfinite(axt) && isfinite(ayt) && isfinite(azt) && isfinite(dud);
 #pragma unroll
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(dS[k]);

@@ -64,6 +64,17 @@ struct Status {
   int pad2_;
 };
 
+// Material parameters in the arithmetic type of a form, with the derived
+// constants the evaluations need; the FP32 copies are made once on the host
+// so that an evaluation converts nothing. FP64 copies of the values that
+// region tests and mu = rho / rho0 - 1 use in FP64.
+template <typename T> struct MatT {
+  int eos, strength, thermal_softening, pad_;
+  double rho0_d, Eiv_d, Ecv_d, c0sq_d, p_min_d;
+  T rho0, inv_rho0, c0, c0sq, A, B, E0, a, b, alpha, beta, inv_dE, floor2;
+  T shear_G, Y0, mu_i, Ym, mu_d, xi, Tm, T0, inv_cv, p_min;
+};
+
 // Kernel-side copy of the run-time parameters.
 struct KParams {
   int n_ngb;
@@ -77,6 +88,8 @@ struct KParams {
   int g_n;
   double g_rmin, g_rmax, g_center[3], g_gm, g_inv_log_ratio;
   const sph_material *mats;
+  const MatT<float> *matf;     // the materials for the FP32 / FP64 forms
+  const MatT<double> *matd;
   // systems
   int nsys, axis_bits;         // Morton bits per axis below the system bits
   int nbuckets, nchunks;
@@ -114,6 +127,44 @@ __device__ __forceinline__ int sys_lookup(const int *bounds, int nsys, int64_t v
   }
   return lo;
 }
+
+template <typename T> __device__ __forceinline__ const MatT<T> &mat_t(const KParams &P, int k);
+template <> __device__ __forceinline__ const MatT<float> &mat_t<float>(const KParams &P, int k) {
+  return P.matf[k & (SPH_MAX_MATERIALS - 1)];
+}
+template <> __device__ __forceinline__ const MatT<double> &mat_t<double>(const KParams &P, int k) {
+  return P.matd[k & (SPH_MAX_MATERIALS - 1)];
+}
+
+// FP64 <-> FP32 conversions on the integer pipe. On this part the
+// conversion instructions run on the FP64 unit, at 1/64 of the FP32 rate,
+// and the per-particle kernels convert tens of values per particle. Built
+// from the IEEE 754 binary64 / binary32 layouts: round to nearest even for
+// results in the binary32 normal range, the conversion instruction
+// otherwise (zero, subnormal results, overflow to infinity, NaN).
+__device__ __forceinline__ float d2f(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu;   // biased binary64 exponent
+  if (e < 897u || e > 1150u) return __double2float_rn(d);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 fraction bits
+  const unsigned rest = lo & 0x1fffffffu;                    // the 29 dropped bits
+  unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ double f2d(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)v;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+template <typename T> __device__ __forceinline__ T to_t(double d);
+template <> __device__ __forceinline__ float to_t<float>(double d) { return d2f(d); }
+template <> __device__ __forceinline__ double to_t<double>(double d) { return d; }
+__device__ __forceinline__ double from_t(float v) { return f2d(v); }
+__device__ __forceinline__ double from_t(double v) { return v; }
 
 // Library-owned per-particle work arrays (sorted order).
 struct Work {
@@ -225,30 +276,28 @@ template <typename T> struct EosT {
 };
 
 template <typename T>
-__device__ inline void till_dense_t(const sph_material &M, T eta, T mu, T rho, T u, T &P, T &Pr,
-                                    T &Pu) {
-  const T A = (T)M.A, B = (T)M.B, a = (T)M.a, b = (T)M.b;
-  const T e0e2 = (T)M.E0 * eta * eta;
+__device__ inline void till_dense_t(const MatT<T> &M, T eta, T mu, T rho, T u, T &P, T &Pr, T &Pu) {
+  const T e0e2 = M.E0 * eta * eta;
   const T w = u / e0e2 + T(1);
-  const T bw = b / w, bw2 = bw / w;            // b / w, b / w^2
-  P = (a + bw) * rho * u + mu * (A + B * mu);
+  const T bw = M.b / w, bw2 = bw / w;           // b / w, b / w^2
+  P = (M.a + bw) * rho * u + mu * (M.A + M.B * mu);
   // dw/drho = -2 (w - 1) / rho, dw/du = 1 / (E0 eta^2)
-  Pr = (a + bw) * u + bw2 * u * T(2) * (w - T(1)) + (A + T(2) * B * mu) / (T)M.rho0;
-  Pu = (a + bw) * rho - bw2 * rho * u / e0e2;
+  Pr = (M.a + bw) * u + bw2 * u * T(2) * (w - T(1)) + (M.A + T(2) * M.B * mu) * M.inv_rho0;
+  Pu = (M.a + bw) * rho - bw2 * rho * u / e0e2;
 }
 
 template <typename T>
-__device__ inline void till_vapour_t(const sph_material &M, T eta, T mu, T rho, T u, T &P, T &Pr,
+__device__ inline void till_vapour_t(const MatT<T> &M, T eta, T mu, T rho, T u, T &P, T &Pr,
                                      T &Pu) {
-  const T A = (T)M.A, a = (T)M.a, b = (T)M.b, al = (T)M.alpha, be = (T)M.beta;
-  const T e0e2 = (T)M.E0 * eta * eta;
+  const T A = M.A, a = M.a, b = M.b, al = M.alpha, be = M.beta;
+  const T e0e2 = M.E0 * eta * eta;
   const T w = u / e0e2 + T(1);
   const T z = -mu / eta;                       // rho0 / rho - 1
   const T zr = T(-1) / (eta * rho);            // dz / drho
   const T eb = exp(-be * z), ea = exp(-al * z * z);
   const T brw = b * rho * u / w;
   const T q = brw + A * mu * eb;
-  const T qr = b * u / w + brw / w * T(2) * (w - T(1)) / rho + A / (T)M.rho0 * eb -
+  const T qr = b * u / w + brw / w * T(2) * (w - T(1)) / rho + A * M.inv_rho0 * eb -
                A * mu * eb * be * zr;
   const T qu = b * rho / w - brw / w / e0e2;
   P = a * rho * u + q * ea;
@@ -257,54 +306,51 @@ __device__ inline void till_vapour_t(const sph_material &M, T eta, T mu, T rho, 
 }
 
 template <typename T>
-__device__ inline EosT<T> eos_t(const sph_material &M, double rhod, double ud) {
+__device__ inline EosT<T> eos_t(const MatT<T> &M, double rhod, double ud) {
   EosT<T> o;
   if (M.eos == SPH_EOS_LINEAR) {
-    o.P = (T)fmax(M.c0 * M.c0 * (rhod - M.rho0), M.p_min);
-    o.c = (T)M.c0;
+    o.P = tmax_(M.c0sq * to_t<T>(rhod - M.rho0_d), M.p_min);
+    o.c = M.c0;
     return o;
   }
-  const T u = (T)ud, rho = (T)rhod;
-  const T mu = (T)(rhod - M.rho0) / (T)M.rho0;
+  const T u = to_t<T>(ud), rho = to_t<T>(rhod);
+  const T mu = to_t<T>(rhod - M.rho0_d) * M.inv_rho0;
   const T eta = T(1) + mu;
   T P, Pr, Pu;
-  if (rhod >= M.rho0 || ud <= M.Eiv) {
+  if (rhod >= M.rho0_d || ud <= M.Eiv_d) {
     till_dense_t<T>(M, eta, mu, rho, u, P, Pr, Pu);
-  } else if (ud >= M.Ecv) {
+  } else if (ud >= M.Ecv_d) {
     till_vapour_t<T>(M, eta, mu, rho, u, P, Pr, Pu);
   } else {
     T P1, Pr1, Pu1, P2, Pr2, Pu2;
     till_dense_t<T>(M, eta, mu, rho, u, P1, Pr1, Pu1);
     till_vapour_t<T>(M, eta, mu, rho, u, P2, Pr2, Pu2);
-    const T s = T(1) / (T)(M.Ecv - M.Eiv);
-    const T wv = (T)(ud - M.Eiv) * s, wd = (T)(M.Ecv - ud) * s;
+    const T wv = to_t<T>(ud - M.Eiv_d) * M.inv_dE, wd = to_t<T>(M.Ecv_d - ud) * M.inv_dE;
     P = wv * P2 + wd * P1;
     Pr = wv * Pr2 + wd * Pr1;
-    Pu = wv * Pu2 + wd * Pu1 + (P2 - P1) * s;
+    Pu = wv * Pu2 + wd * Pu1 + (P2 - P1) * M.inv_dE;
   }
   T c2 = Pr + P * Pu / (rho * rho);
-  const T floor2 = (T)(0.01 * M.A / M.rho0);
-  if (!(c2 >= floor2)) c2 = floor2;
-  o.P = tmax_(P, (T)M.p_min);
+  if (!(c2 >= M.floor2)) c2 = M.floor2;
+  o.P = tmax_(P, M.p_min);
   o.c = sqrt(c2);
   return o;
 }
 
 // Shear modulus: constant, or Eq. 30 with nu = 0.25 (Gamma = 0.6 rho c^2).
-__device__ __forceinline__ double shear_mod(const sph_material &M, double rho, double c) {
-  return M.shear_G >= 0.0 ? M.shear_G : 0.6 * rho * c * c;
+template <typename T> __device__ __forceinline__ T shear_mod_t(const MatT<T> &M, T rho, T c) {
+  return M.shear_G >= T(0) ? M.shear_G : T(0.6) * rho * c * c;
 }
 
 // Yield strength (Eq. 34-37) with the pressure clipped at zero.
-template <typename T> __device__ inline T yield_t(const sph_material &M, T P, T u) {
+template <typename T> __device__ inline T yield_t(const MatT<T> &M, T P, T u) {
   const T p = tmax_(P, T(0));
-  const T Y0 = (T)M.Y0, mi = (T)M.mu_i;
-  const T yi = Y0 + mi * p / (T(1) + mi * p / ((T)M.Ym - Y0));
-  T y = tmin_(yi, (T)M.mu_d * p);
+  const T yi = M.Y0 + M.mu_i * p / (T(1) + M.mu_i * p / (M.Ym - M.Y0));
+  T y = tmin_(yi, M.mu_d * p);
   if (M.thermal_softening) {
-    const T Tk = (T)M.T0 + u / (T)M.cv;
+    const T Tk = M.T0 + u * M.inv_cv;
     if (!(Tk > T(0))) return T(0);
-    y *= tmax_(tanh((T)M.xi * ((T)M.Tm / Tk - T(1))), T(0));
+    y *= tmax_(tanh(M.xi * (M.Tm / Tk - T(1))), T(0));
   }
   return y;
 }
@@ -327,35 +373,36 @@ __device__ inline void ext_field_t(const KParams &P, double x, double y, double 
   g[0] = g[1] = g[2] = T(0);
   if (phi) *phi = T(0);
   if (P.gravity == SPH_GRAVITY_UNIFORM) {
-    g[0] = (T)P.g_uniform[0];
-    g[1] = (T)P.g_uniform[1];
-    g[2] = (T)P.g_uniform[2];
+    g[0] = to_t<T>(P.g_uniform[0]);
+    g[1] = to_t<T>(P.g_uniform[1]);
+    g[2] = to_t<T>(P.g_uniform[2]);
     if (phi) *phi = (T)(-(P.g_uniform[0] * x + P.g_uniform[1] * y + P.g_uniform[2] * z));
     return;
   }
   if (P.gravity != SPH_GRAVITY_RADIAL) return;
-  const T dx = (T)(x - P.g_center[0]), dy = (T)(y - P.g_center[1]), dz = (T)(z - P.g_center[2]);
+  const T dx = to_t<T>(x - P.g_center[0]), dy = to_t<T>(y - P.g_center[1]),
+          dz = to_t<T>(z - P.g_center[2]);
   const T r = sqrt(dx * dx + dy * dy + dz * dz);
   if (!(r > T(0))) return;
-  const T rmin = (T)P.g_rmin, rmax = (T)P.g_rmax;
+  const T rmin = to_t<T>(P.g_rmin), rmax = to_t<T>(P.g_rmax);
   T gm, ph;
   if (r >= rmax) {
-    gm = (T)P.g_gm / (r * r);
-    ph = -(T)P.g_gm / r;
+    gm = to_t<T>(P.g_gm) / (r * r);
+    ph = -to_t<T>(P.g_gm) / r;
   } else if (r <= rmin) {
-    const T g0 = (T)P.g_table[0];
+    const T g0 = to_t<T>(P.g_table[0]);
     gm = g0 * r / rmin;
-    ph = (T)P.phi_table[0] + T(0.5) * g0 / rmin * (r * r - rmin * rmin);
+    ph = to_t<T>(P.phi_table[0]) + T(0.5) * g0 / rmin * (r * r - rmin * rmin);
   } else {
     int k = (int)floorf(log2f((float)(r / rmin)) * (float)P.g_inv_log_ratio);
     k = max(0, min(k, P.g_n - 2));
-    if (r < (T)P.g_radii[k] && k > 0) --k;
-    else if (r >= (T)P.g_radii[k + 1] && k < P.g_n - 2) ++k;
-    const T r0 = (T)P.g_radii[k], r1 = (T)P.g_radii[k + 1];
+    if (r < to_t<T>(P.g_radii[k]) && k > 0) --k;
+    else if (r >= to_t<T>(P.g_radii[k + 1]) && k < P.g_n - 2) ++k;
+    const T r0 = to_t<T>(P.g_radii[k]), r1 = to_t<T>(P.g_radii[k + 1]);
     const T w = (r - r0) / (r1 - r0);
-    const T ga = (T)P.g_table[k], gb = (T)P.g_table[k + 1];
+    const T ga = to_t<T>(P.g_table[k]), gb = to_t<T>(P.g_table[k + 1]);
     gm = ga + w * (gb - ga);
-    const T pa = (T)P.phi_table[k], pb = (T)P.phi_table[k + 1];
+    const T pa = to_t<T>(P.phi_table[k]), pb = to_t<T>(P.phi_table[k + 1]);
     ph = pa + w * (pb - pa);
   }
   g[0] = -gm * dx / r;
@@ -381,6 +428,8 @@ struct sph_ctx {
   cudaStream_t stream;
   sphk::KParams kp;
   sph_material *d_mats;
+  sphk::MatT<float> *d_matf;
+  sphk::MatT<double> *d_matd;
   double *d_gtab, *d_phitab, *d_radii;
   sphk::Work w;
   // sort and cell list

@@ -493,9 +493,9 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
     const double H = s.h[ic];
     const float dtdiv = (float)P.dt[sy] * L.divv[ic];
     const double hp = L.hprev[ic];
-    const sph_material &M = P.mats[s.mat[ic] & (SPH_MAX_MATERIALS - 1)];
+    const MatT<float> &M = mat_t<float>(P, s.mat[ic]);
     // (no FP64 division: it costs tens of FP64 operations on this part)
-    const float rho0 = (float)M.rho0;
+    const float rho0 = M.rho0;
     const float hbar = cbrtf((float)(3.0 * P.n_ngb / (4.0 * kPi)) * ((float)s.m[ic] / rho0));
     const float lhp = hp > 0.0 ? logf((float)H / (float)hp) : 0.f;
     float f[NIN];

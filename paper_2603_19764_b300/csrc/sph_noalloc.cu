@@ -104,3 +104,4 @@ extern "C" sph_status sph_diagnostics_noalloc(const sph_state *st, int64_t n, do
   k_diag_final<<<1, kDiagThreads, 0, stream>>>(scratch, (int)blocks, sums);
   return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
 }
+

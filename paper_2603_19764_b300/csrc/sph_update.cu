@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
   const double dt = kick ? P.dt[sy] : 0.0, hdt = 0.5 * dt;
   double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T tmin = T(INFINITY);
+  const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
   for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
     const double m = s.m[i];
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
     double u = s.u[i];
     if (kick && !fixed) {
-      const sph_material &M = P.mats[s.mat[i] & (SPH_MAX_MATERIALS - 1)];
+      const MatT<T> &M = mat_t<T>(P, s.mat[i]);
       const double dS[5] = {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]};
       double S[5] = {s.sxx[i], s.syy[i], s.sxy[i], s.sxz[i], s.syz[i]};
 #pragma unroll
@@ -44,8 +45,8 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
       for (int k = 0; k < 5; ++k) S[k] += hdt * dS[k];
       if (M.strength) {
         const EosT<T> e = eos_t<T>(M, s.rho[i], u);
-        const T St[5] = {(T)S[0], (T)S[1], (T)S[2], (T)S[3], (T)S[4]};
-        const double f = (double)radial_factor_t<T>(St, yield_t<T>(M, e.P, (T)u), P.yield_norm);
+        const T St[5] = {to_t<T>(S[0]), to_t<T>(S[1]), to_t<T>(S[2]), to_t<T>(S[3]), to_t<T>(S[4])};
+        const double f = from_t(radial_factor_t<T>(St, yield_t<T>(M, e.P, to_t<T>(u)), P.yield_norm));
 #pragma unroll
         for (int k = 0; k < 5; ++k) S[k] *= f;
       } else {
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     ext_field_t<T>(P, x, y, z, g, &phi);
     acc[0] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     acc[1] += m * u;
-    acc[2] += m * (double)phi;
+    acc[2] += m * from_t(phi);
     acc[3] += m * v[0];
     acc[4] += m * v[1];
     acc[5] += m * v[2];
@@ -76,18 +77,18 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     acc[7] += m * (z * v[0] - x * v[2]);
     acc[8] += m * (x * v[1] - y * v[0]);
     if (!fixed) {
-      const T H = (T)s.h[i];
-      const T ax = (T)a[0], ay = (T)a[1], az = (T)a[2];
+      const T H = to_t<T>(s.h[i]);
+      const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
       const T am = sqrt(ax * ax + ay * ay + az * az);
-      const T ta = am > T(0) ? (T)P.eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
-      const T tc = (T)P.eta_c * H / (T)w.vsig[i];                          // Eq. 39
+      const T ta = am > T(0) ? eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
+      const T tc = eta_c * H / to_t<T>(w.vsig[i]);                    // Eq. 39
       tmin = tmin_(tmin, tmin_(ta, tc));
     }
   }
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kNSum; ++k) acc[k] = wsum(acc[k]);
-  double tm = wmin((double)tmin);
+  double tm = wmin(from_t(tmin));
   if (lane == 0) {
     for (int k = 0; k < kNSum; ++k) red[k][wi] = acc[k];
     redt[wi] = tm;

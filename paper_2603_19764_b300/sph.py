@@ -109,7 +109,7 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_set_spans", "sph_mlp_create", "sph_mlp_destroy", "sph_mlp_last_error",
            "sph_mlp_set", "sph_mlp_get", "sph_mlp_fit_norm", "sph_mlp_forward",
            "sph_mlp_loss_grad", "sph_mlp_adam_step", "sph_mlp_train_epoch",
-           "sph_set_learned_h", "sph_learn_samples")
+           "sph_set_learned_h", "sph_learn_samples", "sph_check_conversions")
 MLP_NPARAM, MLP_NNORM = 4673, 14
 GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
@@ -180,6 +180,8 @@ def lib():
         L.sph_set_learned_h.argtypes = [VP, C.c_int32, C.c_int32, VP]
         L.sph_learn_samples.restype = st
         L.sph_learn_samples.argtypes = [VP, VP, VP]
+        L.sph_check_conversions.restype = st
+        L.sph_check_conversions.argtypes = [VP, C.c_int64, _PL, VP]
         L.sph_autotune.restype = st
         L.sph_autotune.argtypes = [VP, C.c_int32]
         L.sph_set_spans.restype = st
