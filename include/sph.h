@@ -161,6 +161,7 @@ typedef struct {
   int64_t groups_density, groups_force;  /* lane groups the pair kernels formed */
   int32_t kernel_launches;               /* kernels the call launched */
   int64_t sweeps_total;                  /* Newton sweeps summed over particles */
+  int32_t n_expanded;                    /* FP32 form: solves closed by the expansion */
 } sph_step_info;
 
 /* Report of the group-span tuner (sph_autotune). The pair kernels give

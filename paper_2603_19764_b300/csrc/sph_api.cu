@@ -173,6 +173,7 @@ void fill_info(const sph_ctx *c, int sys, sph_step_info *info) {
   info->groups_force = (int64_t)h.groups_force;
   info->kernel_launches = c->nlaunch;
   info->sweeps_total = (int64_t)h.sweeps_total;
+  info->n_expanded = h.n_expanded;
 }
 
 // After a synchronisation: per-system dt_next from the mirrors, the report,
@@ -226,7 +227,7 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
   CK(launch_predict_pack(c, predict));
   CK(mark(c, 2));
   CK(tmark(c, 0));
-  CK(launch_density(c));
+  CK(launch_density(c, 1));   // the force pass that follows counts the neighbours
   CK(tmark(c, 1));
   CK(mark(c, 3));
   CK(launch_eos_pack(c));
@@ -740,7 +741,7 @@ sph_status sph_neighbours(sph_ctx *c) {
 sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
   ENTER(c);
   CK(launch_predict_pack(c, 0));
-  CK(launch_density(c));
+  CK(launch_density(c, 0));   // standalone: every solve ends on an evaluation
   sph_step_info info;
   const sph_status s = sync_status(c, &info);
   if (sweeps) *sweeps = info.sweeps;

@@ -71,6 +71,7 @@ struct DensArgs {
   KParams p;
   Status *st;
   void *spill;      // per-warp overflow of the candidate lists (kSpill entries)
+  int expand;       // close Newton steps by the expansion (FP32 form, full steps)
 };
 
 // Candidates beyond the shared-memory list of a warp continue in a private
@@ -78,6 +79,16 @@ struct DensArgs {
 // so that a list of up to CAP + kSpill candidates stays resident across the
 // Newton sweeps instead of being staged again for every sweep.
 constexpr int kSpill = 1024;
+
+// FP32 form within a full step: a Newton step of at most kExpand H is
+// accepted without a new evaluation of the sums when the second-order
+// expansion of rho(H) about the evaluated H already meets the tolerance at
+// the new H. The kernel sum is C^3 in H (the Wendland C2 kernel's (1-q)^4
+// factor), so the omitted third-order term is ~1e-8 of rho, below FP32
+// rounding; pairs entering or leaving the support between the two radii
+// weigh (dH/H)^4. The neighbour count at the accepted H is the force pass's
+// (it visits every pair within max(H_i, H_j)).
+constexpr double kExpand = 3e-3;
 
 template <typename V4> struct SpillView {
   V4 *p;
@@ -103,10 +114,6 @@ template <> struct PosPtr<double> {
   static __device__ __forceinline__ const double4_32a *get(const Work &w) { return w.pos64; }
 };
 
-// Canonical FP64 squared distance (no contraction).
-__device__ __forceinline__ double r2_canon(double dx, double dy, double dz) {
-  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
 
 // Per-lane bit masks over the staged list: bit k set when r_k^2 < R2.
 // Lanes with store = false compute but keep their previous words.
@@ -136,7 +143,7 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              double H2c, double xi64, double yi64, double zi64,
                                              const sph_state &s, int self, T &rs, T &rhs,
-                                             int &cnt) {
+                                             T &rhs2, int &cnt) {
   // every lane advances through its own words: lanes do not wait for each
   // other at word boundaries
   const int nw = (nl + 31) >> 5;
@@ -171,6 +178,8 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
         const T mW = q.w * t * t * t;
         rs += mW * t * (T(1) + T(4) * qq);
         rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
+        if (REL)   // H^5 d2W/dH2 / cW = (1-q)^2 (12 + 24q - 264q^2 + 288q^3)
+          rhs2 += q.w * t * t * (T(12) + qq * (T(24) + qq * (T(-264) + T(288) * qq)));
         // only a pair at r = 0 can be the particle itself
         cnt += r2 > T(0) ? 1 : (Li[k] != self);
       }
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   // persistent warps: each takes the next bucket of 32 particles
   const int nbuckets = A.p.nbuckets;
   long long w_pairs = 0, w_cand = 0;
-  int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0;
+  int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0, w_exp = 0;
   long long w_swt = 0;
   unsigned w_bad = 0;
   for (;;) {
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       const double H2c = __dmul_rn(H, H);
       const T H2 = REL ? Ht * Ht : (T)H2c;
       const T Rneed = wmax(act ? Ht : T(0));
-      T rs = T(0), rhs = T(0);
+      T rs = T(0), rhs = T(0), rhs2 = T(0);
       int cnt = 0;
       const bool resident = complete && Rneed <= Rl;
       if (!resident) {
@@ -305,9 +314,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           __syncwarp();
           if (act) {
             density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
-                                     zi64, A.s, (int)i, rs, rhs, cnt);
+                                     zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
             density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, H2c, xi64,
-                                     yi64, zi64, A.s, (int)i, rs, rhs, cnt);
+                                     yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
           }
           __syncwarp();
           if (stager_finished(sg)) break;
@@ -327,9 +336,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         }
         if (act) {
           density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
-                                   zi64, A.s, (int)i, rs, rhs, cnt);
+                                   zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
           density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, H2c, xi64,
-                                   yi64, zi64, A.s, (int)i, rs, rhs, cnt);
+                                   yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
         }
       }
 
@@ -361,6 +370,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           if (!(Hn <= 1.25 * H)) Hn = 1.25 * H;
           if (hi < INFINITY && (Hn <= lo || Hn >= hi)) Hn = 0.5 * (lo + hi);
           if (Hn > Hcap) Hn = Hcap;
+          if (REL && A.expand && fabs(Hn - H) <= kExpand * H) {
+            // rho, d rho / dH at Hn from the second-order expansion about H
+            const T d = (T)(Hn - H);
+            const T rho2 = T(cW) * ih3 * ih * ih * rhs2;
+            const T r1 = rho + d * (rhoH + T(0.5) * rho2 * d);
+            const T H1 = (T)Hn;
+            const T gq1 = T(4.0 * kPi / 3.0) * H1 * H1 * H1 * r1 / target - T(1);
+            if (fabs(gq1) <= tol && r1 > T(0)) {
+              rho_o = r1;
+              om_o = T(1) + H1 / (T(3) * r1) * (rhoH + rho2 * d);
+              H_o = Hn;
+              state = 1;
+              ++w_exp;
+            }
+          }
           H = Hn;
         }
       }
@@ -393,8 +417,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const unsigned nbad = __ballot_sync(kFull, w_bad != 0u);
   const long long pw = wsum(w_pairs);
   const long long swt = wsum(w_swt);
+  const int nexp = wsum(w_exp);
   if (lane == 0) {
     atomicMax(&A.st->max_sweeps, sw);
+    if (nexp) atomicAdd(&A.st->n_expanded, nexp);
     atomicAdd(&A.st->sweeps_total, (unsigned long long)swt);
     if (nu) {
       atomicAdd(&A.st->n_unconv, nu);
@@ -408,8 +434,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   }
 }
 
-cudaError_t launch_density(sph_ctx *c) {
+cudaError_t launch_density(sph_ctx *c, int expand) {
   DensArgs a;
+  a.expand = expand;
   a.s = c->st;
   a.w = c->w;
   a.n = c->n;

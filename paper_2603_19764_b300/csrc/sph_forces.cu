@@ -7,10 +7,11 @@
 // the cells overlapping the group's box grown by max(H_group, H_max) are
 // kept when within max(H_group, H_j) of the box and staged in shared memory
 // as (x, y, z, H^2). Each lane marks the candidates with
-// 0 < r^2 < max(H_i, H_j)^2 (broadcast reads, one bit per candidate), then
+// r^2 < max(H_i, H_j)^2 (broadcast reads, one bit per candidate), then
 // walks its own set bits independently, so the heavy pair body runs only
-// for real neighbours. A pair at r = 0 contributes nothing to any sum below
-// (every term carries x_ij), so excluding it is exact.
+// for real neighbours. A pair at r = 0 (the particle itself, or a coincident
+// one) contributes nothing to any sum below (every term carries x_ij); the
+// walk also counts the neighbours r < H_i of the smoothing-length solve.
 //
 // The per-pair sums use the algebraically equal contracted forms
 //   a_i   += m_j W'_i/r sig~_i x_ij + W'_j/r (m sig~)_j x_ij      (Eq. 4, 18)
@@ -195,6 +196,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
   const T sxz = a2.x * im, syz = a2.y * im, iOr = a2.z * im;
   const T Hi = p.w, Hi2 = p.w * p.w, invHi = a3.y, Ki = a3.z;
   const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi = a3.x;
+  // neighbour count of particle i (r < H_i by the canonical predicate):
+  // the density solve may close on an expanded sum and leave it to this pass
+  int nngb = 0;
   const T al = pconst<T>(A.p.av_alpha, A.p.av_alpha_f);
   const T be = pconst<T>(A.p.av_beta, A.p.av_beta_f);
   const T ep = pconst<T>(A.p.av_eps, A.p.av_eps_f);
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           const V4 q = Lr[kb + b];
           const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
-          mk |= ((r2 > T(0)) & (r2 < tmax(Hi2, q.w)) ? 1u : 0u) << b;
+          mk |= (r2 < tmax(Hi2, q.w) ? 1u : 0u) << b;
         }
         Lm[wd][lane] = act ? mk : 0u;
       }
@@ -273,6 +277,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           const V4 f0 = V::ld(rj, 0), f1 = V::ld(rj, 1), f2 = V::ld(rj, 2), f3 = V::ld(rj, 3);
           const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
+          {
+            bool inH;
+            if (REL) {
+              inH = r2 < Hi2;
+              if (fabs(r2 - Hi2) < T(1e-5) * Hi2) {   // rare: decide in FP64
+                const double h = A.s.h[i];
+                inH = r2_canon(A.s.x[i] - A.s.x[j], A.s.y[i] - A.s.y[j], A.s.z[i] - A.s.z[j]) <
+                      __dmul_rn(h, h);
+              }
+            } else {
+              const double h = A.s.h[i];
+              inH = r2_canon((double)dx, (double)dy, (double)dz) < __dmul_rn(h, h);
+            }
+            nngb += (inH && (r2 > T(0) || j != (int)i)) ? 1 : 0;
+          }
+          // a pair at r = 0 (the particle itself, or a coincident one)
+          // contributes nothing below: every term carries x_ij
           const T r = root(r2);
           const T ti = tmax(T(1) - r * invHi, T(0));
           const T tj = tmax(T(1) - r * f3.y, T(0));
@@ -312,7 +333,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           const T gx = gs * dx, gy = gs * dy;
           C0.add(gx * dx); C1.add(gx * dy); C2.add(gx * dz);
           C3.add(gy * dy); C4.add(gy * dz); C5.add(gs * dz * dz);
-          ++npairs;
+          npairs += r2 > T(0) ? 1 : 0;
           if (++blk == kSumBlock) {   // lanes stay in step: one pair per pass each
             blk = 0;
             du.flush(); F0.flush(); F1.flush(); F2.flush(); F3.flush();
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
       const T k00 = c11 * c22 - c12 * c12, k01 = c02 * c12 - c01 * c22,
               k02 = c01 * c12 - c02 * c11;
       const T det = c00 * k00 + c01 * k01 + c02 * k02;
-      if (A.s.nngb[i] >= 8 && fabs(det) >= T(1e-3)) {
+      if (nngb >= 8 && fabs(det) >= T(1e-3)) {
         const T id = T(1) / det;
         Cm[0] = k00 * id;
         Cm[1] = Cm[3] = k01 * id;
@@ -388,6 +409,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
       dS[q] = T(2) * Gam * (E[3 * a + b] - (a == b ? tr3 : T(0))) + sg * rot;
     }
     A.w.vsig[i] = from_t((T(1) + T(0.6) * al) * s1.z + T(0.6) * be * mumax);
+    A.s.nngb[i] = nngb;
     A.w.edot2[i] = from_t(T(0.5) * e2);
     if (A.w.divv) A.w.divv[i] = (float)(E[0] + E[4] + E[8]);
     const T axt = ax + s2.x, ayt = ay + s2.y, azt = az + s2.z;

@@ -23,6 +23,7 @@ __global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full) {
     st->groups_density = 0;
     st->groups_force = 0;
     st->sweeps_total = 0;
+    st->n_expanded = 0;
     if (full) st->err = 0;
   }
   for (int k = threadIdx.x; k < nsys; k += blockDim.x) {

@@ -59,6 +59,8 @@ struct Status {
   unsigned long long cand_density, cand_force;   // staged candidates
   unsigned long long groups_density, groups_force;
   unsigned long long sweeps_total;              // Newton sweeps summed over particles
+  int n_expanded;                               // solves closed by the expansion
+  int pad3_;
   unsigned next_bucket[2];                      // persistent-warp work counters
   int total_cells;                              // cells of all systems this step
   int pad2_;
@@ -499,7 +501,7 @@ cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift);
 cudaError_t launch_grid_setup(sph_ctx *c);
 cudaError_t launch_sort_permute(sph_ctx *c);
 cudaError_t launch_predict_pack(sph_ctx *c, int predict);
-cudaError_t launch_density(sph_ctx *c);
+cudaError_t launch_density(sph_ctx *c, int expand);
 cudaError_t launch_eos_pack(sph_ctx *c);
 cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_kick(sph_ctx *c, int kick);

@@ -48,6 +48,12 @@ template <> __device__ __forceinline__ float quot<float>(float a, float b) {
 }
 template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
 
+// Canonical FP64 squared distance (no contraction): the neighbour predicate
+// r < H of every count compares this against H * H.
+__device__ __forceinline__ double r2_canon(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
 // Squared distance of a point to an axis-aligned box (0 inside).
 template <typename T>
 __device__ __forceinline__ T box_d2(T x, T y, T z, T x0, T x1, T y0, T y1, T z0, T z1) {

@@ -81,7 +81,7 @@ class SphStepInfo(C.Structure):
                 ("device_flags", C.c_uint32), ("cand_density", C.c_int64),
                 ("cand_force", C.c_int64), ("groups_density", C.c_int64),
                 ("groups_force", C.c_int64), ("kernel_launches", C.c_int32),
-                ("sweeps_total", C.c_int64)]
+                ("sweeps_total", C.c_int64), ("n_expanded", C.c_int32)]
 
     def as_dict(self) -> dict:
         return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
@@ -91,7 +91,8 @@ class SphStepInfo(C.Structure):
                     pairs_force=self.pairs_force, device_flags=self.device_flags,
                     cand_density=self.cand_density, cand_force=self.cand_force,
                     groups_density=self.groups_density, groups_force=self.groups_force,
-                    kernel_launches=self.kernel_launches, sweeps_total=self.sweeps_total)
+                    kernel_launches=self.kernel_launches, sweeps_total=self.sweeps_total,
+                    n_expanded=self.n_expanded)
 
 
 class SphTuneReport(C.Structure):

@@ -55,7 +55,7 @@ int main(void) {
   O(sph_state, id) O(sph_state, nngb) O(sph_material, strength) O(sph_material, xi)
   O(sph_params, g_table) O(sph_params, g_n) O(sph_params, box_hi) O(sph_params, precision)
   O(sph_step_info, pairs_density) O(sph_step_info, device_flags) O(sph_step_info, sweeps)
-  O(sph_step_info, kernel_launches) O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
+  O(sph_step_info, kernel_launches) O(sph_step_info, n_expanded) O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
   return 0;
 }
 """

@@ -170,3 +170,39 @@ def test_conservation_on_gpu():
     a = np.stack([g["ax"], g["ay"], g["az"]], 1)
     assert np.all(np.abs((m[:, None] * a).sum(0)) < 1e-12 * np.abs(m[:, None] * a).sum(0))
     sim.close()
+
+
+def test_expansion_closed_solves_match_direct_sums():
+    """FP32 form within full steps: a Newton step accepted from the
+    second-order expansion of rho(H) (no new evaluation) still gives the
+    kernel sums at the accepted H -- tighter than the form's tolerance,
+    1.5e-6, as the omitted term is ~1e-8 -- and the force pass's count is
+    the exact count there."""
+    w = wl.impact(20000, 2500, seed=13, precision=1)
+    p = _params(w, 1)
+    sim = sph.Simulation(w.arrays, w.materials, p)
+    sim.prime()
+    infos = [sim.step(0.0) for _ in range(3)]
+    g = sim.to_numpy()
+    sim.close()
+    assert infos[-1]["n_expanded"] > w.n // 4, [i["n_expanded"] for i in infos]
+    rho, om, cnt = oracle.density_given_h(p, g)
+    assert np.array_equal(cnt, g["nngb"])
+    assert np.max(np.abs(g["rho"] / rho - 1)) < 1.5e-6
+    assert np.max(np.abs(g["omega"] - om)) < 2e-5
+
+
+def test_standalone_density_evaluates_at_its_final_radius():
+    """sph_density alone never closes on an expansion: its counts and sums
+    are those of its final H."""
+    w = wl.impact(20000, 2500, seed=14, precision=1)
+    p = _params(w, 1)
+    sim = sph.Simulation(w.arrays, w.materials, p)
+    sim.prime()
+    sim.step(0.0)
+    sim.density()
+    g = sim.to_numpy()
+    sim.close()
+    rho, om, cnt = oracle.density_given_h(p, g)
+    assert np.array_equal(cnt, g["nngb"])
+    assert np.max(np.abs(g["rho"] / rho - 1)) < 1e-5
