@@ -471,16 +471,27 @@ namespace sphk {
 // log(H_now / H_prev) as a training sample; with a guess mode, the starting
 // radius of the next step's solve: H exp(-dt div v / 3) (continuity) or
 // H exp(network) (learned), the ratio limited to [0.8, 1.25].
+// NET: the network guess (the network in shared memory); otherwise the
+// kernel needs no shared memory and keeps more warps in flight.
+struct LearnSmem {
+  Smem S;
+  __nv_bfloat16 xs[4][32 * LD1];
+  float outs[4][32];
+};
+
+template <bool NET>
 __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P, LearnArgs L,
                                                Net N) {
-  __shared__ __align__(16) Smem S;
-  __shared__ __align__(16) __nv_bfloat16 xs[4][32 * LD1];
-  __shared__ float outs[4][32];
-  const bool use_net = L.guess == SPH_GUESS_NETWORK;
-  if (use_net) load_net(S, N, false);
+  extern __shared__ __align__(16) unsigned char learn_smem[];
+  LearnSmem &Q = *reinterpret_cast<LearnSmem *>(learn_smem);
+  Smem &S = Q.S;
+  const bool use_net = NET;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = lane; e < 32 * LD1; e += 32) xs[w][e] = __float2bfloat16_rn(0.f);
-  __syncthreads();
+  if (NET) {
+    load_net(S, N, false);
+    for (int e = lane; e < 32 * LD1; e += 32) Q.xs[w][e] = __float2bfloat16_rn(0.f);
+    __syncthreads();
+  }
   const int64_t nchunks = (n + 31) / 32;
   for (int64_t ch = (int64_t)blockIdx.x * 4 + w; ch < nchunks; ch += (int64_t)gridDim.x * 4) {
     const int64_t i = ch * 32 + lane;
@@ -523,21 +534,21 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
     if (use_net) {
 #pragma unroll
       for (int k = 0; k < NIN; ++k)
-        xs[w][lane * LD1 + k] = __float2bfloat16_rn((f[k] - S.mu[k]) * S.isd[k]);
+        Q.xs[w][lane * LD1 + k] = __float2bfloat16_rn((f[k] - S.mu[k]) * S.isd[k]);
       __syncwarp();
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         uint32_t ax[4];
-        load_a(xs[w], LD1, 16 * half, 0, ax);
+        load_a(Q.xs[w], LD1, 16 * half, 0, ax);
         Tile T;
         forward_tile(S, ax, T);
         if ((lane & 3) == 0) {
-          outs[w][16 * half + (lane >> 2)] = T.out[0];
-          outs[w][16 * half + (lane >> 2) + 8] = T.out[1];
+          Q.outs[w][16 * half + (lane >> 2)] = T.out[0];
+          Q.outs[w][16 * half + (lane >> 2) + 8] = T.out[1];
         }
       }
       __syncwarp();
-      r = S.ymu + S.ysd * outs[w][lane];
+      r = S.ymu + S.ysd * Q.outs[w][lane];
       __syncwarp();
     }
     if (valid) {
@@ -554,7 +565,11 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
 cudaError_t launch_learn(sph_ctx *c) {
   if (!c->learn.hprev) return cudaSuccess;
   const int blocks = (int)((c->n + 127) / 128 < 148 * 8 ? (c->n + 127) / 128 : 148 * 8);
-  k_learn<<<blocks, 128, 0, c->stream>>>(c->st, c->n, c->kp, c->learn, net_of(c->net));
+  if (c->learn.guess == SPH_GUESS_NETWORK)
+    k_learn<true><<<blocks, 128, sizeof(LearnSmem), c->stream>>>(c->st, c->n, c->kp, c->learn,
+                                                                 net_of(c->net));
+  else
+    k_learn<false><<<blocks, 128, 0, c->stream>>>(c->st, c->n, c->kp, c->learn, net_of(c->net));
   c->nlaunch += 1;
   return cudaGetLastError();
 }
