@@ -130,6 +130,25 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+# ------------------------------------------------------------ ranks
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest of every rank's value (the job takes as long as its
+    slowest rank); the identity on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the
+    slowest rank's time (replicas: each rank steps its own copy)."""
+    return world * units_per_rank * steps / seconds
+
+
 # ------------------------------------------------------------ workloads
 def make_workload(scale: float, precision: int):
     from paper_2603_19764_b300 import workloads as wl
@@ -284,9 +303,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clocks = sampler.stop() if sampler else None
     if world > 1:
         dist.barrier()
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     # phase times (for the roofline) from direct launches of the same
     # form: steps replayed from a graph carry no phase events
     sim.set_graph(False)
@@ -297,7 +314,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sim.set_timing(False)
     tune_rep = sim.tune_info()
     ms_step = ms / args.steps
-    value = world * w.n * args.steps / (ms / 1e3)
+    value = job_rate(w.n, world, args.steps, ms / 1e3)
 
     # roofline of the dominant kernel (by CUDA-event phase time)
     nsteps = max(phases["steps"], 1)
@@ -330,11 +347,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         for _ in range(ne):
             r = sim.step_host(host, 0.0)
         te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": world * w.n * ne / te, "unit": "particle-steps/s",
+        te = max_over_ranks(te, world, dev)
+        e2e = {"value": job_rate(w.n, world, ne, te), "unit": "particle-steps/s",
                "h2d_bytes_per_step": r["bytes_in"], "d2h_bytes_per_step": r["bytes_out"],
                "steps": ne}
     # error of this form against the FP64 oracle on a seeded sample, on the
@@ -457,11 +471,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     ms_c, infos, rep, err, clocks = batched(1, args.steps, 2, True, sampler)
-    if world > 1:
-        t = torch.tensor([ms_c], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_c = float(t.item())
-    value = world * w.n * args.steps / (ms_c / 1e3)
+    ms_c = max_over_ranks(ms_c, world, dev)
+    value = job_rate(w.n, world, args.steps, ms_c / 1e3)
     ks = max(1, min(args.steps, args.plain_steps))
     arms = {}
     if rank == 0:
