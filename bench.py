@@ -328,13 +328,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         kname, flops, tk = "k_density", FLOPS_DENSITY_PAIR * pairs_d, t_dens
     achieved = flops / (tk / 1e3) / 1e12
     peak = fp32_peak_tflops(MAX_MHZ) if precision else fp64_peak_tflops(MAX_MHZ)
+    fma = {"fp32": sph.measure_fma_peak(1, 20), "fp64": sph.measure_fma_peak(0, 5)}
+    fma_own = fma["fp32" if precision else "fp64"]
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_per_launch(kname, w.n, precision), "traffic_unit": "bytes",
                 "peak_basis": ("%s lanes x 2 x %.0f MHz (unit counts)" %
                                ("148x128 FP32" if precision else "FP64 nominal 1.25 TFLOP/s",
                                 MAX_MHZ)),
-                "kernel_ms": tk, "pairs_per_step": pairs_f if kname == "k_forces" else pairs_d}
+                "kernel_ms": tk, "pairs_per_step": pairs_f if kname == "k_forces" else pairs_d,
+                "peak_fma_measured": fma_own["tflops"],
+                "frac_of_fma_measured": achieved / fma_own["tflops"]}
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -384,6 +388,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "tuner": tune_rep, "graph": not args.no_graph,
                 "gpu_launches": sum(i["kernel_launches"] for i in infos),
                 "plain_fp64": plain,
+                "fma_peak_measured": {k: {q: v[q] for q in ("tflops", "ms", "sm_mhz")}
+                                      for k, v in fma.items()},
                 "clocks": clocks,
                 "phases_ms_per_step": {k: (v / nsteps if k != "steps" else v)
                                        for k, v in phases.items()},
@@ -653,6 +659,123 @@ def run_learned(args, rank: int, world: int, local_rank: int):
     net.close()
 
 
+def oracle_error(g: dict, w, p, precision: int, idx=None) -> dict:
+    """Derivatives of a GPU state g (rho, omega, H, counts as the GPU left
+    them) against the FP64 oracle evaluated on that same state, on the
+    particles idx (None = all)."""
+    import oracle
+    rho, _, cnt = oracle.density_given_h(p, g, idx=idx)
+    st, S = oracle.eos_yield(p, w.materials, g)
+    out, _ = oracle.forces(p, w.materials, st, S=S, idx=idx)
+    sel = np.arange(g["x"].shape[0]) if idx is None else idx
+    derr = {}
+    for f in ("ax", "ay", "az", "dudt", "dsxx", "dsyy", "dsxy", "dsxz", "dsyz"):
+        scale = float(np.max(np.abs(g[f]))) or 1.0
+        derr[f] = float(np.max(np.abs(g[f][sel] - out[f][sel]))) / scale
+    return {"n": int(sel.size), "rho_rel_max": float(np.max(np.abs(g["rho"][sel] / rho - 1))),
+            "count_mismatches": int(np.count_nonzero(cnt != g["nngb"][sel])),
+            "deriv_maxnorm_rel": max(derr.values()), "deriv_by_field": derr,
+            "tolerance": {"rho_rel": 1e-5 if precision else 1e-6,
+                          "deriv_maxnorm_rel": 1e-4 if precision else 1e-9}}
+
+
+def run_drift(args, rank: int, world: int, local_rank: int):
+    """Error and conservation of the chosen form over `--drift-steps` steps of
+    the impact, beside the plain FP64 form stepped with the same step sizes
+    (the FP64 run's adaptive dt, Eq. 38-39, drives both).
+
+    * one-step error: at every `--spot-every`-th step the FP32 form's state
+      is copied into a fresh context whose derivatives are recomputed and
+      compared with the oracle's on the same state (seeded sample of
+      `--spot` particles); at the checkpoints (1, 10, last) on every
+      particle. The stepping contexts are never touched by the checks.
+    * trajectory: FP32 form against FP64 form, particle by particle.
+    * conservation: total energy (kinetic + internal + potential of the
+      fixed radial field) of both runs against the start. Linear momentum
+      is reported too; the field is external, so it is not conserved."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2603_19764_b300 import build, sph
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.scale, 1)
+    pa = dict(w.params, precision=1, h_tol=1e-6)
+    pb = dict(w.params, precision=0, h_tol=1e-10)
+    A = sph.Simulation(w.arrays, w.materials, pa, device=str(dev))
+    B = sph.Simulation(w.arrays, w.materials, pb, device=str(dev))
+    ia, ib = A.prime(), B.prime()
+    A.set_spans(*[int(v) for v in (args.spans or "1,2").split(",")])
+    A.set_graph(True)
+    m = w.arrays["m"]
+    vscale = float(np.sum(m * np.sqrt(w.arrays["vx"] ** 2 + w.arrays["vy"] ** 2
+                                      + w.arrays["vz"] ** 2)))
+
+    def energy(i):
+        return i["e_kin"] + i["e_int"] + i["e_pot"]
+
+    e0a, e0b = energy(ia), energy(ib)
+    ekin0 = ib["e_kin"]
+    p0a, p0b = np.array(ia["p"]), np.array(ib["p"])
+    keys = ("x", "y", "z", "vx", "vy", "vz", "rho", "u", "h")
+    x0 = _by_id(A.to_numpy(), ("x", "y", "z"))
+    nsteps = args.drift_steps
+    checkpoints = sorted({1, min(10, nsteps), nsteps})
+    rng = np.random.default_rng(11)
+    spot, full, traj, cons = [], [], [], []
+    t_start = time.perf_counter()
+    for k in range(1, nsteps + 1):
+        ib = B.step(0.0)
+        ia = A.step(ib["dt"])
+        cons.append({"step": k, "dt": ib["dt"],
+                     "dE_fp32k": (energy(ia) - e0a) / ekin0, "dE_fp64": (energy(ib) - e0b) / ekin0,
+                     "dp_fp32k": float(np.linalg.norm(np.array(ia["p"]) - p0a)) / vscale,
+                     "dp_fp64": float(np.linalg.norm(np.array(ib["p"]) - p0b)) / vscale})
+        is_cp = k in checkpoints
+        if k % args.spot_every == 0 or is_cp:
+            ga = A.to_numpy()
+            C = sph.Simulation(ga, w.materials, pa, device=str(dev))
+            C.neighbours()
+            C.density()
+            C.forces_strength()
+            gc = C.to_numpy()
+            C.close()
+            idx = np.sort(rng.choice(w.n, min(args.spot, w.n), replace=False))
+            e = oracle_error(gc, w, pa, 1, idx=idx)
+            spot.append(dict(step=k, **{q: e[q] for q in ("n", "rho_rel_max", "count_mismatches",
+                                                          "deriv_maxnorm_rel")}))
+            if is_cp:
+                full.append(dict(step=k, **oracle_error(gc, w, pa, 1)))
+                a = _by_id(ga, keys)
+                b = _by_id(B.to_numpy(), keys)
+                disp = max(float(np.max(np.abs(b[q] - x0[q]))) for q in ("x", "y", "z"))
+                dx = np.sqrt(sum((a[q] - b[q]) ** 2 for q in ("x", "y", "z")))
+                vmax = float(np.max(np.sqrt(b["vx"] ** 2 + b["vy"] ** 2 + b["vz"] ** 2)))
+                dv = np.sqrt(sum((a[q] - b[q]) ** 2 for q in ("vx", "vy", "vz")))
+                drho = np.abs(a["rho"] / b["rho"] - 1)
+                traj.append({"step": k, "max_disp": disp,
+                             "dx_max_over_disp": float(dx.max()) / disp,
+                             "dx_p99_over_disp": float(np.quantile(dx, 0.99)) / disp,
+                             "dv_max_over_vmax": float(dv.max()) / vmax,
+                             "dv_p99_over_vmax": float(np.quantile(dv, 0.99)) / vmax,
+                             "drho_max": float(drho.max()),
+                             "drho_p99": float(np.quantile(drho, 0.99)),
+                             "dh_max": float(np.max(np.abs(a["h"] / b["h"] - 1)))})
+    A.close()
+    B.close()
+    line = {"mode": "drift", "workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg",
+            "particles": w.n, "steps": nsteps, "form": "fp32k (spans %s, graph)" % (args.spans or "1,2"),
+            "seconds": time.perf_counter() - t_start,
+            "dt": "adaptive from the FP64 run, Eq. 38-39, the same for both",
+            "spot_error": spot, "full_error": full, "trajectory_fp32k_vs_fp64": traj,
+            "conservation": [c for c in cons if c["step"] in checkpoints or c["step"] % 10 == 0],
+            "conservation_max": {q: max(abs(c[q]) for c in cons)
+                                 for q in ("dE_fp32k", "dE_fp64", "dp_fp32k", "dp_fp64")},
+            "units": {"dE": "(E - E0) / E_kin0", "dp": "|p - p0| / sum m|v0|"}}
+    print(json.dumps(line), flush=True)
+
+
 def _by_id(g: dict, keys) -> dict:
     order = np.argsort(g["id"], kind="stable")
     return {k: g[k][order] for k in keys}
@@ -676,7 +799,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--spans", default="", help="density,forces group spans (no tuning)")
     ap.add_argument("--plain-steps", type=int, default=3)
-    ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned"])
+    ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned", "drift"])
+    ap.add_argument("--drift-steps", type=int, default=100)
+    ap.add_argument("--spot-every", type=int, default=5)
+    ap.add_argument("--spot", type=int, default=10_000)
     ap.add_argument("--history-steps", type=int, default=200)
     ap.add_argument("--record-every", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=3)
@@ -701,6 +827,8 @@ def main():
             run_batch(args, rank, world, local_rank)
         elif args.workload == "learned":
             run_learned(args, rank, world, local_rank)
+        elif args.workload == "drift":
+            run_drift(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

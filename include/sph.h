@@ -265,6 +265,28 @@ sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces);
 /* The tuner's state and timings. */
 sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out);
 
+/* Measured FMA throughput of the current device. */
+typedef struct {
+  double tflops;    /* FLOP/s / 1e12, an FMA counting 2 FLOP */
+  double ms;        /* average launch duration (CUDA events) */
+  double sm_mhz;    /* SM clock during the last launch: cycles / elapsed ns
+                       of one block spanning the launch */
+  double flops;     /* FLOP per launch */
+  int32_t n_sm;     /* multiprocessors the launch covered */
+  int32_t pad_;
+} sph_peak_report;
+
+/* FMA microbenchmark: one warm-up and then `launches` (1..10000) launches
+ * of a kernel whose threads run eight independent FMA chains each, in FP32
+ * (precision 1) or FP64 (precision 0), over 4 blocks of 256 threads per
+ * multiprocessor. Reports the average launch; the throughput is the peak
+ * the pair kernels' ALU roofline compares against at the clock the GPU
+ * actually holds. Allocates 64 bytes; synchronises `cuda_stream` (NULL =
+ * the legacy default stream). SPH_E_ARG for a bad precision, count or a
+ * NULL out. */
+sph_status sph_measure_fma_peak(int32_t precision, int32_t launches, sph_peak_report *out,
+                                void *cuda_stream);
+
 /* Self-check of the library's own FP64 <-> FP32 conversions (the
  * per-particle kernels convert on the integer pipe, since the conversion
  * instructions run on the FP64 unit): for each of the n DEVICE values, the

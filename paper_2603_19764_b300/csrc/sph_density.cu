@@ -14,8 +14,8 @@
 // FP64 form: absolute positions, canonical predicate r^2 = (dx dx + dy dy) +
 // dz dz without fused multiply-add. FP32 form: positions relative to the
 // group's reference cell, FP32 sums and Newton arithmetic (H itself is kept
-// in FP64); pairs with |r^2 - H^2| < 1e-5 H^2 are re-decided with the FP64
-// predicate so that neighbour counts stay exact.
+// in FP64); pairs with |r^2 - H^2| inside the guard band (sph_pair.cuh) are
+// re-decided with the FP64 predicate so that neighbour counts stay exact.
 #include "sph_pair.cuh"
 
 namespace sphk {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void build_masks(const V4 *Lp, unsigned (*Lm)[32], in
 template <typename T, typename V4, bool REL>
 __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
-                                             double H2c, double xi64, double yi64, double zi64,
+                                             T gb, double H2c, double xi64, double yi64, double zi64,
                                              const sph_state &s, int self, T &rs, T &rhs,
                                              T &rhs2, int &cnt) {
   // every lane advances through its own words: lanes do not wait for each
@@ -164,7 +164,7 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
       if (REL) {
         r2 = dx * dx + dy * dy + dz * dz;
         in = r2 < H2;
-        if (fabs(r2 - H2) < T(1e-5) * H2) {
+        if (fabs(r2 - H2) < gb) {
           const int j = Li[k];
           in = r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]) < H2c;
         }
@@ -265,7 +265,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       const T invHt = T(1) / Ht;
       const double H2c = __dmul_rn(H, H);
       const T H2 = REL ? Ht * Ht : (T)H2c;
-      const T Rneed = wmax(act ? Ht : T(0));
+      const T gb = guard_band(Ht, Lt);
+      // smallest mask radius: Hq^2 > H^2 + gb, so that no pair with r < H
+      // by the FP64 predicate falls outside the mask or the list
+      const T Hq = Ht * T(1.0001) + T(1e-5) * tmax(Ht, Lt);
+      const T Rneed = wmax(act ? Hq : T(0));
       T rs = T(0), rhs = T(0), rhs2 = T(0);
       int cnt = 0;
       const bool resident = complete && Rneed <= Rl;
@@ -309,13 +313,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           // list longer than both buffers: evaluate this segment exactly
           const int n1 = min(nl, CAP), n2 = nl - n1;
           __syncwarp();
-          build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, H2 * T(1.0001), act, lane);
-          build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, H2 * T(1.0001), act, lane);
+          build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, Hq * Hq, act, lane);
+          build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
           __syncwarp();
           if (act) {
-            density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
+            density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
                                      zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-            density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, H2c, xi64,
+            density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
                                      yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
           }
           __syncwarp();
@@ -324,10 +328,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       }
       if (complete) {
         // resident list: refresh the masks of lanes whose H outgrew them
-        const bool rebuild = act && !(Hm >= Ht * T(1.0001));
+        const bool rebuild = act && !(Hm >= Hq);
         const int n1 = min(nl, CAP), n2 = nl - n1;
         if (__any_sync(kFull, rebuild)) {
-          const T Hn = rebuild ? Ht * T(1.02) : Hm;
+          const T Hn = rebuild ? tmax(Ht * T(1.02), Hq) : Hm;
           __syncwarp();
           build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
           build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
@@ -335,9 +339,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           Hm = Hn;
         }
         if (act) {
-          density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, H2c, xi64, yi64,
+          density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
                                    zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-          density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, H2c, xi64,
+          density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
                                    yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
         }
       }

@@ -7,9 +7,10 @@
 // the cells overlapping the group's box grown by max(H_group, H_max) are
 // kept when within max(H_group, H_j) of the box and staged in shared memory
 // as (x, y, z, H^2). Each lane marks the candidates with
-// r^2 < max(H_i, H_j)^2 (broadcast reads, one bit per candidate), then
-// walks its own set bits independently, so the heavy pair body runs only
-// for real neighbours. A pair at r = 0 (the particle itself, or a coincident
+// r^2 < max(H_i, H_j)^2 (broadcast reads, one bit per candidate; the H_i
+// radius is widened by the guard band of sph_pair.cuh so that the count
+// below loses no pair to FP32 rounding), then walks its own set bits
+// independently, so the heavy pair body runs only for real neighbours. A pair at r = 0 (the particle itself, or a coincident
 // one) contributes nothing to any sum below (every term carries x_ij); the
 // walk also counts the neighbours r < H_i of the smoothing-length solve.
 //
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
   const T sxx = a1.x * im, syy = a1.y * im, szz = a1.z * im, sxy = a1.w * im;
   const T sxz = a2.x * im, syz = a2.y * im, iOr = a2.z * im;
   const T Hi = p.w, Hi2 = p.w * p.w, invHi = a3.y, Ki = a3.z;
+  const T gi = guard_band(Hi, Lt);   // r^2 band the FP32 sum cannot decide
   const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi = a3.x;
   // neighbour count of particle i (r < H_i by the canonical predicate):
   // the density solve may close on an expanded sum and leave it to this pass
@@ -218,7 +220,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
     const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
     const T zi = REL ? p.z + (T)(cz - G.rz) * Lt : p.z;
     const T Rb = wmax(act ? Hi : T(0));
-    const T Rf = tmax(Rb, hmax_all);
+    // lists and masks reach r^2 < H_i^2 + gi: no pair with r < H_i by the
+    // FP64 predicate escapes the count
+    const T gmax = guard_band(Rb, Lt);
+    const T Rf = tmax(Rb, hmax_all) + T(1e-5) * tmax(Rb, Lt);
     const Box<T> bx = group_box(act, xi, yi, zi);
     Stager sg = make_stager<T, REL>(bx, Rf, g, invL, G.rx, G.ry, G.rz);
     for (;;) {
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
         const T xj = q.x + ox, yj = q.y + oy, zj = q.z + oz;
         const T R = tmax(Rb, q.w);
         const bool keep =
-            ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R;
+            ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R + gmax;
         const unsigned bal = __ballot_sync(kFull, keep);
         if (keep) {
           const int at = nl + __popc(bal & lanemask_lt());
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
       }
       cand += nl;
       __syncwarp();
-      // membership bits: 0 < r^2 < max(H_i, H_j)^2
+      // membership bits: r^2 < max(H_i^2 + gi, H_j^2)
       const int nw = (nl + 31) >> 5;
       for (int wd = 0; wd < nw; ++wd) {
         const int kb = wd << 5;
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           const V4 q = Lr[kb + b];
           const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
           const T r2 = dx * dx + dy * dy + dz * dz;
-          mk |= (r2 < tmax(Hi2, q.w) ? 1u : 0u) << b;
+          mk |= (r2 < tmax(Hi2 + gi, q.w) ? 1u : 0u) << b;
         }
         Lm[wd][lane] = act ? mk : 0u;
       }
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
             bool inH;
             if (REL) {
               inH = r2 < Hi2;
-              if (fabs(r2 - Hi2) < T(1e-5) * Hi2) {   // rare: decide in FP64
+              if (fabs(r2 - Hi2) < gi) {   // rare: decide in FP64
                 const double h = A.s.h[i];
                 inH = r2_canon(A.s.x[i] - A.s.x[j], A.s.y[i] - A.s.y[j], A.s.z[i] - A.s.z[j]) <
                       __dmul_rn(h, h);
@@ -292,6 +297,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
             }
             nngb += (inH && (r2 > T(0) || j != (int)i)) ? 1 : 0;
           }
+          // a pair marked only for the count (r^2 in the band past both
+          // radii) has no say in the signal velocity and no place in the
+          // pair statistics; its kernel weights are zero up to the rounding
+          // of r / H (below 1e-20 of a neighbour's)
+          const bool inR = r2 < tmax(Hi2, q.w);
           // a pair at r = 0 (the particle itself, or a coincident one)
           // contributes nothing below: every term carries x_ij
           const T r = root(r2);
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           az += mWi * yiz + Wj * yjz;
           T dsum = -mWi * (vx * yix + vy * yiy + vz * yiz);
           const T vr = vx * dx + vy * dy + vz * dz;
-          if (vr < T(0)) {  // Eq. 5-8
+          if (vr < T(0) && inR) {  // Eq. 5-8
             const T hb = T(0.5) * (Hi + f3.w);
             const T mu = quot(hb * vr, r2 + ep * hb * hb);
             const T Pi = quot((be * mu - al * T(0.5) * (ci + f2.w)) * mu, T(0.5) * (rhoi + f3.x));
@@ -333,7 +343,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           const T gx = gs * dx, gy = gs * dy;
           C0.add(gx * dx); C1.add(gx * dy); C2.add(gx * dz);
           C3.add(gy * dy); C4.add(gy * dz); C5.add(gs * dz * dz);
-          npairs += r2 > T(0) ? 1 : 0;
+          npairs += (r2 > T(0) && inR) ? 1 : 0;
           if (++blk == kSumBlock) {   // lanes stay in step: one pair per pass each
             blk = 0;
             du.flush(); F0.flush(); F1.flush(); F2.flush(); F3.flush();

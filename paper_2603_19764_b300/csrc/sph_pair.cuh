@@ -54,6 +54,20 @@ __device__ __forceinline__ double r2_canon(double dx, double dy, double dz) {
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// Half-width of the band around H^2 inside which an FP32 r^2 cannot decide
+// r < H. Coordinates relative to a reference cell of side L lie within six
+// cells of it (a group spans at most three cells, its candidates one search
+// radius more), so each is rounded by at most 7 L 2^-24 and a difference by
+// twice that; for r close to H the squared distance then errs by at most
+// 2 sqrt(3) H 8.4e-7 L plus the roundings of the squares, the sums and H^2
+// (under 3e-7 H^2): below 3.2e-6 H max(H, L). The band is three times that;
+// pairs inside it are decided with the FP64 predicate, and every mask or
+// list test that must not lose a pair with r < H widens its radius^2 by it.
+template <typename T>
+__device__ __forceinline__ T guard_band(T H, T L) {
+  return T(1e-5) * H * tmax(H, L);
+}
+
 // Squared distance of a point to an axis-aligned box (0 inside).
 template <typename T>
 __device__ __forceinline__ T box_d2(T x, T y, T z, T x0, T x1, T y0, T y1, T z0, T z1) {

@@ -102,6 +102,11 @@ class SphTuneReport(C.Structure):
                 ("ms_forces", C.c_double * 4)]
 
 
+class SphPeakReport(C.Structure):
+    _fields_ = [("tflops", C.c_double), ("ms", C.c_double), ("sm_mhz", C.c_double),
+                ("flops", C.c_double), ("n_sm", C.c_int32), ("pad_", C.c_int32)]
+
+
 EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_stress_update", "sph_step", "sph_step_host", "sph_prime", "sph_destroy",
            "sph_status_string", "sph_last_error", "sph_set_timing", "sph_phase_times",
@@ -110,7 +115,8 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_set_spans", "sph_mlp_create", "sph_mlp_destroy", "sph_mlp_last_error",
            "sph_mlp_set", "sph_mlp_get", "sph_mlp_fit_norm", "sph_mlp_forward",
            "sph_mlp_loss_grad", "sph_mlp_adam_step", "sph_mlp_train_epoch",
-           "sph_set_learned_h", "sph_learn_samples", "sph_check_conversions")
+           "sph_set_learned_h", "sph_learn_samples", "sph_check_conversions",
+           "sph_measure_fma_peak")
 MLP_NPARAM, MLP_NNORM = 4673, 14
 GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
@@ -183,6 +189,8 @@ def lib():
         L.sph_learn_samples.argtypes = [VP, VP, VP]
         L.sph_check_conversions.restype = st
         L.sph_check_conversions.argtypes = [VP, C.c_int64, _PL, VP]
+        L.sph_measure_fma_peak.restype = st
+        L.sph_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, C.POINTER(SphPeakReport), VP]
         L.sph_autotune.restype = st
         L.sph_autotune.argtypes = [VP, C.c_int32]
         L.sph_set_spans.restype = st
@@ -202,6 +210,15 @@ def lib():
 
 
 # ------------------------------------------------------------- marshalling
+def measure_fma_peak(precision: int, launches: int = 20) -> dict:
+    """FMA throughput of the current device in FP32 (precision 1) or FP64 (0)."""
+    r = SphPeakReport()
+    rc = lib().sph_measure_fma_peak(int(precision), int(launches), C.byref(r), None)
+    if rc != SPH_OK:
+        raise SphError("sph_measure_fma_peak: %s" % lib().sph_status_string(rc).decode())
+    return dict(tflops=r.tflops, ms=r.ms, sm_mhz=r.sm_mhz, flops=r.flops, n_sm=r.n_sm)
+
+
 def make_material(d: dict) -> SphMaterial:
     m = SphMaterial()
     for name, _ in SphMaterial._fields_:

@@ -372,6 +372,42 @@ def periodic_wave_box(nx: int = 64, ny: int = 8, nz: int = 8, spacing: float = 1
     return Workload("wave_box_%d" % n, a, [mat], p, dt)
 
 
+def elastic_material() -> dict:
+    """Linear EOS with a constant shear modulus and no yield (elastic)."""
+    return dict(eos=EOS_LINEAR, rho0=1000.0, c0=100.0, A=1000.0 * 100.0 ** 2, B=0.0, E0=1.0,
+                a=0.0, b=0.0, alpha=0.0, beta=0.0, Eiv=0.0, Ecv=1.0, shear_G=3.0e6, Y0=1e30,
+                mu_i=0.0, Ym=math.inf, mu_d=1e30, thermal_softening=0, xi=0.0, Tm=0.0,
+                T0=293.0, cv=790.0, strength=1, p_min=-math.inf)
+
+
+def spinning_sphere(n: int = 4000, spacing: float = 1.0, surface_speed: float = 0.5,
+                    seed: int = BASE_SEED + 6, precision: int = 0,
+                    correction: int = 1) -> Workload:
+    """Elastic lattice sphere in rigid rotation about z (the angular-momentum
+    check of the correction tensor): v = omega x r with the equator moving
+    at surface_speed, +-1 % jitter, no gravity. The EOS carries no tension
+    and is soft (c0 = 10 m/s), so the free surface neither pulls the body
+    apart nor pushes it out much, while the shear modulus makes any
+    spurious strain rate of the rotation build deviatoric stress."""
+    rng = SplitMix64(seed)
+    mat = elastic_material()
+    mat.update(c0=10.0, A=1000.0 * 10.0 ** 2, p_min=0.0)
+    pos = lattice_sphere(n, spacing)
+    pos = pos + rng.uniform(3 * n, -0.01 * spacing, 0.01 * spacing).reshape(n, 3)
+    a = _empty_arrays(n)
+    a["x"], a["y"], a["z"] = pos[:, 0].copy(), pos[:, 1].copy(), pos[:, 2].copy()
+    a["m"][:] = mat["rho0"] * spacing ** 3
+    a["h"][:] = lattice_h(mat, a["m"])
+    radius = float(np.sqrt((pos[:, :2] ** 2).sum(1)).max())
+    om = surface_speed / radius
+    a["vx"] = -om * a["y"]
+    a["vy"] = om * a["x"]
+    p = default_params(precision)
+    p.update(correction_tensor=correction)
+    dt = 0.2 * float(a["h"][0]) / longitudinal_speed(mat)
+    return Workload("spinning_sphere_%d" % n, a, [mat], p, dt)
+
+
 def config(index: int, precision: int | None = None, scale: float = 1.0) -> Workload:
     """The five benchmark configurations (index 1..5); scale < 1 shrinks N.
 

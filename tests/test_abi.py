@@ -51,11 +51,12 @@ def _c_layout():
 #define S(T) printf(#T " %zu\n", sizeof(T));
 #define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
-  S(sph_state) S(sph_material) S(sph_params) S(sph_step_info) S(sph_tune_report)
+  S(sph_state) S(sph_material) S(sph_params) S(sph_step_info) S(sph_tune_report) S(sph_peak_report)
   O(sph_state, id) O(sph_state, nngb) O(sph_material, strength) O(sph_material, xi)
   O(sph_params, g_table) O(sph_params, g_n) O(sph_params, box_hi) O(sph_params, precision)
   O(sph_step_info, pairs_density) O(sph_step_info, device_flags) O(sph_step_info, sweeps)
   O(sph_step_info, kernel_launches) O(sph_step_info, n_expanded) O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
+  O(sph_peak_report, sm_mhz) O(sph_peak_report, n_sm)
   return 0;
 }
 """
@@ -72,7 +73,7 @@ def test_struct_layouts_match_binding():
     lay = _c_layout()
     py = {"sph_state": sph.SphState, "sph_material": sph.SphMaterial,
           "sph_params": sph.SphParams, "sph_step_info": sph.SphStepInfo,
-          "sph_tune_report": sph.SphTuneReport}
+          "sph_tune_report": sph.SphTuneReport, "sph_peak_report": sph.SphPeakReport}
     for name, cls in py.items():
         assert int(lay[name]) == C.sizeof(cls), name
     for key, val in lay.items():
@@ -86,6 +87,14 @@ def test_status_strings(libsph):
     for k, name in enumerate(sph.STATUS_NAMES):
         s = libsph.sph_status_string(k)
         assert s and len(s) > 1
+
+
+def test_fma_peak_rejects_bad_arguments_without_touching_the_gpu(libsph):
+    libsph.sph_measure_fma_peak.restype = C.c_int
+    r = sph.SphPeakReport()
+    assert libsph.sph_measure_fma_peak(2, 10, C.byref(r), None) == sph.SPH_E_ARG
+    assert libsph.sph_measure_fma_peak(1, 0, C.byref(r), None) == sph.SPH_E_ARG
+    assert libsph.sph_measure_fma_peak(1, 10, None, None) == sph.SPH_E_ARG
 
 
 def test_init_rejects_bad_arguments_without_touching_the_gpu(libsph):

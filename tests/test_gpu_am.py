@@ -1,0 +1,58 @@
+"""Angular momentum of the spinning elastic sphere on the GPU, both forms,
+with and without the correction tensor (Eq. 20-22), against the FP64
+oracle run over the same steps. The oracle's own pins (exact L without
+strength, C at least five times better than C = I) are in the CPU suite;
+here the CUDA path has to reproduce the oracle's L(t)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_19764_b300 import build, sph
+from paper_2603_19764_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+N, NSTEPS = 4000, 60
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _oracle_L(w, mats):
+    p = dict(w.params, precision=0)
+    st, info0 = oracle.derivatives(p, mats, w.arrays)
+    _, infos = oracle.step(p, mats, st, w.dt, nsteps=NSTEPS)
+    return np.array(info0["L"]), np.array(infos[-1]["L"])
+
+
+def _gpu_L(w, mats, precision):
+    p = dict(w.params, precision=precision, h_tol=1e-10 if precision == 0 else 1e-6)
+    sim = sph.Simulation(w.arrays, mats, p)
+    L0 = np.array(sim.prime()["L"])
+    for _ in range(NSTEPS):
+        info = sim.step(w.dt)
+    sim.close()
+    return L0, np.array(info["L"])
+
+
+@pytest.mark.parametrize("strength", [1, 0])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_angular_momentum_follows_oracle(precision, strength):
+    dl = {}
+    for corr in (1, 0):
+        w = wl.spinning_sphere(N, correction=corr)
+        mats = [dict(m, strength=strength) for m in w.materials]
+        rl0, rl = _oracle_L(w, mats)
+        gl0, gl = _gpu_L(w, mats, precision)
+        scale = np.linalg.norm(rl0)
+        assert np.linalg.norm(gl0 - rl0) < 1e-14 * scale
+        # FP64: round-off; FP32 pair math: far below the drift it tracks
+        tol = 1e-9 if precision == 0 else 2e-6
+        assert np.linalg.norm(gl - rl) < tol * scale, (corr, np.linalg.norm(gl - rl) / scale)
+        dl[corr] = np.linalg.norm(gl - gl0) / scale
+    if strength:
+        assert dl[1] < 1e-4 and dl[0] > 5 * dl[1], dl
+    else:
+        assert max(dl.values()) < (1e-12 if precision == 0 else 2e-6), dl
