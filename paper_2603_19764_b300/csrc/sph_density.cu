@@ -115,31 +115,37 @@ template <> struct PosPtr<double> {
 };
 
 
+// Candidate list layout: paired in the FP32 form (packed mask tests), one
+// record per candidate in the FP64 form.
+template <typename T> struct DList;
+template <> struct DList<float> {
+  using slot = F2Slot;
+  using store = CandPaired;
+};
+template <> struct DList<double> {
+  using slot = double4_32a;
+  using store = CandAoS<double4_32a>;
+};
+
 // Per-lane bit masks over the staged list: bit k set when r_k^2 < R2.
 // Lanes with store = false compute but keep their previous words.
-template <typename T, typename V4>
-__device__ __forceinline__ void build_masks(const V4 *Lp, unsigned (*Lm)[32], int nl, T xi, T yi,
-                                            T zi, T R2, bool store, int lane) {
+template <typename T>
+__device__ __forceinline__ void build_masks(const typename DList<T>::slot *Lp, unsigned (*Lm)[32],
+                                            int nl, T xi, T yi, T zi, T R2, bool store, int lane) {
   const int nw = (nl + 31) >> 5;
   for (int wd = 0; wd < nw; ++wd) {
     const int kb = wd << 5;
-    const int kend = min(32, nl - kb);
-    unsigned mk = 0;
-#pragma unroll 4
-    for (int b = 0; b < kend; ++b) {
-      const V4 q = Lp[kb + b];
-      const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-      const T r2 = dx * dx + dy * dy + dz * dz;
-      mk |= (r2 < R2 ? 1u : 0u) << b;
-    }
+    const unsigned mk = mask_word(Lp, kb, min(32, nl - kb), xi, yi, zi,
+                                  [R2](T) { return R2; });
     if (store) Lm[wd][lane] = mk;
   }
 }
 
 // Walk one lane's marked candidates: exact membership r < H_i, then the
 // kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
-template <typename T, typename V4, bool REL>
-__device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsigned (*Lm)[32],
+template <typename T, bool REL>
+__device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, const int *Li,
+                                             unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              T gb, double H2c, double xi64, double yi64, double zi64,
                                              const sph_state &s, int self, T &rs, T &rhs,
@@ -155,14 +161,15 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
     {
       const int k = (wd << 5) + __ffs(mk) - 1;
       mk &= mk - 1u;
-      const V4 q = Lp[k];
-      const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+      T qx, qy, qz, qm;
+      DList<T>::store::get(Lp, k, qx, qy, qz, qm);
+      const T dx = xi - qx, dy = yi - qy, dz = zi - qz;
       T r2;
       bool in;
       // (Lp, Li, Lm: the shared-memory list or its global overflow; neither
       // is read through the read-only path, the kernel writes both)
       if (REL) {
-        r2 = dx * dx + dy * dy + dz * dz;
+        r2 = dist2(dx, dy, dz);
         in = r2 < H2;
         if (fabs(r2 - H2) < gb) {
           const int j = Li[k];
@@ -175,11 +182,11 @@ __device__ __forceinline__ void density_walk(const V4 *Lp, const int *Li, unsign
       if (in) {
         const T qq = root(r2) * invH;
         const T t = qq < T(1) ? T(1) - qq : T(0);
-        const T mW = q.w * t * t * t;
+        const T mW = qm * t * t * t;
         rs += mW * t * (T(1) + T(4) * qq);
         rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
         if (REL)   // H^5 d2W/dH2 / cW = (1-q)^2 (12 + 24q - 264q^2 + 288q^3)
-          rhs2 += q.w * t * t * (T(12) + qq * (T(24) + qq * (T(-264) + T(288) * qq)));
+          rhs2 += qm * t * t * (T(12) + qq * (T(24) + qq * (T(-264) + T(288) * qq)));
         // only a pair at r = 0 can be the particle itself
         cnt += r2 > T(0) ? 1 : (Li[k] != self);
       }
@@ -196,10 +203,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   __shared__ int s_idx[kWarpsPerBlock][CAP];
   __shared__ unsigned s_mask[kWarpsPerBlock][CAP / 32][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  V4 *Lp = s_pos[wib];
+  using Slot = typename DList<T>::slot;
+  Slot *Lp = reinterpret_cast<Slot *>(s_pos[wib]);   // same bytes: 32 per two FP32 candidates
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
-  const SpillView<V4> Sv = spill_view<V4>(A.spill, blockIdx.x * kWarpsPerBlock + wib);
+  const SpillView<V4> Sv0 = spill_view<V4>(A.spill, blockIdx.x * kWarpsPerBlock + wib);
+  const SpillView<Slot> Sv = {reinterpret_cast<Slot *>(Sv0.p), Sv0.i, Sv0.m};
   constexpr int TCAP = CAP + kSpill;
   // persistent warps: each takes the next bucket of 32 particles
   const int nbuckets = A.p.nbuckets;
@@ -296,10 +305,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
             if (keep) {
               const int at = nl + __popc(bal & lanemask_lt());
               if (at < CAP) {
-                Lp[at] = V::make(xj, yj, zj, q.w);
+                DList<T>::store::put(Lp, at, xj, yj, zj, q.w);
                 Li[at] = j;
               } else {
-                Sv.p[at - CAP] = V::make(xj, yj, zj, q.w);
+                DList<T>::store::put(Sv.p, at - CAP, xj, yj, zj, q.w);
                 Sv.i[at - CAP] = j;
               }
             }
@@ -313,13 +322,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           // list longer than both buffers: evaluate this segment exactly
           const int n1 = min(nl, CAP), n2 = nl - n1;
           __syncwarp();
-          build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, Hq * Hq, act, lane);
-          build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
+          build_masks<T>(Lp, Lm, n1, xi, yi, zi, Hq * Hq, act, lane);
+          build_masks<T>(Sv.p, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
           __syncwarp();
           if (act) {
-            density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
+            density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
                                      zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-            density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
+            density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
                                      yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
           }
           __syncwarp();
@@ -333,15 +342,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         if (__any_sync(kFull, rebuild)) {
           const T Hn = rebuild ? tmax(Ht * T(1.02), Hq) : Hm;
           __syncwarp();
-          build_masks<T, V4>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
-          build_masks<T, V4>(Sv.p, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
+          build_masks<T>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
+          build_masks<T>(Sv.p, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
           __syncwarp();
           Hm = Hn;
         }
         if (act) {
-          density_walk<T, V4, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
+          density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
                                    zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-          density_walk<T, V4, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
+          density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
                                    yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
         }
       }

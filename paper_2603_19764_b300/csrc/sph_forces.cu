@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
         const unsigned bal = __ballot_sync(kFull, keep);
         if (keep) {
           const int at = nl + __popc(bal & lanemask_lt());
-          Lr[at] = V::make(xj, yj, zj, q.w * q.w);
+          CandAoS<V4>::put(Lr, at, xj, yj, zj, q.w * q.w);
           Li[at] = j;
         }
         nl += __popc(bal);
@@ -255,15 +255,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
       const int nw = (nl + 31) >> 5;
       for (int wd = 0; wd < nw; ++wd) {
         const int kb = wd << 5;
-        const int kend = min(32, nl - kb);
-        unsigned mk = 0;
-#pragma unroll 4
-        for (int b = 0; b < kend; ++b) {
-          const V4 q = Lr[kb + b];
-          const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
-          const T r2 = dx * dx + dy * dy + dz * dz;
-          mk |= (r2 < tmax(Hi2 + gi, q.w) ? 1u : 0u) << b;
-        }
+        const T Hi2g = Hi2 + gi;
+        const unsigned mk = mask_word(Lr, kb, min(32, nl - kb), xi, yi, zi,
+                                      [Hi2g](T w) { return tmax(Hi2g, w); });
         Lm[wd][lane] = act ? mk : 0u;
       }
       __syncwarp();
@@ -277,10 +271,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           const int k = (wd << 5) + __ffs(mk) - 1;
           mk &= mk - 1u;
           const int j = Li[k];
-          const V4 q = Lr[k];
+          T qx, qy, qz, qw;   // qw = H_j^2
+          CandAoS<V4>::get(Lr, k, qx, qy, qz, qw);
           const V4 *rj = rec + 4 * j;
           const V4 f0 = V::ld(rj, 0), f1 = V::ld(rj, 1), f2 = V::ld(rj, 2), f3 = V::ld(rj, 3);
-          const T dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+          const T dx = xi - qx, dy = yi - qy, dz = zi - qz;
           const T r2 = dx * dx + dy * dy + dz * dz;
           {
             bool inH;
@@ -301,7 +296,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) 
           // radii) has no say in the signal velocity and no place in the
           // pair statistics; its kernel weights are zero up to the rounding
           // of r / H (below 1e-20 of a neighbour's)
-          const bool inR = r2 < tmax(Hi2, q.w);
+          const bool inR = r2 < tmax(Hi2, qw);
           // a pair at r = 0 (the particle itself, or a coincident one)
           // contributes nothing below: every term carries x_ij
           const T r = root(r2);

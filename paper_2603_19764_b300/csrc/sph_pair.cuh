@@ -31,6 +31,37 @@ template <> struct V4T<double> {
   }
 };
 
+// Two FP32 values in one 64-bit register, and the sm_100-family arithmetic
+// on such pairs: one instruction applies the same IEEE operation (round to
+// nearest, no flush) to both halves, so a packed result equals the two
+// scalar results bit for bit.
+namespace px {
+using u64 = unsigned long long;
+__device__ __forceinline__ u64 dup(float a) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ void split(u64 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 sub(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+}  // namespace px
+
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
@@ -66,6 +97,99 @@ __device__ __forceinline__ double r2_canon(double dx, double dy, double dz) {
 template <typename T>
 __device__ __forceinline__ T guard_band(T H, T L) {
   return T(1e-5) * H * tmax(H, L);
+}
+
+// Squared distance in the fixed order ((dx dx) + dy dy) + dz dz, with the
+// two fused multiply-adds written out, so that a packed mask test and a
+// scalar walk round identically.
+__device__ __forceinline__ float dist2(float dx, float dy, float dz) {
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+__device__ __forceinline__ double dist2(double dx, double dy, double dz) {
+  return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+}
+
+// Staged candidates: x, y, z relative to the group's reference cell and one
+// more value w. Two layouts:
+// * AoS: one 4-vector per candidate (float4 / double4_32a); the walk reads
+//   a candidate with one 16- or 32-byte load.
+// * Paired (FP32): candidates 2m and 2m+1 share a 32-byte slot laid out
+//   (x0 x1 y0 y1 | z0 z1 w0 w1), so that one 16-byte load yields the x and
+//   y pairs and the mask test runs on both candidates with packed
+//   arithmetic; the walk reads a candidate with four 4-byte loads.
+struct F2Slot {
+  float4 a, b;
+};
+template <typename V4> struct CandAoS {
+  template <typename T>
+  static __device__ __forceinline__ void put(V4 *L, int k, T x, T y, T z, T w) {
+    L[k] = V4T<T>::make(x, y, z, w);
+  }
+  template <typename T>
+  static __device__ __forceinline__ void get(const V4 *L, int k, T &x, T &y, T &z, T &w) {
+    const V4 q = L[k];
+    x = q.x;
+    y = q.y;
+    z = q.z;
+    w = q.w;
+  }
+};
+struct CandPaired {
+  static __device__ __forceinline__ void put(F2Slot *L, int k, float x, float y, float z,
+                                             float w) {
+    float *p = reinterpret_cast<float *>(L + (k >> 1)) + (k & 1);
+    p[0] = x;
+    p[2] = y;
+    p[4] = z;
+    p[6] = w;
+  }
+  static __device__ __forceinline__ void get(const F2Slot *L, int k, float &x, float &y, float &z,
+                                             float &w) {
+    const float *p = reinterpret_cast<const float *>(L + (k >> 1)) + (k & 1);
+    x = p[0];
+    y = p[2];
+    z = p[4];
+    w = p[6];
+  }
+};
+
+// One lane's membership word over staged candidates kb .. kb+31 (kb a
+// multiple of 32): bit b set when r^2 < thr(w) for candidate kb + b, for
+// b < count only. The paired form reads whole words, up to 31 slots past
+// the list's end (inside the buffer, whose length is a multiple of 32), and
+// clears those bits.
+template <typename V4, typename T, typename Thr>
+__device__ __forceinline__ unsigned mask_word(const V4 *L, int kb, int count, T xi, T yi, T zi,
+                                              Thr thr) {
+  unsigned mk = 0;
+#pragma unroll 4
+  for (int b = 0; b < count; ++b) {
+    T x, y, z, w;
+    CandAoS<V4>::get(L, kb + b, x, y, z, w);
+    const T dx = xi - x, dy = yi - y, dz = zi - z;
+    mk |= (dx * dx + dy * dy + dz * dz < thr(w) ? 1u : 0u) << b;
+  }
+  return mk;
+}
+template <typename Thr>
+__device__ __forceinline__ unsigned mask_word(const F2Slot *L, int kb, int count, float xi,
+                                              float yi, float zi, Thr thr) {
+  using namespace px;
+  const u64 X = dup(xi), Y = dup(yi), Z = dup(zi);
+  const ulonglong2 *P = reinterpret_cast<const ulonglong2 *>(L + (kb >> 1));
+  unsigned mk = 0;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const ulonglong2 a = P[2 * m], b = P[2 * m + 1];   // (x pair, y pair), (z pair, w pair)
+    const u64 dx = sub(X, a.x), dy = sub(Y, a.y), dz = sub(Z, b.x);
+    const u64 r2 = fma(dz, dz, fma(dy, dy, mul(dx, dx)));
+    float r0, r1, w0, w1;
+    split(r2, r0, r1);
+    split(b.y, w0, w1);
+    if (r0 < thr(w0)) mk |= 1u << (2 * m);
+    if (r1 < thr(w1)) mk |= 2u << (2 * m);
+  }
+  return count < 32 ? mk & ((1u << count) - 1u) : mk;
 }
 
 // Squared distance of a point to an axis-aligned box (0 inside).

@@ -12,7 +12,7 @@ from paper_2603_19764_b300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-N, NSTEPS = 4000, 60
+N, NSTEPS = 4000, 200
 
 
 @pytest.fixture(scope="module", autouse=True)

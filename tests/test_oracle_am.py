@@ -19,7 +19,7 @@ import pytest
 import oracle
 from paper_2603_19764_b300 import workloads as wl
 
-NSTEPS = 60
+NSTEPS = 200
 
 
 def _dl(n, strength, correction, nsteps=NSTEPS):
