@@ -461,7 +461,7 @@ cudaError_t launch_density(sph_ctx *c, int expand) {
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K)
-    k_density<float, 512><<<resident_grid(c, k_density<float, 512>), 32 * kWarpsPerBlock, 0,
+    k_density<float, 576><<<resident_grid(c, k_density<float, 576>), 32 * kWarpsPerBlock, 0,
                             c->stream>>>(a);
   else
     k_density<double, 256><<<resident_grid(c, k_density<double, 256>), 32 * kWarpsPerBlock, 0,
@@ -480,7 +480,7 @@ cudaError_t alloc_density_spill(sph_ctx *c) {
   int per_sm = 0;
   cudaError_t e = c->kp.precision == SPH_FP32K
                       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, k_density<float, 512>, 32 * kWarpsPerBlock, 0)
+                            &per_sm, k_density<float, 576>, 32 * kWarpsPerBlock, 0)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                             &per_sm, k_density<double, 256>, 32 * kWarpsPerBlock, 0);
   if (e != cudaSuccess) return e;

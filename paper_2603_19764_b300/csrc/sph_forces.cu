@@ -462,7 +462,7 @@ cudaError_t launch_forces(sph_ctx *c) {
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[1], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K)
-    k_forces<float, 512><<<resident_grid(c, k_forces<float, 512>), 32 * kWarpsPerBlock, 0,
+    k_forces<float, 800><<<resident_grid(c, k_forces<float, 800>), 32 * kWarpsPerBlock, 0,
                            c->stream>>>(a);
   else
     k_forces<double, 256><<<resident_grid(c, k_forces<double, 256>), 32 * kWarpsPerBlock, 0,
