@@ -208,12 +208,15 @@ cudaError_t mark(sph_ctx *c, int k) {
   return c->timing && !c->capturing ? cudaEventRecord(c->ev[k], c->stream) : cudaSuccess;
 }
 
-sph_status run_neighbours(sph_ctx *c, int drift) {
+// all = 1 permutes every array of the state (sph_neighbours on its own);
+// steps pass 0 and recompute rho, Omega, P, c_s and the counts in the new
+// order.
+sph_status run_neighbours(sph_ctx *c, int drift, int all) {
   CK(mark(c, 0));
   CK(launch_reset_status(c, 0));
   CK(launch_drift_bbox(c, drift));
   CK(launch_grid_setup(c));
-  CK(launch_sort_permute(c));
+  CK(launch_sort_permute(c, all));
   CK(mark(c, 1));
   return SPH_OK;
 }
@@ -243,7 +246,7 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
 // Everything one step enqueues, from the dt upload to the status readback.
 sph_status enqueue_step(sph_ctx *c) {
   sph_status s = upload_dt(c);
-  if (s == SPH_OK) s = run_neighbours(c, 1);
+  if (s == SPH_OK) s = run_neighbours(c, 1, 0);
   if (s == SPH_OK) s = run_derivatives(c, 1);
   if (s != SPH_OK) return s;
   CK(launch_kick(c, 1));
@@ -735,7 +738,7 @@ sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out) {
 
 sph_status sph_neighbours(sph_ctx *c) {
   ENTER(c);
-  return run_neighbours(c, 0);
+  return run_neighbours(c, 0, 1);
 }
 
 sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
@@ -771,7 +774,7 @@ sph_status sph_prime(sph_ctx *c, sph_step_info *info) {
   ENTER(c);
   for (int k = 0; k < c->nsys; ++k) c->h_dt[k] = 0.0;
   sph_status s = upload_dt(c);
-  if (s == SPH_OK) s = run_neighbours(c, 0);
+  if (s == SPH_OK) s = run_neighbours(c, 0, 0);
   if (s != SPH_OK) return s;
   s = run_derivatives(c, 0);
   if (s != SPH_OK) return s;

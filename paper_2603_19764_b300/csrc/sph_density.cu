@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const V4 *pos = PosPtr<T>::get(A.w);
 
   const Grid g = R.grid;
-  const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
+  const T Lt = grid_L<T>(g), invL = grid_invL<T>(g);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
   const V4 p = V::ld(pos, ic);

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   const V4 *rec = PK::rec(A.w);   // 4 consecutive vectors per particle
 
   const Grid g = R.grid;
-  const T Lt = (T)g.L, invL = (T)(1.0 / g.L);
+  const T Lt = grid_L<T>(g), invL = grid_invL<T>(g);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
   const T hmax_all = (T)dec_d(R.hmax2_enc);
@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           T qx, qy, qz, qw;   // qw = H_j^2
           CandAoS<V4>::get(Lr, k, qx, qy, qz, qw);
           const V4 *rj = rec + 4 * j;
-          const V4 f0 = V::ld(rj, 0), f1 = V::ld(rj, 1), f2 = V::ld(rj, 2), f3 = V::ld(rj, 3);
+          V4 f0, f1, f2, f3;   // the 64-byte record in two 32-byte loads
+          V::ld2(rj, f0, f1);
+          V::ld2(rj + 2, f2, f3);
           const T dx = xi - qx, dy = yi - qy, dz = zi - qz;
           const T r2 = dx * dx + dy * dy + dz * dz;
           {

@@ -54,24 +54,34 @@ cudaError_t launch_reset_status(sph_ctx *c, int full) {
 // them with atomics only when the system changes; at the end the block
 // combines the threads that share one system (the common case) before a
 // single set of atomics.
-__device__ __forceinline__ void flush_box(SysRec &r, const double (&lo)[3], const double (&hi)[3],
-                                          double hm) {
+// Running extrema are kept as order-preserving 64-bit encodings (enc_d), so
+// that the per-particle min / max run on the integer pipe: FP64 min / max
+// instructions share the FP64 unit, which runs at 1/64 of the FP32 rate.
+__device__ __forceinline__ void flush_box(SysRec &r, const unsigned long long (&lo)[3],
+                                          const unsigned long long (&hi)[3],
+                                          unsigned long long hm) {
   for (int a = 0; a < 3; ++a) {
-    atomicMin(&r.lo_enc[a], enc_d(lo[a]));
-    atomicMax(&r.hi_enc[a], enc_d(hi[a]));
+    atomicMin(&r.lo_enc[a], lo[a]);
+    atomicMax(&r.hi_enc[a], hi[a]);
   }
-  atomicMax(&r.hmax_enc, enc_d(hm));
+  atomicMax(&r.hmax_enc, hm);
+}
+
+// finite by the exponent field alone (no FP64 instruction)
+__device__ __forceinline__ bool finite_bits(double d) {
+  return ((__double_as_longlong(d) >> 52) & 0x7ff) != 0x7ff;
 }
 
 constexpr int kDriftChunk = 8 * kBlock;
+constexpr unsigned long long kEncMax = ~0ull, kEncMin = 0ull;
 
 __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, KParams P,
                                                       int do_drift) {
-  __shared__ double red[7][kBlock / 32];
+  __shared__ unsigned long long red[7][kBlock / 32];
   __shared__ int wsys[kBlock / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  double hm = 0.0;
+  unsigned long long lo[3] = {kEncMax, kEncMax, kEncMax}, hi[3] = {kEncMin, kEncMin, kEncMin};
+  unsigned long long hm = kEncMin;
   int cur = -1;   // system of the running extrema (-1: none)
   const int64_t c0 = (int64_t)blockIdx.x * kDriftChunk;
   const int64_t c1 = c0 + kDriftChunk < n ? c0 + kDriftChunk : n;
@@ -91,16 +101,21 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
       if (cur >= 0) flush_box(P.sys[cur], lo, hi, hm);
       cur = sy;
       for (int a = 0; a < 3; ++a) {
-        lo[a] = INFINITY;
-        hi[a] = -INFINITY;
+        lo[a] = kEncMax;
+        hi[a] = kEncMin;
       }
-      hm = 0.0;
+      hm = kEncMin;
     }
+    // a non-finite position is left out of the box (the step's checks
+    // report it), as the FP64 min / max would
     for (int a = 0; a < 3; ++a) {
-      lo[a] = fmin(lo[a], p[a]);
-      hi[a] = fmax(hi[a], p[a]);
+      if (!finite_bits(p[a])) continue;
+      const unsigned long long e = enc_d(p[a]);
+      lo[a] = e < lo[a] ? e : lo[a];
+      hi[a] = e > hi[a] ? e : hi[a];
     }
-    hm = fmax(hm, s.h[i]);
+    const unsigned long long eh = enc_d(s.h[i]);
+    hm = eh > hm ? eh : hm;
   }
   // threads of a warp with one common system reduce by shuffles, warps of
   // a block with one common system through shared memory
@@ -110,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
     if (has) any = __shfl_sync(kFull, cur, __ffs(has) - 1);
   }
   const bool warp_uniform = __all_sync(kFull, cur < 0 || cur == any);
-  double v[7] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm};
+  unsigned long long v[7] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm};
   if (warp_uniform) {
     for (int k = 0; k < 3; ++k) v[k] = wmin(v[k]);
     for (int k = 3; k < 7; ++k) v[k] = wmax(v[k]);
@@ -131,19 +146,19 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
       else sb = wsys[q];
     }
     if (one && sb >= 0) {
-      double b[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+      unsigned long long b[7] = {kEncMax, kEncMax, kEncMax, kEncMin, kEncMin, kEncMin, kEncMin};
       for (int q = 0; q < kBlock / 32; ++q) {
         if (wsys[q] < 0) continue;
-        for (int k = 0; k < 3; ++k) b[k] = fmin(b[k], red[k][q]);
-        for (int k = 3; k < 7; ++k) b[k] = fmax(b[k], red[k][q]);
+        for (int k = 0; k < 3; ++k) b[k] = red[k][q] < b[k] ? red[k][q] : b[k];
+        for (int k = 3; k < 7; ++k) b[k] = red[k][q] > b[k] ? red[k][q] : b[k];
       }
-      const double bl[3] = {b[0], b[1], b[2]}, bh[3] = {b[3], b[4], b[5]};
+      const unsigned long long bl[3] = {b[0], b[1], b[2]}, bh[3] = {b[3], b[4], b[5]};
       flush_box(P.sys[sb], bl, bh, b[6]);
     } else {
       for (int q = 0; q < kBlock / 32; ++q) {
         if (wsys[q] < 0) continue;
-        const double bl[3] = {red[0][q], red[1][q], red[2][q]};
-        const double bh[3] = {red[3][q], red[4][q], red[5][q]};
+        const unsigned long long bl[3] = {red[0][q], red[1][q], red[2][q]};
+        const unsigned long long bh[3] = {red[3][q], red[4][q], red[5][q]};
         flush_box(P.sys[wsys[q]], bl, bh, red[6][q]);
       }
     }
@@ -200,6 +215,9 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits) {
       g.dims[a] = d[a];
     }
     g.L = L;
+    g.invL = 1.0 / L;
+    g.Lf = (float)L;
+    g.invLf = (float)(1.0 / L);
     g.ncells = d[0] * d[1] * d[2];
     g.cell_off = off;
     off += g.ncells;
@@ -226,7 +244,7 @@ __global__ void __launch_bounds__(kBlock) k_keys(sph_state s, int64_t n, KParams
        i += (int64_t)gridDim.x * blockDim.x) {
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
     const Grid &g = P.sys[sy].grid;
-    const double invL = 1.0 / g.L;
+    const double invL = g.invL;
     const int cx = cell_coord(s.x[i], g.lo[0], invL, g.dims[0]);
     const int cy = cell_coord(s.y[i], g.lo[1], invL, g.dims[1]);
     const int cz = cell_coord(s.z[i], g.lo[2], invL, g.dims[2]);
@@ -363,6 +381,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *
 // ------------------------------------------------------------ permutation
 // Every array of sph_state is gathered through the sort permutation into a
 // scratch block and copied back, so the caller's arrays end up in cell order.
+// Within a step the arrays that the step itself recomputes before reading
+// them (rho, Omega, P, c_s and the neighbour count) are left out: their
+// values are overwritten in the new order.
 constexpr int kNF64 = 29;   // 28 double arrays + id
 constexpr int kNI32 = 3;
 constexpr int kNLearn = 5;  // learned form: H_prev, H proposal, three feature pairs
@@ -371,19 +392,25 @@ struct PermTable {
   unsigned long long *f64[kNF64 + kNLearn];
   unsigned *i32[kNI32];
   int nf64;   // 8-byte fields in use
+  int ni32;   // 4-byte fields in use
 };
 
-static PermTable perm_table(const sph_state &s, const LearnArgs &L) {
+static PermTable perm_table(const sph_state &s, const LearnArgs &L, bool all) {
   PermTable t;
-  double *d[28] = {s.x,    s.y,    s.z,     s.vx,   s.vy,   s.vz,   s.u,    s.m,    s.h,    s.sxx,
-                   s.syy,  s.sxy,  s.sxz,   s.syz,  s.rho,  s.omega, s.pres, s.cs,  s.ax,   s.ay,
-                   s.az,   s.dudt, s.dsxx,  s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
-  for (int k = 0; k < 28; ++k) t.f64[k] = (unsigned long long *)d[k];
-  t.f64[28] = (unsigned long long *)s.id;
-  t.i32[0] = (unsigned *)s.nngb;
-  t.i32[1] = (unsigned *)s.mat;
-  t.i32[2] = (unsigned *)s.flags;
-  t.nf64 = kNF64;
+  t.nf64 = 0;
+  double *d[24] = {s.x,   s.y,    s.z,    s.vx,   s.vy,   s.vz,   s.u,    s.m,
+                   s.h,   s.sxx,  s.syy,  s.sxy,  s.sxz,  s.syz,  s.ax,   s.ay,
+                   s.az,  s.dudt, s.dsxx, s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
+  for (int k = 0; k < 24; ++k) t.f64[t.nf64++] = (unsigned long long *)d[k];
+  t.f64[t.nf64++] = (unsigned long long *)s.id;
+  t.ni32 = 0;
+  t.i32[t.ni32++] = (unsigned *)s.mat;
+  t.i32[t.ni32++] = (unsigned *)s.flags;
+  if (all) {
+    double *r[4] = {s.rho, s.omega, s.pres, s.cs};
+    for (int k = 0; k < 4; ++k) t.f64[t.nf64++] = (unsigned long long *)r[k];
+    t.i32[t.ni32++] = (unsigned *)s.nngb;
+  }
   // the learned form's per-particle arrays follow their particles
   if (L.hprev) {
     t.f64[t.nf64++] = (unsigned long long *)L.hprev;
@@ -402,8 +429,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm,
 #pragma unroll 4
     for (int f = 0; f < t.nf64; ++f) tmp[f * n + i] = t.f64[f][j];
     unsigned *t32 = (unsigned *)(tmp + t.nf64 * n);
-#pragma unroll
-    for (int f = 0; f < kNI32; ++f) t32[f * n + i] = t.i32[f][j];
+    for (int f = 0; f < t.ni32; ++f) t32[f * n + i] = t.i32[f][j];
   }
 }
 
@@ -414,8 +440,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter_back(PermTable t, int64_t n,
 #pragma unroll 4
     for (int f = 0; f < t.nf64; ++f) t.f64[f][i] = tmp[f * n + i];
     const unsigned *t32 = (const unsigned *)(tmp + t.nf64 * n);
-#pragma unroll
-    for (int f = 0; f < kNI32; ++f) t.i32[f][i] = t32[f * n + i];
+    for (int f = 0; f < t.ni32; ++f) t.i32[f][i] = t32[f * n + i];
   }
 }
 
@@ -450,7 +475,7 @@ static int grid_for(int64_t n, int block) {
   return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_sort_permute(sph_ctx *c) {
+cudaError_t launch_sort_permute(sph_ctx *c, int all) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
   k_keys<<<gb, kBlock, 0, c->stream>>>(c->st, n, c->kp, c->keys, c->vals);
@@ -473,7 +498,7 @@ cudaError_t launch_sort_permute(sph_ctx *c) {
     vb = tv;
   }
   // after four passes the sorted pairs are back in keys / vals
-  PermTable t = perm_table(c->st, c->learn);
+  PermTable t = perm_table(c->st, c->learn, all != 0);
   unsigned long long *tmp = (unsigned long long *)c->tmp;
   k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);

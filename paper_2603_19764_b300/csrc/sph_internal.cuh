@@ -29,10 +29,18 @@ enum : unsigned { ERR_NOCONV = 1u, ERR_NONFINITE = 2u, ERR_CAPACITY = 4u, ERR_TI
 struct Grid {
   double lo[3];
   double L;          // cell edge
+  double invL;       // 1 / L, and both rounded to FP32: formed once per step,
+  float Lf, invLf;   // since FP64 division and conversion run on the FP64 unit
   int dims[3];
   int ncells;
   int cell_off;
 };
+template <typename T> __device__ __forceinline__ T grid_L(const Grid &g);
+template <> __device__ __forceinline__ float grid_L<float>(const Grid &g) { return g.Lf; }
+template <> __device__ __forceinline__ double grid_L<double>(const Grid &g) { return g.L; }
+template <typename T> __device__ __forceinline__ T grid_invL(const Grid &g);
+template <> __device__ __forceinline__ float grid_invL<float>(const Grid &g) { return g.invLf; }
+template <> __device__ __forceinline__ double grid_invL<double>(const Grid &g) { return g.invL; }
 
 // One independent particle system of a context (a context holds one system,
 // or a batch of them that never interact). Its particles occupy the sorted
@@ -307,6 +315,18 @@ __device__ inline void till_vapour_t(const MatT<T> &M, T eta, T mu, T rho, T u, 
   Pu = a * rho + qu * ea;
 }
 
+// a >= b and a <= b on the integer pipe when b > 0 (IEEE-754 bit patterns
+// of a positive b order like the values; a negative a has a negative
+// pattern); the FP64 comparison otherwise.
+__device__ __forceinline__ bool ge_d(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return ib > 0 ? ia >= ib : a >= b;
+}
+__device__ __forceinline__ bool le_d(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return ib > 0 ? ia <= ib : a <= b;
+}
+
 template <typename T>
 __device__ inline EosT<T> eos_t(const MatT<T> &M, double rhod, double ud) {
   EosT<T> o;
@@ -319,9 +339,9 @@ __device__ inline EosT<T> eos_t(const MatT<T> &M, double rhod, double ud) {
   const T mu = to_t<T>(rhod - M.rho0_d) * M.inv_rho0;
   const T eta = T(1) + mu;
   T P, Pr, Pu;
-  if (rhod >= M.rho0_d || ud <= M.Eiv_d) {
+  if (ge_d(rhod, M.rho0_d) || le_d(ud, M.Eiv_d)) {
     till_dense_t<T>(M, eta, mu, rho, u, P, Pr, Pu);
-  } else if (ud >= M.Ecv_d) {
+  } else if (ge_d(ud, M.Ecv_d)) {
     till_vapour_t<T>(M, eta, mu, rho, u, P, Pr, Pu);
   } else {
     T P1, Pr1, Pu1, P2, Pr2, Pu2;
@@ -499,7 +519,8 @@ template <typename K> inline int resident_grid(const sph_ctx *c, K kernel) {
 namespace sphk {
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift);
 cudaError_t launch_grid_setup(sph_ctx *c);
-cudaError_t launch_sort_permute(sph_ctx *c);
+// all = 0: leave out the arrays a step recomputes before reading them
+cudaError_t launch_sort_permute(sph_ctx *c, int all);
 cudaError_t launch_predict_pack(sph_ctx *c, int predict);
 cudaError_t launch_density(sph_ctx *c, int expand);
 cudaError_t launch_eos_pack(sph_ctx *c);

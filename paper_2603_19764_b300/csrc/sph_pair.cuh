@@ -19,6 +19,13 @@ template <typename T> struct V4T;
 template <> struct V4T<float> {
   using type = float4;
   static __device__ __forceinline__ float4 ld(const float4 *p, int64_t i) { return __ldg(p + i); }
+  // two consecutive vectors p[0], p[1] in one 32-byte read-only load (p
+  // 32-byte aligned)
+  static __device__ __forceinline__ void ld2(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+  }
   static __device__ __forceinline__ float4 make(float x, float y, float z, float w) {
     return make_float4(x, y, z, w);
   }
@@ -26,6 +33,11 @@ template <> struct V4T<float> {
 template <> struct V4T<double> {
   using type = double4_32a;
   static __device__ __forceinline__ double4_32a ld(const double4_32a *p, int64_t i) { return p[i]; }
+  static __device__ __forceinline__ void ld2(const double4_32a *p, double4_32a &a,
+                                             double4_32a &b) {
+    a = p[0];
+    b = p[1];
+  }
   static __device__ __forceinline__ double4_32a make(double x, double y, double z, double w) {
     return make_double4_32a(x, y, z, w);
   }

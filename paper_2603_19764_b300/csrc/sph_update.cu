@@ -17,7 +17,7 @@ constexpr int kNSum = 9;
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, KParams P,
                                                 double *partials) {
-  __shared__ double red[kNSum][kBlock / 32];
+  __shared__ double red[kNSum][kBlock];
   __shared__ double redt[kBlock / 32];
   const int b = blockIdx.x;
   const int sy = P.nsys > 1 ? sys_lookup(P.sys_chunk, P.nsys, b) : 0;
@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
         const EosT<T> e = eos_t<T>(M, s.rho[i], u);
         const T St[5] = {to_t<T>(S[0]), to_t<T>(S[1]), to_t<T>(S[2]), to_t<T>(S[3]), to_t<T>(S[4])};
         const double f = from_t(radial_factor_t<T>(St, yield_t<T>(M, e.P, to_t<T>(u)), P.yield_norm));
+        if (f < 1.0) {   // below the yield surface f is exactly 1
 #pragma unroll
-        for (int k = 0; k < 5; ++k) S[k] *= f;
+          for (int k = 0; k < 5; ++k) S[k] *= f;
+        }
       } else {
         S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
       }
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     const double x = s.x[i], y = s.y[i], z = s.z[i];
     T g[3], phi;
     ext_field_t<T>(P, x, y, z, g, &phi);
-    acc[0] += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    acc[0] += m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);   // halved below (exact)
     acc[1] += m * u;
     acc[2] += m * from_t(phi);
     acc[3] += m * v[0];
@@ -85,21 +87,26 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
       tmin = tmin_(tmin, tmin_(ta, tc));
     }
   }
+  // block sums in a fixed order: every thread parks its nine partial sums
+  // in shared memory; warp q then reduces sum q (warp 0 also sum 8) over
+  // the block, each lane adding kBlock / 32 values in sequence before a
+  // shuffle tree. Nine shuffle trees per thread would cost three times the
+  // FP64 additions, and this kernel is bound by the FP64 unit.
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < kNSum; ++k) acc[k] = wsum(acc[k]);
-  double tm = wmin(from_t(tmin));
-  if (lane == 0) {
-    for (int k = 0; k < kNSum; ++k) red[k][wi] = acc[k];
-    redt[wi] = tm;
-  }
+  for (int k = 0; k < kNSum; ++k) red[k][threadIdx.x] = acc[k];
+  const double tm = wmin(from_t(tmin));
+  if (lane == 0) redt[wi] = tm;
   __syncthreads();
+  static_assert(kNSum <= 2 * (kBlock / 32) && kNSum > kBlock / 32, "one or two sums per warp");
+  for (int k = wi; k < kNSum; k += kBlock / 32) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kBlock / 32; ++q) t += red[k][32 * q + lane];
+    t = wsum(t);
+    if (lane == 0) partials[blockIdx.x * kNSum + k] = k == 0 ? 0.5 * t : t;
+  }
   if (threadIdx.x == 0) {
-    for (int k = 0; k < kNSum; ++k) {
-      double t = 0.0;
-      for (int q = 0; q < kBlock / 32; ++q) t += red[k][q];
-      partials[blockIdx.x * kNSum + k] = t;
-    }
     double t = INFINITY;
     for (int q = 0; q < kBlock / 32; ++q) t = fmin(t, redt[q]);
     atomicMin(&R.dtmin_enc, enc_d(t));
