@@ -19,9 +19,10 @@ larger than L2, so no flush is needed between steps.
 The JSON line also carries: e2e (the same metric through sph_step_host with
 pinned host buffers, copies inside the timed region), roofline (the
 dominant kernel's algorithmic FLOP/s over the FP32 or FP64 ALU peak from
-unit counts and clock), cpu_baseline (the FP64 C oracle on a bounded
-spatial sub-volume of the same impact) and the SM clocks sampled during the
-timed region. --impl reference times the oracle itself.
+unit counts and clock, beside the measured FMA peak), cpu_baseline (the
+FP64 C oracle stepping the whole impact on every host core, plus one thread
+on a bounded sub-volume) and the SM clocks sampled during the timed region.
+--impl reference times the oracle itself on a sub-volume.
 """
 from __future__ import annotations
 
@@ -193,13 +194,14 @@ def sampled_error(sim, w, p, precision: int, nsample: int = 1000, seed: int = 7)
                           "deriv_maxnorm_rel": 1e-4 if precision else 1e-9}}
 
 
-def cpu_baseline(w, n_sub: int = 100_000, budget_s: float = 12.0, max_steps: int = 20,
-                 fixed_steps: int | None = None) -> dict:
-    """The FP64 C oracle, as it stands, on a bounded sub-volume."""
+def oracle_rate(w, arrays: dict, budget_s: float, max_steps: int,
+                fixed_steps: int | None = None) -> dict:
+    """The FP64 C oracle, as it stands, stepping `arrays` (a state of w's
+    system) with its adaptive dt; derivatives are formed once before the
+    clock starts."""
     import oracle
-    sub = contact_subvolume(w, min(n_sub, w.n))
     p = dict(w.params, h_tol=1e-10)
-    st, info = oracle.derivatives(p, w.materials, sub)
+    st, info = oracle.derivatives(p, w.materials, arrays)
     steps, t0 = 0, time.perf_counter()
     while True:
         st, infos = oracle.step(p, w.materials, st, info["dt_next"])
@@ -211,11 +213,31 @@ def cpu_baseline(w, n_sub: int = 100_000, budget_s: float = 12.0, max_steps: int
                 break
         elif el >= budget_s or steps >= max_steps:
             break
-    n = sub["x"].shape[0]
-    return {"value": n * steps / el, "unit": "particle-steps/s", "cores": oracle.threads(),
-            "kind": "oracle", "seconds": el,
-            "sample": "%d FP64 oracle steps (OpenMP) of the %d particles of the impact nearest "
-                      "the contact point" % (steps, n)}
+    n = arrays["x"].shape[0]
+    return {"value": n * steps / el, "steps": steps, "particles": n, "seconds": el}
+
+
+def cpu_baseline(w, budget_s: float = 15.0, max_steps: int = 3, n_single: int = 20_000,
+                 single_budget_s: float = 5.0) -> dict:
+    """The oracle on the machine's host cores: full steps of the whole workload
+    on every core, and one thread on the particles nearest the contact
+    point (a bounded sample: one thread would take minutes per full step)."""
+    import oracle
+    nth = oracle.threads()
+    full = oracle_rate(w, w.arrays, budget_s, max_steps)
+    oracle.set_threads(1)
+    try:
+        one = oracle_rate(w, contact_subvolume(w, min(n_single, w.n)), single_budget_s, 20)
+    finally:
+        oracle.set_threads(nth)
+    return {"value": full["value"], "unit": "particle-steps/s", "cores": nth, "kind": "oracle",
+            "seconds": full["seconds"],
+            "sample": "%d FP64 oracle steps (OpenMP, %d threads) of the whole %d-particle impact"
+                      % (full["steps"], nth, full["particles"]),
+            "single_thread": {"value": one["value"], "unit": "particle-steps/s", "cores": 1,
+                              "sample": "%d FP64 oracle steps (one thread) of the %d particles "
+                                        "of the impact nearest the contact point"
+                                        % (one["steps"], one["particles"])}}
 
 
 # --------------------------------------------------------------- arms
@@ -225,7 +247,13 @@ def run_reference(args, rank: int, world: int):
     w = make_workload(args.scale, 1)
     for _ in range(args.warmup):
         pass
-    cb = cpu_baseline(w, n_sub=args.ref_particles, fixed_steps=max(1, args.steps))
+    import oracle
+    r = oracle_rate(w, contact_subvolume(w, min(args.ref_particles, w.n)), 0.0, 0,
+                    fixed_steps=max(1, args.steps))
+    cb = {"value": r["value"], "unit": "particle-steps/s", "cores": oracle.threads(),
+          "kind": "oracle",
+          "sample": "%d FP64 oracle steps (OpenMP) of the %d particles of the impact nearest "
+                    "the contact point" % (r["steps"], r["particles"])}
     line = {"metric": "SPH+strength particle-steps/s (2M part.), chosen vs plain form at stated error",
             "value": cb["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
@@ -365,7 +393,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
-        cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cb = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "single_thread")}
 
     # the plain FP64 form on the same impact, a few steps, for the chosen-vs-plain ratio
     plain = None

@@ -130,6 +130,8 @@ def lib():
         L.ref_diagnostics.argtypes = [C.POINTER(RefParams), C.c_int64, C.POINTER(RefState),
                                       C.POINTER(RefInfo)]
         L.ref_threads.restype = C.c_int32
+        L.ref_set_threads.restype = C.c_int32
+        L.ref_set_threads.argtypes = [C.c_int32]
         _lib = L
     return _lib
 
@@ -286,6 +288,12 @@ def potential(params: dict, x, y, z):
 
 def threads() -> int:
     return int(lib().ref_threads())
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's parallel loops (results do not depend
+    on it); returns the count in effect."""
+    return int(lib().ref_set_threads(int(n)))
 
 
 # --------------------------------------------------------------------------

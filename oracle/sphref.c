@@ -32,6 +32,18 @@ int32_t ref_threads(void) {
 #endif
 }
 
+/* Thread count of the following parallel regions (timing runs only; the
+ * results do not depend on it). Returns the count now in effect. */
+int32_t ref_set_threads(int32_t n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads((int)n);
+  return (int32_t)omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Kernel: Wendland C2 in three dimensions (§3: "Wendland C2 kernel",        */
 /* Dehnen & Aly 2012). Reading: h in Eq. 1-3 is the compact support radius  */

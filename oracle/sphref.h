@@ -169,6 +169,7 @@ void ref_diagnostics(const ref_params *p, int64_t n, const ref_state *s,
 
 /* Threads used by the OpenMP loops. */
 int32_t ref_threads(void);
+int32_t ref_set_threads(int32_t n);
 
 #ifdef __cplusplus
 }
