@@ -49,6 +49,7 @@ typedef enum {
 enum { SPH_EOS_LINEAR = 0, SPH_EOS_TILLOTSON = 1 };
 enum { SPH_FP64 = 0, SPH_FP32K = 1 };
 enum { SPH_JAUMANN_OBJECTIVE = 0, SPH_JAUMANN_PRINTED = 1 };
+enum { SPH_GRADIENT_SYMMETRIC = 0, SPH_GRADIENT_ONE_SIDED = 1 };
 enum { SPH_YIELD_SQRT_J2 = 0, SPH_YIELD_SQRT_3J2 = 1 };
 enum { SPH_GRAVITY_NONE = 0, SPH_GRAVITY_UNIFORM = 1, SPH_GRAVITY_RADIAL = 2 };
 #define SPH_MAX_MATERIALS 8
@@ -126,7 +127,13 @@ typedef struct {
  *                  phi_table are HOST arrays of g_n values on radii
  *                  log-spaced from g_rmin to g_rmax about g_center, copied
  *                  at sph_init; g = g_gm / r^2 beyond g_rmax
- *   periodic       must be 0 (periodic boxes are an oracle-only feature) */
+ *   periodic       must be 0 (periodic boxes are an oracle-only feature)
+ *   gradient_form  SPH_GRADIENT_SYMMETRIC: F and C^-1 as Eq. 20-21 (the mean
+ *                  of the two kernels, each over its own Omega rho);
+ *                  SPH_GRADIENT_ONE_SIDED: the H_i term alone,
+ *                  F_i = -sum_j m_j v_ij (x) dW(H_i)/dx_i / (Omega_i rho_i)
+ *                  and C_i^-1 likewise with x_ij (the non-symmetric form
+ *                  §2.2 mentions beside Eq. 20-21). SPH_E_ARG otherwise. */
 typedef struct {
   int32_t n_ngb;
   double av_alpha, av_beta, av_eps;
@@ -142,6 +149,7 @@ typedef struct {
   double g_rmin, g_rmax, g_center[3], g_gm;
   int32_t periodic;
   double box_lo[3], box_hi[3];
+  int32_t gradient_form;
 } sph_params;
 
 /* Per-step report (filled by the synchronising calls). Energies and

@@ -62,7 +62,7 @@ class RefParams(C.Structure):
                 ("g_n", C.c_int32), ("g_rmin", C.c_double), ("g_rmax", C.c_double),
                 ("g_center", C.c_double * 3), ("g_gm", C.c_double), ("periodic", C.c_int32),
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
-                ("brute_force", C.c_int32)]
+                ("brute_force", C.c_int32), ("gradient_form", C.c_int32)]
 
 
 _STATE_F = ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h", "sxx", "syy", "sxy", "sxz", "syz",
@@ -176,6 +176,8 @@ class Params:
                 continue
             if name == "brute_force":
                 self.p.brute_force = 1 if brute_force else 0
+            elif name == "gradient_form":
+                self.p.gradient_form = int(d.get(name, 0))
             elif name == "g_n":
                 continue
             elif name in ("g_uniform", "g_center", "box_lo", "box_hi"):

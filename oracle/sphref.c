@@ -669,7 +669,9 @@ void ref_eos_yield(const ref_params *p, const ref_material *mats, int64_t n,
 /*   stress acceleration                      Eq. 18 (sum term)             */
 /*   energy equation                          Eq. 19; du/dt|_H read as      */
 /*     P_i / (Omega_i rho_i^2) sum_j m_j v_ij . dW_ij(H_i)/dx_i              */
-/*   velocity gradient F, correction C^-1     Eq. 20-21                     */
+/*   velocity gradient F, correction C^-1     Eq. 20-21; gradient_form = 1: */
+/*     the H_i term of both sums alone, -sum_j m_j v_ij (x) dW(H_i)/dx_i /   */
+/*     (Omega_i rho_i) (Reading: the non-symmetric form named in §2.2)       */
 /*   corrected gradient, R, strain rate       Eq. 22-24                     */
 /*   stress rate                              Eq. 13 / Eq. 25-29            */
 /*   CFL signal of Eq. 39                                                   */
@@ -757,7 +759,8 @@ void ref_forces(const ref_params *p, const ref_material *mats, int64_t n,
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b) {
             Es[a][b] += m * vij[a] * gWi[b];
-            double w = gWi[b] / (Omi * rhoi) + gWj[b] / (Omj * rhoj);
+            double w = p->gradient_form ? 2.0 * gWi[b] / (Omi * rhoi)
+                                        : gWi[b] / (Omi * rhoi) + gWj[b] / (Omj * rhoj);
             F[a][b] += -0.5 * m * vij[a] * w;
             Ci[a][b] += -0.5 * m * xij[a] * w;
           }

@@ -58,6 +58,7 @@ typedef struct {
   int32_t periodic;       /* 1: periodic box [box_lo, box_hi) in x, y and z */
   double box_lo[3], box_hi[3];
   int32_t brute_force;    /* 1: O(N^2) neighbour search; 0: uniform grid */
+  int32_t gradient_form;  /* 0: F, C^-1 as Eq. 20-21; 1: their H_i term alone */
 } ref_params;
 
 /* Particle state. Any output pointer the caller does not need may be NULL

@@ -401,6 +401,8 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   if (p->precision != SPH_FP64 && p->precision != SPH_FP32K) return SPH_E_ARG;
   if (p->jaumann != SPH_JAUMANN_OBJECTIVE && p->jaumann != SPH_JAUMANN_PRINTED) return SPH_E_ARG;
   if (p->yield_norm != SPH_YIELD_SQRT_J2 && p->yield_norm != SPH_YIELD_SQRT_3J2) return SPH_E_ARG;
+  if (p->gradient_form != SPH_GRADIENT_SYMMETRIC && p->gradient_form != SPH_GRADIENT_ONE_SIDED)
+    return SPH_E_ARG;
   if (p->gravity < SPH_GRAVITY_NONE || p->gravity > SPH_GRAVITY_RADIAL) return SPH_E_ARG;
   if (p->gravity == SPH_GRAVITY_RADIAL && n_sys > 1) return SPH_E_ARG;
   if (p->periodic != 0) return SPH_E_ARG;
@@ -542,6 +544,10 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.jaumann = p->jaumann;
   kp.yield_norm = p->yield_norm;
   kp.correction = p->correction_tensor;
+  kp.grad_wi = p->gradient_form == SPH_GRADIENT_ONE_SIDED ? -1.0 : -0.5;
+  kp.grad_wj = p->gradient_form == SPH_GRADIENT_ONE_SIDED ? 0.0 : -0.5;
+  kp.grad_wi_f = (float)kp.grad_wi;
+  kp.grad_wj_f = (float)kp.grad_wj;
   kp.gravity = p->gravity;
   for (int a = 0; a < 3; ++a) {
     kp.g_uniform[a] = p->g_uniform[a];

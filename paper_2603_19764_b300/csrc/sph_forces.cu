@@ -197,7 +197,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
            a3 = V::ld(rec, 4 * ic + 3);
   const T im = T(1) / a0.w;
   const T sxx = a1.x * im, syy = a1.y * im, szz = a1.z * im, sxy = a1.w * im;
-  const T sxz = a2.x * im, syz = a2.y * im, iOr = a2.z * im;
+  // iOr: the H_i weight of Eq. 20-21 over Omega_i rho_i
+  const T sxz = a2.x * im, syz = a2.y * im,
+          iOr = a2.z * im * pconst<T>(A.p.grad_wi, A.p.grad_wi_f);
   const T Hi = p.w, Hi2 = p.w * p.w, invHi = a3.y, Ki = a3.z;
   const T gi = guard_band(Hi, Lt);   // r^2 band the FP32 sum cannot decide
   const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi = a3.x;
@@ -335,7 +337,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
             mumax = tmax(mumax, -mu);
           }
           du.add(dsum);
-          const T gs = T(-0.5) * (mWi * iOr + Wj * f2.z);  // Eq. 20-21 weight
+          // Eq. 20-21 weight (the one-sided form: H_j weight 0)
+          const T gs = mWi * iOr + Wj * (f2.z * pconst<T>(A.p.grad_wj, A.p.grad_wj_f));
           const T gvx = gs * vx, gvy = gs * vy, gvz = gs * vz;
           F0.add(gvx * dx); F1.add(gvx * dy); F2.add(gvx * dz);
           F3.add(gvy * dx); F4.add(gvy * dy); F5.add(gvy * dz);

@@ -69,7 +69,8 @@ class SphParams(C.Structure):
                 ("g_uniform", C.c_double * 3), ("g_table", _P), ("phi_table", _P),
                 ("g_n", C.c_int32), ("g_rmin", C.c_double), ("g_rmax", C.c_double),
                 ("g_center", C.c_double * 3), ("g_gm", C.c_double), ("periodic", C.c_int32),
-                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+                ("gradient_form", C.c_int32)]
 
 
 class SphStepInfo(C.Structure):
@@ -233,6 +234,8 @@ def make_params(d: dict, keep: list) -> SphParams:
             continue
         if name in ("g_uniform", "g_center", "box_lo", "box_hi"):
             getattr(p, name)[:] = tuple(float(v) for v in d[name])
+        elif name == "gradient_form":
+            p.gradient_form = int(d.get(name, 0))
         else:
             setattr(p, name, d[name])
     if d.get("g_table") is not None:

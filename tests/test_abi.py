@@ -54,6 +54,7 @@ int main(void) {
   S(sph_state) S(sph_material) S(sph_params) S(sph_step_info) S(sph_tune_report) S(sph_peak_report)
   O(sph_state, id) O(sph_state, nngb) O(sph_material, strength) O(sph_material, xi)
   O(sph_params, g_table) O(sph_params, g_n) O(sph_params, box_hi) O(sph_params, precision)
+  O(sph_params, gradient_form)
   O(sph_step_info, pairs_density) O(sph_step_info, device_flags) O(sph_step_info, sweeps)
   O(sph_step_info, kernel_launches) O(sph_step_info, n_expanded) O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
   O(sph_peak_report, sm_mhz) O(sph_peak_report, n_sm)
@@ -136,4 +137,10 @@ def test_batch_init_rejects_bad_system_bounds_without_touching_the_gpu(libsph):
     assert call([0, 100], nsys=0) == sph.SPH_E_ARG      # no system
     assert call([0] * 1026, nsys=sph.SPH_MAX_SYSTEMS + 1) == sph.SPH_E_ARG
     assert f(C.byref(ctx), C.byref(p), mats, 1, C.byref(st), n, 2, None, None) == sph.SPH_E_ARG
+    assert ctx.value is None
+    # an unknown gradient form is refused before any CUDA call as well
+    for bad in (2, -1):
+        q = sph.make_params(dict(w.params, precision=0, gradient_form=bad), keep)
+        b = (C.c_int64 * 2)(0, n)
+        assert f(C.byref(ctx), C.byref(q), mats, 1, C.byref(st), n, 1, b, None) == sph.SPH_E_ARG
     assert ctx.value is None

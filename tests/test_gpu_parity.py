@@ -80,12 +80,14 @@ def test_density_solve(name, precision):
     sim.close()
 
 
+@pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", ["column", "impact", "sphere"])
-def test_forces_given_density(name, precision):
-    """Pair loop + finalize on identical inputs: the GPU's own density."""
+def test_forces_given_density(name, precision, form):
+    """Pair loop + finalize on identical inputs: the GPU's own density; both
+    gradient forms (symmetric Eq. 20-21, and their H_i term alone)."""
     w = WL[name]
-    p = _params(w, precision)
+    p = dict(_params(w, precision), gradient_form=form)
     sim = sph.Simulation(w.arrays, w.materials, p)
     sim.neighbours()
     sim.density()

@@ -255,3 +255,54 @@ def test_elastic_wave_speed():
     f = lambda tt, A, om, ph: A * np.cos(om * tt + ph)
     (A, om, ph), _ = optimize.curve_fit(f, t, amps, p0=[amps[0], c_l * k, 0.0])
     assert abs(om / k / c_l - 1) < 0.01
+
+
+# ------------------------------------------------- gradient forms (§2.2) ---
+@pytest.mark.parametrize("form", [0, 1])
+def test_linear_field_exact_in_both_gradient_forms(form):
+    """With the correction tensor built in the same form as F, G = F C = A
+    for any linear field, whatever the kernel weights (they cancel)."""
+    p, mats, st, S = _forces_state(seed=9)
+    A = np.array([[0.3, -1.1, 0.4], [0.7, 0.2, -0.5], [-0.2, 0.9, -0.6]])
+    x = np.stack([st["x"], st["y"], st["z"]], 1)
+    v = x @ A.T - np.array([1.0, 2.0, 0.5])
+    _, info = oracle.forces(dict(p, gradient_form=form), mats, st,
+                            v=(v[:, 0], v[:, 1], v[:, 2]), S=S, want_tensors=True)
+    assert info["n_cfallback"] == 0
+    assert np.allclose(info["G"], A[None], rtol=0, atol=1e-9)
+
+
+def test_symmetric_gradient_is_better_at_a_material_interface():
+    """§2.2: the symmetric form of Eq. 20-21 does better at material
+    interfaces than the non-symmetric one. A 24^3 block with a density jump
+    of 3 across z = 0 (same spacing, masses in proportion), a linear
+    velocity field, no correction tensor: the worst gradient error on the
+    interface layer is smaller with the symmetric form; away from the
+    interface the two forms are alike."""
+    mats = [wl.basalt_material(), dict(wl.basalt_material(), rho0=900.0, strength=0)]
+    a = cloud(13824, seed=3, jitter=0.05, spacing=100.0, shape="box")
+    z = a["z"]
+    zc = np.median(z)
+    top = z > zc
+    a["mat"][top] = 1
+    a["m"][top] *= 900.0 / 2700.0
+    p = _params(correction_tensor=0)
+    st, _ = oracle.density_solve(p, mats, a)
+    st, S = oracle.eos_yield(p, mats, st)
+    A = np.array([[0.3, -1.1, 0.4], [0.7, 0.2, -0.5], [-0.2, 0.9, -0.6]])
+    x = np.stack([st["x"], st["y"], st["z"]], 1)
+    v = x @ A.T
+    lo, hi = x.min(0), x.max(0)
+    inner = np.all((x[:, :2] > lo[:2] + 600) & (x[:, :2] < hi[:2] - 600), axis=1)
+    iface = inner & (np.abs(z - zc) < 150)
+    bulk = inner & (np.abs(z - zc) > 450) & (z > lo[2] + 600) & (z < hi[2] - 600)
+    err = {}
+    for form in (0, 1):
+        _, info = oracle.forces(dict(p, gradient_form=form), mats, st,
+                                v=(v[:, 0], v[:, 1], v[:, 2]), S=S, want_tensors=True)
+        err[form] = np.abs(info["G"] - A[None]).max(axis=(1, 2))
+    assert iface.sum() > 300 and bulk.sum() > 300
+    assert err[0][iface].max() < 0.9 * err[1][iface].max(), (err[0][iface].max(), err[1][iface].max())
+    assert np.median(err[0][iface]) < np.median(err[1][iface])
+    ratio = np.median(err[0][bulk]) / np.median(err[1][bulk])
+    assert 0.5 < ratio < 2.0, ratio
