@@ -566,7 +566,12 @@ static double lattice_h(const ref_params *p, const ref_material *mt, double m) {
  * midpoint of the bracket [lo, hi] of the root when it leaves it, and capped
  * at h_cap_factor times the lattice radius (a particle at the cap with
  * g < 0 is accepted and counted as capped). A particle that has not met
- * the tolerance after max_sweeps keeps its last evaluated H. */
+ * the tolerance after max_sweeps keeps its last evaluated H.
+ * Reading: Eq. 3 leaves the grad-h factor of a capped particle without
+ * meaning -- it falls to 0 as the neighbours vanish (a lone particle's
+ * rho = m W(0, H) gives exactly 1 + (H / 3 rho)(-3 rho / H) = 0), and every
+ * term over Omega rho then divides by zero -- so a capped particle takes
+ * Omega = 1. */
 int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
                           int64_t n, ref_state *s, int32_t *n_unconv,
                           int32_t *n_capped) {
@@ -615,7 +620,10 @@ int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
       }
       if (sweep > p->max_sweeps) sweep = p->max_sweeps;
       if (!done) ++unconv;
-      if (done == 2) ++capped;
+      if (done == 2) {
+        ++capped;
+        Om = 1.0;
+      }
       if (sweep > worst) worst = sweep;
       s->h[i] = Heval; /* rho, Omega and the count belong to this H */
       s->rho[i] = rho;

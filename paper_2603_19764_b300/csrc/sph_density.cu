@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           state = 1;
         } else if (gq < T(0) && H >= Hcap) {
           state = 2;
+          om_o = T(1);   // Eq. 3 tends to 0 without neighbours (0 for a lone particle)
         } else {
           if (gq < T(0)) lo = H;
           else hi = H;

@@ -306,3 +306,20 @@ def test_symmetric_gradient_is_better_at_a_material_interface():
     assert np.median(err[0][iface]) < np.median(err[1][iface])
     ratio = np.median(err[0][bulk]) / np.median(err[1][bulk])
     assert 0.5 < ratio < 2.0, ratio
+
+
+def test_lone_particle_grad_h_term_and_cap():
+    """A particle alone: rho = m W(0, H) = 21 m / (2 pi H^3), and Eq. 3
+    gives Omega = 1 + (H / 3 rho)(-3 rho / H) = 0 exactly. The solve caps
+    its H and, by the cap reading, gives it Omega = 1, so that the terms
+    over Omega rho stay finite (no neighbours: du/dt = 0, dS/dt = 0)."""
+    a = cloud(1, seed=3, spacing=100.0, vsig=5.0, ssig=1e6)
+    p = _params()
+    H = float(a["h"][0])
+    rho, om, cnt = oracle.density_given_h(p, a)
+    assert rho[0] == pytest.approx(21.0 * a["m"][0] / (2.0 * math.pi * H ** 3), rel=1e-14)
+    assert abs(om[0]) < 1e-14 and cnt[0] == 0
+    st, info = oracle.derivatives(p, [wl.basalt_material()], a)
+    assert info["n_capped"] == 1 and st["omega"][0] == 1.0
+    for f in ("ax", "ay", "az", "dudt", "dsxx", "dsyz"):
+        assert st[f][0] == 0.0, f
