@@ -535,6 +535,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.eta_a = p->eta_a;
   kp.h_tol = p->h_tol;
   kp.av_alpha_f = (float)p->av_alpha;
+  kp.lattice_k_f = (float)(3.0 * p->n_ngb / (4.0 * kPi));
   kp.av_beta_f = (float)p->av_beta;
   kp.av_eps_f = (float)p->av_eps;
   kp.h_tol_f = (float)p->h_tol;

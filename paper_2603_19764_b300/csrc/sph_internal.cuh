@@ -112,6 +112,7 @@ struct KParams {
   // FP32 copies of the constants the FP32 pair loops use, so that a
   // constant the compiler reloads inside a loop needs no FP64 conversion
   float av_alpha_f, av_beta_f, av_eps_f, h_tol_f;
+  float lattice_k_f;           // 3 n_ngb / (4 pi): H_bar^3 = lattice_k m / rho0
   // weights of the H_i and H_j terms of Eq. 20-21: -1/2 and -1/2
   // (symmetric), -1 and 0 (one-sided form)
   double grad_wi, grad_wj;

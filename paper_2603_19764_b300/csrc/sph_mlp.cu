@@ -502,23 +502,26 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
     // the features are FP32 quantities: ratios, logarithms and the cube
     // root in FP32
     const double H = s.h[ic];
-    const float dtdiv = (float)P.dt[sy] * L.divv[ic];
+    const float Hf = d2f(H);
+    const float dtdiv = d2f(P.dt[sy]) * L.divv[ic];
     const double hp = L.hprev[ic];
+    const bool have_prev = __double_as_longlong(hp) > 0;   // hp > 0 on the integer pipe
     const MatT<float> &M = mat_t<float>(P, s.mat[ic]);
-    // (no FP64 division: it costs tens of FP64 operations on this part)
+    // (no FP64 division or conversion: both run on the FP64 unit at 1/64
+    // of the FP32 rate; d2f rounds on the integer pipe)
     const float rho0 = M.rho0;
-    const float hbar = cbrtf((float)(3.0 * P.n_ngb / (4.0 * kPi)) * ((float)s.m[ic] / rho0));
-    const float lhp = hp > 0.0 ? logf((float)H / (float)hp) : 0.f;
+    const float hbar = cbrtf(P.lattice_k_f * (d2f(s.m[ic]) / rho0));
+    const float lhp = have_prev ? logf(Hf / d2f(hp)) : 0.f;
     float f[NIN];
-    f[0] = logf((float)H / hbar);
+    f[0] = logf(Hf / hbar);
     f[1] = (float)s.nngb[ic] / (float)P.n_ngb - 1.f;
-    f[2] = logf((float)s.rho[ic] / rho0);
+    f[2] = logf(d2f(s.rho[ic]) / rho0);
     f[3] = dtdiv;
     f[4] = lhp;
-    f[5] = (float)(s.omega[ic] - 1.0);
+    f[5] = d2f(s.omega[ic]) - 1.f;
     if (valid && L.record) {
       float *xo = L.x_out + id * NIN;
-      const bool have = hp > 0.0;
+      const bool have = have_prev;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const float2 fp = L.feat[k][ic];
@@ -540,11 +543,11 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
       for (int half = 0; half < 2; ++half) {
         uint32_t ax[4];
         load_a(Q.xs[w], LD1, 16 * half, 0, ax);
-        Tile T;
-        forward_tile(S, ax, T);
+        float o[2];
+        infer_tile(S, ax, o);
         if ((lane & 3) == 0) {
-          Q.outs[w][16 * half + (lane >> 2)] = T.out[0];
-          Q.outs[w][16 * half + (lane >> 2) + 8] = T.out[1];
+          Q.outs[w][16 * half + (lane >> 2)] = o[0];
+          Q.outs[w][16 * half + (lane >> 2) + 8] = o[1];
         }
       }
       __syncwarp();
@@ -555,7 +558,7 @@ __global__ void __launch_bounds__(128) k_learn(sph_state s, int64_t n, KParams P
       if (L.guess != SPH_GUESS_PREVIOUS) {
         const float lo = -0.22314355f, hi = 0.22314355f;   // log 0.8, log 1.25
         r = isfinite(r) ? fminf(fmaxf(r, lo), hi) : 0.f;
-        L.hprop[ic] = H * (double)expf(r);
+        L.hprop[ic] = H * f2d(expf(r));
       }
       L.hprev[ic] = H;
     }

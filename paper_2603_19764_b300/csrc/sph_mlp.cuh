@@ -188,5 +188,59 @@ __device__ __forceinline__ void forward_tile(const Smem &S, const uint32_t (&ax)
   T.out[1] = p1 + S.b3;
 }
 
+// Inference only (the in-step guess): both hidden layers through the
+// hardware tanh on bf16 pairs, one special-function instruction per two
+// units. The first layer's result is then already the bf16 operand of the
+// second product; the second layer's pairs are widened to FP32 for the
+// output's dot product. bf16 activations put about 4e-3 relative error on
+// the proposal of log(H_n+1 / H_n), a few 1e-5 on H itself, which the
+// Newton solve that follows removes. Training and the forward entry point
+// keep FP32 activations (tanh_fast).
+__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t v) {
+  uint32_t y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(v));
+  return y;
+}
+
+__device__ __forceinline__ void infer_tile(const Smem &S, const uint32_t (&ax)[4], float (&out)[2]) {
+  const int t = threadIdx.x & 3;
+  uint32_t a1f[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    uint32_t b0, b1;
+    load_b(S.w1, LD1, 8 * nt, 0, b0, b1);
+    mma16816(c, ax, b0, b1);
+    const int col = 8 * nt + 2 * t;
+    // rows g and g + 8 of columns col, col + 1: the A-fragment halves of
+    // the next product (see to_a)
+    a1f[nt >> 1][2 * (nt & 1)] = tanh_bf16x2(pack_bf16(c[0] + S.b1[col], c[1] + S.b1[col + 1]));
+    a1f[nt >> 1][2 * (nt & 1) + 1] =
+        tanh_bf16x2(pack_bf16(c[2] + S.b1[col], c[3] + S.b1[col + 1]));
+  }
+  float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+      uint32_t b0, b1;
+      load_b(S.w2, LD2, 8 * nt, 16 * kt, b0, b1);
+      mma16816(c, a1f[kt], b0, b1);
+    }
+    const int col = 8 * nt + 2 * t;
+    const uint32_t lo = tanh_bf16x2(pack_bf16(c[0] + S.b2[col], c[1] + S.b2[col + 1]));
+    const uint32_t hi = tanh_bf16x2(pack_bf16(c[2] + S.b2[col], c[3] + S.b2[col + 1]));
+    p0 += __uint_as_float(lo << 16) * S.w3[col] + __uint_as_float(lo & 0xffff0000u) * S.w3[col + 1];
+    p1 += __uint_as_float(hi << 16) * S.w3[col] + __uint_as_float(hi & 0xffff0000u) * S.w3[col + 1];
+  }
+  p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+  p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+  p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+  p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+  out[0] = p0 + S.b3;
+  out[1] = p1 + S.b3;
+}
+
 }  // namespace mlp
 }  // namespace sphk
