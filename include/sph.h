@@ -376,10 +376,16 @@ sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sp
  * without a previous step are NaN. SPH_E_STATE unless recording. */
 sph_status sph_learn_samples(sph_ctx *c, float *X, float *y);
 
-/* sph_step with HOST state: the caller passes pinned or pageable host
- * arrays in `host`; the library copies them to the context's device state,
- * runs one step and copies the state back. h2d / d2h byte counts go to
- * *bytes_in / *bytes_out (may be NULL). */
+/* sph_step with HOST state: the caller passes pinned (for overlap) or
+ * pageable host arrays in `host`; the library copies to the context's device
+ * state every array the step reads (rho, Omega, P, c_s and the counts are
+ * recomputed by the step and are not copied in), runs one step with direct
+ * launches, and copies each group of arrays back as soon as the step has
+ * finished writing it, on a library copy stream that overlaps the rest of
+ * the step (positions, masses, ids after the sort; H, rho, Omega after the
+ * density solve; P, c_s after the EOS; derivatives and counts after the
+ * force pass; v, u, S, strain invariant after the kicks). Synchronises.
+ * h2d / d2h byte counts go to *bytes_in / *bytes_out (may be NULL). */
 sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_info *info,
                          int64_t *bytes_in, int64_t *bytes_out);
 

@@ -208,6 +208,47 @@ cudaError_t mark(sph_ctx *c, int k) {
   return c->timing && !c->capturing ? cudaEventRecord(c->ev[k], c->stream) : cudaSuccess;
 }
 
+// Copy-out of sph_step_host, overlapped with the rest of the step: group g
+// of the state is final once the phase before this call has run (0: after
+// the sort -- positions, masses, ids, materials, flags; 1: after the
+// density solve -- H, rho, Omega; 2: after the EOS -- P, c_s; 3: after the
+// force pass -- derivatives and counts; 4: after the kicks -- v, u, S and
+// the strain invariant).
+sph_status copy_out(sph_ctx *c, int g) {
+  if (!c->host_out || c->capturing) return SPH_OK;
+  const sph_state &d = c->st, &h = *c->host_out;
+  const size_t b8 = sizeof(double) * (size_t)c->n, b4 = sizeof(int32_t) * (size_t)c->n;
+  CK(cudaEventRecord(c->out_ev[g], c->stream));
+  CK(cudaStreamWaitEvent(c->cstream, c->out_ev[g], 0));
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->cstream);
+  };
+  switch (g) {
+    case 0:
+      CK(cp(h.x, d.x, b8)); CK(cp(h.y, d.y, b8)); CK(cp(h.z, d.z, b8)); CK(cp(h.m, d.m, b8));
+      CK(cp(h.id, d.id, b8)); CK(cp(h.mat, d.mat, b4)); CK(cp(h.flags, d.flags, b4));
+      break;
+    case 1:
+      CK(cp(h.h, d.h, b8)); CK(cp(h.rho, d.rho, b8)); CK(cp(h.omega, d.omega, b8));
+      break;
+    case 2:
+      CK(cp(h.pres, d.pres, b8)); CK(cp(h.cs, d.cs, b8));
+      break;
+    case 3:
+      CK(cp(h.ax, d.ax, b8)); CK(cp(h.ay, d.ay, b8)); CK(cp(h.az, d.az, b8));
+      CK(cp(h.dudt, d.dudt, b8)); CK(cp(h.dsxx, d.dsxx, b8)); CK(cp(h.dsyy, d.dsyy, b8));
+      CK(cp(h.dsxy, d.dsxy, b8)); CK(cp(h.dsxz, d.dsxz, b8)); CK(cp(h.dsyz, d.dsyz, b8));
+      CK(cp(h.nngb, d.nngb, b4));
+      break;
+    default:
+      CK(cp(h.vx, d.vx, b8)); CK(cp(h.vy, d.vy, b8)); CK(cp(h.vz, d.vz, b8)); CK(cp(h.u, d.u, b8));
+      CK(cp(h.sxx, d.sxx, b8)); CK(cp(h.syy, d.syy, b8)); CK(cp(h.sxy, d.sxy, b8));
+      CK(cp(h.sxz, d.sxz, b8)); CK(cp(h.syz, d.syz, b8)); CK(cp(h.eps_ii, d.eps_ii, b8));
+      break;
+  }
+  return SPH_OK;
+}
+
 // all = 1 permutes every array of the state (sph_neighbours on its own);
 // steps pass 0 and recompute rho, Omega, P, c_s and the counts in the new
 // order.
@@ -218,7 +259,7 @@ sph_status run_neighbours(sph_ctx *c, int drift, int all) {
   CK(launch_grid_setup(c));
   CK(launch_sort_permute(c, all));
   CK(mark(c, 1));
-  return SPH_OK;
+  return copy_out(c, 0);
 }
 
 // Tuner marker k (density start / end, forces start / end) on tuning steps.
@@ -233,14 +274,18 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
   CK(launch_density(c, 1));   // the force pass that follows counts the neighbours
   CK(tmark(c, 1));
   CK(mark(c, 3));
+  sph_status s = copy_out(c, 1);
+  if (s != SPH_OK) return s;
   CK(launch_eos_pack(c));
   CK(mark(c, 4));
+  s = copy_out(c, 2);
+  if (s != SPH_OK) return s;
   CK(tmark(c, 2));
   CK(launch_forces(c));
   CK(tmark(c, 3));
   CK(launch_learn(c));
   CK(mark(c, 5));
-  return SPH_OK;
+  return copy_out(c, 3);
 }
 
 // Everything one step enqueues, from the dt upload to the status readback.
@@ -251,6 +296,8 @@ sph_status enqueue_step(sph_ctx *c) {
   if (s != SPH_OK) return s;
   CK(launch_kick(c, 1));
   CK(mark(c, 6));
+  s = copy_out(c, 4);
+  if (s != SPH_OK) return s;
   return enqueue_status_readback(c);
 }
 
@@ -692,6 +739,11 @@ sph_status sph_destroy(sph_ctx *c) {
   drop_graph(c);
   if (c->gstream) cudaStreamDestroy(c->gstream);
   if (c->fence) cudaEventDestroy(c->fence);
+  if (c->cstream) {
+    cudaStreamSynchronize(c->cstream);
+    cudaStreamDestroy(c->cstream);
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(c->out_ev[k]);
+  }
   if (c->timing)
     for (int k = 0; k <= SPH_NUM_PHASES; ++k) cudaEventDestroy(c->ev[k]);
   if (c->tev[0])
@@ -894,31 +946,38 @@ sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_
                          int64_t *bytes_in, int64_t *bytes_out) {
   ENTER(c);
   if (!host || !state_complete(host)) return fail(c, SPH_E_ARG, "incomplete host state");
+  if (!c->cstream) {
+    CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreateWithFlags(&c->out_ev[k], cudaEventDisableTiming));
+  }
   const sph_state &d = c->st;
   const int64_t n = c->n;
-  double *const hd[28] = {host->x,    host->y,    host->z,     host->vx,    host->vy,   host->vz,
-                          host->u,    host->m,    host->h,     host->sxx,   host->syy,  host->sxy,
-                          host->sxz,  host->syz,  host->rho,   host->omega, host->pres, host->cs,
-                          host->ax,   host->ay,   host->az,    host->dudt,  host->dsxx, host->dsyy,
-                          host->dsxy, host->dsxz, host->dsyz,  host->eps_ii};
-  double *const dd[28] = {d.x,    d.y,    d.z,     d.vx,    d.vy,   d.vz,   d.u,    d.m,
-                          d.h,    d.sxx,  d.syy,   d.sxy,   d.sxz,  d.syz,  d.rho,  d.omega,
-                          d.pres, d.cs,   d.ax,    d.ay,    d.az,   d.dudt, d.dsxx, d.dsyy,
-                          d.dsxy, d.dsxz, d.dsyz,  d.eps_ii};
-  int32_t *const hi[3] = {host->nngb, host->mat, host->flags};
-  int32_t *const di[3] = {d.nngb, d.mat, d.flags};
+  // in: everything the step reads before writing it (rho, Omega, P, c_s and
+  // the counts are recomputed in the step, so they stay on the host)
+  double *const hd[24] = {host->x,    host->y,    host->z,    host->vx,   host->vy,   host->vz,
+                          host->u,    host->m,    host->h,    host->sxx,  host->syy,  host->sxy,
+                          host->sxz,  host->syz,  host->ax,   host->ay,   host->az,   host->dudt,
+                          host->dsxx, host->dsyy, host->dsxy, host->dsxz, host->dsyz, host->eps_ii};
+  double *const dd[24] = {d.x,   d.y,    d.z,    d.vx,   d.vy,   d.vz,   d.u,    d.m,
+                          d.h,   d.sxx,  d.syy,  d.sxy,  d.sxz,  d.syz,  d.ax,   d.ay,
+                          d.az,  d.dudt, d.dsxx, d.dsyy, d.dsxy, d.dsxz, d.dsyz, d.eps_ii};
   const size_t b8 = sizeof(double) * (size_t)n, b4 = sizeof(int32_t) * (size_t)n;
-  for (int k = 0; k < 28; ++k) CK(cudaMemcpyAsync(dd[k], hd[k], b8, cudaMemcpyHostToDevice, c->stream));
-  for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(di[k], hi[k], b4, cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < 24; ++k) CK(cudaMemcpyAsync(dd[k], hd[k], b8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.mat, host->mat, b4, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.flags, host->flags, b4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.id, host->id, b8, cudaMemcpyHostToDevice, c->stream));
+  // out: each array group as soon as the step has finished it, on the copy
+  // stream (direct launches: the captured graph has no copy-out)
+  c->host_out = host;
+  const int graph = c->use_graph;
+  c->use_graph = 0;
   const sph_status s = sph_step(c, dt, info);
-  for (int k = 0; k < 28; ++k) CK(cudaMemcpyAsync(hd[k], dd[k], b8, cudaMemcpyDeviceToHost, c->stream));
-  for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(hi[k], di[k], b4, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(host->id, d.id, b8, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  const int64_t bytes = 29 * (int64_t)b8 + 3 * (int64_t)b4;
-  if (bytes_in) *bytes_in = bytes;
-  if (bytes_out) *bytes_out = bytes;
+  c->use_graph = graph;
+  c->host_out = nullptr;
+  const cudaError_t e = cudaStreamSynchronize(c->cstream);
+  if (e != cudaSuccess) return fail_cuda(c, e, "copy-out");
+  if (bytes_in) *bytes_in = 25 * (int64_t)b8 + 2 * (int64_t)b4;
+  if (bytes_out) *bytes_out = 29 * (int64_t)b8 + 3 * (int64_t)b4;
   return s;
 }
 

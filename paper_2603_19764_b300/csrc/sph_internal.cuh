@@ -488,6 +488,11 @@ struct sph_ctx {
   int capturing;                // the step is being captured into a graph
   cudaStream_t gstream;         // library stream that graphs are captured on
   cudaEvent_t fence;            // caller stream -> library stream ordering
+  // sph_step_host: each group of state arrays is copied back on cstream as
+  // soon as the step has finished writing it (host_out != null only then)
+  const sph_state *host_out;
+  cudaStream_t cstream;
+  cudaEvent_t out_ev[5];
   cudaGraphExec_t graph_exec;   // captured step
   cudaEvent_t ev[SPH_NUM_PHASES + 1];
   // online tuning of the group spans over the coming steps
