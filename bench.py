@@ -41,11 +41,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic FLOPs per in-range pair, counted from the arithmetic of
-# Eq. 1-3 (density) and Eq. 4-8, 18-21 (forces) in their contracted form;
-# candidate rejection, compensation and index work are not counted.
-FLOPS_DENSITY_PAIR = 26
-FLOPS_FORCE_PAIR = 151
+# Algorithmic FLOPs per in-range pair, counted term by term from the
+# formulas as the oracle writes them out (Eq. 1 and 3 for the density, one
+# evaluation; Eq. 4-8 and 18-21 with du/dt|_H for the forces), an add, sub,
+# mul, div or sqrt counting 1; factors that belong to one particle
+# (P/(Omega rho^2), S/(Omega rho^2), 1/(Omega rho), kernel normalisation)
+# are formed once per particle and not counted per pair. The kernels
+# contract the force terms and execute fewer operations; candidate
+# rejection, compensation and index work are not counted either way.
+FLOPS_DENSITY_PAIR = 27
+FLOPS_FORCE_PAIR = 209
 # B300 unit counts: 148 SMs x 128 FP32 lanes, 2 FLOP per FMA; FP64 at the
 # nominal 1.25 TFLOP/s at the 2032 MHz maximum clock.
 N_SM, FP32_LANES, MAX_MHZ = 148, 128, 2032.0
