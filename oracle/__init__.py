@@ -121,6 +121,10 @@ def lib():
         L.ref_forces.argtypes = [C.POINTER(RefParams), C.POINTER(RefMaterial), C.c_int64,
                                  C.POINTER(RefState), _P, _P, _P, _P, _P, _P, _P, _P,
                                  C.c_int64, _PL, _P, _P, _PI]
+        L.ref_step_rungs.restype = C.c_int32
+        L.ref_step_rungs.argtypes = [C.POINTER(RefParams), C.POINTER(RefMaterial), C.c_int64,
+                                     C.POINTER(RefState), C.c_double, C.c_int32, _PI, _PL,
+                                     C.POINTER(RefInfo)]
         L.ref_step.restype = C.c_int32
         L.ref_step.argtypes = [C.POINTER(RefParams), C.POINTER(RefMaterial), C.c_int64,
                                C.POINTER(RefState), d, C.POINTER(RefInfo)]
@@ -408,6 +412,30 @@ def step(params: dict, mats: list, arrays: dict, dt: float, nsteps: int = 1,
         if callback is not None:
             callback(k, st.a, d)
     return st.a, infos
+
+
+def step_rungs(params: dict, mats: list, arrays: dict, dt: float, max_rung: int,
+               nsteps: int = 1):
+    """Advance nsteps big steps of length dt with hierarchical individual
+    steps on 2^max_rung substeps (ref_step_rungs). Returns (state dict,
+    list of infos, rungs at the end, particle updates per big step)."""
+    P = Params(params)
+    M = materials(mats)
+    st = State(arrays)
+    rung = np.zeros(st.n, np.int32)
+    infos, updates = [], []
+    for _ in range(nsteps):
+        info = RefInfo()
+        na = C.c_int64(0)
+        rc = lib().ref_step_rungs(P.ref, M, st.n, st.ref, float(dt), int(max_rung), _ip(rung),
+                                  C.byref(na), C.byref(info))
+        if rc == 4:
+            raise ValueError("ref_step_rungs: max_rung outside 0..15 or no vsig in the state")
+        d = info.as_dict()
+        d["status"] = rc
+        infos.append(d)
+        updates.append(int(na.value))
+    return st.a, infos, rung, updates
 
 
 def diagnostics(params: dict, arrays: dict) -> dict:

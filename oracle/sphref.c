@@ -572,9 +572,21 @@ static double lattice_h(const ref_params *p, const ref_material *mt, double m) {
  * rho = m W(0, H) gives exactly 1 + (H / 3 rho)(-3 rho / H) = 0), and every
  * term over Omega rho then divides by zero -- so a capped particle takes
  * Omega = 1. */
+static int32_t density_solve_sel(const ref_params *p, const ref_material *mats, int64_t n,
+                                 ref_state *s, const unsigned char *active, int32_t *n_unconv,
+                                 int32_t *n_capped);
+
 int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
                           int64_t n, ref_state *s, int32_t *n_unconv,
                           int32_t *n_capped) {
+  return density_solve_sel(p, mats, n, s, NULL, n_unconv, n_capped);
+}
+
+/* The solve for the particles with active[i] != 0 (all when active is
+ * NULL); the others keep H, rho, Omega and their count. */
+static int32_t density_solve_sel(const ref_params *p, const ref_material *mats, int64_t n,
+                                 ref_state *s, const unsigned char *active, int32_t *n_unconv,
+                                 int32_t *n_capped) {
   double hmax = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double cap = p->h_cap_factor * lattice_h(p, &mats[s->mat[i]], s->m[i]);
@@ -589,6 +601,7 @@ int32_t ref_density_solve(const ref_params *p, const ref_material *mats,
     int64_t cap = 256, *buf = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
 #pragma omp for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
+      if (active && !active[i]) continue;
       double target = p->n_ngb * s->m[i];
       double Hcap = p->h_cap_factor * lattice_h(p, &mats[s->mat[i]], s->m[i]);
       double H = s->h[i] < Hcap ? s->h[i] : Hcap;
@@ -990,6 +1003,151 @@ int32_t ref_step(const ref_params *p, const ref_material *mats, int64_t n,
     s->vsig = NULL;
   }
   free(G);
+  for (int c = 0; c < 3; ++c) free(vp[c]);
+  free(up);
+  for (int c = 0; c < 5; ++c) free(Sp[c]);
+  return unconv ? 3 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchical individual time steps. §2.4 takes its step sizes from the   */
+/* criteria of Eq. 38-39 within the hierarchical scheme of the paper's      */
+/* Paper I, which is not printed here. Reading: power-of-two rungs with the */
+/* predictor-corrector of ref_step applied per particle:                    */
+/*   the big step dt is split into L = 2^R substeps of delta = dt / L; a    */
+/*   particle on rung r steps dt_r = dt / 2^r, i.e. len = 2^(R-r) substeps, */
+/*   and its steps start at multiples of len;                               */
+/*   every substep drifts every moving particle by delta with its half-step */
+/*   velocity; the particles whose step ends at the substep's end are       */
+/*   active: their density is solved, their derivatives are formed from the */
+/*   state predicted to that time, and they are kicked (closing and opening */
+/*   kicks of dt_r / 2, rescale, strain invariant over dt_r);               */
+/*   the other particles enter as neighbours with v, u, S predicted to the  */
+/*   same time, q + (t - t_mid) dq with t_mid the midpoint of their current */
+/*   step and dq their last derivatives, and with their last H, rho, Omega; */
+/*   the EOS and radial return of the predicted state run for every one;   */
+/*   a kicked particle takes the rung its criteria ask for (the smallest r  */
+/*   with dt / 2^r <= min(dt_a, dt_CFL), at most R), but no coarser than    */
+/*   the coarsest rung whose steps start at the next substep; rungs are set */
+/*   from the criteria of the last derivatives at the start of a big step.  */
+/* Fixed particles are never kicked; their density is solved at the end of  */
+/* the big step (rung 0). R = 0 is ref_step.                                */
+/* ------------------------------------------------------------------------ */
+static int32_t rung_for(const ref_params *p, const ref_state *s, int64_t i, double dt,
+                        int32_t R) {
+  double a = sqrt(s->ax[i] * s->ax[i] + s->ay[i] * s->ay[i] + s->az[i] * s->az[i]);
+  double ta = a > 0.0 ? p->eta_a * sqrt(s->h[i] / a) : INFINITY;
+  double tc = p->eta_c * s->h[i] / s->vsig[i];
+  double t = ta < tc ? ta : tc;
+  int32_t r = 0;
+  while (r < R && dt / (double)(1 << r) > t) ++r;
+  return r;
+}
+
+int32_t ref_step_rungs(const ref_params *p, const ref_material *mats, int64_t n,
+                       ref_state *s, double dt, int32_t R, int32_t *rung,
+                       int64_t *active_updates, ref_info *info) {
+  if (R < 0 || R > 15 || !s->vsig || !rung) return 4;
+  const int64_t L = (int64_t)1 << R;
+  const double delta = dt / (double)L;
+  for (int64_t i = 0; i < n; ++i) rung[i] = (s->flags[i] & 1) ? 0 : rung_for(p, s, i, dt, R);
+  double *vp[3] = {dup(s->vx, n), dup(s->vy, n), dup(s->vz, n)};
+  double *up = dup(s->u, n);
+  double *Sp[5] = {dup(s->sxx, n), dup(s->syy, n), dup(s->sxy, n), dup(s->sxz, n), dup(s->syz, n)};
+  double *G = (double *)malloc(sizeof(double) * 9 * (size_t)n);
+  unsigned char *act = (unsigned char *)malloc((size_t)n);
+  int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  double *S[5] = {s->sxx, s->syy, s->sxy, s->sxz, s->syz};
+  double *dS[5] = {s->dsxx, s->dsyy, s->dsxy, s->dsxz, s->dsyz};
+  double *v[3] = {s->vx, s->vy, s->vz};
+  double *a[3] = {s->ax, s->ay, s->az};
+  int32_t unconv = 0, capped = 0, fb = 0, sweeps = 0, worst = 0;
+  int64_t updates = 0;
+  for (int64_t sub = 0; sub < L; ++sub) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (s->flags[i] & 1) continue;
+      s->x[i] += delta * s->vx[i];
+      s->y[i] += delta * s->vy[i];
+      s->z[i] += delta * s->vz[i];
+    }
+    int64_t na = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t len = (int64_t)1 << (R - rung[i]);
+      const int64_t start = (sub / len) * len;
+      act[i] = (unsigned char)((sub + 1) % len == 0);
+      if (act[i]) idx[na++] = i;
+      const double k = (s->flags[i] & 1) ? 0.0 : ((double)(sub + 1 - start) - 0.5 * (double)len) * delta;
+      for (int c = 0; c < 3; ++c) vp[c][i] = v[c][i] + k * a[c][i];
+      up[i] = s->u[i] + k * s->dudt[i];
+      for (int c = 0; c < 5; ++c) Sp[c][i] = S[c][i] + k * dS[c][i];
+    }
+    int32_t uc = 0, cp = 0, f = 0;
+    sweeps = density_solve_sel(p, mats, n, s, act, &uc, &cp);
+    if (sweeps > worst) worst = sweeps;
+    unconv += uc;
+    capped += cp;
+    ref_eos_yield(p, mats, n, s, up, Sp[0], Sp[1], Sp[2], Sp[3], Sp[4]);
+    ref_forces(p, mats, n, s, vp[0], vp[1], vp[2], Sp[0], Sp[1], Sp[2], Sp[3], Sp[4], na, idx,
+               G, NULL, &f);
+    fb += f;
+    /* closing kick of the active particles to their step's end */
+    for (int64_t k = 0; k < na; ++k) {
+      const int64_t i = idx[k];
+      if (s->flags[i] & 1) continue;
+      ++updates;
+      const ref_material *mt = &mats[s->mat[i]];
+      const double dti = (double)((int64_t)1 << (R - rung[i])) * delta, hdt = 0.5 * dti;
+      for (int c = 0; c < 3; ++c) v[c][i] += hdt * a[c][i];
+      s->u[i] += hdt * s->dudt[i];
+      double Sv[5];
+      for (int c = 0; c < 5; ++c) Sv[c] = S[c][i] + hdt * dS[c][i];
+      if (mt->strength) {
+        double P, cs;
+        ref_eos(mt, s->rho[i], s->u[i], &P, &cs);
+        ref_radial_return(Sv, ref_yield(mt, P, s->u[i]), p->yield_norm);
+      } else {
+        Sv[0] = Sv[1] = Sv[2] = Sv[3] = Sv[4] = 0.0;
+      }
+      for (int c = 0; c < 5; ++c) S[c][i] = Sv[c];
+      const double *Gi = G + 9 * k;
+      double ee = 0.0;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+          double e = 0.5 * (Gi[3 * r + c] + Gi[3 * c + r]);
+          ee += e * e;
+        }
+      s->eps_ii[i] += dti * 0.5 * ee;
+    }
+    if (sub == L - 1 && info) {   /* every particle is at the big step's end */
+      ref_diagnostics(p, n, s, info);
+      info->dt_next = next_dt(p, n, s);
+    }
+    /* new rungs, then the opening kicks */
+    int32_t r_al = R;   /* coarsest rung whose steps start at sub + 1 */
+    for (int64_t m = sub + 1; r_al > 0 && (m & 1) == 0; m >>= 1) --r_al;
+    if (sub + 1 == L) r_al = 0;
+    for (int64_t k = 0; k < na; ++k) {
+      const int64_t i = idx[k];
+      if (s->flags[i] & 1) continue;
+      int32_t r = rung_for(p, s, i, dt, R);
+      if (r < r_al) r = r_al;
+      rung[i] = r;
+      const double hdt = 0.5 * (double)((int64_t)1 << (R - r)) * delta;
+      for (int c = 0; c < 3; ++c) v[c][i] += hdt * a[c][i];
+      s->u[i] += hdt * s->dudt[i];
+      for (int c = 0; c < 5; ++c) S[c][i] += hdt * dS[c][i];
+    }
+  }
+  if (info) {
+    info->max_sweeps = worst;
+    info->n_unconverged = unconv;
+    info->n_capped = capped;
+    info->n_cfallback = fb;
+  }
+  if (active_updates) *active_updates = updates;
+  free(G);
+  free(act);
+  free(idx);
   for (int c = 0; c < 3; ++c) free(vp[c]);
   free(up);
   for (int c = 0; c < 5; ++c) free(Sp[c]);

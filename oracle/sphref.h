@@ -158,6 +158,13 @@ void ref_forces(const ref_params *p, const ref_material *mats, int64_t n,
  * solve did not converge for some particle. */
 int32_t ref_step(const ref_params *p, const ref_material *mats, int64_t n,
                  ref_state *s, double dt, ref_info *info);
+/* Hierarchical individual steps over one big step dt with 2^R substeps;
+ * rung (n, out) receives each particle's rung at the end. The state must
+ * carry vsig from the last derivatives. Returns 4 for R outside 0..15 or a
+ * missing vsig / rung, 3 if a solve did not converge. */
+int32_t ref_step_rungs(const ref_params *p, const ref_material *mats, int64_t n,
+                       ref_state *s, double dt, int32_t R, int32_t *rung,
+                       int64_t *active_updates, ref_info *info);
 
 /* Derivatives of the given state without moving it (predict with dt = 0):
  * density, EOS + yield on a copy of S, forces. Used to start a run. */
