@@ -133,7 +133,17 @@ typedef struct {
  *                  SPH_GRADIENT_ONE_SIDED: the H_i term alone,
  *                  F_i = -sum_j m_j v_ij (x) dW(H_i)/dx_i / (Omega_i rho_i)
  *                  and C_i^-1 likewise with x_ij (the non-symmetric form
- *                  §2.2 mentions beside Eq. 20-21). SPH_E_ARG otherwise. */
+ *                  §2.2 mentions beside Eq. 20-21). SPH_E_ARG otherwise.
+ *   max_rung       0: one global step per sph_step (dt for every particle).
+ *                  1..15: hierarchical individual steps -- sph_step's dt is
+ *                  a big step of 2^max_rung substeps; a particle on rung r
+ *                  steps dt / 2^r (the smallest r with dt / 2^r within its
+ *                  Eq. 38-39 criteria, at most max_rung), is drifted every
+ *                  substep, and is solved, given derivatives and kicked only
+ *                  at the end of its own steps; neighbours between their
+ *                  steps enter with v, u, S predicted linearly to the
+ *                  substep time and their last H, rho, Omega. Every
+ *                  particle is at time t + dt when the call returns. */
 typedef struct {
   int32_t n_ngb;
   double av_alpha, av_beta, av_eps;
@@ -150,6 +160,7 @@ typedef struct {
   int32_t periodic;
   double box_lo[3], box_hi[3];
   int32_t gradient_form;
+  int32_t max_rung;
 } sph_params;
 
 /* Per-step report (filled by the synchronising calls). Energies and
@@ -157,7 +168,10 @@ typedef struct {
  * L = sum m r x v (Eq. 46). dt_next is the minimum of Eq. 38-39.
  * pairs_density counts the in-range pairs evaluated over all Newton sweeps,
  * pairs_force the pairs of the force loop; cand_* count the candidates the
- * two pair kernels staged (work done to find those pairs). */
+ * two pair kernels staged (work done to find those pairs). With
+ * hierarchical steps the counters add up over the substeps, and
+ * particle_updates counts the particles kicked (n per step otherwise);
+ * rung_counts[r] the moving particles on rung r when the step ends. */
 typedef struct {
   double dt, dt_next;
   double e_kin, e_int, e_pot;
@@ -170,6 +184,8 @@ typedef struct {
   int32_t kernel_launches;               /* kernels the call launched */
   int64_t sweeps_total;                  /* Newton sweeps summed over particles */
   int32_t n_expanded;                    /* FP32 form: solves closed by the expansion */
+  int64_t particle_updates;              /* particle steps taken (kicks) */
+  int32_t rung_counts[16];
 } sph_step_info;
 
 /* Report of the group-span tuner (sph_autotune). The pair kernels give
@@ -379,7 +395,8 @@ sph_status sph_learn_samples(sph_ctx *c, float *X, float *y);
 /* sph_step with HOST state: the caller passes pinned (for overlap) or
  * pageable host arrays in `host`; the library copies to the context's device
  * state every array the step reads (rho, Omega, P, c_s and the counts are
- * recomputed by the step and are not copied in), runs one step with direct
+ * recomputed by the step and are not copied in, except rho, Omega and the
+ * counts with hierarchical steps), runs one step with direct
  * launches, and copies each group of arrays back as soon as the step has
  * finished writing it, on a library copy stream that overlaps the rest of
  * the step (positions, masses, ids after the sort; H, rho, Omega after the

@@ -113,7 +113,7 @@ void free_all(sph_ctx *c) {
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
                  c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->w.divv,
                  c->learn.hprev, c->learn.hprop, c->learn.feat[0], c->learn.feat[1],
-                 c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill};
+                 c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill, c->w.rung};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -174,6 +174,9 @@ void fill_info(const sph_ctx *c, int sys, sph_step_info *info) {
   info->kernel_launches = c->nlaunch;
   info->sweeps_total = (int64_t)h.sweeps_total;
   info->n_expanded = h.n_expanded;
+  info->particle_updates = (int64_t)h.updates;
+  for (int r = 0; r < 16; ++r) info->rung_counts[r] = h.rung_hist[r];
+  if (c->rungs == 0) info->rung_counts[0] = (int32_t)h.updates;   // one global step
 }
 
 // After a synchronisation: per-system dt_next from the mirrors, the report,
@@ -251,7 +254,8 @@ sph_status copy_out(sph_ctx *c, int g) {
 
 // all = 1 permutes every array of the state (sph_neighbours on its own);
 // steps pass 0 and recompute rho, Omega, P, c_s and the counts in the new
-// order.
+// order (with hierarchical steps rho, Omega and the counts still follow the
+// sort: particles between their steps keep them).
 sph_status run_neighbours(sph_ctx *c, int drift, int all) {
   CK(mark(c, 0));
   CK(launch_reset_status(c, 0));
@@ -289,12 +293,36 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
 }
 
 // Everything one step enqueues, from the dt upload to the status readback.
+// With hierarchical steps: the rungs from the last derivatives, then every
+// substep's drift, sort, solve, force pass and kicks (kernel parameters
+// carry the substep index; the copy-out of sph_step_host follows the last
+// substep).
 sph_status enqueue_step(sph_ctx *c) {
   sph_status s = upload_dt(c);
-  if (s == SPH_OK) s = run_neighbours(c, 1, 0);
-  if (s == SPH_OK) s = run_derivatives(c, 1);
   if (s != SPH_OK) return s;
-  CK(launch_kick(c, 1));
+  const int L = 1 << c->rungs;
+  c->kp.max_rung = c->rungs;
+  c->kp.sub_scale = ldexp(1.0, -c->rungs);
+  if (L > 1) {
+    const cudaError_t e = launch_rung_init(c);
+    if (e != cudaSuccess) s = fail_cuda(c, e, "launch_rung_init");
+  }
+  const sph_state *out = c->host_out;
+  for (int sub = 0; sub < L && s == SPH_OK; ++sub) {
+    c->kp.substep = sub;
+    c->host_out = sub == L - 1 ? out : nullptr;
+    s = run_neighbours(c, 1, 0);
+    if (s == SPH_OK) s = run_derivatives(c, 1);
+    if (s == SPH_OK) {
+      const cudaError_t e = launch_kick(c, 1);
+      if (e != cudaSuccess) s = fail_cuda(c, e, "launch_kick");
+    }
+  }
+  c->kp.substep = 0;
+  c->kp.max_rung = 0;
+  c->kp.sub_scale = 1.0;
+  c->host_out = out;
+  if (s != SPH_OK) return s;
   CK(mark(c, 6));
   s = copy_out(c, 4);
   if (s != SPH_OK) return s;
@@ -450,6 +478,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   if (p->yield_norm != SPH_YIELD_SQRT_J2 && p->yield_norm != SPH_YIELD_SQRT_3J2) return SPH_E_ARG;
   if (p->gradient_form != SPH_GRADIENT_SYMMETRIC && p->gradient_form != SPH_GRADIENT_ONE_SIDED)
     return SPH_E_ARG;
+  if (p->max_rung < 0 || p->max_rung > 15) return SPH_E_ARG;
   if (p->gravity < SPH_GRAVITY_NONE || p->gravity > SPH_GRAVITY_RADIAL) return SPH_E_ARG;
   if (p->gravity == SPH_GRAVITY_RADIAL && n_sys > 1) return SPH_E_ARG;
   if (p->periodic != 0) return SPH_E_ARG;
@@ -596,6 +625,12 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.grad_wj = p->gradient_form == SPH_GRADIENT_ONE_SIDED ? 0.0 : -0.5;
   kp.grad_wi_f = (float)kp.grad_wi;
   kp.grad_wj_f = (float)kp.grad_wj;
+  // hierarchical steps are switched on only while a step is enqueued: every
+  // other call (sph_prime, sph_density, ...) treats all particles alike
+  c->rungs = p->max_rung;
+  kp.max_rung = 0;
+  kp.substep = 0;
+  kp.sub_scale = 1.0;
   kp.gravity = p->gravity;
   for (int a = 0; a < 3; ++a) {
     kp.g_uniform[a] = p->g_uniform[a];
@@ -636,6 +671,11 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   CKI(dalloc(&w.edot2, n));
   CKI(dalloc(&w.yld, n));
   CKI(dalloc(&w.cc, n));
+  if (p->max_rung > 0) {
+    CKI(dalloc(&w.rung, n));
+    CKI(cudaMemset(w.rung, 0, sizeof(int) * (size_t)n));
+  }
+  kp.rung = w.rung;
   if (fp32) {
     CKI(dalloc(&w.pos32, n));
     CKI(dalloc(&w.posh32, n));
@@ -966,6 +1006,13 @@ sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_
   CK(cudaMemcpyAsync(d.mat, host->mat, b4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.flags, host->flags, b4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.id, host->id, b8, cudaMemcpyHostToDevice, c->stream));
+  int64_t in = 25 * (int64_t)b8 + 2 * (int64_t)b4;
+  if (c->rungs > 0) {   // particles between their steps keep H, rho, Omega and their count
+    CK(cudaMemcpyAsync(d.rho, host->rho, b8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.omega, host->omega, b8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.nngb, host->nngb, b4, cudaMemcpyHostToDevice, c->stream));
+    in += 2 * (int64_t)b8 + (int64_t)b4;
+  }
   // out: each array group as soon as the step has finished it, on the copy
   // stream (direct launches: the captured graph has no copy-out)
   c->host_out = host;
@@ -976,7 +1023,7 @@ sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_
   c->host_out = nullptr;
   const cudaError_t e = cudaStreamSynchronize(c->cstream);
   if (e != cudaSuccess) return fail_cuda(c, e, "copy-out");
-  if (bytes_in) *bytes_in = 25 * (int64_t)b8 + 2 * (int64_t)b4;
+  if (bytes_in) *bytes_in = in;
   if (bytes_out) *bytes_out = 29 * (int64_t)b8 + 3 * (int64_t)b4;
   return s;
 }

@@ -30,7 +30,9 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
     const Grid &g = P.sys[sy].grid;
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
-    const double k = (fixed || !predict) ? 0.0 : 0.5 * P.dt[sy];
+    // offset from the half step: dt / 2, or with rungs the time from the
+    // midpoint of the particle's own step to the end of this substep
+    const double k = (fixed || !predict) ? 0.0 : predict_offset(P, i, P.dt[sy] * P.sub_scale);
     w.vp[0][i] = s.vx[i] + k * s.ax[i];
     w.vp[1][i] = s.vy[i] + k * s.ay[i];
     w.vp[2][i] = s.vz[i] + k * s.az[i];
@@ -227,6 +229,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
   const int64_t i = base + lane;
   const bool valid = i < R.end;
+  // with hierarchical steps only particles whose step ends are solved; the
+  // others keep H, rho, Omega and their count
+  const bool solve = valid && rung_active(A.p, i);
   const int64_t ic = valid ? i : base;
   const V4 *pos = PosPtr<T>::get(A.w);
 
@@ -250,13 +255,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   H = fmin(H, Hcap);
   const double xi64 = A.s.x[ic], yi64 = A.s.y[ic], zi64 = A.s.z[ic];
   // Newton state: 0 running, 1 converged, 2 capped, 3 gave up, 4 idle lane
-  int state = valid ? 0 : 4;
+  int state = solve ? 0 : 4;
   double lo = 0.0, hi = INFINITY, H_o = H;
   T rho_o = T(0), om_o = T(1);
   int cnt_o = 0, sweeps_o = 0;
   long long pairs = 0, cand = 0;
 
-  unsigned todo = __ballot_sync(kFull, valid);
+  unsigned todo = __ballot_sync(kFull, solve);
   while (todo) {
     const Group G = next_group(todo, cx, cy, cz, A.p.span_d);
     ++w_groups;
@@ -406,20 +411,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
     if (G.member && state == 0) state = 3;
   }
 
-  if (valid) {
+  if (solve) {
     A.s.h[i] = H_o;
     A.s.rho[i] = from_t(rho_o);
     A.s.omega[i] = from_t(om_o);
     A.s.nngb[i] = cnt_o;
   }
-  w_sw = max(w_sw, valid ? sweeps_o : 0);
-  w_swt += valid ? sweeps_o : 0;
+  w_sw = max(w_sw, solve ? sweeps_o : 0);
+  w_swt += solve ? sweeps_o : 0;
   w_nu += state == 3;
   w_ncap += state == 2;
-  w_bad |= (valid && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0))) ? 1u
-                                                                                           : 0u;
+  w_bad |= (solve && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0))) ? 1u
+                                                                                         : 0u;
   {
-    const double hb = wmax(valid ? H_o : 0.0);
+    // every particle's radius bounds the force pass's search, solved or not
+    const double hb = wmax(valid ? (solve ? H_o : A.s.h[i]) : 0.0);
     if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, enc_d(hb));
   }
   w_pairs += pairs;

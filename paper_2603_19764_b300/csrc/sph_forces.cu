@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   const SysRec &R = A.p.sys[sy];
   const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
   const int64_t i = base + lane;
-  const bool valid = i < R.end;
+  // with hierarchical steps only particles whose step ends get derivatives
+  const bool valid = i < R.end && rung_active(A.p, i);
   const int64_t ic = valid ? i : base;
   const V4 *posh = PK::posh(A.w);
   const V4 *rec = PK::rec(A.w);   // 4 consecutive vectors per particle

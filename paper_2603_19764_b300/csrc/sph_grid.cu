@@ -10,8 +10,12 @@
 namespace sphk {
 
 // ---------------------------------------------------------------- status
-__global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full) {
-  if (threadIdx.x == 0) {
+// counters = 0 (substeps after the first of a big step): the work counters
+// keep adding up; the per-system boxes and extrema always restart.
+__global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full, int counters) {
+  if (threadIdx.x < 16 && counters) st->rung_hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0 && counters) {
+    st->updates = 0;
     st->max_sweeps = 0;
     st->n_unconv = 0;
     st->n_capped = 0;
@@ -24,8 +28,8 @@ __global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full) {
     st->groups_force = 0;
     st->sweeps_total = 0;
     st->n_expanded = 0;
-    if (full) st->err = 0;
   }
+  if (threadIdx.x == 0 && full) st->err = 0;
   for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
     SysRec &r = sys[k];
     for (int a = 0; a < 3; ++a) {
@@ -39,7 +43,8 @@ __global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full) {
 }
 
 cudaError_t launch_reset_status(sph_ctx *c, int full) {
-  k_reset_status<<<1, 256, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, full);
+  k_reset_status<<<1, 256, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, full,
+                                           c->kp.substep == 0);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
     double p[3] = {s.x[i], s.y[i], s.z[i]};
     if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
-      const double dt = P.dt[sy];
+      const double dt = P.dt[sy] * P.sub_scale;   // the substep (the step without rungs)
       p[0] += dt * s.vx[i];
       p[1] += dt * s.vy[i];
       p[2] += dt * s.vz[i];
@@ -382,10 +387,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *
 // Every array of sph_state is gathered through the sort permutation into a
 // scratch block and copied back, so the caller's arrays end up in cell order.
 // Within a step the arrays that the step itself recomputes before reading
-// them (rho, Omega, P, c_s and the neighbour count) are left out: their
-// values are overwritten in the new order.
+// them are left out: their values are overwritten in the new order.
 constexpr int kNF64 = 29;   // 28 double arrays + id
-constexpr int kNI32 = 3;
+constexpr int kNI32 = 4;   // mat, flags, count; the rungs of hierarchical steps
 constexpr int kNLearn = 5;  // learned form: H_prev, H proposal, three feature pairs
 
 struct PermTable {
@@ -395,7 +399,8 @@ struct PermTable {
   int ni32;   // 4-byte fields in use
 };
 
-static PermTable perm_table(const sph_state &s, const LearnArgs &L, bool all) {
+static PermTable perm_table(const sph_state &s, const Work &w, const LearnArgs &L, bool all,
+                            bool rungs) {
   PermTable t;
   t.nf64 = 0;
   double *d[24] = {s.x,   s.y,    s.z,    s.vx,   s.vy,   s.vz,   s.u,    s.m,
@@ -406,11 +411,19 @@ static PermTable perm_table(const sph_state &s, const LearnArgs &L, bool all) {
   t.ni32 = 0;
   t.i32[t.ni32++] = (unsigned *)s.mat;
   t.i32[t.ni32++] = (unsigned *)s.flags;
-  if (all) {
-    double *r[4] = {s.rho, s.omega, s.pres, s.cs};
-    for (int k = 0; k < 4; ++k) t.f64[t.nf64++] = (unsigned long long *)r[k];
+  // rho, Omega and the counts are recomputed in a step only for the
+  // particles that are solved: with hierarchical steps they must follow
+  // the sort (solved or not), P and c_s are always recomputed
+  if (all || rungs) {
+    t.f64[t.nf64++] = (unsigned long long *)s.rho;
+    t.f64[t.nf64++] = (unsigned long long *)s.omega;
     t.i32[t.ni32++] = (unsigned *)s.nngb;
   }
+  if (all) {
+    t.f64[t.nf64++] = (unsigned long long *)s.pres;
+    t.f64[t.nf64++] = (unsigned long long *)s.cs;
+  }
+  if (w.rung) t.i32[t.ni32++] = (unsigned *)w.rung;   // hierarchical steps
   // the learned form's per-particle arrays follow their particles
   if (L.hprev) {
     t.f64[t.nf64++] = (unsigned long long *)L.hprev;
@@ -498,7 +511,7 @@ cudaError_t launch_sort_permute(sph_ctx *c, int all) {
     vb = tv;
   }
   // after four passes the sorted pairs are back in keys / vals
-  PermTable t = perm_table(c->st, c->learn, all != 0);
+  PermTable t = perm_table(c->st, c->w, c->learn, all != 0, c->kp.max_rung > 0);
   unsigned long long *tmp = (unsigned long long *)c->tmp;
   k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);

@@ -72,7 +72,11 @@ struct Status {
   unsigned next_bucket[2];                      // persistent-warp work counters
   int total_cells;                              // cells of all systems this step
   int pad2_;
+  unsigned long long updates;                   // particles kicked in the step
+  int rung_hist[16];                            // rungs of the moving particles at its end
 };
+
+
 
 // Material parameters in the arithmetic type of a form, with the derived
 // constants the evaluations need; the FP32 copies are made once on the host
@@ -118,7 +122,37 @@ struct KParams {
   double grad_wi, grad_wj;
   float grad_wi_f, grad_wj_f;
   const double *h_guess;       // starting radius of the solve (sorted order), or null
+  // hierarchical steps: dt[] holds each system's big step; this launch
+  // belongs to substep `substep` of 2^max_rung, of length dt * sub_scale
+  int max_rung, substep;
+  double sub_scale;            // 2^-max_rung (exact)
+  const int *rung;             // per particle (sorted order), or null
 };
+
+// Hierarchical steps: a particle on rung r steps 2^(R - r) substeps and is
+// active (solved, given derivatives, kicked) at the end of each of them.
+__device__ __forceinline__ int rung_len(const KParams &P, int64_t i) {
+  return P.max_rung == 0 ? 1 : 1 << (P.max_rung - P.rung[i]);
+}
+__device__ __forceinline__ bool rung_active(const KParams &P, int64_t i) {
+  return P.max_rung == 0 || ((P.substep + 1) & (rung_len(P, i) - 1)) == 0;
+}
+// Half-step offset of the predictor at the end of the current substep:
+// q(t) = q_half + k dq with k = t - t_mid of the particle's current step
+// (dt / 2 of its own step when the step ends there; dt / 2 without rungs).
+__device__ __forceinline__ double predict_offset(const KParams &P, int64_t i, double sub_dt) {
+  if (P.max_rung == 0) return 0.5 * sub_dt;
+  const int len = rung_len(P, i);
+  const int start = P.substep & ~(len - 1);
+  return ((double)(P.substep + 1 - start) - 0.5 * (double)len) * sub_dt;
+}
+// The rung a particle's criteria ask for: the smallest r with
+// big_dt / 2^r <= crit, at most R (big_dt / 2^r = sub_dt 2^(R - r) exactly).
+__device__ __forceinline__ int rung_want(const KParams &P, double sub_dt, double crit) {
+  int r = 0;
+  while (r < P.max_rung && sub_dt * (double)(1 << (P.max_rung - r)) > crit) ++r;
+  return r;
+}
 
 // A run-time constant in the pair loops' arithmetic type.
 template <typename T> __device__ __forceinline__ T pconst(double d, float f);
@@ -195,6 +229,7 @@ struct Work {
   float4 *fs32[3];              // own stress, shear modulus, c_L, external g
   double4_32a *fs64[3];
   float *divv;                  // tr of the corrected velocity gradient (learned form)
+  int *rung;                    // hierarchical steps: rung of every particle, or null
 };
 
 // Arrays of the learned form. hprev, hprop and feat are per-particle
@@ -491,6 +526,7 @@ struct sph_ctx {
   // sph_step_host: each group of state arrays is copied back on cstream as
   // soon as the step has finished writing it (host_out != null only then)
   const sph_state *host_out;
+  int rungs;                    // sph_params.max_rung
   cudaStream_t cstream;
   cudaEvent_t out_ev[5];
   cudaGraphExec_t graph_exec;   // captured step
@@ -537,6 +573,7 @@ cudaError_t launch_eos_pack(sph_ctx *c);
 cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_kick(sph_ctx *c, int kick);
 cudaError_t launch_reset_status(sph_ctx *c, int full);
+cudaError_t launch_rung_init(sph_ctx *c);
 cudaError_t launch_learn(sph_ctx *c);
 cudaError_t alloc_density_spill(sph_ctx *c);
 }  // namespace sphk

@@ -16,15 +16,21 @@ constexpr int kNSum = 9;
 // that every system's sums are formed in a fixed order of its own.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, KParams P,
-                                                double *partials) {
+                                                double *partials, Status *st) {
   __shared__ double red[kNSum][kBlock];
   __shared__ double redt[kBlock / 32];
+  __shared__ int hist[16];
+  if (threadIdx.x < 16) hist[threadIdx.x] = 0;
+  __syncthreads();
   const int b = blockIdx.x;
   const int sy = P.nsys > 1 ? sys_lookup(P.sys_chunk, P.nsys, b) : 0;
   SysRec &R = P.sys[sy];
   const int64_t c0 = R.begin + (int64_t)(b - R.chunk_off) * kChunk;
   const int64_t c1 = c0 + kChunk < R.end ? c0 + kChunk : R.end;
-  const double dt = kick ? P.dt[sy] : 0.0, hdt = 0.5 * dt;
+  // the substep; without rungs the step (sub_scale = 1)
+  const double sub = kick ? P.dt[sy] * P.sub_scale : 0.0;
+  const bool last = P.substep + 1 == (1 << P.max_rung);   // every particle's step ends
+  int updates = 0;
   double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T tmin = T(INFINITY);
   const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
@@ -34,7 +40,9 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
     double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
     double u = s.u[i];
-    if (kick && !fixed) {
+    // kicked: moving particles whose own step ends with this substep
+    if (kick && !fixed && rung_active(P, i)) {
+      const double dt = sub * (double)rung_len(P, i), hdt = 0.5 * dt;
       const MatT<T> &M = mat_t<T>(P, s.mat[i]);
       const double dS[5] = {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]};
       double S[5] = {s.sxx[i], s.syy[i], s.sxy[i], s.sxz[i], s.syz[i]};
@@ -55,16 +63,33 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
         S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
       }
       s.eps_ii[i] += dt * w.edot2[i];
-      // opening kick from the state at i
-      s.vx[i] = v[0] + hdt * a[0];
-      s.vy[i] = v[1] + hdt * a[1];
-      s.vz[i] = v[2] + hdt * a[2];
-      s.u[i] = u + hdt * s.dudt[i];
-      s.sxx[i] = S[0] + hdt * dS[0];
-      s.syy[i] = S[1] + hdt * dS[1];
-      s.sxy[i] = S[2] + hdt * dS[2];
-      s.sxz[i] = S[3] + hdt * dS[3];
-      s.syz[i] = S[4] + hdt * dS[4];
+      // opening kick from the state at i; with rungs over the next step of
+      // the rung the criteria ask for, no coarser than the coarsest rung
+      // whose steps start at the next substep
+      double ho = hdt;
+      if (P.max_rung) {
+        const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        const double h = s.h[i];
+        const double ta = am > 0.0 ? P.eta_a * sqrt(h / am) : INFINITY;
+        const double tc = P.eta_c * h / w.vsig[i];
+        int r = rung_want(P, sub, ta < tc ? ta : tc);
+        int r_al = P.max_rung;
+        for (int m = P.substep + 1; r_al > 0 && (m & 1) == 0; m >>= 1) --r_al;
+        r = r > r_al ? r : r_al;
+        w.rung[i] = r;
+        ho = 0.5 * sub * (double)(1 << (P.max_rung - r));
+        if (last) atomicAdd(&hist[r], 1);
+      }
+      ++updates;
+      s.vx[i] = v[0] + ho * a[0];
+      s.vy[i] = v[1] + ho * a[1];
+      s.vz[i] = v[2] + ho * a[2];
+      s.u[i] = u + ho * s.dudt[i];
+      s.sxx[i] = S[0] + ho * dS[0];
+      s.syy[i] = S[1] + ho * dS[1];
+      s.sxy[i] = S[2] + ho * dS[2];
+      s.sxz[i] = S[3] + ho * dS[3];
+      s.syz[i] = S[4] + ho * dS[4];
     }
     const double x = s.x[i], y = s.y[i], z = s.z[i];
     T g[3], phi;
@@ -106,6 +131,9 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     t = wsum(t);
     if (lane == 0) partials[blockIdx.x * kNSum + k] = k == 0 ? 0.5 * t : t;
   }
+  const int wu = wsum(updates);
+  if (lane == 0 && wu) atomicAdd(&st->updates, (unsigned long long)wu);
+  if (threadIdx.x < 16 && hist[threadIdx.x]) atomicAdd(&st->rung_hist[threadIdx.x], hist[threadIdx.x]);
   if (threadIdx.x == 0) {
     double t = INFINITY;
     for (int q = 0; q < kBlock / 32; ++q) t = fmin(t, redt[q]);
@@ -134,11 +162,40 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *partials,
   }
 }
 
+// Hierarchical steps: at the start of a big step every moving particle
+// takes the rung its criteria ask for (from the last derivatives; every
+// particle is at the same time, so any rung is aligned).
+__global__ void __launch_bounds__(kBlock) k_rung_init(sph_state s, Work w, int64_t n, KParams P) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (s.flags[i] & SPH_FLAG_FIXED) {
+      w.rung[i] = 0;
+      continue;
+    }
+    const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
+    const double am = sqrt(s.ax[i] * s.ax[i] + s.ay[i] * s.ay[i] + s.az[i] * s.az[i]);
+    const double h = s.h[i];
+    const double ta = am > 0.0 ? P.eta_a * sqrt(h / am) : INFINITY;
+    const double tc = P.eta_c * h / w.vsig[i];
+    w.rung[i] = rung_want(P, P.dt[sy] * P.sub_scale, ta < tc ? ta : tc);
+  }
+}
+
+cudaError_t launch_rung_init(sph_ctx *c) {
+  int64_t b = (c->n + kBlock - 1) / kBlock;
+  if (b > 148 * 16) b = 148 * 16;
+  k_rung_init<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kick(sph_ctx *c, int kick) {
   if (c->kp.precision == SPH_FP32K)
-    k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials);
+    k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials,
+                                                         c->d_status);
   else
-    k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials);
+    k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials,
+                                                          c->d_status);
   k_reduce_final<<<c->nsys, kBlock, 0, c->stream>>>(c->partials, c->kp);
   c->nlaunch += 2;
   return cudaGetLastError();

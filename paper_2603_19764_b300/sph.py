@@ -70,7 +70,7 @@ class SphParams(C.Structure):
                 ("g_n", C.c_int32), ("g_rmin", C.c_double), ("g_rmax", C.c_double),
                 ("g_center", C.c_double * 3), ("g_gm", C.c_double), ("periodic", C.c_int32),
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
-                ("gradient_form", C.c_int32)]
+                ("gradient_form", C.c_int32), ("max_rung", C.c_int32)]
 
 
 class SphStepInfo(C.Structure):
@@ -82,7 +82,8 @@ class SphStepInfo(C.Structure):
                 ("device_flags", C.c_uint32), ("cand_density", C.c_int64),
                 ("cand_force", C.c_int64), ("groups_density", C.c_int64),
                 ("groups_force", C.c_int64), ("kernel_launches", C.c_int32),
-                ("sweeps_total", C.c_int64), ("n_expanded", C.c_int32)]
+                ("sweeps_total", C.c_int64), ("n_expanded", C.c_int32),
+                ("particle_updates", C.c_int64), ("rung_counts", C.c_int32 * 16)]
 
     def as_dict(self) -> dict:
         return dict(dt=self.dt, dt_next=self.dt_next, e_kin=self.e_kin, e_int=self.e_int,
@@ -93,7 +94,8 @@ class SphStepInfo(C.Structure):
                     cand_density=self.cand_density, cand_force=self.cand_force,
                     groups_density=self.groups_density, groups_force=self.groups_force,
                     kernel_launches=self.kernel_launches, sweeps_total=self.sweeps_total,
-                    n_expanded=self.n_expanded)
+                    n_expanded=self.n_expanded, particle_updates=self.particle_updates,
+                    rung_counts=tuple(self.rung_counts))
 
 
 class SphTuneReport(C.Structure):
@@ -234,8 +236,8 @@ def make_params(d: dict, keep: list) -> SphParams:
             continue
         if name in ("g_uniform", "g_center", "box_lo", "box_hi"):
             getattr(p, name)[:] = tuple(float(v) for v in d[name])
-        elif name == "gradient_form":
-            p.gradient_form = int(d.get(name, 0))
+        elif name in ("gradient_form", "max_rung"):
+            setattr(p, name, int(d.get(name, 0)))
         else:
             setattr(p, name, d[name])
     if d.get("g_table") is not None:

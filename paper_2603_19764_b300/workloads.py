@@ -101,7 +101,7 @@ def default_params(precision: int = 0) -> dict:
     return dict(n_ngb=64, av_alpha=1.0, av_beta=2.0, av_eps=0.01, eta_c=0.3, eta_a=0.3,
                 h_tol=1e-10 if precision == 0 else 1e-6, max_sweeps=32, h_cap_factor=4.0,
                 precision=precision, jaumann=0, yield_norm=0, correction_tensor=1,
-                gradient_form=0,
+                gradient_form=0, max_rung=0,
                 gravity=0, g_uniform=(0.0, 0.0, 0.0), g_table=None, phi_table=None,
                 g_rmin=1.0, g_rmax=2.0, g_center=(0.0, 0.0, 0.0), g_gm=0.0,
                 periodic=0, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0))

@@ -56,7 +56,9 @@ int main(void) {
   O(sph_params, g_table) O(sph_params, g_n) O(sph_params, box_hi) O(sph_params, precision)
   O(sph_params, gradient_form)
   O(sph_step_info, pairs_density) O(sph_step_info, device_flags) O(sph_step_info, sweeps)
-  O(sph_step_info, kernel_launches) O(sph_step_info, n_expanded) O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
+  O(sph_step_info, kernel_launches) O(sph_step_info, n_expanded)
+  O(sph_step_info, particle_updates) O(sph_step_info, rung_counts) O(sph_params, max_rung)
+  O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
   O(sph_peak_report, sm_mhz) O(sph_peak_report, n_sm)
   return 0;
 }
@@ -138,9 +140,10 @@ def test_batch_init_rejects_bad_system_bounds_without_touching_the_gpu(libsph):
     assert call([0] * 1026, nsys=sph.SPH_MAX_SYSTEMS + 1) == sph.SPH_E_ARG
     assert f(C.byref(ctx), C.byref(p), mats, 1, C.byref(st), n, 2, None, None) == sph.SPH_E_ARG
     assert ctx.value is None
-    # an unknown gradient form is refused before any CUDA call as well
-    for bad in (2, -1):
-        q = sph.make_params(dict(w.params, precision=0, gradient_form=bad), keep)
+    # an unknown gradient form or rung limit is refused before any CUDA call
+    for bad in (dict(gradient_form=2), dict(gradient_form=-1), dict(max_rung=16),
+                dict(max_rung=-1)):
+        q = sph.make_params(dict(w.params, precision=0, **bad), keep)
         b = (C.c_int64 * 2)(0, n)
         assert f(C.byref(ctx), C.byref(q), mats, 1, C.byref(st), n, 1, b, None) == sph.SPH_E_ARG
     assert ctx.value is None
