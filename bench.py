@@ -809,6 +809,70 @@ def run_drift(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_rungs(args, rank: int, world: int, local_rank: int):
+    """Hierarchical individual steps against one global step, on the impact
+    (FP32 form, graphs): both advance the same physical time, the global
+    run with dt = dt_next (Eq. 38-39, the smallest criterion), the rung run
+    with big steps of 2^R dt_next, so the particles that need it still step
+    dt_next and the rest take 2x to 2^R x longer steps."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2603_19764_b300 import build, sph
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.scale, 1)
+    R = args.max_rung
+    arms = {}
+    t_target = None
+    for name, mr in (("global", 0), ("rungs", R)):
+        p = dict(w.params, precision=1, h_tol=1e-6, max_rung=mr)
+        sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
+        info = sim.prime()
+        e0 = info["e_kin"] + info["e_int"] + info["e_pot"]
+        sim.set_spans(1, 2)
+        sim.set_graph(True)
+        for _ in range(args.warmup):
+            info = sim.step((2 ** mr) * info["dt_next"])
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_sim, calls, updates, hist = 0.0, 0, 0, np.zeros(16, np.int64)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        while True:
+            dt = (2 ** mr) * info["dt_next"]
+            info = sim.step(dt)
+            t_sim += dt
+            calls += 1
+            updates += info["particle_updates"]
+            hist += np.array(info["rung_counts"])
+            if (t_target is None and calls >= args.steps) or (t_target is not None and t_sim >= t_target):
+                break
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1)
+        wall = time.perf_counter() - t0
+        if t_target is None:
+            t_target = t_sim
+        e1 = info["e_kin"] + info["e_int"] + info["e_pot"]
+        arms[name] = {"calls": calls, "simulated_s": t_sim, "device_ms": ms, "wall_s": wall,
+                      "simulated_per_device_s": t_sim / (ms / 1e3),
+                      "particle_updates_per_s": updates / (ms / 1e3),
+                      "updates_per_particle_per_sim_s": updates / w.n / t_sim,
+                      "rung_share": (hist / max(1, hist.sum())).round(4).tolist()[:max(1, mr + 1)],
+                      "dE_over_Ekin0": (e1 - e0) / info["e_kin"]}
+        sim.close()
+    g, r = arms["global"], arms["rungs"]
+    line = {"mode": "rungs", "workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg",
+            "particles": w.n, "max_rung": R, "form": "fp32k, graph",
+            "arms": arms,
+            "speedup_simulated_time": r["simulated_per_device_s"] / g["simulated_per_device_s"],
+            "note": "same physical time; the rung run's big step is 2^R dt_next"}
+    print(json.dumps(line), flush=True)
+
+
 def _by_id(g: dict, keys) -> dict:
     order = np.argsort(g["id"], kind="stable")
     return {k: g[k][order] for k in keys}
@@ -832,7 +896,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--spans", default="", help="density,forces group spans (no tuning)")
     ap.add_argument("--plain-steps", type=int, default=3)
-    ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned", "drift"])
+    ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned", "drift", "rungs"])
+    ap.add_argument("--max-rung", type=int, default=3)
     ap.add_argument("--drift-steps", type=int, default=100)
     ap.add_argument("--spot-every", type=int, default=5)
     ap.add_argument("--spot", type=int, default=10_000)
@@ -862,6 +927,8 @@ def main():
             run_learned(args, rank, world, local_rank)
         elif args.workload == "drift":
             run_drift(args, rank, world, local_rank)
+        elif args.workload == "rungs":
+            run_rungs(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:
