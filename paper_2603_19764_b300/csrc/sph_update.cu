@@ -35,6 +35,9 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
   T tmin = T(INFINITY);
   const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
   for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    // hierarchical steps: before the last substep only the kicked particles
+    // matter (the sums and the time step are those of the big step's end)
+    if (!last && !rung_active(P, i)) continue;
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
     const double m = s.m[i];
     const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
