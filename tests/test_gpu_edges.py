@@ -12,15 +12,16 @@
 * a batch of many tiny systems (1 to 40 particles each, far apart).
 
 Tolerances as in the parity suite: counts bit-exact given the GPU's H;
-density 1e-6 (FP64) / 1e-5 (FP32) relative; derivatives 1e-9 / 1e-4 of
-the field's max norm."""
+density 1e-6 (FP64) / 1e-5 (FP32) relative at the GPU's H, and against the
+oracle's own solve within the window its stopping rule leaves; derivatives
+1e-9 / 1e-4 of the field's max norm."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2603_19764_b300 import build, sph
 from paper_2603_19764_b300 import workloads as wl
-from tests.conftest import cloud
+from tests.conftest import check_density_solve, cloud
 
 pytestmark = pytest.mark.gpu
 
@@ -43,10 +44,8 @@ def _maxnorm_err(a, b):
     return np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0)
 
 
-def _compare(g, ref, p, arrays, precision):
-    cnt = oracle.count_neighbours(p, dict(arrays, h=g["h"]))
-    assert np.array_equal(cnt, g["nngb"])
-    assert np.max(np.abs(g["rho"] / ref["rho"] - 1)) < RHO_TOL[precision]
+def _compare(g, ref, p, mats, arrays, precision):
+    check_density_solve(g, ref, p, mats, arrays, RHO_TOL[precision])
     for f in DERIVS:
         e = _maxnorm_err(g[f], ref[f])
         assert e < DERIV_TOL[precision], (f, e)
@@ -61,7 +60,7 @@ def _prime_check(arrays, mats, params, precision):
     ref, rinfo = oracle.derivatives(p, mats, arrays)
     assert info["n_capped"] == rinfo["n_capped"]
     assert info["n_cfallback"] == rinfo["n_cfallback"]
-    _compare(g, ref, p, arrays, precision)
+    _compare(g, ref, p, mats, arrays, precision)
     assert info["dt_next"] == pytest.approx(rinfo["dt_next"], rel=1e-6 if precision == 0 else 1e-4)
     return g, info
 
@@ -177,7 +176,7 @@ def test_batch_of_many_tiny_systems(precision):
         a["id"] = np.arange(nk, dtype=np.int64)
         ref, rinfo = oracle.derivatives(p, mats, a)
         gk = {f: v[sl] for f, v in g.items()}
-        _compare(gk, ref, p, dict(a), precision)
+        _compare(gk, ref, p, mats, dict(a), precision)
         capped += rinfo["n_capped"]
         # per-system reports carry the system's own time step and sums
         assert infos[k]["dt_next"] == pytest.approx(rinfo["dt_next"],
