@@ -149,7 +149,7 @@ template <typename T, bool REL>
 __device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, const int *Li,
                                              unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
-                                             T gb, double H2c, double xi64, double yi64, double zi64,
+                                             T gb, T H, double xi64, double yi64, double zi64,
                                              const sph_state &s, int self, T &rs, T &rhs,
                                              T &rhs2, int &cnt) {
   // every lane advances through its own words: lanes do not wait for each
@@ -175,7 +175,9 @@ __device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, 
         in = r2 < H2;
         if (fabs(r2 - H2) < gb) {
           const int j = Li[k];
-          in = r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]) < H2c;
+          // the square of an FP32 radius is exact in FP64
+          in = r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]) <
+               __dmul_rn((double)H, (double)H);
         }
       } else {
         r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
@@ -244,19 +246,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const sph_material &M = A.p.mats[A.s.mat[ic] & (SPH_MAX_MATERIALS - 1)];
   const T target = (T)A.p.n_ngb * mi;
   const T tol = pconst<T>(A.p.h_tol, A.p.h_tol_f);
-  const double Hcap =
-      A.p.h_cap_factor * (double)cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
+  // the Newton state is kept in T: the FP32 form's radius carries 24 bits,
+  // far below h_tol, and its FP64 predicate uses the exact square of it
+  const T Hcap =
+      (T)A.p.h_cap_factor * cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
   // starting radius: the previous H, or the proposal of the learned form
-  double H = A.s.h[ic];
+  T H = (T)A.s.h[ic];
   if (A.p.h_guess) {
     const double hg = A.p.h_guess[ic];
-    if (hg > 0.0) H = hg;
+    if (hg > 0.0) H = (T)hg;
   }
-  H = fmin(H, Hcap);
+  H = tmin(H, Hcap);
   const double xi64 = A.s.x[ic], yi64 = A.s.y[ic], zi64 = A.s.z[ic];
   // Newton state: 0 running, 1 converged, 2 capped, 3 gave up, 4 idle lane
   int state = solve ? 0 : 4;
-  double lo = 0.0, hi = INFINITY, H_o = H;
+  T lo = T(0), hi = T(INFINITY), H_o = H;
   T rho_o = T(0), om_o = T(1);
   int cnt_o = 0, sweeps_o = 0;
   long long pairs = 0, cand = 0;
@@ -275,10 +279,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
     for (int sweep = 1; sweep <= A.p.max_sweeps; ++sweep) {
       const bool act = G.member && state == 0;
       if (!__any_sync(kFull, act)) break;
-      const T Ht = (T)H;
+      const T Ht = H;
       const T invHt = T(1) / Ht;
-      const double H2c = __dmul_rn(H, H);
-      const T H2 = REL ? Ht * Ht : (T)H2c;
+      const T H2 = REL ? Ht * Ht : (T)__dmul_rn((double)Ht, (double)Ht);
       const T gb = guard_band(Ht, Lt);
       // smallest mask radius: Hq^2 > H^2 + gb, so that no pair with r < H
       // by the FP64 predicate falls outside the mask or the list
@@ -331,9 +334,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           build_masks<T>(Sv.p, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
           __syncwarp();
           if (act) {
-            density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
+            density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64, yi64,
                                      zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-            density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
+            density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                      yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
           }
           __syncwarp();
@@ -353,9 +356,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           Hm = Hn;
         }
         if (act) {
-          density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64, yi64,
+          density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64, yi64,
                                    zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-          density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, H2c, xi64,
+          density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                    yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
         }
       }
@@ -384,21 +387,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           if (gq < T(0)) lo = H;
           else hi = H;
           const T gp = T(4.0 * kPi) * Ht * Ht * rho * om / target;
-          double Hn = gp > T(0) ? H - (double)(gq / gp) : (gq < T(0) ? 1.25 * H : 0.75 * H);
-          if (!(Hn >= 0.75 * H)) Hn = 0.75 * H;
-          if (!(Hn <= 1.25 * H)) Hn = 1.25 * H;
-          if (hi < INFINITY && (Hn <= lo || Hn >= hi)) Hn = 0.5 * (lo + hi);
+          T Hn = gp > T(0) ? H - gq / gp : (gq < T(0) ? T(1.25) * H : T(0.75) * H);
+          if (!(Hn >= T(0.75) * H)) Hn = T(0.75) * H;
+          if (!(Hn <= T(1.25) * H)) Hn = T(1.25) * H;
+          if (hi < T(INFINITY) && (Hn <= lo || Hn >= hi)) Hn = T(0.5) * (lo + hi);
           if (Hn > Hcap) Hn = Hcap;
-          if (REL && A.expand && fabs(Hn - H) <= kExpand * H) {
+          if (REL && A.expand && fabs(Hn - H) <= T(kExpand) * H) {
             // rho, d rho / dH at Hn from the second-order expansion about H
-            const T d = (T)(Hn - H);
+            const T d = Hn - H;
             const T rho2 = T(cW) * ih3 * ih * ih * rhs2;
             const T r1 = rho + d * (rhoH + T(0.5) * rho2 * d);
-            const T H1 = (T)Hn;
+            const T H1 = Hn;
             const T gq1 = T(4.0 * kPi / 3.0) * H1 * H1 * H1 * r1 / target - T(1);
-            if (fabs(gq1) <= tol && r1 > T(0)) {
+            const T om1 = T(1) + H1 / (T(3) * r1) * (rhoH + rho2 * d);
+            // the estimate's error in d rho / dH reaches Omega scaled by
+            // |1 - Omega| / Omega, and the forces carry 1 / Omega: a
+            // particle with few neighbours (small Omega) is closed only on
+            // an exact sum
+            if (fabs(gq1) <= tol && r1 > T(0) && om1 >= T(0.5)) {
               rho_o = r1;
-              om_o = T(1) + H1 / (T(3) * r1) * (rhoH + rho2 * d);
+              om_o = om1;
               H_o = Hn;
               state = 1;
               ++w_exp;
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   }
 
   if (solve) {
-    A.s.h[i] = H_o;
+    A.s.h[i] = (double)H_o;
     A.s.rho[i] = from_t(rho_o);
     A.s.omega[i] = from_t(om_o);
     A.s.nngb[i] = cnt_o;
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
                                                                                          : 0u;
   {
     // every particle's radius bounds the force pass's search, solved or not
-    const double hb = wmax(valid ? (solve ? H_o : A.s.h[i]) : 0.0);
+    const double hb = wmax(valid ? (solve ? (double)H_o : A.s.h[i]) : 0.0);
     if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, enc_d(hb));
   }
   w_pairs += pairs;

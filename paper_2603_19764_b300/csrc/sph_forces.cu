@@ -267,22 +267,49 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
         Lm[wd][lane] = act ? mk : 0u;
       }
       __syncwarp();
-      // each lane walks its own neighbours, independently of the others
+      // each lane walks its own neighbours, independently of the others.
+      // FP32 form: the next neighbour's 64-byte record is loaded one pair
+      // ahead, so that its latency overlaps the current pair's arithmetic
+      // (the FP64 record would take 32 more registers and spill)
+      constexpr bool PF = REL;
       int wd = 0;
       unsigned mk = nw > 0 ? Lm[0][lane] : 0u;
-      for (;;) {
-        while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
-        if (mk == 0u) break;
+      while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
+      bool more = mk != 0u;
+      int kn = 0, jn = 0;
+      V4 g0, g1, g2, g3;   // the prefetched record, in two 32-byte loads
+      if (more) {
+        kn = (wd << 5) + __ffs(mk) - 1;
+        mk &= mk - 1u;
+        jn = Li[kn];
+        if (PF) {
+          V::ld2(rec + 4 * jn, g0, g1);
+          V::ld2(rec + 4 * jn + 2, g2, g3);
+        }
+      }
+      while (more) {
         {
-          const int k = (wd << 5) + __ffs(mk) - 1;
-          mk &= mk - 1u;
-          const int j = Li[k];
+          const int k = kn, j = jn;
+          V4 f0, f1, f2, f3;
+          if (PF) {
+            f0 = g0; f1 = g1; f2 = g2; f3 = g3;
+          } else {
+            V::ld2(rec + 4 * j, f0, f1);
+            V::ld2(rec + 4 * j + 2, f2, f3);
+          }
+          while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
+          more = mk != 0u;
+          if (more) {
+            kn = (wd << 5) + __ffs(mk) - 1;
+            mk &= mk - 1u;
+            jn = Li[kn];
+            if (PF) {
+              V::ld2(rec + 4 * jn, g0, g1);
+              V::ld2(rec + 4 * jn + 2, g2, g3);
+            }
+          }
           T qx, qy, qz, qw;   // qw = H_j^2
           CandAoS<V4>::get(Lr, k, qx, qy, qz, qw);
-          const V4 *rj = rec + 4 * j;
-          V4 f0, f1, f2, f3;   // the 64-byte record in two 32-byte loads
-          V::ld2(rj, f0, f1);
-          V::ld2(rj + 2, f2, f3);
           const T dx = xi - qx, dy = yi - qy, dz = zi - qz;
           const T r2 = dx * dx + dy * dy + dz * dz;
           {
