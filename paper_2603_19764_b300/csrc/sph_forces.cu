@@ -353,9 +353,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           az += mWi * yiz + Wj * yjz;
           T dsum = -mWi * (vx * yix + vy * yiy + vz * yiz);
           const T vr = vx * dx + vy * dy + vz * dz;
-          if (vr < T(0) && inR) {  // Eq. 5-8
+          // Eq. 5-8 for approaching pairs. FP32 form: evaluated for every pair
+          // with mu = 0 for the others (cheaper than the divergent branch);
+          // FP64 form: branched, its divides being costly
+          const bool av = vr < T(0) && inR;
+          if (REL || av) {
             const T hb = T(0.5) * (Hi + f3.w);
-            const T mu = quot(hb * vr, r2 + ep * hb * hb);
+            const T mu0 = quot(hb * vr, r2 + ep * hb * hb);
+            const T mu = av ? mu0 : T(0);
             const T Pi = quot((be * mu - al * T(0.5) * (ci + f2.w)) * mu, T(0.5) * (rhoi + f3.x));
             const T t = T(0.5) * mj * Pi * (Wi + Wj);
             ax -= t * dx;
