@@ -13,9 +13,10 @@
 //
 // FP64 form: absolute positions, canonical predicate r^2 = (dx dx + dy dy) +
 // dz dz without fused multiply-add. FP32 form: positions relative to the
-// group's reference cell, FP32 sums and Newton arithmetic (H itself is kept
-// in FP64); pairs with |r^2 - H^2| inside the guard band (sph_pair.cuh) are
-// re-decided with the FP64 predicate so that neighbour counts stay exact.
+// group's reference cell, FP32 sums and Newton arithmetic, the radius
+// included (stored as FP64); pairs with |r^2 - H^2| inside the guard band
+// (sph_pair.cuh) are re-decided with the FP64 predicate against the exact
+// square of that radius, so that neighbour counts stay exact.
 #include "sph_pair.cuh"
 
 namespace sphk {
