@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   while (todo) {
     const Group G = next_group(todo, cx, cy, cz, A.p.span_d);
     ++w_groups;
-    const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
-    const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
-    const T zi = REL ? p.z + (T)(cz - G.rz) * Lt : p.z;
+    const T xi = REL ? rel_coord(p.x, cx - G.rx, Lt) : p.x;
+    const T yi = REL ? rel_coord(p.y, cy - G.ry, Lt) : p.y;
+    const T zi = REL ? rel_coord(p.z, cz - G.rz, Lt) : p.z;
     bool complete = false;   // the list holds every particle within Rl of the box
     T Rl = T(0), Hm = T(0);  // list radius; this lane's mask radius
     int nl = 0;
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
                                       ok, ox, oy, oz))
               break;
             const V4 q = ok ? V::ld(pos, j) : V::make(0, 0, 0, 0);
-            const T xj = q.x + ox, yj = q.y + oy, zj = q.z + oz;
+            const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
             const bool keep =
                 ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < Rl * Rl;
             const unsigned bal = __ballot_sync(kFull, keep);

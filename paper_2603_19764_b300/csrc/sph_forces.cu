@@ -222,9 +222,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     const Group G = next_group(todo, cx, cy, cz, A.p.span_f);
     ++w_groups;
     const bool act = G.member;
-    const T xi = REL ? p.x + (T)(cx - G.rx) * Lt : p.x;
-    const T yi = REL ? p.y + (T)(cy - G.ry) * Lt : p.y;
-    const T zi = REL ? p.z + (T)(cz - G.rz) * Lt : p.z;
+    const T xi = REL ? rel_coord(p.x, cx - G.rx, Lt) : p.x;
+    const T yi = REL ? rel_coord(p.y, cy - G.ry, Lt) : p.y;
+    const T zi = REL ? rel_coord(p.z, cz - G.rz, Lt) : p.z;
     const T Rb = wmax(act ? Hi : T(0));
     // lists and masks reach r^2 < H_i^2 + gi: no pair with r < H_i by the
     // FP64 predicate escapes the count
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
                                   ox, oy, oz))
           break;
         const V4 q = ok ? V::ld(posh, j) : V::make(0, 0, 0, 0);
-        const T xj = q.x + ox, yj = q.y + oy, zj = q.z + oz;
+        const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
         const T R = tmax(Rb, q.w);
         const bool keep =
             ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R + gmax;

@@ -75,6 +75,21 @@ __device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) {
 }  // namespace px
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+// Products and sums that the compiler may not fuse into one rounding.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+// A coordinate relative to the group's reference cell: c (relative to the
+// particle's own cell) plus k cells of side L, rounded once for the product
+// and once for the sum. The lane's own particle and the same particle staged
+// as a candidate are formed this way from the same inputs, so their bits
+// agree whatever the compiler contracts elsewhere, and the pair of a particle
+// with itself sits at r = 0 exactly (the counts exclude it there).
+template <typename T> __device__ __forceinline__ T rel_coord(T c, int k, T L) {
+  return add_rn(c, mul_rn((T)k, L));
+}
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
 // Square root of x >= 0 and a quotient: correctly rounded in FP64; in FP32
@@ -366,9 +381,10 @@ __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int
   j = __shfl_sync(kFull, s.s0, own) + (k - p0);
   const int off = __shfl_sync(kFull, s.off, own);
   if (REL) {
-    ox = (T)((off & 1023) - 512) * Lt;
-    oy = (T)(((off >> 10) & 1023) - 512) * Lt;
-    oz = (T)(((off >> 20) & 1023) - 512) * Lt;
+    // the candidate's coordinate is add_rn(c, o), as rel_coord forms it
+    ox = mul_rn((T)((off & 1023) - 512), Lt);
+    oy = mul_rn((T)(((off >> 10) & 1023) - 512), Lt);
+    oz = mul_rn((T)(((off >> 20) & 1023) - 512), Lt);
   } else {
     ox = oy = oz = T(0);
   }
