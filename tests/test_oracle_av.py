@@ -1,5 +1,5 @@
-"""Artificial viscosity of the oracle (Eq. 5-8) against its closed form for
-one pair.
+"""Artificial viscosity (Eq. 5-8) and the time step (Eq. 38-39) of the
+oracle against their closed forms for one pair.
 
 Two particles on the x axis inside each other's support. The viscous terms
 are the difference between the oracle's derivatives with (alpha, beta) on
@@ -10,7 +10,9 @@ state (H, rho, c_s): an approaching pair gets a_i = -m_j Pi grad W_bar and
 du_i = 1/2 m_j Pi v_ij . grad W_bar, with mu from the averaged support
 radius; a receding pair gets nothing. A dropped 1/2, a wrong sign of the
 approach test, W(H_i) in place of the averaged kernel, or epsilon on the
-wrong term each fail it."""
+wrong term each fail it. The time step is restated the same way: the
+smaller of the acceleration and CFL criteria, the latter with the
+longitudinal sound speed and the pair's mu where it approaches."""
 import numpy as np
 import pytest
 
@@ -84,3 +86,42 @@ def test_viscous_momentum_and_energy_balance():
                       + a["vz"][k] * da["az"][k]) for k in range(2))
     heat = m[0] * da["dudt"][0] + m[1] * da["dudt"][1]
     assert heat == pytest.approx(-dke, rel=1e-10)
+
+
+def _dt_by_hand(a, st, p, mats, approach):
+    """Eq. 38-39 for the pair, restated: eps = H (the reading of the
+    softening length), c the longitudinal speed sqrt(c^2 + 4 Gamma / (3 rho))
+    of a material with strength, mu_ij of Eq. 6 where the pair approaches."""
+    G = mats[0]["shear_G"]
+    out = []
+    for i, j in ((0, 1), (1, 0)):
+        acc = np.sqrt(st["ax"][i] ** 2 + st["ay"][i] ** 2 + st["az"][i] ** 2)
+        ta = p["eta_a"] * np.sqrt(st["h"][i] / acc) if acc > 0 else np.inf
+        rij = np.array([a["x"][i] - a["x"][j], a["y"][i] - a["y"][j], a["z"][i] - a["z"][j]])
+        vij = np.array([a["vx"][i] - a["vx"][j], a["vy"][i] - a["vy"][j], a["vz"][i] - a["vz"][j]])
+        hb = 0.5 * (st["h"][i] + st["h"][j])
+        mu = hb * (vij @ rij) / (rij @ rij + p["av_eps"] * hb * hb)
+        assert (mu < 0) == approach
+        cl = np.sqrt(st["cs"][i] ** 2 + 4.0 / 3.0 * G / st["rho"][i])
+        vsig = (1 + 0.6 * p["av_alpha"]) * cl + 0.6 * p["av_beta"] * abs(min(0.0, mu))
+        out.append(min(ta, p["eta_c"] * st["h"][i] / vsig))
+    return min(out)
+
+
+@pytest.mark.parametrize("v", [300.0, -300.0])
+def test_time_step_cfl_bound(v):
+    a, mats = _pair(v)
+    p = wl.default_params(0)
+    st, info = oracle.derivatives(p, mats, a)
+    assert info["dt_next"] == pytest.approx(_dt_by_hand(a, st, p, mats, v > 0), rel=1e-12)
+
+
+def test_time_step_acceleration_bound():
+    """A strong uniform field makes the acceleration criterion bind."""
+    a, mats = _pair(300.0)
+    p = dict(wl.default_params(0), gravity=1, g_uniform=(0.0, 0.0, -1.0e12))
+    st, info = oracle.derivatives(p, mats, a)
+    acc = np.sqrt(st["ax"] ** 2 + st["ay"] ** 2 + st["az"] ** 2)
+    ta = p["eta_a"] * np.sqrt(st["h"] / acc)
+    assert info["dt_next"] == pytest.approx(ta.min(), rel=1e-12)
+    assert info["dt_next"] == pytest.approx(_dt_by_hand(a, st, p, mats, True), rel=1e-12)
