@@ -22,7 +22,8 @@ dominant kernel's algorithmic FLOP/s over the FP32 or FP64 ALU peak from
 unit counts and clock, beside the measured FMA peak), cpu_baseline (the
 FP64 C oracle stepping the whole impact on every host core, plus one thread
 on a bounded sub-volume) and the SM clocks sampled during the timed region.
---impl reference times the oracle itself on a sub-volume.
+--impl reference times the oracle itself, whole FP64 steps of the same
+impact on the host cores.
 """
 from __future__ import annotations
 
@@ -51,9 +52,10 @@ sys.path.insert(0, ROOT)
 # rejection, compensation and index work are not counted either way.
 FLOPS_DENSITY_PAIR = 27
 FLOPS_FORCE_PAIR = 209
-# B300 unit counts: 148 SMs x 128 FP32 lanes, 2 FLOP per FMA; FP64 at the
-# nominal 1.25 TFLOP/s at the 2032 MHz maximum clock.
-N_SM, FP32_LANES, MAX_MHZ = 148, 128, 2032.0
+# B300 unit counts: 128 FP32 lanes per SM, 2 FLOP per FMA, at the 2032 MHz
+# maximum clock (the SM count is read from the device); FP64 at the nominal
+# 1.25 TFLOP/s.
+FP32_LANES, MAX_MHZ = 128, 2032.0
 FP64_NOMINAL_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per particle per launch of the FP32 pair kernels,
@@ -83,8 +85,8 @@ def traffic_per_launch(kernel: str, n: int, precision: int):
     return per * n if source_hash(kernel) == h else None
 
 
-def fp32_peak_tflops(mhz: float) -> float:
-    return N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+def fp32_peak_tflops(mhz: float, n_sm: int) -> float:
+    return n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
 def fp64_peak_tflops(mhz: float) -> float:
@@ -250,52 +252,65 @@ def cpu_baseline(w, budget_s: float = 15.0, max_steps: int = 3, n_single: int = 
 
 # --------------------------------------------------------------- arms
 def run_reference(args, rank: int, world: int):
+    """The oracle as it stands, timed on the host cores: W untimed and then
+    K timed FP64 steps of the whole impact (every particle, adaptive dt), so
+    ms_per_step is a measured step of the same workload as the GPU arm."""
     if rank != 0:
         return
     w = make_workload(args.scale, 1)
     import oracle
-    r = oracle_rate(w, contact_subvolume(w, min(args.ref_particles, w.n)), 0.0, 0,
-                    fixed_steps=max(1, args.steps), warmup=args.warmup)
+    r = oracle_rate(w, w.arrays, 0.0, 0, fixed_steps=max(1, args.steps), warmup=args.warmup)
     cb = {"value": r["value"], "unit": "particle-steps/s", "cores": oracle.threads(),
           "kind": "oracle",
-          "sample": "%d FP64 oracle steps (OpenMP) of the %d particles of the impact nearest "
-                    "the contact point" % (r["steps"], r["particles"])}
+          "sample": "%d FP64 oracle steps (OpenMP, %d threads) of the whole %d-particle impact, "
+                    "after %d untimed" % (r["steps"], oracle.threads(), r["particles"],
+                                          args.warmup)}
     line = {"metric": "SPH+strength particle-steps/s (2M part.), chosen vs plain form at stated error",
             "value": cb["value"], "unit": "particle-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            # the sample's rate carried to one step of the whole workload
-            "ms_per_step": 1e3 * w.n / cb["value"],
+            "steps": r["steps"], "warmup": args.warmup,
+            "ms_per_step": 1e3 * r["seconds"] / r["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg (sub-volume)",
-                       "particles": w.n, "precision": "fp64 oracle"},
+            "config": {"workload": "basalt impact 1.8M+0.2M particles, 5 km/s, 45 deg",
+                       "particles": r["particles"], "precision": "fp64 oracle",
+                       "dt": "adaptive, Eq. 38-39 (dt_next of the previous step)"},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def time_plain(w, dev, steps: int = 3, warmup: int = 3) -> dict:
-    """The plain FP64 form on workload w: particle-steps/s over `steps`."""
+def time_plain(w, dev, snapshot: dict, dts: list, warmup: int = 3, graph: bool = True) -> dict:
+    """The plain FP64 form doing the chosen form's timed work: it starts
+    from the same state (`snapshot`, the chosen form's caller arrays at the
+    start of its timed steps, derivatives included) and takes the same step
+    sizes `dts`, replayed from a CUDA graph like the chosen form. Warm-up
+    steps (graph capture) run from the snapshot too; the state is then put
+    back in place, so the graph's pointers stay valid."""
     import torch
     from paper_2603_19764_b300 import sph
     p = dict(w.params, precision=0, h_tol=1e-10)
-    sim = sph.Simulation(w.arrays, w.materials, p, device=str(dev))
-    sim.prime()
-    for _ in range(warmup):
-        sim.step(0.0)
+    sim = sph.Simulation(snapshot, w.materials, p, device=str(dev))
+    if graph:
+        sim.set_graph(True)
+    for k in range(warmup):
+        sim.step(dts[k % len(dts)])
+    torch.cuda.synchronize(dev)
+    for f, t in sim.t.items():
+        t.copy_(torch.as_tensor(snapshot[f]).to(dev))
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
-    for _ in range(steps):
-        sim.step(0.0)
+    for dt in dts:
+        sim.step(dt)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
     sim.close()
-    return {"value": w.n * steps / (ms / 1e3), "unit": "particle-steps/s",
-            "ms_per_step": ms / steps, "steps": steps, "precision": "fp64"}
+    return {"value": w.n * len(dts) / (ms / 1e3), "unit": "particle-steps/s",
+            "ms_per_step": ms / len(dts), "steps": len(dts), "precision": "fp64",
+            "graph": graph, "work": "same start state and step sizes as the timed chosen steps"}
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -323,6 +338,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         sim.set_graph(True)
     for _ in range(args.warmup):
         sim.step(0.0)
+    # start state of the timed steps, for the plain form's identical work
+    snapshot = sim.to_numpy() if (rank == 0 and precision == 1 and not args.no_plain) else None
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if world > 1:
         dist.barrier()
@@ -363,14 +380,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     else:
         kname, flops, tk = "k_density", FLOPS_DENSITY_PAIR * pairs_d, t_dens
     achieved = flops / (tk / 1e3) / 1e12
-    peak = fp32_peak_tflops(MAX_MHZ) if precision else fp64_peak_tflops(MAX_MHZ)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(MAX_MHZ, n_sm) if precision else fp64_peak_tflops(MAX_MHZ)
     fma = {"fp32": sph.measure_fma_peak(1, 20), "fp64": sph.measure_fma_peak(0, 5)}
     fma_own = fma["fp32" if precision else "fp64"]
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_per_launch(kname, w.n, precision), "traffic_unit": "bytes",
                 "peak_basis": ("%s lanes x 2 x %.0f MHz (unit counts)" %
-                               ("148x128 FP32" if precision else "FP64 nominal 1.25 TFLOP/s",
+                               ("%dx128 FP32" % n_sm if precision else "FP64 nominal 1.25 TFLOP/s",
                                 MAX_MHZ)),
                 "kernel_ms": tk, "pairs_per_step": pairs_f if kname == "k_forces" else pairs_d,
                 "peak_fma_measured": fma_own["tflops"],
@@ -406,7 +424,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # the plain FP64 form on the same impact, a few steps, for the chosen-vs-plain ratio
     plain = None
     if rank == 0 and args.precision == "fp32k" and not args.no_plain:
-        plain = time_plain(w, dev, steps=args.plain_steps)
+        plain = time_plain(w, dev, snapshot, [i["dt"] for i in infos][:args.plain_steps or None],
+                           warmup=args.warmup, graph=not args.no_graph)
+        snapshot = None
 
     if rank == 0:
         line = {"metric": "SPH+strength particle-steps/s (2M part.), chosen vs plain form at stated error",
@@ -515,7 +535,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     ms_c, infos, rep, err, clocks = batched(1, args.steps, 2, True, sampler)
     ms_c = max_over_ranks(ms_c, world, dev)
     value = job_rate(w.n, world, args.steps, ms_c / 1e3)
-    ks = max(1, min(args.steps, args.plain_steps))
+    ks = max(1, min(args.steps, args.plain_steps or 3))
     arms = {}
     if rank == 0:
         ms_b64, _, rep64, err64, _ = batched(0, ks, 2, True)
@@ -890,7 +910,6 @@ def main():
     ap.add_argument("--precision", default="fp32k", choices=["fp32k", "fp64"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--ref-particles", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
@@ -898,7 +917,8 @@ def main():
     ap.add_argument("--tune", type=int, default=2)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--spans", default="", help="density,forces group spans (no tuning)")
-    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--plain-steps", type=int, default=0,
+                    help="plain-form steps (0: all of the chosen form's timed steps)")
     ap.add_argument("--workload", default="impact", choices=["impact", "batch64", "learned", "drift", "rungs"])
     ap.add_argument("--max-rung", type=int, default=3)
     ap.add_argument("--drift-steps", type=int, default=100)

@@ -22,8 +22,8 @@
  *    thread-safe for one context. A call returns after enqueueing its work,
  *    except where it says it synchronises.
  *  - Every call returns a status. Device-side conditions (no convergence,
- *    non-finite results, capacity) are latched in a device word and reported
- *    at the next synchronising call. After SPH_E_CUDA the context is left in
+ *    non-finite results) are latched in a device word and reported at the
+ *    next synchronising call. After SPH_E_CUDA the context is left in
  *    SPH_E_STATE and can only be destroyed. sph_last_error() gives detail.
  */
 #ifndef SPH_H
@@ -40,9 +40,14 @@ typedef enum {
   SPH_E_ARG = 1,        /* invalid argument; nothing was enqueued */
   SPH_E_CUDA = 2,       /* a CUDA runtime call failed */
   SPH_E_NOCONV = 3,     /* smoothing-length solve did not converge */
-  SPH_E_CAPACITY = 4,   /* a scratch capacity was exceeded */
+  SPH_E_CAPACITY = 4,   /* a periodic box axis is not wider than twice a
+                           search radius (the minimum image would not be the
+                           only image in range); the step's results are not
+                           valid. Candidate lists that outgrow their buffers
+                           never fail: they continue in further segments. */
   SPH_E_NONFINITE = 5,  /* a derivative or density came out NaN or Inf */
-  SPH_E_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+  SPH_E_TIMEOUT = 6,    /* reserved: no kernel waits on a flag or on another
+                           block, so none can time out */
   SPH_E_STATE = 7       /* context unusable after an earlier failure */
 } sph_status;
 
@@ -127,7 +132,16 @@ typedef struct {
  *                  phi_table are HOST arrays of g_n values on radii
  *                  log-spaced from g_rmin to g_rmax about g_center, copied
  *                  at sph_init; g = g_gm / r^2 beyond g_rmax
- *   periodic       must be 0 (periodic boxes are an oracle-only feature)
+ *   periodic       0: open space. 1: periodic box [box_lo, box_hi) on all
+ *                  three axes (one system, max_rung = 0, no radial table;
+ *                  SPH_E_ARG otherwise, or if a position lies outside the
+ *                  box at sph_init): drifted positions wrap back into the
+ *                  box, and every pair takes the minimum image, in the
+ *                  neighbour predicate (x_i - x_j shifted by a box length
+ *                  where |x_i - x_j| > box / 2, as FP64) and in every pair
+ *                  term. Each box length must exceed twice the largest
+ *                  search radius (about 2.1 H_max); a step that finds a
+ *                  narrower box returns SPH_E_CAPACITY.
  *   gradient_form  SPH_GRADIENT_SYMMETRIC: F and C^-1 as Eq. 20-21 (the mean
  *                  of the two kernels, each over its own Omega rho);
  *                  SPH_GRADIENT_ONE_SIDED: the H_i term alone,
@@ -392,6 +406,14 @@ sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sp
  * without a previous step are NaN. SPH_E_STATE unless recording. */
 sph_status sph_learn_samples(sph_ctx *c, float *X, float *y);
 
+/* The starting radii that the last step proposed for the next solve:
+ * n doubles into the DEVICE array h_next, in the particle order the step
+ * left the state arrays in (the sorted order); 0 for a particle without a
+ * proposal yet (none is made before the first step after
+ * sph_set_learned_h). SPH_E_STATE unless a guess mode other than
+ * SPH_GUESS_PREVIOUS is set; ordered on the context's stream. */
+sph_status sph_learn_proposal(sph_ctx *c, double *h_next);
+
 /* sph_step with HOST state: the caller passes pinned (for overlap) or
  * pageable host arrays in `host`; the library copies to the context's device
  * state every array the step reads (rho, Omega, P, c_s and the counts are
@@ -433,17 +455,34 @@ sph_status sph_phase_times(const sph_ctx *c, double *ms, int32_t n, int32_t *ste
  * arrays of length n, other pointers may be NULL) and writes 8 doubles to
  * the caller-owned DEVICE array `sums`: kinetic energy, internal energy,
  * linear momentum (3) and angular momentum L = sum m r x v (3), each an
- * FP64 sum over all particles. Its scratch is a fixed array compiled into
- * the library (partial sums of at most 1184 blocks, 75,776 bytes, held by
- * every GPU that loads the library until the process exits). The first
- * call on each device looks up that array's device address; make it before
- * any stream capture. Every call on a device shares the array, so calls
- * that overlap on the GPU (different streams, no ordering) race. Ordered on
+ * FP64 sum over all particles OF THE ARRAYS AS STORED. Between steps the
+ * state holds x at time i but v and u at i+1/2 (the kick-drift-kick of
+ * §2.4), so these are half-step sums, not the time-i sums of
+ * sph_step_info; no potential energy is included. Its scratch is a fixed
+ * array compiled into the library (partial sums of at most 1184 blocks,
+ * 75,776 bytes, held by every GPU that loads the library until the
+ * process exits). Every call made outside a stream capture looks up that
+ * array's device address on the current device (so the first call on each
+ * device must come before any stream capture: SPH_E_STATE otherwise); a
+ * captured call uses the address last looked up. Every call on a device
+ * shares the array, so calls that overlap on the GPU (different streams,
+ * no ordering) race. An error left pending by earlier work is cleared on
+ * entry, so SPH_E_CUDA reports this call's own launches. Ordered on
  * `cuda_stream`; returns after enqueueing. Errors: SPH_E_ARG (NULL
- * pointer, n < 1 or n > SPH_NOALLOC_MAX_N), SPH_E_CUDA. */
+ * pointer, n < 1 or n > SPH_NOALLOC_MAX_N), SPH_E_STATE, SPH_E_CUDA. */
 #define SPH_NOALLOC_MAX_N ((int64_t)1 << 31)
 sph_status sph_diagnostics_noalloc(const sph_state *st, int64_t n, double *sums,
                                    void *cuda_stream);
+
+/* Host-side fault injection for tests of the error paths: the `after`-th
+ * CUDA runtime call that the context checks from now on (1 = the next) is
+ * reported as failed with cudaErrorUnknown although it succeeded, exactly as
+ * a real failure of that call would be: the calling entry point returns
+ * SPH_E_CUDA (work it enqueued before that call stays enqueued and runs to
+ * completion) and every later call on the context returns SPH_E_STATE until
+ * sph_destroy. Nothing is done to the GPU. after = 0 cancels a pending
+ * injection; SPH_E_ARG for after < 0. */
+sph_status sph_inject_cuda_failure(sph_ctx *c, int32_t after);
 
 /* Free the context and its scratch; the caller's arrays are untouched.
  * Accepts NULL. */

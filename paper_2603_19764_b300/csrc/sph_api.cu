@@ -26,17 +26,28 @@ sph_status fail_cuda(sph_ctx *c, cudaError_t e, const char *what) {
   return SPH_E_CUDA;
 }
 
+// A checked CUDA runtime call. An injected failure (sph_inject_cuda_failure)
+// turns the chosen successful call into cudaErrorUnknown.
+inline cudaError_t injected(sph_ctx *c, cudaError_t e) {
+  if (e == cudaSuccess && c && c->fail_after > 0 && --c->fail_after == 0) return cudaErrorUnknown;
+  return e;
+}
+
 #define CK(call)                                          \
   do {                                                    \
-    cudaError_t e_ = (call);                              \
+    cudaError_t e_ = injected(c, (call));                 \
     if (e_ != cudaSuccess) return fail_cuda(c, e_, #call); \
   } while (0)
 
+// Entry of a context call. An error that earlier, unrelated work left
+// pending (not sticky) is cleared, so that the launch checks of this call
+// report its own launches.
 #define ENTER(c)                                                                 \
   do {                                                                           \
     if (!(c)) return SPH_E_ARG;                                                  \
     if ((c)->broken) return fail(c, SPH_E_STATE, "context unusable after a CUDA error"); \
     (c)->nlaunch = 0;                                                            \
+    (void)cudaGetLastError();                                                    \
   } while (0)
 
 template <typename T> cudaError_t dalloc(T **p, size_t count) {
@@ -93,12 +104,18 @@ bool state_complete(const sph_state *s) {
 
 // Validation of the device state at set-up: material index in range,
 // positive mass and H, finite positions; in a batch, ids in 0..n-1.
-__global__ void k_validate(sph_state s, int64_t n, int nmat, int check_id, unsigned *bad) {
+// In a periodic box every position must lie in [box_lo, box_hi).
+__global__ void k_validate(sph_state s, int64_t n, int nmat, int check_id, KParams P,
+                           unsigned *bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     bool ok = s.mat[i] >= 0 && s.mat[i] < nmat && s.m[i] > 0.0 && s.h[i] > 0.0 &&
               isfinite(s.x[i]) && isfinite(s.y[i]) && isfinite(s.z[i]) && isfinite(s.h[i]);
     if (check_id) ok = ok && s.id[i] >= 0 && s.id[i] < n;
+    if (P.periodic) {
+      const double c[3] = {s.x[i], s.y[i], s.z[i]};
+      for (int a = 0; a < 3; ++a) ok = ok && c[a] >= P.box_lo[a] && c[a] < P.box_hi[a];
+    }
     if (!ok) atomicOr(bad, 1u);
   }
 }
@@ -126,7 +143,8 @@ void free_all(sph_ctx *c) {
 sph_status status_from_flags(sph_ctx *c, unsigned flags) {
   if (flags & ERR_NONFINITE) return fail(c, SPH_E_NONFINITE, "non-finite density or derivative");
   if (flags & ERR_TIMEOUT) return fail(c, SPH_E_TIMEOUT, "device wait timed out");
-  if (flags & ERR_CAPACITY) return fail(c, SPH_E_CAPACITY, "scratch capacity exceeded");
+  if (flags & ERR_CAPACITY)
+    return fail(c, SPH_E_CAPACITY, "periodic box not wider than twice a search radius");
   if (flags & ERR_NOCONV) return fail(c, SPH_E_NOCONV, "smoothing-length solve did not converge");
   return SPH_OK;
 }
@@ -452,7 +470,7 @@ const char *sph_status_string(sph_status s) {
     case SPH_E_ARG: return "invalid argument";
     case SPH_E_CUDA: return "CUDA error";
     case SPH_E_NOCONV: return "smoothing-length solve did not converge";
-    case SPH_E_CAPACITY: return "scratch capacity exceeded";
+    case SPH_E_CAPACITY: return "periodic box too narrow for the search radius";
     case SPH_E_NONFINITE: return "non-finite result";
     case SPH_E_TIMEOUT: return "device wait timed out";
     case SPH_E_STATE: return "context unusable";
@@ -461,6 +479,12 @@ const char *sph_status_string(sph_status s) {
 }
 
 const char *sph_last_error(const sph_ctx *c) { return c ? c->err : "no context"; }
+
+sph_status sph_inject_cuda_failure(sph_ctx *c, int32_t after) {
+  if (!c || after < 0) return SPH_E_ARG;
+  c->fail_after = after;
+  return SPH_OK;
+}
 
 sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material *mats,
                           int32_t n_mat, const sph_state *st, int64_t n, int32_t n_sys,
@@ -481,7 +505,14 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   if (p->max_rung < 0 || p->max_rung > 15) return SPH_E_ARG;
   if (p->gravity < SPH_GRAVITY_NONE || p->gravity > SPH_GRAVITY_RADIAL) return SPH_E_ARG;
   if (p->gravity == SPH_GRAVITY_RADIAL && n_sys > 1) return SPH_E_ARG;
-  if (p->periodic != 0) return SPH_E_ARG;
+  if (p->periodic != 0 && p->periodic != 1) return SPH_E_ARG;
+  if (p->periodic) {
+    // one system, one global step, no radial field
+    if (n_sys != 1 || p->max_rung != 0 || p->gravity == SPH_GRAVITY_RADIAL) return SPH_E_ARG;
+    for (int a = 0; a < 3; ++a)
+      if (!(p->box_hi[a] > p->box_lo[a]) || !isfinite(p->box_lo[a]) || !isfinite(p->box_hi[a]))
+        return SPH_E_ARG;
+  }
   if (!(p->n_ngb >= 1) || !(p->h_tol > 0.0) || p->max_sweeps < 1 || !(p->h_cap_factor > 0.0))
     return SPH_E_ARG;
   if (p->gravity == SPH_GRAVITY_RADIAL &&
@@ -631,6 +662,12 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.max_rung = 0;
   kp.substep = 0;
   kp.sub_scale = 1.0;
+  kp.periodic = p->periodic;
+  for (int a = 0; a < 3; ++a) {
+    kp.box_lo[a] = p->box_lo[a];
+    kp.box_hi[a] = p->box_hi[a];
+    kp.box_len[a] = p->box_hi[a] - p->box_lo[a];
+  }
   kp.gravity = p->gravity;
   for (int a = 0; a < 3; ++a) {
     kp.g_uniform[a] = p->g_uniform[a];
@@ -715,7 +752,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   unsigned *bad = nullptr;
   CKI(dalloc(&bad, 1));
   CKI(cudaMemset(bad, 0, sizeof(unsigned)));
-  k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, n_mat, n_sys > 1, bad);
+  k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, n_mat, n_sys > 1, c->kp, bad);
   unsigned hbad = 0;
   CKI(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   CKI(cudaStreamSynchronize(c->stream));
@@ -744,7 +781,10 @@ sph_status sph_set_timing(sph_ctx *c, int32_t on) {
     for (int k = 0; k <= SPH_NUM_PHASES; ++k) CK(cudaEventCreate(&c->ev[k]));
   }
   if (!on && c->timing) {
-    for (int k = 0; k <= SPH_NUM_PHASES; ++k) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k <= SPH_NUM_PHASES; ++k) {
+      cudaEventDestroy(c->ev[k]);
+      c->ev[k] = nullptr;
+    }
   }
   c->timing = on ? 1 : 0;
   for (int k = 0; k < SPH_NUM_PHASES; ++k) c->phase_ms[k] = 0.0;
@@ -782,14 +822,18 @@ sph_status sph_destroy(sph_ctx *c) {
   if (c->cstream) {
     cudaStreamSynchronize(c->cstream);
     cudaStreamDestroy(c->cstream);
-    for (int k = 0; k < 5; ++k) cudaEventDestroy(c->out_ev[k]);
   }
-  if (c->timing)
-    for (int k = 0; k <= SPH_NUM_PHASES; ++k) cudaEventDestroy(c->ev[k]);
-  if (c->tev[0])
-    for (int k = 0; k < 4; ++k) cudaEventDestroy(c->tev[k]);
+  // handles that a failed set-up never created stay null and are skipped
+  for (int k = 0; k < 5; ++k)
+    if (c->out_ev[k]) cudaEventDestroy(c->out_ev[k]);
+  for (int k = 0; k <= SPH_NUM_PHASES; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  for (int k = 0; k < 4; ++k)
+    if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   free_all(c);
   free(c);
+  // teardown reports nothing to the caller; leave no error pending
+  (void)cudaGetLastError();
   return SPH_OK;
 }
 
@@ -927,7 +971,7 @@ sph_status sph_set_learned_h(sph_ctx *c, int32_t guess, int32_t record, const sp
     unsigned *bad = nullptr;
     CK(dalloc(&bad, 1));
     CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->stream));
-    k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, c->nmat, 1, bad);
+    k_validate<<<148 * 4, kBlock, 0, c->stream>>>(c->st, n, c->nmat, 1, c->kp, bad);
     unsigned hbad = 0;
     CK(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -972,6 +1016,16 @@ sph_status sph_learn_samples(sph_ctx *c, float *X, float *y) {
   CK(cudaMemcpyAsync(X, c->learn.x_out, sizeof(float) * 6 * c->n, cudaMemcpyDeviceToDevice,
                      c->stream));
   CK(cudaMemcpyAsync(y, c->learn.y_out, sizeof(float) * c->n, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  return SPH_OK;
+}
+
+sph_status sph_learn_proposal(sph_ctx *c, double *h_next) {
+  ENTER(c);
+  if (!h_next) return fail(c, SPH_E_ARG, "NULL output");
+  if (!c->learn.hprop || c->learn.guess == SPH_GUESS_PREVIOUS)
+    return fail(c, SPH_E_STATE, "no proposal mode");
+  CK(cudaMemcpyAsync(h_next, c->learn.hprop, sizeof(double) * c->n, cudaMemcpyDeviceToDevice,
                      c->stream));
   return SPH_OK;
 }

@@ -146,13 +146,13 @@ __device__ __forceinline__ void build_masks(const typename DList<T>::slot *Lp, u
 
 // Walk one lane's marked candidates: exact membership r < H_i, then the
 // kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
-template <typename T, bool REL>
+template <typename T, bool REL, bool PER>
 __device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, const int *Li,
                                              unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              T gb, T H, double xi64, double yi64, double zi64,
-                                             const sph_state &s, int self, T &rs, T &rhs,
-                                             T &rhs2, int &cnt) {
+                                             const sph_state &s, const double *blen, int self,
+                                             T &rs, T &rhs, T &rhs2, int &cnt) {
   // every lane advances through its own words: lanes do not wait for each
   // other at word boundaries
   const int nw = (nl + 31) >> 5;
@@ -177,12 +177,21 @@ __device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, 
         if (fabs(r2 - H2) < gb) {
           const int j = Li[k];
           // the square of an FP32 radius is exact in FP64
-          in = r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]) <
-               __dmul_rn((double)H, (double)H);
+          const double c2 = PER ? r2_canon_periodic(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j],
+                                                    blen)
+                                : r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]);
+          in = c2 < __dmul_rn((double)H, (double)H);
         }
       } else {
         r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
         in = r2 < H2;
+        // a shifted image's coordinate was rounded once more than the
+        // minimum image of x_i - x_j: decide the rare pair at the boundary
+        // with the canonical arithmetic
+        if (PER && fabs(r2 - H2) < gb) {
+          const int j = Li[k];
+          in = r2_canon_periodic(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j], blen) < (double)H2;
+        }
       }
       if (in) {
         const T qq = root(r2) * invH;
@@ -199,7 +208,7 @@ __device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, 
   }
 }
 
-template <typename T, int CAP>
+template <typename T, int CAP, bool PER>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
@@ -220,7 +229,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   long long w_pairs = 0, w_cand = 0;
   int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0, w_exp = 0;
   long long w_swt = 0;
-  unsigned w_bad = 0;
+  unsigned w_bad = 0, w_box = 0;
+  // a periodic box must be wider than twice every search radius
+  const T box_min = PER ? (T)fmin(fmin(A.p.box_len[0], A.p.box_len[1]), A.p.box_len[2]) : T(0);
   for (;;) {
   unsigned bk = 0;
   if (lane == 0) bk = atomicAdd(&A.st->next_bucket[0], 1u);
@@ -283,7 +294,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       const T Ht = H;
       const T invHt = T(1) / Ht;
       const T H2 = REL ? Ht * Ht : (T)__dmul_rn((double)Ht, (double)Ht);
-      const T gb = guard_band(Ht, Lt);
+      // FP64 form in a periodic box: the band of the shifted images' extra
+      // rounding (far below the FP32 band)
+      const T gb = REL ? guard_band(Ht, Lt) : T(1e-12) * Ht * tmax(Ht, box_min);
       // smallest mask radius: Hq^2 > H^2 + gb, so that no pair with r < H
       // by the FP64 predicate falls outside the mask or the list
       const T Hq = Ht * T(1.0001) + T(1e-5) * tmax(Ht, Lt);
@@ -293,8 +306,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       const bool resident = complete && Rneed <= Rl;
       if (!resident) {
         Rl = Rneed * T(1.05);
+        if (PER && !(T(2) * Rl < box_min)) w_box = 1u;
         const Box<T> bx = group_box(act, xi, yi, zi);
-        Stager sg = make_stager<T, REL>(bx, Rl, g, invL, G.rx, G.ry, G.rz);
+        auto sg = make_stager_for<T, REL, PER>(bx, Rl, g, invL, A.p, G.rx, G.ry, G.rz);
         Hm = T(0);
         complete = false;
         for (int seg = 0;; ++seg) {
@@ -303,8 +317,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
             int j;
             bool ok;
             T ox, oy, oz;
-            if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, G.rx, G.ry, G.rz, j,
-                                      ok, ox, oy, oz))
+            if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz,
+                                      j, ok, ox, oy, oz))
               break;
             const V4 q = ok ? V::ld(pos, j) : V::make(0, 0, 0, 0);
             const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
@@ -335,10 +349,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           build_masks<T>(Sv.p, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
           __syncwarp();
           if (act) {
-            density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64, yi64,
-                                     zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-            density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
-                                     yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
+            density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
+                                          yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
+                                          cnt);
+            density_walk<T, REL, PER>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
+                                          xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
+                                          rhs2, cnt);
           }
           __syncwarp();
           if (stager_finished(sg)) break;
@@ -357,10 +373,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           Hm = Hn;
         }
         if (act) {
-          density_walk<T, REL>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64, yi64,
-                                   zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
-          density_walk<T, REL>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
-                                   yi64, zi64, A.s, (int)i, rs, rhs, rhs2, cnt);
+          density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
+                                        yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
+                                        cnt);
+          density_walk<T, REL, PER>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
+                                        xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
+                                        rhs2, cnt);
         }
       }
 
@@ -457,6 +475,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
     }
     if (ncap) atomicAdd(&A.st->n_capped, ncap);
     if (nbad) atomicOr(&A.st->err, ERR_NONFINITE);
+    if (PER && __any_sync(kFull, w_box)) atomicOr(&A.st->err, ERR_CAPACITY);
     atomicAdd(&A.st->pairs_density, (unsigned long long)pw);
     atomicAdd(&A.st->cand_density, (unsigned long long)w_cand);
     atomicAdd(&A.st->groups_density, (unsigned long long)w_groups);
@@ -476,12 +495,21 @@ cudaError_t launch_density(sph_ctx *c, int expand) {
   a.spill = c->dens_spill;
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
-  if (c->kp.precision == SPH_FP32K)
-    k_density<float, 576><<<resident_grid(c, k_density<float, 576>), 32 * kWarpsPerBlock, 0,
-                            c->stream>>>(a);
-  else
-    k_density<double, 256><<<resident_grid(c, k_density<double, 256>), 32 * kWarpsPerBlock, 0,
-                             c->stream>>>(a);
+  if (c->kp.precision == SPH_FP32K) {
+    if (c->kp.periodic)
+      k_density<float, 576, true><<<resident_grid(c, k_density<float, 576, true>),
+                                    32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    else
+      k_density<float, 576, false><<<resident_grid(c, k_density<float, 576, false>),
+                                     32 * kWarpsPerBlock, 0, c->stream>>>(a);
+  } else {
+    if (c->kp.periodic)
+      k_density<double, 256, true><<<resident_grid(c, k_density<double, 256, true>),
+                                     32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    else
+      k_density<double, 256, false><<<resident_grid(c, k_density<double, 256, false>),
+                                      32 * kWarpsPerBlock, 0, c->stream>>>(a);
+  }
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -493,12 +521,22 @@ namespace sphk {
 // Overflow region of the density lists: one kSpill-entry region per warp
 // that can be resident, at most one warp per bucket.
 cudaError_t alloc_density_spill(sph_ctx *c) {
+  // sized for the variant with the most resident blocks (closed or
+  // periodic box), so that every launched warp owns a region
   int per_sm = 0;
-  cudaError_t e = c->kp.precision == SPH_FP32K
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, k_density<float, 576>, 32 * kWarpsPerBlock, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, k_density<double, 256>, 32 * kWarpsPerBlock, 0);
+  cudaError_t e = cudaSuccess;
+  for (int per = 0; per < 2 && e == cudaSuccess; ++per) {
+    int k = 0;
+    if (c->kp.precision == SPH_FP32K)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &k, per ? k_density<float, 576, true> : k_density<float, 576, false>,
+          32 * kWarpsPerBlock, 0);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &k, per ? k_density<double, 256, true> : k_density<double, 256, false>,
+          32 * kWarpsPerBlock, 0);
+    per_sm = k > per_sm ? k : per_sm;
+  }
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t need = ((int64_t)c->kp.nbuckets + kWarpsPerBlock - 1) / kWarpsPerBlock;

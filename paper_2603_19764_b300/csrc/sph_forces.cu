@@ -153,7 +153,7 @@ struct ForceArgs {
 // Three 4-warp blocks per SM: the pair body and its compensated sums fit in
 // the ~170 registers a thread then has, without spilling (at four blocks,
 // 128 registers, they spill and the kernel runs 1.5 % slower).
-template <typename T, int CAP>
+template <typename T, int CAP, bool PER>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
@@ -170,6 +170,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   const int nbuckets = A.p.nbuckets;
   long long w_pairs = 0, w_cand = 0;
   int w_fb = 0, w_groups = 0;
+  unsigned w_box = 0;
+  // a periodic box must be wider than twice every search radius
+  const T box_min = PER ? (T)fmin(fmin(A.p.box_len[0], A.p.box_len[1]), A.p.box_len[2]) : T(0);
   for (;;) {
   unsigned bk = 0;
   if (lane == 0) bk = atomicAdd(&A.st->next_bucket[1], 1u);
@@ -230,8 +233,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     // FP64 predicate escapes the count
     const T gmax = guard_band(Rb, Lt);
     const T Rf = tmax(Rb, hmax_all) + T(1e-5) * tmax(Rb, Lt);
+    if (PER && !(T(2) * Rf < box_min)) w_box = 1u;
     const Box<T> bx = group_box(act, xi, yi, zi);
-    Stager sg = make_stager<T, REL>(bx, Rf, g, invL, G.rx, G.ry, G.rz);
+    auto sg = make_stager_for<T, REL, PER>(bx, Rf, g, invL, A.p, G.rx, G.ry, G.rz);
     for (;;) {
       // stage candidates
       int nl = 0;
@@ -239,8 +243,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
         int j;
         bool ok;
         T ox, oy, oz;
-        if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, G.rx, G.ry, G.rz, j, ok,
-                                  ox, oy, oz))
+        if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, j,
+                                  ok, ox, oy, oz))
           break;
         const V4 q = ok ? V::ld(posh, j) : V::make(0, 0, 0, 0);
         const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
@@ -318,12 +322,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
               inH = r2 < Hi2;
               if (fabs(r2 - Hi2) < gi) {   // rare: decide in FP64
                 const double h = A.s.h[i];
-                inH = r2_canon(A.s.x[i] - A.s.x[j], A.s.y[i] - A.s.y[j], A.s.z[i] - A.s.z[j]) <
+                const double ex = A.s.x[i] - A.s.x[j], ey = A.s.y[i] - A.s.y[j],
+                             ez = A.s.z[i] - A.s.z[j];
+                inH = (PER ? r2_canon_periodic(ex, ey, ez, A.p.box_len) : r2_canon(ex, ey, ez)) <
                       __dmul_rn(h, h);
               }
             } else {
               const double h = A.s.h[i];
-              inH = r2_canon((double)dx, (double)dy, (double)dz) < __dmul_rn(h, h);
+              const double h2 = __dmul_rn(h, h);
+              const double c2 = r2_canon((double)dx, (double)dy, (double)dz);
+              inH = c2 < h2;
+              // a shifted image's coordinate was rounded once more than the
+              // minimum image of x_i - x_j: decide the rare pair at the
+              // boundary with the canonical arithmetic
+              if (PER && fabs(c2 - h2) < 1e-12 * h * fmax(h, (double)box_min))
+                inH = r2_canon_periodic(A.s.x[i] - A.s.x[j], A.s.y[i] - A.s.y[j],
+                                        A.s.z[i] - A.s.z[j], A.p.box_len) < h2;
             }
             nngb += (inH && (r2 > T(0) || j != (int)i)) ? 1 : 0;
           }
@@ -480,7 +494,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   }  // bucket loop
   const int nfb = wsum(w_fb);
   const long long pw = wsum(w_pairs);
+  const bool box_bad = PER && __any_sync(kFull, w_box);
   if (lane == 0) {
+    if (box_bad) atomicOr(&A.st->err, ERR_CAPACITY);
     if (nfb) atomicAdd(&A.st->n_cfallback, nfb);
     atomicAdd(&A.st->pairs_force, (unsigned long long)pw);
     atomicAdd(&A.st->cand_force, (unsigned long long)w_cand);
@@ -499,12 +515,21 @@ cudaError_t launch_forces(sph_ctx *c) {
   a.st = c->d_status;
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[1], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
-  if (c->kp.precision == SPH_FP32K)
-    k_forces<float, 800><<<resident_grid(c, k_forces<float, 800>), 32 * kWarpsPerBlock, 0,
-                           c->stream>>>(a);
-  else
-    k_forces<double, 256><<<resident_grid(c, k_forces<double, 256>), 32 * kWarpsPerBlock, 0,
-                            c->stream>>>(a);
+  if (c->kp.precision == SPH_FP32K) {
+    if (c->kp.periodic)
+      k_forces<float, 800, true><<<resident_grid(c, k_forces<float, 800, true>),
+                                   32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    else
+      k_forces<float, 800, false><<<resident_grid(c, k_forces<float, 800, false>),
+                                    32 * kWarpsPerBlock, 0, c->stream>>>(a);
+  } else {
+    if (c->kp.periodic)
+      k_forces<double, 256, true><<<resident_grid(c, k_forces<double, 256, true>),
+                                    32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    else
+      k_forces<double, 256, false><<<resident_grid(c, k_forces<double, 256, false>),
+                                     32 * kWarpsPerBlock, 0, c->stream>>>(a);
+  }
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -98,6 +98,12 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
       p[0] += dt * s.vx[i];
       p[1] += dt * s.vy[i];
       p[2] += dt * s.vz[i];
+      if (P.periodic) {   // back into [box_lo, box_hi): one box length at most
+        for (int a = 0; a < 3; ++a) {
+          if (p[a] >= P.box_hi[a]) p[a] -= P.box_len[a];
+          else if (p[a] < P.box_lo[a]) p[a] += P.box_len[a];
+        }
+      }
       s.x[i] = p[0];
       s.y[i] = p[1];
       s.z[i] = p[2];
@@ -180,8 +186,11 @@ cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
 // ------------------------------------------------------------ grid setup
 // Per system: cell edge L_c = max H; at most 2^axis_bits cells per axis and
 // the system's cell capacity in all, growing L_c by 2^(1/3) until both hold.
-// Then the systems' cell ranges are laid out one after the other.
-__global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits) {
+// Then the systems' cell ranges are laid out one after the other. In a
+// periodic box the grid starts at box_lo and its ceil(box / L_c) cells per
+// axis cover [box_lo, box_hi) (the last one may reach past box_hi, where no
+// particle lies).
+__global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, KParams P) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double max_axis = (double)(1 << axis_bits);
   int off = 0;
@@ -189,8 +198,8 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits) {
     SysRec &r = sys[k];
     double lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-      lo[a] = dec_d(r.lo_enc[a]);
-      hi[a] = dec_d(r.hi_enc[a]);
+      lo[a] = P.periodic ? P.box_lo[a] : dec_d(r.lo_enc[a]);
+      hi[a] = P.periodic ? P.box_hi[a] : dec_d(r.hi_enc[a]);
     }
     double L = dec_d(r.hmax_enc);
     const double ext = fmax(fmax(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
@@ -201,7 +210,8 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits) {
       long long tot = 1;
       ok = true;
       for (int a = 0; a < 3; ++a) {
-        const double kk = floor((hi[a] - lo[a]) / L) + 1.0;
+        const double kk = P.periodic ? fmax(ceil((hi[a] - lo[a]) / L), 1.0)
+                                     : floor((hi[a] - lo[a]) / L) + 1.0;
         if (!(kk <= max_axis)) ok = false;
         d[a] = (int)fmin(fmax(kk, 1.0), 2.0 * max_axis);
         tot *= d[a];
@@ -231,7 +241,7 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits) {
 }
 
 cudaError_t launch_grid_setup(sph_ctx *c) {
-  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, c->kp.axis_bits);
+  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, c->kp.axis_bits, c->kp);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

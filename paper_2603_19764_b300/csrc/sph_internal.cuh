@@ -127,7 +127,21 @@ struct KParams {
   int max_rung, substep;
   double sub_scale;            // 2^-max_rung (exact)
   const int *rung;             // per particle (sorted order), or null
+  // periodic box [box_lo, box_hi) on every axis (one system only): drifted
+  // positions wrap into it, the cell grid tiles it from box_lo, and pairs
+  // take the minimum image
+  int periodic;
+  double box_lo[3], box_hi[3], box_len[3];
 };
+
+// Minimum-image separation along one periodic axis of length `box`, the
+// image nearest to d = x_i - x_j (the FP64 arithmetic of the neighbour
+// predicate in a periodic box).
+__device__ __forceinline__ double min_image(double d, double box) {
+  if (d > 0.5 * box) return d - box;
+  if (d < -0.5 * box) return d + box;
+  return d;
+}
 
 // Hierarchical steps: a particle on rung r steps 2^(R - r) substeps and is
 // active (solved, given derivatives, kicked) at the end of each of them.
@@ -546,6 +560,7 @@ struct sph_ctx {
   int timed_steps;
   int primed;
   int broken;
+  int fail_after;               // injected failure: the fail_after-th checked call (0: none)
   char err[512];
 };
 

@@ -24,7 +24,8 @@ constexpr int kMaxDevices = 64;
 // launches before it reads them, so nothing has to start at zero.
 static __device__ __align__(256) double g_diag_scratch[kDiagBlocks * kDiagSums];
 
-// Device address of g_diag_scratch per device, looked up on first use.
+// Device address of g_diag_scratch per device: looked up by every call made
+// outside a stream capture; a captured call uses the last address found.
 std::mutex g_diag_mutex;
 double *g_diag_addr[kMaxDevices];
 
@@ -87,21 +88,29 @@ extern "C" sph_status sph_diagnostics_noalloc(const sph_state *st, int64_t n, do
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SPH_E_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return SPH_E_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  // An error left pending by earlier, unrelated work is not this call's.
+  (void)cudaGetLastError();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return SPH_E_CUDA;
   double *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_diag_mutex);
-    if (!g_diag_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
+      // Looked up again on every call outside a capture: after a device
+      // reset the module, and so the array, may sit at another address.
       void *p = nullptr;
       if (cudaGetSymbolAddress(&p, g_diag_scratch) != cudaSuccess || !p) return SPH_E_CUDA;
       g_diag_addr[dev] = (double *)p;
+    } else if (!g_diag_addr[dev]) {
+      return SPH_E_STATE;   // the first call on a device must not be captured
     }
     scratch = g_diag_addr[dev];
   }
   int64_t blocks = (n + kDiagThreads - 1) / kDiagThreads;
   if (blocks > kDiagBlocks) blocks = kDiagBlocks;
-  cudaStream_t stream = (cudaStream_t)cuda_stream;
   k_diag_partials<<<(int)blocks, kDiagThreads, 0, stream>>>(*st, n, scratch);
+  if (cudaGetLastError() != cudaSuccess) return SPH_E_CUDA;
   k_diag_final<<<1, kDiagThreads, 0, stream>>>(scratch, (int)blocks, sums);
   return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
 }
-

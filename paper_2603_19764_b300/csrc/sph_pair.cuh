@@ -392,4 +392,201 @@ __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int
   return true;
 }
 
+
+// ------------------------------------------------------------ periodic box
+// In a periodic box the range box +- R may cross the box's faces. The part
+// past a face holds the images of the particles at the opposite side, one
+// box length away, so per axis the range is up to three runs of cells:
+// [lo0, dims) shifted by -len (the part below box_lo), [m0, m0 + nm)
+// unshifted, and [0, nu) shifted by +len (the part at or past box_hi).
+// Each run stages its cells' particles with that shift added to their
+// coordinates. While the box is wider than twice every search radius
+// (checked by the kernels), a lane finds at most one image of any particle
+// within its radius, and it is the minimum image; the particle itself
+// appears unshifted only.
+template <typename T> struct StagerP {
+  int lo0[3], nlo[3], m0[3], nm[3], nu[3];   // the three runs per axis
+  int nx, ny, ncell;                         // run-concatenated extents
+  int c0;                                    // first cell of the next batch
+  int s0, pre;                               // this lane's cell: start, prefix
+  T ox, oy, oz;                              // this lane's cell: offset to the frame
+  int total, pos;
+};
+
+template <typename T> __device__ __forceinline__ bool stager_finished(const StagerP<T> &s) {
+  return s.c0 >= s.ncell && s.pos >= s.total;
+}
+
+// Runs of axis a for the range [b0 - R, b1 + R] (in the frame: relative to
+// the reference cell's origin for REL, absolute otherwise). Cell indices
+// come from the same floor((x - lo) / L) as the particles' own cells, in
+// FP64.
+template <typename T, bool REL>
+__device__ __forceinline__ void periodic_runs(StagerP<T> &s, int a, T b0, T b1, T R,
+                                              const Grid &g, const KParams &P, int r) {
+  const double o = REL ? g.lo[a] + (double)r * g.L : 0.0;
+  const double A = o + (double)(b0 - R), B = o + (double)(b1 + R);
+  const int dims = g.dims[a];
+  const double len = P.box_len[a];
+  const int k0 = (int)floor((A - g.lo[a]) * g.invL), k1 = (int)floor((B - g.lo[a]) * g.invL);
+  s.m0[a] = max(k0, 0);
+  s.nm[a] = max(0, min(k1, dims - 1) - s.m0[a] + 1);
+  s.lo0[a] = 0;
+  s.nlo[a] = 0;
+  s.nu[a] = 0;
+  if (A < P.box_lo[a]) {
+    const int kl = min(max((int)floor((A + len - g.lo[a]) * g.invL), 0), dims - 1);
+    s.lo0[a] = kl;
+    s.nlo[a] = dims - kl;
+  }
+  if (B >= P.box_hi[a]) {
+    const int ku = min(max((int)floor((B - len - g.lo[a]) * g.invL), 0), dims - 1);
+    s.nu[a] = ku + 1;
+  }
+}
+
+template <typename T, bool REL>
+__device__ __forceinline__ StagerP<T> make_stager_periodic(const Box<T> &b, T R, const Grid &g,
+                                                           const KParams &P, int rx, int ry,
+                                                           int rz) {
+  StagerP<T> s;
+  periodic_runs<T, REL>(s, 0, b.x0, b.x1, R, g, P, rx);
+  periodic_runs<T, REL>(s, 1, b.y0, b.y1, R, g, P, ry);
+  periodic_runs<T, REL>(s, 2, b.z0, b.z1, R, g, P, rz);
+  const long long n0 = s.nlo[0] + s.nm[0] + s.nu[0], n1 = s.nlo[1] + s.nm[1] + s.nu[1],
+                  n2 = s.nlo[2] + s.nm[2] + s.nu[2];
+  const long long nc = n0 * n1 * n2;
+  s.nx = (int)n0;
+  s.ny = (int)n1;
+  s.ncell = nc > 0x7fffffffLL ? 0x7fffffff : (int)nc;
+  s.c0 = 0;
+  s.s0 = 0;
+  s.pre = 0;
+  s.ox = s.oy = s.oz = T(0);
+  s.total = 0;
+  s.pos = 0;
+  return s;
+}
+
+// Position v of axis a's runs: the cell and its shift in box lengths.
+template <typename T>
+__device__ __forceinline__ int periodic_cell(const StagerP<T> &s, int a, int v, int &shift) {
+  if (v < s.nlo[a]) {
+    shift = -1;
+    return s.lo0[a] + v;
+  }
+  v -= s.nlo[a];
+  if (v < s.nm[a]) {
+    shift = 0;
+    return s.m0[a] + v;
+  }
+  shift = 1;
+  return v - s.nm[a];
+}
+
+// The candidate's coordinate offset for cell k of axis a at `shift` box
+// lengths. REL: the unshifted offset is mul_rn(k - r, L) as for a closed
+// box (and as rel_coord forms the lane's own coordinate); a shifted one is
+// formed in FP64 and rounded once, so that its error is that of a small
+// offset, not of a box length. Absolute frame: the shift alone.
+template <typename T, bool REL>
+__device__ __forceinline__ T periodic_offset(int k, int r, int shift, T Lt, const Grid &g,
+                                             double len) {
+  if (REL) {
+    if (shift == 0) return mul_rn((T)(k - r), Lt);
+    return (T)((double)(k - r) * g.L + (double)shift * len);
+  }
+  return shift == 0 ? T(0) : (T)((double)shift * len);
+}
+
+// As stager_chunk for a closed box, over the periodic runs.
+template <typename T, bool REL>
+__device__ __forceinline__ bool stager_chunk(StagerP<T> &s, const Grid &g, const int *cstart,
+                                             const int *cend, T Lt, const KParams &P, int rx,
+                                             int ry, int rz, int &j, bool &ok, T &ox, T &oy,
+                                             T &oz) {
+  const int lane = threadIdx.x & 31;
+  while (s.pos >= s.total) {
+    if (s.c0 >= s.ncell) return false;
+    const int c = s.c0 + lane;
+    int cnt = 0, st = 0;
+    T cx = T(0), cy = T(0), cz = T(0);
+    if (c < s.ncell) {
+      const int vx = c % s.nx, t = c / s.nx;
+      const int vy = t % s.ny, vz = t / s.ny;
+      int shx, shy, shz;
+      const int gx = periodic_cell(s, 0, vx, shx);
+      const int gy = periodic_cell(s, 1, vy, shy);
+      const int gz = periodic_cell(s, 2, vz, shz);
+      const int cell = g.cell_off + (gz * g.dims[1] + gy) * g.dims[0] + gx;
+      st = cstart[cell];
+      if (st >= 0) cnt = cend[cell] - st;
+      cx = periodic_offset<T, REL>(gx, rx, shx, Lt, g, P.box_len[0]);
+      cy = periodic_offset<T, REL>(gy, ry, shy, Lt, g, P.box_len[1]);
+      cz = periodic_offset<T, REL>(gz, rz, shz, Lt, g, P.box_len[2]);
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += v;
+    }
+    s.s0 = st;
+    s.pre = inc - cnt;
+    s.ox = cx;
+    s.oy = cy;
+    s.oz = cz;
+    s.total = __shfl_sync(kFull, inc, 31);
+    s.pos = 0;
+    s.c0 += 32;
+  }
+  const int k = s.pos + lane;
+  ok = k < s.total;
+  int own = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = own + step;
+    const int pc = __shfl_sync(kFull, s.pre, cand & 31);
+    if (cand < 32 && pc <= k) own = cand;
+  }
+  const int p0 = __shfl_sync(kFull, s.pre, own);
+  j = __shfl_sync(kFull, s.s0, own) + (k - p0);
+  ox = __shfl_sync(kFull, s.ox, own);
+  oy = __shfl_sync(kFull, s.oy, own);
+  oz = __shfl_sync(kFull, s.oz, own);
+  s.pos += 32;
+  return true;
+}
+
+// One stager type per box kind, so that the closed-box kernels are
+// unchanged.
+template <typename T, bool PER> struct StagerOf {
+  using type = Stager;
+};
+template <typename T> struct StagerOf<T, true> {
+  using type = StagerP<T>;
+};
+template <typename T, bool REL, bool PER>
+__device__ __forceinline__ typename StagerOf<T, PER>::type make_stager_for(
+    const Box<T> &b, T R, const Grid &g, T invL, const KParams &P, int rx, int ry, int rz) {
+  if constexpr (PER)
+    return make_stager_periodic<T, REL>(b, R, g, P, rx, ry, rz);
+  else
+    return make_stager<T, REL>(b, R, g, invL, rx, ry, rz);
+}
+template <typename T, bool REL>
+__device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int *cstart,
+                                             const int *cend, T Lt, const KParams &, int rx,
+                                             int ry, int rz, int &j, bool &ok, T &ox, T &oy,
+                                             T &oz) {
+  return stager_chunk<T, REL>(s, g, cstart, cend, Lt, rx, ry, rz, j, ok, ox, oy, oz);
+}
+
+// FP64 squared distance of the neighbour predicate in a periodic box: the
+// minimum image along every axis, then the canonical sum.
+__device__ __forceinline__ double r2_canon_periodic(double dx, double dy, double dz,
+                                                    const double *len) {
+  return r2_canon(min_image(dx, len[0]), min_image(dy, len[1]), min_image(dz, len[2]));
+}
+
 }  // namespace sphk

@@ -119,7 +119,7 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_mlp_set", "sph_mlp_get", "sph_mlp_fit_norm", "sph_mlp_forward",
            "sph_mlp_loss_grad", "sph_mlp_adam_step", "sph_mlp_train_epoch",
            "sph_set_learned_h", "sph_learn_samples", "sph_check_conversions",
-           "sph_measure_fma_peak")
+           "sph_measure_fma_peak", "sph_inject_cuda_failure", "sph_learn_proposal")
 MLP_NPARAM, MLP_NNORM = 4673, 14
 GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
@@ -204,6 +204,10 @@ def lib():
         L.sph_set_graph.argtypes = [VP, C.c_int32]
         L.sph_diagnostics_noalloc.restype = st
         L.sph_diagnostics_noalloc.argtypes = [C.POINTER(SphState), C.c_int64, VP, VP]
+        L.sph_learn_proposal.restype = st
+        L.sph_learn_proposal.argtypes = [VP, VP]
+        L.sph_inject_cuda_failure.restype = st
+        L.sph_inject_cuda_failure.argtypes = [VP, C.c_int32]
         L.sph_status_string.restype = C.c_char_p
         L.sph_status_string.argtypes = [st]
         L.sph_last_error.restype = C.c_char_p
@@ -374,6 +378,15 @@ class Simulation:
         self.stream.synchronize()
         return X, y
 
+    def learn_proposal(self):
+        """Starting radii proposed for the next solve, in the current
+        (sorted) particle order, as a torch tensor."""
+        h = self.torch.zeros(self.n, dtype=self.torch.float64, device=self.device)
+        self._check(lib().sph_learn_proposal(self.ctx, C.c_void_p(h.data_ptr())),
+                    "sph_learn_proposal")
+        self.stream.synchronize()
+        return h
+
     def set_spans(self, span_density: int, span_forces: int):
         return self._check(lib().sph_set_spans(self.ctx, int(span_density), int(span_forces)),
                            "sph_set_spans")
@@ -397,6 +410,12 @@ class Simulation:
         d = info.as_dict()
         d.update(bytes_in=bi.value, bytes_out=bo.value)
         return d
+
+    def inject_cuda_failure(self, after: int = 1):
+        """Report the after-th checked CUDA call of this context as failed
+        (host-side fault injection for tests of the error paths)."""
+        return self._check(lib().sph_inject_cuda_failure(self.ctx, int(after)),
+                           "sph_inject_cuda_failure")
 
     def set_timing(self, on: bool = True):
         return self._check(lib().sph_set_timing(self.ctx, 1 if on else 0), "sph_set_timing")

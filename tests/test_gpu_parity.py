@@ -128,10 +128,10 @@ def test_full_steps_granular_column(precision):
         if k in (0, nsteps - 1):
             g = sim.by_id()
             rel = np.abs(g["rho"] - ref_state["rho"]) / ref_state["rho"]
-            assert rel.max() < 10 * RHO_TOL[precision], (k, rel.max())
+            assert rel.max() < RHO_TOL[precision], (k, rel.max())
             for f in DERIVS:
                 e = _maxnorm_err(g[f], ref_state[f])
-                assert e < max(DERIV_TOL[precision], 1e-6) * (1 if k == 0 else 10), (k, f, e)
+                assert e < DERIV_TOL[precision], (k, f, e)
             xg = np.stack([g[f] for f in ("x", "y", "z")])
             xr = np.stack([ref_state[f] for f in ("x", "y", "z")])
             disp = np.max(np.abs(xr - x0))
@@ -218,3 +218,37 @@ def test_standalone_density_evaluates_at_its_final_radius():
     rho, om, cnt = oracle.density_given_h(p, g)
     assert np.array_equal(cnt, g["nngb"])
     assert np.max(np.abs(g["rho"] / rho - 1)) < 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_strain_invariant_closed_form(precision):
+    """Eq. 43 on the GPU against its closed form: a force-free body (P = 0,
+    no viscosity, no strength) with v = A x0 + b keeps every velocity, so
+    after the k-th drift G_k = A (I + k dt A)^-1 exactly (correction
+    tensor) and eps_ii = sum_k dt 1/2 |sym(G_k)|^2."""
+    from tests.conftest import cloud
+    mat = wl.elastic_material()
+    mat.update(c0=0.0, A=0.0, strength=0)
+    a = cloud(1500, seed=31, jitter=0.25, spacing=1.0, mat=mat)
+    a["u"][:] = 0.0
+    A = np.array([[0.30, -0.45, 0.20], [0.15, -0.10, 0.35], [-0.25, 0.40, 0.05]])
+    x0 = np.stack([a["x"], a["y"], a["z"]], 1)
+    v = x0 @ A.T + np.array([0.7, -0.2, 0.4])
+    a["vx"], a["vy"], a["vz"] = v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+    p = dict(wl.default_params(precision), av_alpha=0.0, av_beta=0.0,
+             h_tol=1e-10 if precision == 0 else 1e-6)
+    dt, nsteps = 0.05, 4
+    sim = sph.Simulation(a, [mat], p)
+    info = sim.prime()
+    assert info["n_cfallback"] == 0
+    for _ in range(nsteps):
+        assert sim.step(dt)["n_cfallback"] == 0
+    g = sim.by_id()
+    sim.close()
+    want = 0.0
+    for k in range(1, nsteps + 1):
+        G = A @ np.linalg.inv(np.eye(3) + k * dt * A)
+        e = 0.5 * (G + G.T)
+        want += dt * 0.5 * float((e * e).sum())
+    err = np.max(np.abs(g["eps_ii"] / want - 1.0))
+    assert err < (1e-9 if precision == 0 else 1e-4), err
