@@ -130,7 +130,8 @@ void free_all(sph_ctx *c) {
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
                  c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->w.divv,
                  c->learn.hprev, c->learn.hprop, c->learn.feat[0], c->learn.feat[1],
-                 c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill, c->w.rung};
+                 c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill, c->w.rung,
+                 c->w.act, c->w.act_tiles};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -279,7 +280,7 @@ sph_status run_neighbours(sph_ctx *c, int drift, int all) {
   CK(launch_reset_status(c, 0));
   CK(launch_drift_bbox(c, drift));
   CK(launch_grid_setup(c));
-  CK(launch_sort_permute(c, all));
+  CK(launch_sort_permute(c, all, c->split_in ? 1 : 0));
   CK(mark(c, 1));
   return copy_out(c, 0);
 }
@@ -290,7 +291,9 @@ cudaError_t tmark(sph_ctx *c, int k) {
 }
 
 sph_status run_derivatives(sph_ctx *c, int predict) {
-  CK(launch_predict_pack(c, predict));
+  // split copy-in: the density solve needs only the positions; the
+  // predictor waits for the rest of the state
+  CK(launch_predict_pack(c, predict, c->split_in ? 2 : 3));
   CK(mark(c, 2));
   CK(tmark(c, 0));
   CK(launch_density(c, 1));   // the force pass that follows counts the neighbours
@@ -298,6 +301,11 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
   CK(mark(c, 3));
   sph_status s = copy_out(c, 1);
   if (s != SPH_OK) return s;
+  if (c->split_in) {
+    CK(cudaStreamWaitEvent(c->stream, c->in_ev, 0));
+    CK(launch_permute_rest(c));
+    CK(launch_predict_pack(c, predict, 1));
+  }
   CK(launch_eos_pack(c));
   CK(mark(c, 4));
   s = copy_out(c, 2);
@@ -326,10 +334,16 @@ sph_status enqueue_step(sph_ctx *c) {
     if (e != cudaSuccess) s = fail_cuda(c, e, "launch_rung_init");
   }
   const sph_state *out = c->host_out;
+  // one system: the pair kernels take buckets of active particles only
+  c->kp.act = L > 1 ? c->w.act : nullptr;
   for (int sub = 0; sub < L && s == SPH_OK; ++sub) {
     c->kp.substep = sub;
     c->host_out = sub == L - 1 ? out : nullptr;
     s = run_neighbours(c, 1, 0);
+    if (s == SPH_OK && c->kp.act) {
+      const cudaError_t e = launch_compact_active(c);
+      if (e != cudaSuccess) s = fail_cuda(c, e, "launch_compact_active");
+    }
     if (s == SPH_OK) s = run_derivatives(c, 1);
     if (s == SPH_OK) {
       const cudaError_t e = launch_kick(c, 1);
@@ -339,6 +353,7 @@ sph_status enqueue_step(sph_ctx *c) {
   c->kp.substep = 0;
   c->kp.max_rung = 0;
   c->kp.sub_scale = 1.0;
+  c->kp.act = nullptr;
   c->host_out = out;
   if (s != SPH_OK) return s;
   CK(mark(c, 6));
@@ -711,6 +726,10 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   if (p->max_rung > 0) {
     CKI(dalloc(&w.rung, n));
     CKI(cudaMemset(w.rung, 0, sizeof(int) * (size_t)n));
+    if (n_sys == 1) {   // active-particle list of every substep
+      CKI(dalloc(&w.act, n));
+      CKI(dalloc(&w.act_tiles, (n + 2047) / 2048));
+    }
   }
   kp.rung = w.rung;
   if (fp32) {
@@ -823,6 +842,12 @@ sph_status sph_destroy(sph_ctx *c) {
     cudaStreamSynchronize(c->cstream);
     cudaStreamDestroy(c->cstream);
   }
+  if (c->istream) {
+    cudaStreamSynchronize(c->istream);
+    cudaStreamDestroy(c->istream);
+  }
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->in_ev) cudaEventDestroy(c->in_ev);
   // handles that a failed set-up never created stay null and are skipped
   for (int k = 0; k < 5; ++k)
     if (c->out_ev[k]) cudaEventDestroy(c->out_ev[k]);
@@ -886,7 +911,7 @@ sph_status sph_neighbours(sph_ctx *c) {
 
 sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
   ENTER(c);
-  CK(launch_predict_pack(c, 0));
+  CK(launch_predict_pack(c, 0, 3));
   CK(launch_density(c, 0));   // standalone: every solve ends on an evaluation
   sph_step_info info;
   const sph_status s = sync_status(c, &info);
@@ -896,7 +921,7 @@ sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
 
 sph_status sph_forces_strength(sph_ctx *c) {
   ENTER(c);
-  CK(launch_predict_pack(c, 0));
+  CK(launch_predict_pack(c, 0, 3));
   CK(launch_eos_pack(c));
   CK(launch_forces(c));
   return SPH_OK;
@@ -1044,22 +1069,40 @@ sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_
     CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
     for (int k = 0; k < 5; ++k) CK(cudaEventCreateWithFlags(&c->out_ev[k], cudaEventDisableTiming));
   }
+  if (!c->istream) {
+    CK(cudaStreamCreateWithFlags(&c->istream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming));
+  }
   const sph_state &d = c->st;
   const int64_t n = c->n;
-  // in: everything the step reads before writing it (rho, Omega, P, c_s and
-  // the counts are recomputed in the step, so they stay on the host)
-  double *const hd[24] = {host->x,    host->y,    host->z,    host->vx,   host->vy,   host->vz,
-                          host->u,    host->m,    host->h,    host->sxx,  host->syy,  host->sxy,
-                          host->sxz,  host->syz,  host->ax,   host->ay,   host->az,   host->dudt,
-                          host->dsxx, host->dsyy, host->dsxy, host->dsxz, host->dsyz, host->eps_ii};
-  double *const dd[24] = {d.x,   d.y,    d.z,    d.vx,   d.vy,   d.vz,   d.u,    d.m,
-                          d.h,   d.sxx,  d.syy,  d.sxy,  d.sxz,  d.syz,  d.ax,   d.ay,
-                          d.az,  d.dudt, d.dsxx, d.dsyy, d.dsxy, d.dsxz, d.dsyz, d.eps_ii};
   const size_t b8 = sizeof(double) * (size_t)n, b4 = sizeof(int32_t) * (size_t)n;
-  for (int k = 0; k < 24; ++k) CK(cudaMemcpyAsync(dd[k], hd[k], b8, cudaMemcpyHostToDevice, c->stream));
+  // in: everything the step reads before writing it (rho, Omega, P, c_s and
+  // the counts are recomputed in the step, so they stay on the host). First,
+  // on the context's stream, what the drift, the sort and the density solve
+  // read; then, on the input stream once those copies are done, the rest,
+  // which arrives while the sort and the density solve run (with
+  // hierarchical steps every substep needs the whole state: one stream)
+  double *const ha[8] = {host->x, host->y, host->z, host->vx, host->vy, host->vz, host->m, host->h};
+  double *const da[8] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.m, d.h};
+  double *const hb[16] = {host->u,    host->sxx,  host->syy,  host->sxy,  host->sxz,  host->syz,
+                          host->ax,   host->ay,   host->az,   host->dudt, host->dsxx, host->dsyy,
+                          host->dsxy, host->dsxz, host->dsyz, host->eps_ii};
+  double *const db[16] = {d.u,    d.sxx,  d.syy,  d.sxy,  d.sxz,  d.syz,  d.ax,   d.ay,
+                          d.az,   d.dudt, d.dsxx, d.dsyy, d.dsxy, d.dsxz, d.dsyz, d.eps_ii};
+  const int split = c->rungs == 0;
+  for (int k = 0; k < 8; ++k) CK(cudaMemcpyAsync(da[k], ha[k], b8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.id, host->id, b8, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.mat, host->mat, b4, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.flags, host->flags, b4, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(d.id, host->id, b8, cudaMemcpyHostToDevice, c->stream));
+  cudaStream_t bs = c->stream;
+  if (split) {
+    CK(cudaEventRecord(c->ev_a, c->stream));
+    CK(cudaStreamWaitEvent(c->istream, c->ev_a, 0));
+    bs = c->istream;
+  }
+  for (int k = 0; k < 16; ++k) CK(cudaMemcpyAsync(db[k], hb[k], b8, cudaMemcpyHostToDevice, bs));
+  if (split) CK(cudaEventRecord(c->in_ev, c->istream));
   int64_t in = 25 * (int64_t)b8 + 2 * (int64_t)b4;
   if (c->rungs > 0) {   // particles between their steps keep H, rho, Omega and their count
     CK(cudaMemcpyAsync(d.rho, host->rho, b8, cudaMemcpyHostToDevice, c->stream));
@@ -1070,11 +1113,17 @@ sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_
   // out: each array group as soon as the step has finished it, on the copy
   // stream (direct launches: the captured graph has no copy-out)
   c->host_out = host;
+  c->split_in = split;
   const int graph = c->use_graph;
   c->use_graph = 0;
   const sph_status s = sph_step(c, dt, info);
   c->use_graph = graph;
   c->host_out = nullptr;
+  c->split_in = 0;
+  // the input stream is idle once the step has waited for it; if the step
+  // stopped early it may still be copying
+  const cudaError_t ei = cudaStreamSynchronize(c->istream);
+  if (ei != cudaSuccess) return fail_cuda(c, ei, "copy-in");
   const cudaError_t e = cudaStreamSynchronize(c->cstream);
   if (e != cudaSuccess) return fail_cuda(c, e, "copy-out");
   if (bytes_in) *bytes_in = in;

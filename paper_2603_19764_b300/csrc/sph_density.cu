@@ -23,26 +23,31 @@ namespace sphk {
 
 // Evaluation state and position packing. predict = 1: v, u, S at i from
 // the half-step values and the derivatives at i-1 (Eq. 40); predict = 0:
-// the state as it stands.
+// the state as it stands. parts: bit 0 the evaluation state, bit 1 the
+// packed positions (both in one pass, except where sph_step_host's split
+// copy-in packs the positions before the rest of the state has arrived).
 __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, int64_t n, KParams P,
-                                                        int predict, int fp32) {
+                                                        int predict, int fp32, int parts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
     const Grid &g = P.sys[sy].grid;
-    const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
-    // offset from the half step: dt / 2, or with rungs the time from the
-    // midpoint of the particle's own step to the end of this substep
-    const double k = (fixed || !predict) ? 0.0 : predict_offset(P, i, P.dt[sy] * P.sub_scale);
-    w.vp[0][i] = s.vx[i] + k * s.ax[i];
-    w.vp[1][i] = s.vy[i] + k * s.ay[i];
-    w.vp[2][i] = s.vz[i] + k * s.az[i];
-    w.up[i] = s.u[i] + k * s.dudt[i];
-    w.sp[0][i] = s.sxx[i] + k * s.dsxx[i];
-    w.sp[1][i] = s.syy[i] + k * s.dsyy[i];
-    w.sp[2][i] = s.sxy[i] + k * s.dsxy[i];
-    w.sp[3][i] = s.sxz[i] + k * s.dsxz[i];
-    w.sp[4][i] = s.syz[i] + k * s.dsyz[i];
+    if (parts & 1) {
+      const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
+      // offset from the half step: dt / 2, or with rungs the time from the
+      // midpoint of the particle's own step to the end of this substep
+      const double k = (fixed || !predict) ? 0.0 : predict_offset(P, i, P.dt[sy] * P.sub_scale);
+      w.vp[0][i] = s.vx[i] + k * s.ax[i];
+      w.vp[1][i] = s.vy[i] + k * s.ay[i];
+      w.vp[2][i] = s.vz[i] + k * s.az[i];
+      w.up[i] = s.u[i] + k * s.dudt[i];
+      w.sp[0][i] = s.sxx[i] + k * s.dsxx[i];
+      w.sp[1][i] = s.syy[i] + k * s.dsyy[i];
+      w.sp[2][i] = s.sxy[i] + k * s.dsxy[i];
+      w.sp[3][i] = s.sxz[i] + k * s.dsxz[i];
+      w.sp[4][i] = s.syz[i] + k * s.dsyz[i];
+    }
+    if (!(parts & 2)) continue;
     const double x = s.x[i], y = s.y[i], z = s.z[i], m = s.m[i];
     if (fp32) {
       const int c = w.cc[i];
@@ -56,11 +61,11 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
   }
 }
 
-cudaError_t launch_predict_pack(sph_ctx *c, int predict) {
+cudaError_t launch_predict_pack(sph_ctx *c, int predict, int parts) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
   k_predict_pack<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp, predict,
-                                                  c->kp.precision == SPH_FP32K);
+                                                  c->kp.precision == SPH_FP32K, parts);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -118,22 +123,27 @@ template <> struct PosPtr<double> {
 };
 
 
-// Candidate list layout: paired in the FP32 form (packed mask tests), one
-// record per candidate in the FP64 form.
+// Candidate list layout over a buffer of S candidates: planes in the FP32
+// form (packed mask tests, bank-spread walk reads), one record per
+// candidate in the FP64 form.
 template <typename T> struct DList;
 template <> struct DList<float> {
-  using slot = F2Slot;
-  using store = CandPaired;
+  template <int S> using view = ViewPlanes<S>;
+  template <int S> static __device__ __forceinline__ ViewPlanes<S> at(void *p) {
+    return ViewPlanes<S>{reinterpret_cast<float *>(p)};
+  }
 };
 template <> struct DList<double> {
-  using slot = double4_32a;
-  using store = CandAoS<double4_32a>;
+  template <int S> using view = ViewAoS<double4_32a>;
+  template <int S> static __device__ __forceinline__ ViewAoS<double4_32a> at(void *p) {
+    return ViewAoS<double4_32a>{reinterpret_cast<double4_32a *>(p)};
+  }
 };
 
 // Per-lane bit masks over the staged list: bit k set when r_k^2 < R2.
 // Lanes with store = false compute but keep their previous words.
-template <typename T>
-__device__ __forceinline__ void build_masks(const typename DList<T>::slot *Lp, unsigned (*Lm)[32],
+template <typename T, typename LV>
+__device__ __forceinline__ void build_masks(const LV &Lp, unsigned (*Lm)[32],
                                             int nl, T xi, T yi, T zi, T R2, bool store, int lane) {
   const int nw = (nl + 31) >> 5;
   for (int wd = 0; wd < nw; ++wd) {
@@ -146,8 +156,8 @@ __device__ __forceinline__ void build_masks(const typename DList<T>::slot *Lp, u
 
 // Walk one lane's marked candidates: exact membership r < H_i, then the
 // kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
-template <typename T, bool REL, bool PER>
-__device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, const int *Li,
+template <typename T, bool REL, bool PER, typename LV>
+__device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
                                              unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              T gb, T H, double xi64, double yi64, double zi64,
@@ -165,7 +175,7 @@ __device__ __forceinline__ void density_walk(const typename DList<T>::slot *Lp, 
       const int k = (wd << 5) + __ffs(mk) - 1;
       mk &= mk - 1u;
       T qx, qy, qz, qm;
-      DList<T>::store::get(Lp, k, qx, qy, qz, qm);
+      Lp.get(k, qx, qy, qz, qm);
       const T dx = xi - qx, dy = yi - qy, dz = zi - qz;
       T r2;
       bool in;
@@ -217,15 +227,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   __shared__ int s_idx[kWarpsPerBlock][CAP];
   __shared__ unsigned s_mask[kWarpsPerBlock][CAP / 32][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  using Slot = typename DList<T>::slot;
-  Slot *Lp = reinterpret_cast<Slot *>(s_pos[wib]);   // same bytes: 32 per two FP32 candidates
+  // the list in this warp's shared buffer, and its overflow in global memory
+  const auto Lp = DList<T>::template at<CAP>(s_pos[wib]);
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
   const SpillView<V4> Sv0 = spill_view<V4>(A.spill, blockIdx.x * kWarpsPerBlock + wib);
-  const SpillView<Slot> Sv = {reinterpret_cast<Slot *>(Sv0.p), Sv0.i, Sv0.m};
+  const auto Sp = DList<T>::template at<kSpill>(Sv0.p);
+  struct {
+    int *i;
+    unsigned (*m)[32];
+  } const Sv = {Sv0.i, Sv0.m};
   constexpr int TCAP = CAP + kSpill;
   // persistent warps: each takes the next bucket of 32 particles
-  const int nbuckets = A.p.nbuckets;
+  const int n_act = A.p.act ? A.st->n_active : 0;
+  const int nbuckets = bucket_count(A.p, n_act);
   long long w_pairs = 0, w_cand = 0;
   int w_sw = 0, w_nu = 0, w_ncap = 0, w_groups = 0, w_exp = 0;
   long long w_swt = 0;
@@ -238,15 +253,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   bk = __shfl_sync(kFull, bk, 0);
   if ((int)bk >= nbuckets) break;
   // the bucket's system and its sorted range
-  const int sy = A.p.nsys > 1 ? sys_lookup(A.p.sys_bucket, A.p.nsys, bk) : 0;
+  const BucketLane bl = bucket_lane(A.p, n_act, bk, lane);
+  const int sy = bl.sy;
   const SysRec &R = A.p.sys[sy];
-  const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
-  const int64_t i = base + lane;
-  const bool valid = i < R.end;
+  const int64_t i = bl.i;
+  const bool valid = bl.valid;
   // with hierarchical steps only particles whose step ends are solved; the
   // others keep H, rho, Omega and their count
   const bool solve = valid && rung_active(A.p, i);
-  const int64_t ic = valid ? i : base;
+  const int64_t ic = bl.ic;
   const V4 *pos = PosPtr<T>::get(A.w);
 
   const Grid g = R.grid;
@@ -328,10 +343,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
             if (keep) {
               const int at = nl + __popc(bal & lanemask_lt());
               if (at < CAP) {
-                DList<T>::store::put(Lp, at, xj, yj, zj, q.w);
+                Lp.put(at, xj, yj, zj, q.w);
                 Li[at] = j;
               } else {
-                DList<T>::store::put(Sv.p, at - CAP, xj, yj, zj, q.w);
+                Sp.put(at - CAP, xj, yj, zj, q.w);
                 Sv.i[at - CAP] = j;
               }
             }
@@ -346,13 +361,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           const int n1 = min(nl, CAP), n2 = nl - n1;
           __syncwarp();
           build_masks<T>(Lp, Lm, n1, xi, yi, zi, Hq * Hq, act, lane);
-          build_masks<T>(Sv.p, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
+          build_masks<T>(Sp, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
           __syncwarp();
           if (act) {
             density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                           yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
                                           cnt);
-            density_walk<T, REL, PER>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
+            density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
                                           xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
                                           rhs2, cnt);
           }
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           const T Hn = rebuild ? tmax(Ht * T(1.02), Hq) : Hm;
           __syncwarp();
           build_masks<T>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
-          build_masks<T>(Sv.p, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
+          build_masks<T>(Sp, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
           __syncwarp();
           Hm = Hn;
         }
@@ -376,7 +391,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                         yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
                                         cnt);
-          density_walk<T, REL, PER>(Sv.p, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
+          density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
                                         xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
                                         rhs2, cnt);
         }

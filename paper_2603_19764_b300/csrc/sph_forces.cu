@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
   // persistent warps: each takes the next bucket of 32 particles
-  const int nbuckets = A.p.nbuckets;
+  const int n_act = A.p.act ? A.st->n_active : 0;
+  const int nbuckets = bucket_count(A.p, n_act);
   long long w_pairs = 0, w_cand = 0;
   int w_fb = 0, w_groups = 0;
   unsigned w_box = 0;
@@ -179,13 +180,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   bk = __shfl_sync(kFull, bk, 0);
   if ((int)bk >= nbuckets) break;
   // the bucket's system and its sorted range
-  const int sy = A.p.nsys > 1 ? sys_lookup(A.p.sys_bucket, A.p.nsys, bk) : 0;
+  const BucketLane bl = bucket_lane(A.p, n_act, bk, lane);
+  const int sy = bl.sy;
   const SysRec &R = A.p.sys[sy];
-  const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
-  const int64_t i = base + lane;
+  const int64_t i = bl.i;
   // with hierarchical steps only particles whose step ends get derivatives
-  const bool valid = i < R.end && rung_active(A.p, i);
-  const int64_t ic = valid ? i : base;
+  const bool valid = bl.valid && rung_active(A.p, i);
+  const int64_t ic = bl.ic;
   const V4 *posh = PK::posh(A.w);
   const V4 *rec = PK::rec(A.w);   // 4 consecutive vectors per particle
 

@@ -224,6 +224,10 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, K
       L = INFINITY;
       atomicOr(&st->err, ERR_NONFINITE);
     }
+    // the force pass's search radius covers the largest H: the density
+    // solve raises it for the particles it solves; when it solves only the
+    // active list, everyone else's H must be in it from the start
+    if (P.act) r.hmax2_enc = r.hmax_enc;
     Grid &g = r.grid;
     for (int a = 0; a < 3; ++a) {
       g.lo[a] = lo[a];
@@ -409,16 +413,25 @@ struct PermTable {
   int ni32;   // 4-byte fields in use
 };
 
+// part 0: every array a step permutes; part 1 (the copy-in of
+// sph_step_host is split in two): what the drift, the sort and the density
+// solve read -- positions, velocities, H, masses, ids, materials, flags and
+// the library's per-particle arrays; part 2: the rest -- u, S, the
+// derivatives at i-1 and the strain invariant, which only the predictor and
+// the kicks read.
 static PermTable perm_table(const sph_state &s, const Work &w, const LearnArgs &L, bool all,
-                            bool rungs) {
+                            bool rungs, int part = 0) {
   PermTable t;
   t.nf64 = 0;
-  double *d[24] = {s.x,   s.y,    s.z,    s.vx,   s.vy,   s.vz,   s.u,    s.m,
-                   s.h,   s.sxx,  s.syy,  s.sxy,  s.sxz,  s.syz,  s.ax,   s.ay,
-                   s.az,  s.dudt, s.dsxx, s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
-  for (int k = 0; k < 24; ++k) t.f64[t.nf64++] = (unsigned long long *)d[k];
-  t.f64[t.nf64++] = (unsigned long long *)s.id;
   t.ni32 = 0;
+  double *a[8] = {s.x, s.y, s.z, s.vx, s.vy, s.vz, s.m, s.h};
+  double *b[16] = {s.u,    s.sxx,  s.syy,  s.sxy,  s.sxz,  s.syz,  s.ax,   s.ay,
+                   s.az,   s.dudt, s.dsxx, s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
+  if (part != 1)
+    for (int k = 0; k < 16; ++k) t.f64[t.nf64++] = (unsigned long long *)b[k];
+  if (part == 2) return t;
+  for (int k = 0; k < 8; ++k) t.f64[t.nf64++] = (unsigned long long *)a[k];
+  t.f64[t.nf64++] = (unsigned long long *)s.id;
   t.i32[t.ni32++] = (unsigned *)s.mat;
   t.i32[t.ni32++] = (unsigned *)s.flags;
   // rho, Omega and the counts are recomputed in a step only for the
@@ -498,7 +511,23 @@ static int grid_for(int64_t n, int block) {
   return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_sort_permute(sph_ctx *c, int all) {
+// Gather and copy back the arrays of one part of the permutation table
+// through the last sort's permutation (c->vals).
+static void enqueue_permute(sph_ctx *c, const PermTable &t) {
+  const int64_t n = c->n;
+  const int gb = grid_for(n, kBlock);
+  unsigned long long *tmp = (unsigned long long *)c->tmp;
+  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
+  k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
+  c->nlaunch += 2;
+}
+
+cudaError_t launch_permute_rest(sph_ctx *c) {
+  enqueue_permute(c, perm_table(c->st, c->w, c->learn, false, false, 2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_permute(sph_ctx *c, int all, int part) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
   k_keys<<<gb, kBlock, 0, c->stream>>>(c->st, n, c->kp, c->keys, c->vals);
@@ -521,14 +550,11 @@ cudaError_t launch_sort_permute(sph_ctx *c, int all) {
     vb = tv;
   }
   // after four passes the sorted pairs are back in keys / vals
-  PermTable t = perm_table(c->st, c->w, c->learn, all != 0, c->kp.max_rung > 0);
-  unsigned long long *tmp = (unsigned long long *)c->tmp;
-  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
-  k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
+  enqueue_permute(c, perm_table(c->st, c->w, c->learn, all != 0, c->kp.max_rung > 0, part));
   k_clear_cells<<<grid_for(c->max_cells, kBlock), kBlock, 0, c->stream>>>(c->cell_start,
                                                                           c->d_status);
   k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->kp, c->cell_start, c->cell_end, c->w.cc);
-  c->nlaunch += 1 + 4 * 5 + 4;   // keys, four radix passes, permutation, cells
+  c->nlaunch += 1 + 4 * 5 + 2;   // keys, four radix passes, cells (permutation counted above)
   return cudaGetLastError();
 }
 

@@ -74,7 +74,10 @@ struct Status {
   int pad2_;
   unsigned long long updates;                   // particles kicked in the step
   int rung_hist[16];                            // rungs of the moving particles at its end
+  int n_active;                                 // entries of KParams::act this substep
+  int pad4_;
 };
+
 
 
 
@@ -127,6 +130,11 @@ struct KParams {
   int max_rung, substep;
   double sub_scale;            // 2^-max_rung (exact)
   const int *rung;             // per particle (sorted order), or null
+  // hierarchical steps of one system: the sorted positions of the particles
+  // active in the current substep, in sorted order (Status::n_active of
+  // them); the pair kernels take their buckets from this list. Null: the
+  // buckets are 32 consecutive sorted positions and inactive lanes idle.
+  const int *act;
   // periodic box [box_lo, box_hi) on every axis (one system only): drifted
   // positions wrap into it, the cell grid tiles it from box_lo, and pairs
   // take the minimum image
@@ -191,6 +199,38 @@ __device__ __forceinline__ int sys_lookup(const int *bounds, int nsys, int64_t v
   return lo;
 }
 
+// Lane `lane` of bucket bk of a pair kernel: its sorted position i (valid
+// lanes only), a position safe to read for every lane (ic), and the system.
+// From the active list when there is one (n_act entries), else 32
+// consecutive positions of the bucket's system.
+struct BucketLane {
+  int64_t i, ic;
+  bool valid;
+  int sy;
+};
+__device__ __forceinline__ int bucket_count(const KParams &P, int n_act) {
+  return P.act ? (n_act + 31) >> 5 : P.nbuckets;
+}
+__device__ __forceinline__ BucketLane bucket_lane(const KParams &P, int n_act, unsigned bk,
+                                                  int lane) {
+  BucketLane b;
+  if (P.act) {
+    const int k = (int)bk * 32 + lane;
+    b.valid = k < n_act;
+    b.i = P.act[b.valid ? k : (int)bk * 32];
+    b.ic = b.i;
+    b.sy = 0;
+    return b;
+  }
+  b.sy = P.nsys > 1 ? sys_lookup(P.sys_bucket, P.nsys, bk) : 0;
+  const SysRec &R = P.sys[b.sy];
+  const int64_t base = R.begin + (int64_t)(bk - R.bucket_off) * 32;
+  b.i = base + lane;
+  b.valid = b.i < R.end;
+  b.ic = b.valid ? b.i : base;
+  return b;
+}
+
 template <typename T> __device__ __forceinline__ const MatT<T> &mat_t(const KParams &P, int k);
 template <> __device__ __forceinline__ const MatT<float> &mat_t<float>(const KParams &P, int k) {
   return P.matf[k & (SPH_MAX_MATERIALS - 1)];
@@ -244,6 +284,8 @@ struct Work {
   double4_32a *fs64[3];
   float *divv;                  // tr of the corrected velocity gradient (learned form)
   int *rung;                    // hierarchical steps: rung of every particle, or null
+  int *act;                     // hierarchical steps of one system: active list (n)
+  int *act_tiles;               // and its per-tile counts / offsets
 };
 
 // Arrays of the learned form. hprev, hprop and feat are per-particle
@@ -543,6 +585,13 @@ struct sph_ctx {
   int rungs;                    // sph_params.max_rung
   cudaStream_t cstream;
   cudaEvent_t out_ev[5];
+  // sph_step_host's split copy-in: the arrays the sort and the density
+  // solve read come first on the context's stream; the rest follow on
+  // istream (after ev_a) while those kernels run, and in_ev marks their
+  // arrival (split_in: the step waits for it before the predictor)
+  cudaStream_t istream;
+  cudaEvent_t ev_a, in_ev;
+  int split_in;
   cudaGraphExec_t graph_exec;   // captured step
   cudaEvent_t ev[SPH_NUM_PHASES + 1];
   // online tuning of the group spans over the coming steps
@@ -580,15 +629,21 @@ template <typename K> inline int resident_grid(const sph_ctx *c, K kernel) {
 namespace sphk {
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift);
 cudaError_t launch_grid_setup(sph_ctx *c);
-// all = 0: leave out the arrays a step recomputes before reading them
-cudaError_t launch_sort_permute(sph_ctx *c, int all);
-cudaError_t launch_predict_pack(sph_ctx *c, int predict);
+// all = 0: leave out the arrays a step recomputes before reading them;
+// part 1: only what the drift, sort and density solve read (the rest
+// follows with launch_permute_rest once it has been copied in)
+cudaError_t launch_sort_permute(sph_ctx *c, int all, int part);
+cudaError_t launch_permute_rest(sph_ctx *c);
+// parts: bit 0 the evaluation (predicted) state, bit 1 the packed positions
+cudaError_t launch_predict_pack(sph_ctx *c, int predict, int parts);
 cudaError_t launch_density(sph_ctx *c, int expand);
 cudaError_t launch_eos_pack(sph_ctx *c);
 cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_kick(sph_ctx *c, int kick);
 cudaError_t launch_reset_status(sph_ctx *c, int full);
 cudaError_t launch_rung_init(sph_ctx *c);
+// hierarchical steps: the list of the substep's active particles (KParams::act)
+cudaError_t launch_compact_active(sph_ctx *c);
 cudaError_t launch_learn(sph_ctx *c);
 cudaError_t alloc_density_spill(sph_ctx *c);
 }  // namespace sphk

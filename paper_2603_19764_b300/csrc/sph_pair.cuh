@@ -180,6 +180,45 @@ struct CandPaired {
   }
 };
 
+// List views with the staging and walking interface of the density kernel
+// (put / get of candidate k), over a buffer of S candidates:
+// * ViewAoS: one 4-vector per candidate (the FP64 form).
+// * ViewPlanes (FP32): x, y, z and w of candidate k in four planes of S
+//   floats, so that a lane reading one candidate hits bank k mod 32 of
+//   each plane (32 banks across the lanes of a walk, where the paired
+//   layout reached 8), staging writes are consecutive, and the packed mask
+//   test reads the x (y, z) of four candidates with one 16-byte load.
+template <typename V4> struct ViewAoS {
+  V4 *p;
+  template <typename T>
+  __device__ __forceinline__ void put(int k, T x, T y, T z, T w) const {
+    p[k] = V4T<T>::make(x, y, z, w);
+  }
+  template <typename T>
+  __device__ __forceinline__ void get(int k, T &x, T &y, T &z, T &w) const {
+    const V4 q = p[k];
+    x = q.x;
+    y = q.y;
+    z = q.z;
+    w = q.w;
+  }
+};
+template <int S> struct ViewPlanes {
+  float *p;
+  __device__ __forceinline__ void put(int k, float x, float y, float z, float w) const {
+    p[k] = x;
+    p[S + k] = y;
+    p[2 * S + k] = z;
+    p[3 * S + k] = w;
+  }
+  __device__ __forceinline__ void get(int k, float &x, float &y, float &z, float &w) const {
+    x = p[k];
+    y = p[S + k];
+    z = p[2 * S + k];
+    w = p[3 * S + k];
+  }
+};
+
 // One lane's membership word over staged candidates kb .. kb+31 (kb a
 // multiple of 32): bit b set when r^2 < thr(w) for candidate kb + b, for
 // b < count only. The paired form reads whole words, up to 31 slots past
@@ -215,6 +254,40 @@ __device__ __forceinline__ unsigned mask_word(const F2Slot *L, int kb, int count
     split(b.y, w0, w1);
     if (r0 < thr(w0)) mk |= 1u << (2 * m);
     if (r1 < thr(w1)) mk |= 2u << (2 * m);
+  }
+  return count < 32 ? mk & ((1u << count) - 1u) : mk;
+}
+
+template <typename V4, typename T, typename Thr>
+__device__ __forceinline__ unsigned mask_word(const ViewAoS<V4> &L, int kb, int count, T xi, T yi,
+                                              T zi, Thr thr) {
+  return mask_word(static_cast<const V4 *>(L.p), kb, count, xi, yi, zi, thr);
+}
+// Planes: reads whole 32-candidate words (S a multiple of 32), clearing the
+// bits past the list's end.
+template <int S, typename Thr>
+__device__ __forceinline__ unsigned mask_word(const ViewPlanes<S> &L, int kb, int count,
+                                              float xi, float yi, float zi, Thr thr) {
+  using namespace px;
+  const u64 X = dup(xi), Y = dup(yi), Z = dup(zi);
+  const ulonglong2 *PX = reinterpret_cast<const ulonglong2 *>(L.p + kb);
+  const ulonglong2 *PY = reinterpret_cast<const ulonglong2 *>(L.p + S + kb);
+  const ulonglong2 *PZ = reinterpret_cast<const ulonglong2 *>(L.p + 2 * S + kb);
+  const ulonglong2 *PW = reinterpret_cast<const ulonglong2 *>(L.p + 3 * S + kb);
+  unsigned mk = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const ulonglong2 a = PX[q], b = PY[q], c = PZ[q], w = PW[q];   // candidates 4q .. 4q+3
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const u64 dx = sub(X, h ? a.y : a.x), dy = sub(Y, h ? b.y : b.x), dz = sub(Z, h ? c.y : c.x);
+      const u64 r2 = fma(dz, dz, fma(dy, dy, mul(dx, dx)));
+      float r0, r1, w0, w1;
+      split(r2, r0, r1);
+      split(h ? w.y : w.x, w0, w1);
+      if (r0 < thr(w0)) mk |= 1u << (4 * q + 2 * h);
+      if (r1 < thr(w1)) mk |= 2u << (4 * q + 2 * h);
+    }
   }
   return count < 32 ? mk & ((1u << count) - 1u) : mk;
 }

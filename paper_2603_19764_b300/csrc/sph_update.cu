@@ -192,6 +192,92 @@ cudaError_t launch_rung_init(sph_ctx *c) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- active-particle list
+// Hierarchical steps of one system: the sorted positions of the particles
+// whose step ends with the current substep, in sorted (Morton) order, so
+// that 32 consecutive entries are a spatially compact bucket of active
+// particles. Three passes over tiles of kActTile particles: per-tile
+// counts, one exclusive scan of the counts (which also gives n_active),
+// and the stable scatter.
+constexpr int kActTile = 2048;
+
+__global__ void __launch_bounds__(kBlock) k_active_count(int64_t n, KParams P, int *tiles) {
+  __shared__ int wc[kBlock / 32];
+  const int64_t t0 = (int64_t)blockIdx.x * kActTile;
+  int c = 0;
+  for (int64_t i = t0 + threadIdx.x; i < n && i < t0 + kActTile; i += blockDim.x)
+    c += rung_active(P, i) ? 1 : 0;
+  c = wsum(c);
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int q = 0; q < kBlock / 32; ++q) t += wc[q];
+    tiles[blockIdx.x] = t;
+  }
+}
+
+// One block: exclusive scan of the tile counts in place, in chunks of
+// kBlock tiles, and the total into the status record.
+__global__ void __launch_bounds__(kBlock) k_active_scan(int *tiles, int ntiles, Status *st) {
+  __shared__ int wsums[kBlock / 32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < ntiles; b0 += kBlock) {
+    const int k = b0 + threadIdx.x;
+    const int v = k < ntiles ? tiles[k] : 0;
+    int inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += u;
+    }
+    if (lane == 31) wsums[w] = inc;
+    __syncthreads();
+    int before = carry;
+    for (int q = 0; q < w; ++q) before += wsums[q];
+    if (k < ntiles) tiles[k] = before + inc - v;
+    __syncthreads();
+    if (threadIdx.x == kBlock - 1) carry = before + inc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->n_active = carry;
+}
+
+__global__ void __launch_bounds__(kBlock) k_active_scatter(int64_t n, KParams P, const int *tiles,
+                                                          int *act) {
+  __shared__ int wc[kBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t t0 = (int64_t)blockIdx.x * kActTile;
+  int base = tiles[blockIdx.x];
+  // the tile in rounds of kBlock particles, each round in order
+  for (int64_t r0 = t0; r0 < n && r0 < t0 + kActTile; r0 += blockDim.x) {
+    const int64_t i = r0 + threadIdx.x;
+    const bool a = i < n && i < t0 + kActTile && rung_active(P, i);
+    const unsigned bal = __ballot_sync(kFull, a);
+    if (lane == 0) wc[w] = __popc(bal);
+    __syncthreads();
+    int before = base;
+    for (int q = 0; q < w; ++q) before += wc[q];
+    if (a) act[before + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+    int total = 0;
+    for (int q = 0; q < kBlock / 32; ++q) total += wc[q];
+    __syncthreads();
+    base += total;
+  }
+}
+
+cudaError_t launch_compact_active(sph_ctx *c) {
+  const int nt = (int)((c->n + kActTile - 1) / kActTile);
+  k_active_count<<<nt, kBlock, 0, c->stream>>>(c->n, c->kp, c->w.act_tiles);
+  k_active_scan<<<1, kBlock, 0, c->stream>>>(c->w.act_tiles, nt, c->d_status);
+  k_active_scatter<<<nt, kBlock, 0, c->stream>>>(c->n, c->kp, c->w.act_tiles, c->w.act);
+  c->nlaunch += 3;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kick(sph_ctx *c, int kick) {
   if (c->kp.precision == SPH_FP32K)
     k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials,

@@ -171,3 +171,75 @@ def test_learned_mode_needs_ids_in_range_and_a_network():
     with pytest.raises(sph.SphError):
         sim.learn_samples()
     sim.close()
+
+
+def _proposal_run(guess, theta=None, norm=None, seed=43):
+    """Proposal of step 1 (by id), the features it was made from (recorded
+    by step 2, by id) and the radii of step 1."""
+    w = wl.impact(20000, 2500, precision=1, seed=seed)
+    p = _p(w)
+    sim = sph.Simulation(w.arrays, w.materials, p)
+    net = None
+    if guess == sph.GUESS_NETWORK:
+        net = sph.Mlp()
+        net.set(theta, norm)
+    sim.set_learned_h(guess, record=True, net=net)
+    sim.prime()
+    sim.step(0.0)
+    s1 = sim.to_numpy(["h", "id"])
+    prop = sim.learn_proposal().cpu().numpy()
+    sim.step(0.0)
+    X, _ = sim.learn_samples()
+    sim.close()
+    if net is not None:
+        net.close()
+    order = np.argsort(s1["id"], kind="stable")
+    return prop[order], s1["h"][order], X.cpu().numpy().astype(np.float64)
+
+
+LOG_LIM = np.log(1.25)   # proposals limited to [0.8, 1.25] H
+
+
+def test_in_step_network_proposal_matches_the_oracle():
+    """The in-step guess (k_learn: tanh.approx on bf16 pairs) element by
+    element against oracle/mlp.py's forward pass on the same features.
+    Error bound per particle, from the in-step path's extra roundings: the
+    standardised features (FP32, then bf16: one bf16 ulp apart at most)
+    through |W1|; the first layer's pre-activation rounded to bf16 (2^-9
+    relative) and its tanh approximate (within 3 2^-9 absolute of the
+    oracle's bf16 value), carried through |W2|; the second layer likewise;
+    then |W3| and y_sd."""
+    theta = wl.mlp_init()
+    x_sd = [0.05, 0.2, 0.05, 2e-3, 0.01, 0.1]
+    norm = np.array([0.0] * 6 + x_sd + [0.0, 0.05])
+    prop, H, X = _proposal_run(sph.GUESS_NETWORK, theta, norm)
+    pred, t = mlp.forward(theta, norm, X, bf16=True, keep=True)
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(theta)
+    xb = mlp.bf16_round(t["x"])
+    W1b = mlp.bf16_round(W1)
+    z1 = xb @ W1b.T + b1
+    # the FP32 standardisation may round a feature to the neighbouring bf16
+    # value (one bf16 ulp, 2^-8 relative)
+    ez1 = 2.0 ** -9 * np.abs(z1) + (2.0 ** -8 * np.abs(xb)) @ np.abs(W1b).T
+    e1 = ez1 / np.cosh(z1) ** 2 + 3 * 2.0 ** -9
+    z2 = mlp.bf16_round(t["a1"]) @ mlp.bf16_round(W2).T + b2
+    e2 = e1 @ np.abs(mlp.bf16_round(W2)).T + 2.0 ** -9 * np.abs(z2) + 3 * 2.0 ** -9
+    bound = norm[13] * (e2 @ np.abs(W3)) + 1e-6
+    want = np.clip(pred, -LOG_LIM, LOG_LIM)
+    got = np.log(prop / H)
+    err = np.abs(got - want)
+    assert np.all(np.isfinite(got))
+    assert np.all(err <= bound), (err.max(), bound[np.argmax(err - bound)])
+    # typical error far inside the bound, far below the spread of the proposals
+    rms = float(np.sqrt(np.mean(err ** 2)))
+    print("proposal error: rms %.3e, max %.3e, median bound %.3e, spread %.3e"
+          % (rms, err.max(), np.median(bound), np.std(want)))
+    assert rms < 0.05 * np.std(want)
+
+
+def test_in_step_continuity_proposal_is_exact():
+    """The continuity guess H exp(-dt tr G / 3) from the recorded f3 = dt
+    tr G, to FP32 rounding."""
+    prop, H, X = _proposal_run(sph.GUESS_CONTINUITY)
+    want = np.clip(-X[:, 3] / 3.0, -LOG_LIM, LOG_LIM)
+    assert np.max(np.abs(np.log(prop / H) - want)) < 1e-6
