@@ -141,6 +141,18 @@ template <typename T> struct Plain {
   __device__ __forceinline__ T get() const { return s; }
 };
 
+template <typename T> struct FList;
+template <> struct FList<float> {
+  template <int S> static __device__ __forceinline__ ViewPlanes<S> at(void *p) {
+    return ViewPlanes<S>{reinterpret_cast<float *>(p)};
+  }
+};
+template <> struct FList<double> {
+  template <int S> static __device__ __forceinline__ ViewAoS<double4_32a> at(void *p) {
+    return ViewAoS<double4_32a>{reinterpret_cast<double4_32a *>(p)};
+  }
+};
+
 struct ForceArgs {
   sph_state s;
   Work w;
@@ -163,7 +175,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   __shared__ int s_idx[kWarpsPerBlock][CAP];
   __shared__ unsigned s_mask[kWarpsPerBlock][CAP / 32][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  V4 *Lr = s_rec[wib];
+  // the candidate list: planes in the FP32 form (packed mask tests),
+  // one record per candidate in the FP64 form
+  const auto Lr = FList<T>::template at<CAP>(s_rec[wib]);
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
   // persistent warps: each takes the next bucket of 32 particles
@@ -255,7 +269,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
         const unsigned bal = __ballot_sync(kFull, keep);
         if (keep) {
           const int at = nl + __popc(bal & lanemask_lt());
-          CandAoS<V4>::put(Lr, at, xj, yj, zj, q.w * q.w);
+          Lr.put(at, xj, yj, zj, q.w * q.w);
           Li[at] = j;
         }
         nl += __popc(bal);
@@ -314,9 +328,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
             }
           }
           T qx, qy, qz, qw;   // qw = H_j^2
-          CandAoS<V4>::get(Lr, k, qx, qy, qz, qw);
+          Lr.get(k, qx, qy, qz, qw);
           const T dx = xi - qx, dy = yi - qy, dz = zi - qz;
-          const T r2 = dx * dx + dy * dy + dz * dz;
+          // the mask test's rounding order, so that the walk and the marks
+          // agree on every pair
+          const T r2 = dist2(dx, dy, dz);
           {
             bool inH;
             if (REL) {

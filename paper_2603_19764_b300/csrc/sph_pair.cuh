@@ -233,7 +233,7 @@ __device__ __forceinline__ unsigned mask_word(const V4 *L, int kb, int count, T 
     T x, y, z, w;
     CandAoS<V4>::get(L, kb + b, x, y, z, w);
     const T dx = xi - x, dy = yi - y, dz = zi - z;
-    mk |= (dx * dx + dy * dy + dz * dz < thr(w) ? 1u : 0u) << b;
+    mk |= (dist2(dx, dy, dz) < thr(w) ? 1u : 0u) << b;
   }
   return mk;
 }
