@@ -15,6 +15,9 @@
   rotation term acting on S = 0), so every particle's dS/dt over 2 edot is
   its Gamma; and a longitudinal wave in a periodic box then travels at
   sqrt((K + 4/3 Gamma) / rho) = c0 sqrt(1 + 4/3 * 0.6).
+* The global sums of the step report (kinetic, internal and potential
+  energy, momentum, angular momentum L = sum m r x v of Eq. 46) against
+  rigid-body mechanics (inertia tensor about the centre of mass).
 """
 import math
 
@@ -140,3 +143,39 @@ def test_elastic_wave_speed_with_eq30_modulus():
     # the constant modulus of the same box would give a clearly different speed
     c_const = math.sqrt(mat["c0"] ** 2 + 4.0 / 3.0 * 3.0e6 / 1000.0)
     assert abs(c_const / c_l - 1) > 0.05
+
+
+def test_global_sums_of_a_rigid_motion():
+    """The diagnostics of the step (energies, momentum and angular momentum
+    of Eq. 46) against rigid-body mechanics: for v = v0 + w x (r - c) with c
+    the centre of mass, p = M v0, L = M c x v0 + I_c w (I_c the inertia
+    tensor about c), E_kin = 1/2 M |v0|^2 + 1/2 w.I_c w, E_int = sum m u and,
+    in a uniform field g, E_pot = -M g.c."""
+    rng = np.random.default_rng(91)
+    n = 500
+    a = wl._empty_arrays(n)
+    m = rng.uniform(0.5, 2.0, n)
+    r = rng.normal(size=(n, 3)) * np.array([3.0, 1.0, 2.0])
+    c = np.array([10.0, -4.0, 7.0])
+    r = r - (m[:, None] * r).sum(0) / m.sum() + c          # centre of mass at c
+    v0 = np.array([1.5, -0.5, 2.0])
+    w = np.array([0.3, -0.2, 0.7])
+    v = v0 + np.cross(w, r - c)
+    a["m"][:] = m
+    a["x"], a["y"], a["z"] = r[:, 0].copy(), r[:, 1].copy(), r[:, 2].copy()
+    a["vx"], a["vy"], a["vz"] = v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+    a["u"][:] = rng.uniform(0.0, 5.0, n)
+    g = np.array([0.0, -1.0, -9.81])
+    p = dict(wl.default_params(0), gravity=1, g_uniform=tuple(g))
+    d = oracle.diagnostics(p, a)
+    M = m.sum()
+    q = r - c
+    I = (m[:, None, None] * ((q * q).sum(1)[:, None, None] * np.eye(3)
+                             - q[:, :, None] * q[:, None, :])).sum(0)
+    L = M * np.cross(c, v0) + I @ w
+    scale = M * (np.linalg.norm(c) + 5.0) * (np.linalg.norm(v0) + 5.0)
+    assert np.allclose(d["p"], M * v0, rtol=0, atol=1e-12 * M * 5.0)
+    assert np.allclose(d["L"], L, rtol=0, atol=1e-12 * scale)
+    assert d["e_kin"] == pytest.approx(0.5 * M * v0 @ v0 + 0.5 * w @ I @ w, rel=1e-12)
+    assert d["e_int"] == pytest.approx((m * a["u"]).sum(), rel=1e-14)
+    assert d["e_pot"] == pytest.approx(-M * g @ c, rel=1e-12)
