@@ -60,13 +60,13 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per particle per launch of the FP32 pair kernels,
 # from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` on the
-# 600k-particle impact (bench.py --scale 0.3 --spans 1,1; profiles/ has the
+# 600k-particle impact (bench.py --scale 0.3 --spans 1,2; profiles/ has the
 # command) and scaled by particles. Keyed by a hash of the kernel's sources: once the
 # kernel changes the figure no longer applies and traffic is reported null.
 KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (184.5, "17a000220866"),
-                        "k_density": (61.6, "00da3d0ce1f0")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (184.2, "2c8624b83764"),
+                        "k_density": (61.2, "8bf119360c9d")}
 
 
 def source_hash(kernel: str) -> str:
