@@ -336,6 +336,9 @@ sph_status enqueue_step(sph_ctx *c) {
   const sph_state *out = c->host_out;
   // one system: the pair kernels take buckets of active particles only
   c->kp.act = L > 1 ? c->w.act : nullptr;
+  // global steps: the arrays the step rewrites are read from the
+  // permutation's scratch instead of being copied back
+  c->lazy = L == 1;
   for (int sub = 0; sub < L && s == SPH_OK; ++sub) {
     c->kp.substep = sub;
     c->host_out = sub == L - 1 ? out : nullptr;
@@ -354,6 +357,8 @@ sph_status enqueue_step(sph_ctx *c) {
   c->kp.max_rung = 0;
   c->kp.sub_scale = 1.0;
   c->kp.act = nullptr;
+  c->lazy = 0;
+  c->src = c->st;
   c->host_out = out;
   if (s != SPH_OK) return s;
   CK(mark(c, 6));
@@ -543,6 +548,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   for (int k = 0; k < SPH_MAX_MATERIALS; ++k) c->mats[k] = mats[k < n_mat ? k : n_mat - 1];
   c->nmat = n_mat;
   c->st = *st;
+  c->src = *st;
   c->n = n;
   c->stream = (cudaStream_t)cuda_stream;
   c->nsys = n_sys;

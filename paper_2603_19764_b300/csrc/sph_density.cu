@@ -64,7 +64,9 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
 cudaError_t launch_predict_pack(sph_ctx *c, int predict, int parts) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
-  k_predict_pack<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp, predict,
+  // reads through the step's read view (the permuted copies of v, u, S
+  // and the derivatives when they were not copied back)
+  k_predict_pack<<<(int)b, kBlock, 0, c->stream>>>(c->src, c->w, c->n, c->kp, predict,
                                                   c->kp.precision == SPH_FP32K, parts);
   c->nlaunch += 1;
   return cudaGetLastError();
@@ -80,6 +82,7 @@ struct DensArgs {
   Status *st;
   void *spill;      // per-warp overflow of the candidate lists (kSpill entries)
   int expand;       // close Newton steps by the expansion (FP32 form, full steps)
+  const double *h_in;   // H before the solve (the step's read view); h is written to s.h
 };
 
 // Candidates beyond the shared-memory list of a warp continue in a private
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const T Hcap =
       (T)A.p.h_cap_factor * cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
   // starting radius: the previous H, or the proposal of the learned form
-  T H = (T)A.s.h[ic];
+  T H = (T)A.h_in[ic];
   if (A.p.h_guess) {
     const double hg = A.p.h_guess[ic];
     if (hg > 0.0) H = (T)hg;
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
                                                                                          : 0u;
   {
     // every particle's radius bounds the force pass's search, solved or not
-    const double hb = wmax(valid ? (solve ? (double)H_o : A.s.h[i]) : 0.0);
+    const double hb = wmax(valid ? (solve ? (double)H_o : A.h_in[i]) : 0.0);
     if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, enc_d(hb));
   }
   w_pairs += pairs;
@@ -508,6 +511,7 @@ cudaError_t launch_density(sph_ctx *c, int expand) {
   a.p = c->kp;
   a.st = c->d_status;
   a.spill = c->dens_spill;
+  a.h_in = c->src.h;
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K) {

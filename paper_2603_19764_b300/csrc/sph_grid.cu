@@ -409,8 +409,9 @@ constexpr int kNLearn = 5;  // learned form: H_prev, H proposal, three feature p
 struct PermTable {
   unsigned long long *f64[kNF64 + kNLearn];
   unsigned *i32[kNI32];
-  int nf64;   // 8-byte fields in use
-  int ni32;   // 4-byte fields in use
+  int nf64;    // 8-byte fields in use
+  int nback;   // the first nback of them are copied back to the caller's arrays
+  int ni32;    // 4-byte fields in use (always copied back)
 };
 
 // part 0: every array a step permutes; part 1 (the copy-in of
@@ -418,42 +419,60 @@ struct PermTable {
 // solve read -- positions, velocities, H, masses, ids, materials, flags and
 // the library's per-particle arrays; part 2: the rest -- u, S, the
 // derivatives at i-1 and the strain invariant, which only the predictor and
-// the kicks read.
+// the kicks read. lazy: the arrays that a later kernel of the step rewrites
+// for every particle (v, H, u, S, the derivatives, the strain invariant) are
+// gathered but not copied back (sph_ctx::src reads them from the scratch).
 static PermTable perm_table(const sph_state &s, const Work &w, const LearnArgs &L, bool all,
-                            bool rungs, int part = 0) {
+                            bool rungs, int part = 0, bool lazy = false) {
   PermTable t;
   t.nf64 = 0;
   t.ni32 = 0;
-  double *a[8] = {s.x, s.y, s.z, s.vx, s.vy, s.vz, s.m, s.h};
-  double *b[16] = {s.u,    s.sxx,  s.syy,  s.sxy,  s.sxz,  s.syz,  s.ax,   s.ay,
-                   s.az,   s.dudt, s.dsxx, s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
-  if (part != 1)
-    for (int k = 0; k < 16; ++k) t.f64[t.nf64++] = (unsigned long long *)b[k];
-  if (part == 2) return t;
-  for (int k = 0; k < 8; ++k) t.f64[t.nf64++] = (unsigned long long *)a[k];
-  t.f64[t.nf64++] = (unsigned long long *)s.id;
-  t.i32[t.ni32++] = (unsigned *)s.mat;
-  t.i32[t.ni32++] = (unsigned *)s.flags;
-  // rho, Omega and the counts are recomputed in a step only for the
-  // particles that are solved: with hierarchical steps they must follow
-  // the sort (solved or not), P and c_s are always recomputed
-  if (all || rungs) {
-    t.f64[t.nf64++] = (unsigned long long *)s.rho;
-    t.f64[t.nf64++] = (unsigned long long *)s.omega;
-    t.i32[t.ni32++] = (unsigned *)s.nngb;
+  unsigned long long *later[24];   // candidates for the lazy part
+  int nl = 0;
+  auto add = [&](double *p, bool rewritten) {
+    if (lazy && rewritten) later[nl++] = (unsigned long long *)p;
+    else t.f64[t.nf64++] = (unsigned long long *)p;
+  };
+  if (part != 2) {
+    add(s.x, false);
+    add(s.y, false);
+    add(s.z, false);
+    add(s.m, false);
+    t.f64[t.nf64++] = (unsigned long long *)s.id;
+    t.i32[t.ni32++] = (unsigned *)s.mat;
+    t.i32[t.ni32++] = (unsigned *)s.flags;
+    // rho, Omega and the counts are recomputed in a step only for the
+    // particles that are solved: with hierarchical steps they must follow
+    // the sort (solved or not), P and c_s are always recomputed
+    if (all || rungs) {
+      t.f64[t.nf64++] = (unsigned long long *)s.rho;
+      t.f64[t.nf64++] = (unsigned long long *)s.omega;
+      t.i32[t.ni32++] = (unsigned *)s.nngb;
+    }
+    if (all) {
+      t.f64[t.nf64++] = (unsigned long long *)s.pres;
+      t.f64[t.nf64++] = (unsigned long long *)s.cs;
+    }
+    if (w.rung) t.i32[t.ni32++] = (unsigned *)w.rung;   // hierarchical steps
+    // the learned form's per-particle arrays follow their particles
+    if (L.hprev) {
+      t.f64[t.nf64++] = (unsigned long long *)L.hprev;
+      t.f64[t.nf64++] = (unsigned long long *)L.hprop;
+      if (L.feat[0])
+        for (int k = 0; k < 3; ++k) t.f64[t.nf64++] = (unsigned long long *)L.feat[k];
+    }
+    add(s.vx, true);
+    add(s.vy, true);
+    add(s.vz, true);
+    add(s.h, true);
   }
-  if (all) {
-    t.f64[t.nf64++] = (unsigned long long *)s.pres;
-    t.f64[t.nf64++] = (unsigned long long *)s.cs;
+  if (part != 1) {
+    double *b[16] = {s.u,    s.sxx,  s.syy,  s.sxy,  s.sxz,  s.syz,  s.ax,   s.ay,
+                     s.az,   s.dudt, s.dsxx, s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
+    for (int k = 0; k < 16; ++k) add(b[k], true);
   }
-  if (w.rung) t.i32[t.ni32++] = (unsigned *)w.rung;   // hierarchical steps
-  // the learned form's per-particle arrays follow their particles
-  if (L.hprev) {
-    t.f64[t.nf64++] = (unsigned long long *)L.hprev;
-    t.f64[t.nf64++] = (unsigned long long *)L.hprop;
-    if (L.feat[0])
-      for (int k = 0; k < 3; ++k) t.f64[t.nf64++] = (unsigned long long *)L.feat[k];
-  }
+  t.nback = t.nf64;
+  for (int k = 0; k < nl; ++k) t.f64[t.nf64++] = later[k];
   return t;
 }
 
@@ -474,7 +493,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter_back(PermTable t, int64_t n,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll 4
-    for (int f = 0; f < t.nf64; ++f) t.f64[f][i] = tmp[f * n + i];
+    for (int f = 0; f < t.nback; ++f) t.f64[f][i] = tmp[f * n + i];
     const unsigned *t32 = (const unsigned *)(tmp + t.nf64 * n);
     for (int f = 0; f < t.ni32; ++f) t.i32[f][i] = t32[f * n + i];
   }
@@ -512,18 +531,40 @@ static int grid_for(int64_t n, int block) {
 }
 
 // Gather and copy back the arrays of one part of the permutation table
-// through the last sort's permutation (c->vals).
-static void enqueue_permute(sph_ctx *c, const PermTable &t) {
+// through the last sort's permutation (c->vals), into the scratch block from
+// word `base` on. The lazy fields (not copied back) become the read view
+// c->src.
+static void enqueue_permute(sph_ctx *c, const PermTable &t, int64_t base) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
-  unsigned long long *tmp = (unsigned long long *)c->tmp;
+  unsigned long long *tmp = (unsigned long long *)c->tmp + base * n;
   k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
   c->nlaunch += 2;
+  for (int f = t.nback; f < t.nf64; ++f) {
+    double *permuted = (double *)(tmp + (int64_t)f * n);
+    const sph_state &s = c->st;
+    sph_state &r = c->src;
+    double *const caller[20] = {s.vx,   s.vy,   s.vz,   s.h,    s.u,    s.sxx,  s.syy,
+                                s.sxy,  s.sxz,  s.syz,  s.ax,   s.ay,   s.az,   s.dudt,
+                                s.dsxx, s.dsyy, s.dsxy, s.dsxz, s.dsyz, s.eps_ii};
+    double **view[20] = {&r.vx,   &r.vy,   &r.vz,   &r.h,    &r.u,    &r.sxx,  &r.syy,
+                         &r.sxy,  &r.sxz,  &r.syz,  &r.ax,   &r.ay,   &r.az,   &r.dudt,
+                         &r.dsxx, &r.dsyy, &r.dsxy, &r.dsxz, &r.dsyz, &r.eps_ii};
+    for (int k = 0; k < 20; ++k)
+      if ((unsigned long long *)caller[k] == t.f64[f]) *view[k] = permuted;
+  }
 }
 
+// Words of the scratch block a table's fields take (8-byte fields, then
+// the 4-byte ones two to a word).
+static int64_t table_words(const PermTable &t) { return t.nf64 + (t.ni32 + 1) / 2; }
+
 cudaError_t launch_permute_rest(sph_ctx *c) {
-  enqueue_permute(c, perm_table(c->st, c->w, c->learn, false, false, 2));
+  // after the first part's fields in the scratch block
+  const PermTable first = perm_table(c->st, c->w, c->learn, false, false, 1, c->lazy != 0);
+  enqueue_permute(c, perm_table(c->st, c->w, c->learn, false, false, 2, c->lazy != 0),
+                  table_words(first));
   return cudaGetLastError();
 }
 
@@ -550,7 +591,10 @@ cudaError_t launch_sort_permute(sph_ctx *c, int all, int part) {
     vb = tv;
   }
   // after four passes the sorted pairs are back in keys / vals
-  enqueue_permute(c, perm_table(c->st, c->w, c->learn, all != 0, c->kp.max_rung > 0, part));
+  c->src = c->st;
+  enqueue_permute(c, perm_table(c->st, c->w, c->learn, all != 0, c->kp.max_rung > 0, part,
+                                c->lazy != 0 && all == 0),
+                  0);
   k_clear_cells<<<grid_for(c->max_cells, kBlock), kBlock, 0, c->stream>>>(c->cell_start,
                                                                           c->d_status);
   k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->kp, c->cell_start, c->cell_end, c->w.cc);

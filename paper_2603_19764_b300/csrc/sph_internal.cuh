@@ -592,6 +592,16 @@ struct sph_ctx {
   cudaStream_t istream;
   cudaEvent_t ev_a, in_ev;
   int split_in;
+  // Read view of the state between a step's sort and the kernels that
+  // rewrite it (lazy = 1: steps without hierarchical rungs). The arrays
+  // that a later kernel of the step rewrites for every particle (v, u, S
+  // and the strain invariant by the kicks, H by the density solve, the
+  // derivatives by the force pass) are not copied back after the
+  // permutation: src points at their permuted copies in the scratch block
+  // and the first readers take them from there; the rest of src is the
+  // caller's arrays. Outside a lazy step src equals st.
+  sph_state src;
+  int lazy;
   cudaGraphExec_t graph_exec;   // captured step
   cudaEvent_t ev[SPH_NUM_PHASES + 1];
   // online tuning of the group spans over the coming steps

@@ -14,9 +14,13 @@ constexpr int kNSum = 9;
 // are evaluated in T.
 // One block per chunk of kChunk consecutive particles of one system, so
 // that every system's sums are formed in a fixed order of its own.
+// src: where v, u, S and the strain invariant are read (the step's read
+// view: their permuted copies when the permutation did not copy them
+// back); s: where they are written, for every particle then.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, KParams P,
-                                                double *partials, Status *st) {
+__global__ void __launch_bounds__(kBlock) k_kick(sph_state s, sph_state src, Work w, int kick,
+                                                KParams P, double *partials, Status *st) {
+  const bool copy = src.vx != s.vx;   // lazy step: write every particle
   __shared__ double red[kNSum][kBlock];
   __shared__ double redt[kBlock / 32];
   __shared__ int hist[16];
@@ -41,14 +45,14 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
     const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
     const double m = s.m[i];
     const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
-    double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
-    double u = s.u[i];
+    double v[3] = {src.vx[i], src.vy[i], src.vz[i]};
+    double u = src.u[i];
     // kicked: moving particles whose own step ends with this substep
     if (kick && !fixed && rung_active(P, i)) {
       const double dt = sub * (double)rung_len(P, i), hdt = 0.5 * dt;
       const MatT<T> &M = mat_t<T>(P, s.mat[i]);
       const double dS[5] = {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]};
-      double S[5] = {s.sxx[i], s.syy[i], s.sxy[i], s.sxz[i], s.syz[i]};
+      double S[5] = {src.sxx[i], src.syy[i], src.sxy[i], src.sxz[i], src.syz[i]};
 #pragma unroll
       for (int k = 0; k < 3; ++k) v[k] += hdt * a[k];
       u += hdt * s.dudt[i];
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
       } else {
         S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
       }
-      s.eps_ii[i] += dt * w.edot2[i];
+      s.eps_ii[i] = src.eps_ii[i] + dt * w.edot2[i];
       // opening kick from the state at i; with rungs over the next step of
       // the rung the criteria ask for, no coarser than the coarsest rung
       // whose steps start at the next substep
@@ -93,6 +97,17 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, Work w, int kick, 
       s.sxy[i] = S[2] + ho * dS[2];
       s.sxz[i] = S[3] + ho * dS[3];
       s.syz[i] = S[4] + ho * dS[4];
+    } else if (copy) {   // not kicked: the state as read
+      s.vx[i] = v[0];
+      s.vy[i] = v[1];
+      s.vz[i] = v[2];
+      s.u[i] = u;
+      s.sxx[i] = src.sxx[i];
+      s.syy[i] = src.syy[i];
+      s.sxy[i] = src.sxy[i];
+      s.sxz[i] = src.sxz[i];
+      s.syz[i] = src.syz[i];
+      s.eps_ii[i] = src.eps_ii[i];
     }
     const double x = s.x[i], y = s.y[i], z = s.z[i];
     T g[3], phi;
@@ -280,11 +295,11 @@ cudaError_t launch_compact_active(sph_ctx *c) {
 
 cudaError_t launch_kick(sph_ctx *c, int kick) {
   if (c->kp.precision == SPH_FP32K)
-    k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials,
-                                                         c->d_status);
+    k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
+                                                         c->partials, c->d_status);
   else
-    k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->w, kick, c->kp, c->partials,
-                                                          c->d_status);
+    k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
+                                                          c->partials, c->d_status);
   k_reduce_final<<<c->nsys, kBlock, 0, c->stream>>>(c->partials, c->kp);
   c->nlaunch += 2;
   return cudaGetLastError();
