@@ -48,7 +48,11 @@ typedef enum {
   SPH_E_NONFINITE = 5,  /* a derivative or density came out NaN or Inf */
   SPH_E_TIMEOUT = 6,    /* reserved: no kernel waits on a flag or on another
                            block, so none can time out */
-  SPH_E_STATE = 7       /* context unusable after an earlier failure */
+  SPH_E_STATE = 7,      /* context unusable after an earlier failure */
+  SPH_E_INTERNAL = 8    /* checked build only (compiled with
+                           -DSPH_BOUNDS_CHECK): an index that came from data
+                           fell outside its array; the access was redirected
+                           and the call's results are not valid */
 } sph_status;
 
 enum { SPH_EOS_LINEAR = 0, SPH_EOS_TILLOTSON = 1 };

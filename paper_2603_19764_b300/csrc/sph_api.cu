@@ -7,11 +7,24 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sph_internal.cuh"
 
 using namespace sphk;
 
 namespace {
+
+// Host-side trace ranges (NVTX, header-only): inert unless a profiler or
+// tracer attaches. They mark where each call and phase is enqueued -- with
+// direct launches, the kernels that follow; under stream capture, the
+// capture itself.
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 sph_status fail(sph_ctx *c, sph_status s, const char *msg) {
   if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
@@ -142,6 +155,8 @@ void free_all(sph_ctx *c) {
 }
 
 sph_status status_from_flags(sph_ctx *c, unsigned flags) {
+  if (flags & ERR_BOUNDS)
+    return fail(c, SPH_E_INTERNAL, "an index check of the checked build failed");
   if (flags & ERR_NONFINITE) return fail(c, SPH_E_NONFINITE, "non-finite density or derivative");
   if (flags & ERR_TIMEOUT) return fail(c, SPH_E_TIMEOUT, "device wait timed out");
   if (flags & ERR_CAPACITY)
@@ -276,6 +291,7 @@ sph_status copy_out(sph_ctx *c, int g) {
 // order (with hierarchical steps rho, Omega and the counts still follow the
 // sort: particles between their steps keep them).
 sph_status run_neighbours(sph_ctx *c, int drift, int all) {
+  const TraceRange tr("sph neighbours");
   CK(mark(c, 0));
   CK(launch_reset_status(c, 0));
   CK(launch_drift_bbox(c, drift));
@@ -291,6 +307,7 @@ cudaError_t tmark(sph_ctx *c, int k) {
 }
 
 sph_status run_derivatives(sph_ctx *c, int predict) {
+  const TraceRange tr("sph derivatives");
   // split copy-in: the density solve needs only the positions; the
   // predictor waits for the rest of the state
   CK(launch_predict_pack(c, predict, c->split_in ? 2 : 3));
@@ -494,6 +511,7 @@ const char *sph_status_string(sph_status s) {
     case SPH_E_NONFINITE: return "non-finite result";
     case SPH_E_TIMEOUT: return "device wait timed out";
     case SPH_E_STATE: return "context unusable";
+    case SPH_E_INTERNAL: return "internal index check failed";
   }
   return "unknown status";
 }
@@ -945,6 +963,7 @@ sph_status sph_stress_update(sph_ctx *c, double dt) {
 }
 
 sph_status sph_prime(sph_ctx *c, sph_step_info *info) {
+  const TraceRange tr("sph_prime");
   ENTER(c);
   for (int k = 0; k < c->nsys; ++k) c->h_dt[k] = 0.0;
   sph_status s = upload_dt(c);
@@ -959,12 +978,14 @@ sph_status sph_prime(sph_ctx *c, sph_step_info *info) {
 }
 
 sph_status sph_step(sph_ctx *c, double dt, sph_step_info *info) {
+  const TraceRange tr("sph_step");
   ENTER(c);
   const sph_status s = stage_dt(c, nullptr, dt);
   return s != SPH_OK ? s : run_step(c, info);
 }
 
 sph_status sph_step_batch(sph_ctx *c, const double *dt, sph_step_info *info) {
+  const TraceRange tr("sph_step_batch");
   ENTER(c);
   if (!dt) return fail(c, SPH_E_ARG, "dt array is NULL");
   const sph_status s = stage_dt(c, dt, 0.0);
@@ -1069,6 +1090,7 @@ sph_status sph_batch_info(const sph_ctx *c, sph_step_info *info, int32_t n) {
 
 sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_info *info,
                          int64_t *bytes_in, int64_t *bytes_out) {
+  const TraceRange tr("sph_step_host");
   ENTER(c);
   if (!host || !state_complete(host)) return fail(c, SPH_E_ARG, "incomplete host state");
   if (!c->cstream) {

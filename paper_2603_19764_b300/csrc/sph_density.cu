@@ -83,6 +83,7 @@ struct DensArgs {
   void *spill;      // per-warp overflow of the candidate lists (kSpill entries)
   int expand;       // close Newton steps by the expansion (FP32 form, full steps)
   const double *h_in;   // H before the solve (the step's read view); h is written to s.h
+  int spill_warps;      // warps the overflow region has room for
 };
 
 // Candidates beyond the shared-memory list of a warp continue in a private
@@ -165,7 +166,8 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              T gb, T H, double xi64, double yi64, double zi64,
                                              const sph_state &s, const double *blen, int self,
-                                             T &rs, T &rhs, T &rhs2, int &cnt) {
+                                             T &rs, T &rhs, T &rhs2, int &cnt, int64_t n_all,
+                                             unsigned *err) {
   // every lane advances through its own words: lanes do not wait for each
   // other at word boundaries
   const int nw = (nl + 31) >> 5;
@@ -188,7 +190,7 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
         r2 = dist2(dx, dy, dz);
         in = r2 < H2;
         if (fabs(r2 - H2) < gb) {
-          const int j = Li[k];
+          const int j = (int)checked(Li[k], n_all, err);
           // the square of an FP32 radius is exact in FP64
           const double c2 = PER ? r2_canon_periodic(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j],
                                                     blen)
@@ -202,7 +204,7 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
         // minimum image of x_i - x_j: decide the rare pair at the boundary
         // with the canonical arithmetic
         if (PER && fabs(r2 - H2) < gb) {
-          const int j = Li[k];
+          const int j = (int)checked(Li[k], n_all, err);
           in = r2_canon_periodic(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j], blen) < (double)H2;
         }
       }
@@ -234,7 +236,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const auto Lp = DList<T>::template at<CAP>(s_pos[wib]);
   int *Li = s_idx[wib];
   unsigned(*Lm)[32] = s_mask[wib];
-  const SpillView<V4> Sv0 = spill_view<V4>(A.spill, blockIdx.x * kWarpsPerBlock + wib);
+  const SpillView<V4> Sv0 =
+      spill_view<V4>(A.spill, (int)checked(blockIdx.x * kWarpsPerBlock + wib, A.spill_warps,
+                                           &A.st->err));
   const auto Sp = DList<T>::template at<kSpill>(Sv0.p);
   struct {
     int *i;
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   bk = __shfl_sync(kFull, bk, 0);
   if ((int)bk >= nbuckets) break;
   // the bucket's system and its sorted range
-  const BucketLane bl = bucket_lane(A.p, n_act, bk, lane);
+  const BucketLane bl = bucket_lane(A.p, n_act, bk, lane, A.n, &A.st->err);
   const int sy = bl.sy;
   const SysRec &R = A.p.sys[sy];
   const int64_t i = bl.i;
@@ -336,15 +340,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
             bool ok;
             T ox, oy, oz;
             if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz,
-                                      j, ok, ox, oy, oz))
+                                      j, ok, ox, oy, oz, &A.st->err))
               break;
+            if (ok) j = (int)checked(j, A.n, &A.st->err);
             const V4 q = ok ? V::ld(pos, j) : V::make(0, 0, 0, 0);
             const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
             const bool keep =
                 ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < Rl * Rl;
             const unsigned bal = __ballot_sync(kFull, keep);
             if (keep) {
-              const int at = nl + __popc(bal & lanemask_lt());
+              const int at = (int)checked(nl + __popc(bal & lanemask_lt()), TCAP, &A.st->err);
               if (at < CAP) {
                 Lp.put(at, xj, yj, zj, q.w);
                 Li[at] = j;
@@ -369,10 +374,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           if (act) {
             density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                           yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
-                                          cnt);
+                                          cnt, A.n, &A.st->err);
             density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
                                           xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
-                                          rhs2, cnt);
+                                          rhs2, cnt, A.n, &A.st->err);
           }
           __syncwarp();
           if (stager_finished(sg)) break;
@@ -393,10 +398,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         if (act) {
           density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                         yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
-                                        cnt);
+                                        cnt, A.n, &A.st->err);
           density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
                                         xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
-                                        rhs2, cnt);
+                                        rhs2, cnt, A.n, &A.st->err);
         }
       }
 
@@ -512,6 +517,7 @@ cudaError_t launch_density(sph_ctx *c, int expand) {
   a.st = c->d_status;
   a.spill = c->dens_spill;
   a.h_in = c->src.h;
+  a.spill_warps = c->spill_warps;
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K) {
@@ -563,6 +569,7 @@ cudaError_t alloc_density_spill(sph_ctx *c) {
   if (blocks > need) blocks = need;
   const size_t v4 = c->kp.precision == SPH_FP32K ? sizeof(float4) : sizeof(double4_32a);
   const size_t per = (size_t)kSpill * (v4 + 2 * sizeof(int));
+  c->spill_warps = (int)(blocks * kWarpsPerBlock);
   return cudaMalloc(&c->dens_spill, per * (size_t)(blocks * kWarpsPerBlock));
 }
 

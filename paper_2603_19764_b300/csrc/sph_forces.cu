@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   bk = __shfl_sync(kFull, bk, 0);
   if ((int)bk >= nbuckets) break;
   // the bucket's system and its sorted range
-  const BucketLane bl = bucket_lane(A.p, n_act, bk, lane);
+  const BucketLane bl = bucket_lane(A.p, n_act, bk, lane, A.n, &A.st->err);
   const int sy = bl.sy;
   const SysRec &R = A.p.sys[sy];
   const int64_t i = bl.i;
@@ -259,8 +259,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
         bool ok;
         T ox, oy, oz;
         if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, j,
-                                  ok, ox, oy, oz))
+                                  ok, ox, oy, oz, &A.st->err))
           break;
+        if (ok) j = (int)checked(j, A.n, &A.st->err);
         const V4 q = ok ? V::ld(posh, j) : V::make(0, 0, 0, 0);
         const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
         const T R = tmax(Rb, q.w);
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
             ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R + gmax;
         const unsigned bal = __ballot_sync(kFull, keep);
         if (keep) {
-          const int at = nl + __popc(bal & lanemask_lt());
+          const int at = (int)checked(nl + __popc(bal & lanemask_lt()), CAP, &A.st->err);
           Lr.put(at, xj, yj, zj, q.w * q.w);
           Li[at] = j;
         }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
       if (more) {
         kn = (wd << 5) + __ffs(mk) - 1;
         mk &= mk - 1u;
-        jn = Li[kn];
+        jn = (int)checked(Li[kn], A.n, &A.st->err);
         if (PF) {
           V::ld2(rec + 4 * jn, g0, g1);
           V::ld2(rec + 4 * jn + 2, g2, g3);
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           if (more) {
             kn = (wd << 5) + __ffs(mk) - 1;
             mk &= mk - 1u;
-            jn = Li[kn];
+            jn = (int)checked(Li[kn], A.n, &A.st->err);
             if (PF) {
               V::ld2(rec + 4 * jn, g0, g1);
               V::ld2(rec + 4 * jn + 2, g2, g3);

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kScanSeg) k_scan_apply(unsigned *hist, int m,
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *kin, const int *vin,
                                                                 unsigned *kout, int *vout, int n,
                                                                 int shift, const unsigned *hist,
-                                                                int ntiles) {
+                                                                int ntiles, unsigned *err) {
   constexpr int NW = kSortThreads / 32;
   __shared__ unsigned base[256];
   __shared__ unsigned wcnt[NW][256];
@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *
     if (ok) {
       unsigned pos = base[d] + rank_w;
       for (int k = 0; k < w; ++k) pos += wcnt[k][d];
+      pos = (unsigned)checked(pos, n, err);
       kout[pos] = key;
       vout[pos] = vin[i];
     }
@@ -477,10 +478,10 @@ static PermTable perm_table(const sph_state &s, const Work &w, const LearnArgs &
 }
 
 __global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm, int64_t n,
-                                                  unsigned long long *tmp) {
+                                                  unsigned long long *tmp, unsigned *err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = perm[i];
+    const int64_t j = checked(perm[i], n, err);
 #pragma unroll 4
     for (int f = 0; f < t.nf64; ++f) tmp[f * n + i] = t.f64[f][j];
     unsigned *t32 = (unsigned *)(tmp + t.nf64 * n);
@@ -507,7 +508,8 @@ __global__ void __launch_bounds__(kBlock) k_clear_cells(int *start, const Status
 }
 
 __global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys, int64_t n, KParams P,
-                                                 int *start, int *end, int *cc) {
+                                                 int *start, int *end, int *cc, int max_cells,
+                                                 unsigned *err) {
   const int sh = 3 * P.axis_bits;
   const unsigned mask = sh >= 32 ? ~0u : ((1u << sh) - 1u);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -517,7 +519,8 @@ __global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys, int64_t 
     const unsigned mc = k & mask;
     const Grid &g = P.sys[sy].grid;
     const int cx = compact1by2(mc), cy = compact1by2(mc >> 1), cz = compact1by2(mc >> 2);
-    const int lin = g.cell_off + (cz * g.dims[1] + cy) * g.dims[0] + cx;
+    const int lin = (int)checked(g.cell_off + (cz * g.dims[1] + cy) * g.dims[0] + cx, max_cells,
+                                 err);
     cc[i] = cx | (cy << 10) | (cz << 20);
     if (i == 0 || keys[i - 1] != k) start[lin] = (int)i;
     if (i == n - 1 || keys[i + 1] != k) end[lin] = (int)(i + 1);
@@ -538,7 +541,7 @@ static void enqueue_permute(sph_ctx *c, const PermTable &t, int64_t base) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
   unsigned long long *tmp = (unsigned long long *)c->tmp + base * n;
-  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp);
+  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp, &c->d_status->err);
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
   c->nlaunch += 2;
   for (int f = t.nback; f < t.nf64; ++f) {
@@ -582,7 +585,8 @@ cudaError_t launch_sort_permute(sph_ctx *c, int all, int part) {
     k_scan_of_totals<<<1, kScanSeg, 0, c->stream>>>(c->scan_tot, nseg);
     k_scan_apply<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot);
     k_radix_scatter<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, (int)n, shift,
-                                                               c->hist, c->ntiles);
+                                                               c->hist, c->ntiles,
+                                                               &c->d_status->err);
     unsigned *tk = ka;
     ka = kb;
     kb = tk;
@@ -597,7 +601,8 @@ cudaError_t launch_sort_permute(sph_ctx *c, int all, int part) {
                   0);
   k_clear_cells<<<grid_for(c->max_cells, kBlock), kBlock, 0, c->stream>>>(c->cell_start,
                                                                           c->d_status);
-  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->kp, c->cell_start, c->cell_end, c->w.cc);
+  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->kp, c->cell_start, c->cell_end, c->w.cc,
+                                        c->max_cells, &c->d_status->err);
   c->nlaunch += 1 + 4 * 5 + 2;   // keys, four radix passes, cells (permutation counted above)
   return cudaGetLastError();
 }

@@ -22,7 +22,32 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double cW = 21.0 / (2.0 * kPi);
 constexpr double cG = -210.0 / kPi;
 
-enum : unsigned { ERR_NOCONV = 1u, ERR_NONFINITE = 2u, ERR_CAPACITY = 4u, ERR_TIMEOUT = 8u };
+enum : unsigned {
+  ERR_NOCONV = 1u,
+  ERR_NONFINITE = 2u,
+  ERR_CAPACITY = 4u,
+  ERR_TIMEOUT = 8u,
+  ERR_BOUNDS = 16u   // checked builds: an index check failed
+};
+
+// Checked builds (-DSPH_BOUNDS_CHECK): every index that comes from data
+// (cell ranges, sort positions, candidate lists, the active list) is tested
+// before its access. A failed test latches ERR_BOUNDS in the status word
+// and the access goes to index 0 instead -- never a trap -- and the
+// synchronising call reports SPH_E_INTERNAL. Release builds compile the
+// tests out: checked(i, n, err) is i.
+__device__ __forceinline__ int64_t checked(int64_t i, int64_t n, unsigned *err) {
+#ifdef SPH_BOUNDS_CHECK
+  if (i < 0 || i >= n) {
+    atomicOr(err, ERR_BOUNDS);
+    return 0;
+  }
+#else
+  (void)n;
+  (void)err;
+#endif
+  return i;
+}
 
 // Uniform cell grid of one system for one step, written on the device by
 // k_grid_setup. Global cell index = cell_off + (z * dims[1] + y) * dims[0] + x.
@@ -212,12 +237,12 @@ __device__ __forceinline__ int bucket_count(const KParams &P, int n_act) {
   return P.act ? (n_act + 31) >> 5 : P.nbuckets;
 }
 __device__ __forceinline__ BucketLane bucket_lane(const KParams &P, int n_act, unsigned bk,
-                                                  int lane) {
+                                                  int lane, int64_t n, unsigned *err) {
   BucketLane b;
   if (P.act) {
     const int k = (int)bk * 32 + lane;
     b.valid = k < n_act;
-    b.i = P.act[b.valid ? k : (int)bk * 32];
+    b.i = checked(P.act[checked(b.valid ? k : (int)bk * 32, n, err)], n, err);
     b.ic = b.i;
     b.sy = 0;
     return b;
@@ -573,6 +598,7 @@ struct sph_ctx {
   double *dt_next;          // host, per system
   int occ_density, occ_forces;   // resident blocks per SM of the pair kernels
   void *dens_spill;              // overflow of the density kernel's candidate lists
+  int spill_warps;               // warps it has room for
   int num_sms;
   int timing;
   int use_graph;

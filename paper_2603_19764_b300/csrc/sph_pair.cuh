@@ -411,7 +411,8 @@ __device__ __forceinline__ Stager make_stager(const Box<T> &b, T R, const Grid &
 template <typename T, bool REL>
 __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int *cstart,
                                              const int *cend, T Lt, int rx, int ry, int rz,
-                                             int &j, bool &ok, T &ox, T &oy, T &oz) {
+                                             int &j, bool &ok, T &ox, T &oy, T &oz,
+                                             unsigned *err) {
   const int lane = threadIdx.x & 31;
   while (s.pos >= s.total) {
     if (s.c0 >= s.ncell) return false;
@@ -422,7 +423,8 @@ __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int
       const int x = c % s.nx, t = c / s.nx;
       const int y = t % s.ny, z = t / s.ny;
       const int gx = s.kx0 + x, gy = s.ky0 + y, gz = s.kz0 + z;
-      const int cell = g.cell_off + (gz * g.dims[1] + gy) * g.dims[0] + gx;
+      const int cell = g.cell_off + (int)checked((gz * g.dims[1] + gy) * g.dims[0] + gx,
+                                                 g.ncells, err);
       st = cstart[cell];
       if (st >= 0) cnt = cend[cell] - st;
       off = (gx - rx + 512) | ((gy - ry + 512) << 10) | ((gz - rz + 512) << 20);
@@ -577,7 +579,7 @@ template <typename T, bool REL>
 __device__ __forceinline__ bool stager_chunk(StagerP<T> &s, const Grid &g, const int *cstart,
                                              const int *cend, T Lt, const KParams &P, int rx,
                                              int ry, int rz, int &j, bool &ok, T &ox, T &oy,
-                                             T &oz) {
+                                             T &oz, unsigned *err) {
   const int lane = threadIdx.x & 31;
   while (s.pos >= s.total) {
     if (s.c0 >= s.ncell) return false;
@@ -591,7 +593,8 @@ __device__ __forceinline__ bool stager_chunk(StagerP<T> &s, const Grid &g, const
       const int gx = periodic_cell(s, 0, vx, shx);
       const int gy = periodic_cell(s, 1, vy, shy);
       const int gz = periodic_cell(s, 2, vz, shz);
-      const int cell = g.cell_off + (gz * g.dims[1] + gy) * g.dims[0] + gx;
+      const int cell = g.cell_off + (int)checked((gz * g.dims[1] + gy) * g.dims[0] + gx,
+                                                 g.ncells, err);
       st = cstart[cell];
       if (st >= 0) cnt = cend[cell] - st;
       cx = periodic_offset<T, REL>(gx, rx, shx, Lt, g, P.box_len[0]);
@@ -651,8 +654,8 @@ template <typename T, bool REL>
 __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int *cstart,
                                              const int *cend, T Lt, const KParams &, int rx,
                                              int ry, int rz, int &j, bool &ok, T &ox, T &oy,
-                                             T &oz) {
-  return stager_chunk<T, REL>(s, g, cstart, cend, Lt, rx, ry, rz, j, ok, ox, oy, oz);
+                                             T &oz, unsigned *err) {
+  return stager_chunk<T, REL>(s, g, cstart, cend, Lt, rx, ry, rz, j, ok, ox, oy, oz, err);
 }
 
 // FP64 squared distance of the neighbour predicate in a periodic box: the

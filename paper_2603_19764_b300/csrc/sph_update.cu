@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kBlock) k_active_scan(int *tiles, int ntiles, 
 }
 
 __global__ void __launch_bounds__(kBlock) k_active_scatter(int64_t n, KParams P, const int *tiles,
-                                                          int *act) {
+                                                          int *act, unsigned *err) {
   __shared__ int wc[kBlock / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t t0 = (int64_t)blockIdx.x * kActTile;
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_active_scatter(int64_t n, KParams P,
     __syncthreads();
     int before = base;
     for (int q = 0; q < w; ++q) before += wc[q];
-    if (a) act[before + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+    if (a) act[checked(before + __popc(bal & ((1u << lane) - 1u)), n, err)] = (int)i;
     int total = 0;
     for (int q = 0; q < kBlock / 32; ++q) total += wc[q];
     __syncthreads();
@@ -288,7 +288,8 @@ cudaError_t launch_compact_active(sph_ctx *c) {
   const int nt = (int)((c->n + kActTile - 1) / kActTile);
   k_active_count<<<nt, kBlock, 0, c->stream>>>(c->n, c->kp, c->w.act_tiles);
   k_active_scan<<<1, kBlock, 0, c->stream>>>(c->w.act_tiles, nt, c->d_status);
-  k_active_scatter<<<nt, kBlock, 0, c->stream>>>(c->n, c->kp, c->w.act_tiles, c->w.act);
+  k_active_scatter<<<nt, kBlock, 0, c->stream>>>(c->n, c->kp, c->w.act_tiles, c->w.act,
+                                                 &c->d_status->err);
   c->nlaunch += 3;
   return cudaGetLastError();
 }

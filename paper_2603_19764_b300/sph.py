@@ -17,13 +17,16 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsph.so")
+# SPH_CHECKED=1 in the environment selects the checked build (index tests on
+# every data-derived index; paper_2603_19764_b300.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "libsph_check.so" if os.environ.get("SPH_CHECKED") == "1"
+                        else "libsph.so")
 _lib = None
 
 SPH_OK, SPH_E_ARG, SPH_E_CUDA, SPH_E_NOCONV, SPH_E_CAPACITY, SPH_E_NONFINITE, \
-    SPH_E_TIMEOUT, SPH_E_STATE = range(8)
+    SPH_E_TIMEOUT, SPH_E_STATE, SPH_E_INTERNAL = range(9)
 STATUS_NAMES = ["SPH_OK", "SPH_E_ARG", "SPH_E_CUDA", "SPH_E_NOCONV", "SPH_E_CAPACITY",
-                "SPH_E_NONFINITE", "SPH_E_TIMEOUT", "SPH_E_STATE"]
+                "SPH_E_NONFINITE", "SPH_E_TIMEOUT", "SPH_E_STATE", "SPH_E_INTERNAL"]
 MAX_MATERIALS = 8
 SPH_MAX_SYSTEMS = 1024
 
