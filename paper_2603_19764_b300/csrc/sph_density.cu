@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
       int cnt = 0;
       const bool resident = complete && Rneed <= Rl;
       if (!resident) {
-        Rl = Rneed * T(1.05);
+        Rl = Rneed * T(1.02);
         if (PER && !(T(2) * Rl < box_min)) w_box = 1u;
         const Box<T> bx = group_box(act, xi, yi, zi);
         auto sg = make_stager_for<T, REL, PER>(bx, Rl, g, invL, A.p, G.rx, G.ry, G.rz);
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         const bool rebuild = act && !(Hm >= Hq);
         const int n1 = min(nl, CAP), n2 = nl - n1;
         if (__any_sync(kFull, rebuild)) {
-          const T Hn = rebuild ? tmax(Ht * T(1.02), Hq) : Hm;
+          const T Hn = rebuild ? tmax(Ht * T(1.005), Hq) : Hm;
           __syncwarp();
           build_masks<T>(Lp, Lm, n1, xi, yi, zi, Hn * Hn, rebuild, lane);
           build_masks<T>(Sp, Sv.m, n2, xi, yi, zi, Hn * Hn, rebuild, lane);
