@@ -74,7 +74,11 @@ __device__ __forceinline__ u64 fma(u64 a, u64 b, u64 c) {
 }
 }  // namespace px
 
-template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+// Larger / smaller of two values: one min / max instruction (a compare and
+// a select otherwise). The operands are finite wherever these are used; for
+// a NaN operand the other one is returned.
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
 
 // Products and sums that the compiler may not fuse into one rounding.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
@@ -90,7 +94,8 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 template <typename T> __device__ __forceinline__ T rel_coord(T c, int k, T L) {
   return add_rn(c, mul_rn((T)k, L));
 }
-template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
 
 // Square root of x >= 0 and a quotient: correctly rounded in FP64; in FP32
 // through the hardware reciprocal square root and the fast divide (a few
