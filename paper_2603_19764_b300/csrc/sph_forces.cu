@@ -319,14 +319,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           }
           while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
           more = mk != 0u;
-          if (more) {
+          if (PF) {
+            // without a branch: after the lane's last pair the index stays
+            // at the current pair and its record is loaded once more
+            kn = more ? (wd << 5) + __ffs(mk) - 1 : kn;
+            mk &= mk - 1u;
+            jn = (int)checked(Li[kn], A.n, &A.st->err);
+            V::ld2(rec + 4 * jn, g0, g1);
+            V::ld2(rec + 4 * jn + 2, g2, g3);
+          } else if (more) {
             kn = (wd << 5) + __ffs(mk) - 1;
             mk &= mk - 1u;
             jn = (int)checked(Li[kn], A.n, &A.st->err);
-            if (PF) {
-              V::ld2(rec + 4 * jn, g0, g1);
-              V::ld2(rec + 4 * jn + 2, g2, g3);
-            }
           }
           T qx, qy, qz, qw;   // qw = H_j^2
           Lr.get(k, qx, qy, qz, qw);
