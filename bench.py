@@ -65,8 +65,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 # kernel changes the figure no longer applies and traffic is reported null.
 KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (184.2, "32e2fc8417d3"),
-                        "k_density": (61.9, "71de705b53c0")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (184.6, "d6177f54f9c4"),
+                        "k_density": (62.1, "1cd71a8ca953")}
 
 
 def source_hash(kernel: str) -> str:
@@ -107,15 +107,19 @@ class ClockSampler:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+            return
+        # the timed region starts once the sampler has written its first row
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and os.path.getsize(self.f.name) == 0:
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.3)
         self.p.terminate()
         self.p.wait()
         self.f.flush()
