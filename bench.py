@@ -402,6 +402,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     e2e = None
     if not args.no_e2e:
         host = sph.HostState(sim.to_numpy())
+        if args.copy_chunks:
+            sim.set_copy_chunks(args.copy_chunks)
         sim.step_host(host, 0.0)
         torch.cuda.synchronize(dev)
         ne = max(1, min(args.steps, args.e2e_steps))
@@ -412,7 +414,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         te = max_over_ranks(te, world, dev)
         e2e = {"value": job_rate(w.n, world, ne, te), "unit": "particle-steps/s",
                "h2d_bytes_per_step": r["bytes_in"], "d2h_bytes_per_step": r["bytes_out"],
-               "steps": ne}
+               "steps": ne, "copy_chunks": args.copy_chunks or 8}
     # error of this form against the FP64 oracle on a seeded sample, on the
     # state the timed steps produced (derivatives recomputed as it stands)
     err = None
@@ -928,6 +930,9 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--copy-chunks", type=int, default=0,
+                    help="force-pass launches whose outputs sph_step_host copies back as "
+                         "each completes (0: the library's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--no-plain", action="store_true")

@@ -63,6 +63,7 @@ enum { SPH_YIELD_SQRT_J2 = 0, SPH_YIELD_SQRT_3J2 = 1 };
 enum { SPH_GRAVITY_NONE = 0, SPH_GRAVITY_UNIFORM = 1, SPH_GRAVITY_RADIAL = 2 };
 #define SPH_MAX_MATERIALS 8
 #define SPH_MAX_SYSTEMS 1024
+#define SPH_MAX_COPY_CHUNKS 16
 #define SPH_FLAG_FIXED 1
 
 typedef struct sph_ctx sph_ctx;
@@ -426,11 +427,25 @@ sph_status sph_learn_proposal(sph_ctx *c, double *h_next);
  * launches, and copies each group of arrays back as soon as the step has
  * finished writing it, on a library copy stream that overlaps the rest of
  * the step (positions, masses, ids after the sort; H, rho, Omega after the
- * density solve; P, c_s after the EOS; derivatives and counts after the
- * force pass; v, u, S, strain invariant after the kicks). Synchronises.
- * h2d / d2h byte counts go to *bytes_in / *bytes_out (may be NULL). */
+ * density solve; P, c_s after the EOS; in a global step the derivatives,
+ * counts, v, u, S and strain invariant of each range of the force pass as
+ * that range completes, see sph_set_copy_chunks; with hierarchical steps
+ * derivatives and counts after the force pass and v, u, S, strain
+ * invariant after the kicks). Synchronises. h2d / d2h byte counts go to
+ * *bytes_in / *bytes_out (may be NULL). */
 sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_info *info,
                          int64_t *bytes_in, int64_t *bytes_out);
+
+/* Copy-back granularity of sph_step_host with global steps (max_rung = 0):
+ * the force pass, which in a global step also applies each particle's
+ * closing and opening kicks (§2.4) as soon as its derivatives are formed,
+ * runs as `chunks` launches over consecutive ranges of 32-particle buckets
+ * (sorted order), and the final state of each range (derivatives, counts,
+ * v, u, S, strain invariant) is copied back while the next ranges are
+ * computed. chunks = 1 copies those arrays after the whole pass. The
+ * results do not depend on it. 1 <= chunks <= SPH_MAX_COPY_CHUNKS, else
+ * SPH_E_ARG; the default is 8. Takes effect at the next sph_step_host. */
+sph_status sph_set_copy_chunks(sph_ctx *c, int32_t chunks);
 
 /* Derivatives of the initial state: sph_neighbours, sph_density and
  * sph_forces_strength in one call, plus the diagnostics and dt_next in
@@ -440,7 +455,9 @@ sph_status sph_prime(sph_ctx *c, sph_step_info *info);
 /* Phase timing with CUDA events recorded on the context's stream around the
  * phases of every sph_step: 0 neighbours (drift, keys, sort, permutation,
  * cells), 1 prediction and packing, 2 density solve, 3 EOS, yield and
- * packing, 4 pair loop with finalize, 5 kicks and reductions.
+ * packing, 4 pair loop with finalize (in global steps also the kicks,
+ * applied per particle in its epilogue), 5 kicks and reductions (in global
+ * steps the reductions only).
  * sph_set_timing(c, 1) enables it and zeroes the accumulators. Steps
  * replayed from a graph (sph_set_graph) are not phase-timed;
  * sph_phase_times copies up to n accumulated milliseconds per phase into

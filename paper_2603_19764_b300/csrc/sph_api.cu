@@ -7,9 +7,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include <nvtx3/nvToolsExt.h>
 
-#include "sph_internal.cuh"
+#include "sph_kick.cuh"
 
 using namespace sphk;
 
@@ -141,7 +143,8 @@ void free_all(sph_ctx *c) {
                  c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
                  c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
-                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->w.divv,
+                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->d_red_tile,
+                 c->tile_partials, c->d_chunk_ctr, c->w.divv,
                  c->learn.hprev, c->learn.hprop, c->learn.feat[0], c->learn.feat[1],
                  c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill, c->w.rung,
                  c->w.act, c->w.act_tiles};
@@ -286,6 +289,56 @@ sph_status copy_out(sph_ctx *c, int g) {
   return SPH_OK;
 }
 
+// First sorted position of bucket b (the bucket count: n). Buckets are 32
+// consecutive positions of one system, the systems' buckets in order.
+int64_t bucket_first(const sph_ctx *c, int b) {
+  int64_t off = 0;
+  for (int k = 0; k < c->nsys; ++k) {
+    const int64_t nb = (c->sys_first[k + 1] - c->sys_first[k] + 31) / 32;
+    if (b < off + nb) return c->sys_first[k] + 32 * (b - off);
+    off += nb;
+  }
+  return c->n;
+}
+
+// Force pass of a global step of sph_step_host in copy_chunks launches over
+// consecutive bucket ranges (the force pass kicks, so a range's state is
+// final when its launch completes), alternating between two streams so
+// that one launch's last buckets overlap the next launch's first; each
+// range's derivatives, counts, v, u, S and strain invariant are copied back
+// on the copy stream as soon as its launch completes.
+sph_status forces_chunked(sph_ctx *c) {
+  const int K = c->copy_chunks;
+  const int nb = c->kp.nbuckets;
+  const sph_state &d = c->st, &h = *c->host_out;
+  CK(cudaMemsetAsync(c->d_chunk_ctr, 0, sizeof(unsigned) * K, c->stream));
+  CK(cudaEventRecord(c->ev_pre, c->stream));
+  CK(cudaStreamWaitEvent(c->fstream[0], c->ev_pre, 0));
+  CK(cudaStreamWaitEvent(c->fstream[1], c->ev_pre, 0));
+  double *const hd[19] = {h.ax,  h.ay,  h.az,  h.dudt, h.dsxx, h.dsyy, h.dsxy, h.dsxz, h.dsyz, h.vx,
+                          h.vy,  h.vz,  h.u,   h.sxx,  h.syy,  h.sxy,  h.sxz,  h.syz,  h.eps_ii};
+  double *const dd[19] = {d.ax,  d.ay,  d.az,  d.dudt, d.dsxx, d.dsyy, d.dsxy, d.dsxz, d.dsyz, d.vx,
+                          d.vy,  d.vz,  d.u,   d.sxx,  d.syy,  d.sxy,  d.sxz,  d.syz,  d.eps_ii};
+  for (int k = 0; k < K; ++k) {
+    const int b0 = (int)((int64_t)nb * k / K), b1 = (int)((int64_t)nb * (k + 1) / K);
+    cudaStream_t fs = c->fstream[k & 1];
+    CK(launch_forces_range(c, b0, b1, c->d_chunk_ctr + k, fs));
+    CK(cudaEventRecord(c->chunk_ev[k], fs));
+    CK(cudaStreamWaitEvent(c->cstream, c->chunk_ev[k], 0));
+    const int64_t p0 = bucket_first(c, b0), p1 = bucket_first(c, b1);
+    if (p1 <= p0) continue;
+    const size_t n8 = sizeof(double) * (size_t)(p1 - p0);
+    for (int q = 0; q < 19; ++q)
+      CK(cudaMemcpyAsync(hd[q] + p0, dd[q] + p0, n8, cudaMemcpyDeviceToHost, c->cstream));
+    CK(cudaMemcpyAsync(h.nngb + p0, d.nngb + p0, sizeof(int32_t) * (size_t)(p1 - p0),
+                       cudaMemcpyDeviceToHost, c->cstream));
+  }
+  // the rest of the step follows the last launch of each stream
+  CK(cudaStreamWaitEvent(c->stream, c->chunk_ev[K - 1], 0));
+  if (K > 1) CK(cudaStreamWaitEvent(c->stream, c->chunk_ev[K - 2], 0));
+  return SPH_OK;
+}
+
 // all = 1 permutes every array of the state (sph_neighbours on its own);
 // steps pass 0 and recompute rho, Omega, P, c_s and the counts in the new
 // order (with hierarchical steps rho, Omega and the counts still follow the
@@ -328,11 +381,29 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
   s = copy_out(c, 2);
   if (s != SPH_OK) return s;
   CK(tmark(c, 2));
-  CK(launch_forces(c));
+  // sph_step_host, global step: the pass in ranges, each copied back as it
+  // completes; otherwise one launch, and with the kicks in it the whole
+  // final state is copied back after it
+  const bool chunked = c->host_out && c->fuse_kick && c->copy_chunks > 1;
+  if (chunked) {
+    s = forces_chunked(c);
+    if (s != SPH_OK) return s;
+  } else {
+    CK(launch_forces(c));
+  }
   CK(tmark(c, 3));
   CK(launch_learn(c));
   CK(mark(c, 5));
-  return copy_out(c, 3);
+  if (chunked || !c->host_out) {
+    c->out_done = c->host_out != nullptr;
+    return SPH_OK;
+  }
+  s = copy_out(c, 3);
+  if (s == SPH_OK && c->fuse_kick) {
+    s = copy_out(c, 4);
+    c->out_done = 1;
+  }
+  return s;
 }
 
 // Everything one step enqueues, from the dt upload to the status readback.
@@ -364,11 +435,15 @@ sph_status enqueue_step(sph_ctx *c) {
       const cudaError_t e = launch_compact_active(c);
       if (e != cudaSuccess) s = fail_cuda(c, e, "launch_compact_active");
     }
+    // global steps: the force pass kicks each particle as soon as its
+    // derivatives are formed, leaving the sums to one small kernel
+    c->fuse_kick = L == 1;
     if (s == SPH_OK) s = run_derivatives(c, 1);
     if (s == SPH_OK) {
-      const cudaError_t e = launch_kick(c, 1);
+      const cudaError_t e = c->fuse_kick ? launch_reduce_buckets(c) : launch_kick(c, 1);
       if (e != cudaSuccess) s = fail_cuda(c, e, "launch_kick");
     }
+    c->fuse_kick = 0;
   }
   c->kp.substep = 0;
   c->kp.max_rung = 0;
@@ -379,7 +454,8 @@ sph_status enqueue_step(sph_ctx *c) {
   c->host_out = out;
   if (s != SPH_OK) return s;
   CK(mark(c, 6));
-  s = copy_out(c, 4);
+  s = c->out_done ? SPH_OK : copy_out(c, 4);
+  c->out_done = 0;
   if (s != SPH_OK) return s;
   return enqueue_status_readback(c);
 }
@@ -658,6 +734,32 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.sys_begin = c->d_sys_begin;
   kp.sys_bucket = c->d_sys_bucket;
   kp.sys_chunk = c->d_sys_chunk;
+  {
+    // reduction tiles of kRedTile buckets within each system
+    std::vector<int> t0, t1, st;
+    int b1 = 0;
+    for (int k = 0; k < n_sys; ++k) {
+      st.push_back((int)t0.size());
+      const int b0 = b1;
+      b1 = b0 + (int)((c->sys_first[k + 1] - c->sys_first[k] + 31) / 32);
+      for (int b = b0; b < b1; b += kRedTile) {
+        t0.push_back(b);
+        t1.push_back(b + kRedTile < b1 ? b + kRedTile : b1);
+      }
+    }
+    st.push_back((int)t0.size());
+    const int nt = (int)t0.size();
+    std::vector<int> all(t0);
+    all.insert(all.end(), t1.begin(), t1.end());
+    all.insert(all.end(), st.begin(), st.end());
+    CKI(dalloc(&c->d_red_tile, all.size()));
+    CKI(cudaMemcpy(c->d_red_tile, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+    CKI(dalloc(&c->tile_partials, (size_t)nt * kNSum));
+    kp.red_tile = c->d_red_tile;
+    kp.red_tile_end = c->d_red_tile + nt;
+    kp.sys_tile = c->d_red_tile + 2 * nt;
+    kp.nred_tiles = nt;
+  }
 
   CKI(dalloc(&c->d_mats, SPH_MAX_MATERIALS));
   CKI(cudaMemcpy(c->d_mats, c->mats, sizeof(c->mats), cudaMemcpyHostToDevice));
@@ -698,6 +800,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   // hierarchical steps are switched on only while a step is enqueued: every
   // other call (sph_prime, sph_density, ...) treats all particles alike
   c->rungs = p->max_rung;
+  c->copy_chunks = 8;
   kp.max_rung = 0;
   kp.substep = 0;
   kp.sub_scale = 1.0;
@@ -779,7 +882,8 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   c->tmp_words = 32;
   CKI(cudaMalloc(&c->tmp, (size_t)n * c->tmp_words * 8));
   CKI(alloc_density_spill(c));
-  CKI(dalloc(&c->partials, (size_t)c->nchunks * 9));
+  CKI(dalloc(&c->partials,
+             (size_t)(c->nchunks > c->kp.nbuckets ? c->nchunks : c->kp.nbuckets) * kNSum));
   CKI(dalloc(&c->d_dt, n_sys));
   CKI(cudaMemset(c->d_dt, 0, sizeof(double) * n_sys));
   kp.dt = c->d_dt;
@@ -870,6 +974,14 @@ sph_status sph_destroy(sph_ctx *c) {
     cudaStreamSynchronize(c->istream);
     cudaStreamDestroy(c->istream);
   }
+  for (int k = 0; k < 2; ++k)
+    if (c->fstream[k]) {
+      cudaStreamSynchronize(c->fstream[k]);
+      cudaStreamDestroy(c->fstream[k]);
+    }
+  if (c->ev_pre) cudaEventDestroy(c->ev_pre);
+  for (int k = 0; k < SPH_MAX_COPY_CHUNKS; ++k)
+    if (c->chunk_ev[k]) cudaEventDestroy(c->chunk_ev[k]);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->in_ev) cudaEventDestroy(c->in_ev);
   // handles that a failed set-up never created stay null and are skipped
@@ -897,6 +1009,14 @@ sph_status sph_autotune(sph_ctx *c, int32_t rounds) {
     c->tune_ms_d[k] = c->tune_ms_f[k] = 0.0;
     c->tune_n[k] = 0;
   }
+  return SPH_OK;
+}
+
+sph_status sph_set_copy_chunks(sph_ctx *c, int32_t chunks) {
+  ENTER(c);
+  if (chunks < 1 || chunks > SPH_MAX_COPY_CHUNKS)
+    return fail(c, SPH_E_ARG, "chunks must be in 1..SPH_MAX_COPY_CHUNKS");
+  c->copy_chunks = chunks;
   return SPH_OK;
 }
 
@@ -1101,6 +1221,13 @@ sph_status sph_step_host(sph_ctx *c, const sph_state *host, double dt, sph_step_
     CK(cudaStreamCreateWithFlags(&c->istream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming));
+  }
+  if (!c->fstream[0]) {
+    for (int k = 0; k < 2; ++k) CK(cudaStreamCreateWithFlags(&c->fstream[k], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_pre, cudaEventDisableTiming));
+    for (int k = 0; k < SPH_MAX_COPY_CHUNKS; ++k)
+      CK(cudaEventCreateWithFlags(&c->chunk_ev[k], cudaEventDisableTiming));
+    CK(cudaMalloc(&c->d_chunk_ctr, sizeof(unsigned) * SPH_MAX_COPY_CHUNKS));
   }
   const sph_state &d = c->st;
   const int64_t n = c->n;

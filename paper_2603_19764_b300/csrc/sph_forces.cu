@@ -24,6 +24,7 @@
 // FP32 form the energy and the F, C^-1 sums are Kahan-compensated, and the
 // per-particle finalize runs in FP32 as well: FP64 stays in positions,
 // integration and global sums.
+#include "sph_kick.cuh"
 #include "sph_pair.cuh"
 
 namespace sphk {
@@ -160,6 +161,15 @@ struct ForceArgs {
   const int *cell_start, *cell_end;
   KParams p;
   Status *st;
+  // global steps: kick each particle once its derivatives are formed (v,
+  // u, S and the strain invariant read from src, written to s), with the
+  // step's sums per bucket in partials
+  int kick;
+  sph_state src;
+  double *partials;
+  // buckets [b_begin, min(b_end, bucket count)) taken through *counter
+  int b_begin, b_end;
+  unsigned *counter;
 };
 
 // Three 4-warp blocks per SM: the pair body and its compensated sums fit in
@@ -184,15 +194,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   const int n_act = A.p.act ? A.st->n_active : 0;
   const int nbuckets = bucket_count(A.p, n_act);
   long long w_pairs = 0, w_cand = 0;
-  int w_fb = 0, w_groups = 0;
+  int w_fb = 0, w_groups = 0, w_upd = 0;
   unsigned w_box = 0;
   // a periodic box must be wider than twice every search radius
   const T box_min = PER ? (T)fmin(fmin(A.p.box_len[0], A.p.box_len[1]), A.p.box_len[2]) : T(0);
   for (;;) {
   unsigned bk = 0;
-  if (lane == 0) bk = atomicAdd(&A.st->next_bucket[1], 1u);
+  if (lane == 0) bk = (unsigned)A.b_begin + atomicAdd(A.counter, 1u);
   bk = __shfl_sync(kFull, bk, 0);
-  if ((int)bk >= nbuckets) break;
+  if ((int)bk >= nbuckets || (int)bk >= A.b_end) break;
   // the bucket's system and its sorted range
   const BucketLane bl = bucket_lane(A.p, n_act, bk, lane, A.n, &A.st->err);
   const int sy = bl.sy;
@@ -204,6 +214,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   const V4 *posh = PK::posh(A.w);
   const V4 *rec = PK::rec(A.w);   // 4 consecutive vectors per particle
 
+  if (A.kick && valid) {
+    // the kick in this bucket's epilogue reads these: ask L2 for them now,
+    // so that their DRAM latency passes while the pair loop runs
+    const void *const pf[] = {A.src.vx + i, A.src.vy + i, A.src.vz + i, A.src.u + i,
+                              A.src.sxx + i, A.src.syy + i, A.src.sxy + i, A.src.sxz + i,
+                              A.src.syz + i, A.src.eps_ii + i, A.s.m + i, A.s.rho + i,
+                              A.s.x + i, A.s.y + i, A.s.z + i, A.s.mat + i};
+#pragma unroll
+    for (const void *q : pf) prefetch_l2(q);
+  }
   const Grid g = R.grid;
   const T Lt = grid_L<T>(g), invL = grid_invL<T>(g);
   const int cc = A.w.cc[ic];
@@ -432,6 +452,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   F4.flush(); F5.flush(); F6.flush(); F7.flush(); F8.flush();
   // ---------------------------------------- finalize (Eq. 21-29, 38-39)
   int fallback = 0;
+  double kacc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // the kick's sums (A.kick)
+  T ktmin = T(INFINITY);
   if (valid) {
     const V4 s0 = V::ld(PK::fs(A.w, 0), i), s1 = V::ld(PK::fs(A.w, 1), i),
              s2 = V::ld(PK::fs(A.w, 2), i);
@@ -490,43 +512,89 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
       for (int k = 0; k < 3; ++k) rot += R[3 * a + k] * Sm[3 * k + b] - Sm[3 * a + k] * R[3 * k + b];
       dS[q] = T(2) * Gam * (E[3 * a + b] - (a == b ? tr3 : T(0))) + sg * rot;
     }
-    A.w.vsig[i] = from_t((T(1) + T(0.6) * al) * s1.z + T(0.6) * be * mumax);
+    KickIn kd;
+    kd.vsig = from_t((T(1) + T(0.6) * al) * s1.z + T(0.6) * be * mumax);
+    kd.edot2 = from_t(T(0.5) * e2);
+    A.w.vsig[i] = kd.vsig;
     A.s.nngb[i] = nngb;
-    A.w.edot2[i] = from_t(T(0.5) * e2);
+    A.w.edot2[i] = kd.edot2;
     if (A.w.divv) A.w.divv[i] = (float)(E[0] + E[4] + E[8]);
     const T axt = ax + s2.x, ayt = ay + s2.y, azt = az + s2.z;
     const T dud = du.get();
-    A.s.ax[i] = fixed ? 0.0 : from_t(axt);
-    A.s.ay[i] = fixed ? 0.0 : from_t(ayt);
-    A.s.az[i] = fixed ? 0.0 : from_t(azt);
-    A.s.dudt[i] = fixed ? 0.0 : from_t(dud);
-    A.s.dsxx[i] = fixed ? 0.0 : from_t(dS[0]);
-    A.s.dsyy[i] = fixed ? 0.0 : from_t(dS[1]);
-    A.s.dsxy[i] = fixed ? 0.0 : from_t(dS[2]);
-    A.s.dsxz[i] = fixed ? 0.0 : from_t(dS[3]);
-    A.s.dsyz[i] = fixed ? 0.0 : from_t(dS[4]);
+    kd.a[0] = fixed ? 0.0 : from_t(axt);
+    kd.a[1] = fixed ? 0.0 : from_t(ayt);
+    kd.a[2] = fixed ? 0.0 : from_t(azt);
+    kd.dudt = fixed ? 0.0 : from_t(dud);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) kd.dS[k] = fixed ? 0.0 : from_t(dS[k]);
+    A.s.ax[i] = kd.a[0];
+    A.s.ay[i] = kd.a[1];
+    A.s.az[i] = kd.a[2];
+    A.s.dudt[i] = kd.dudt;
+    A.s.dsxx[i] = kd.dS[0];
+    A.s.dsyy[i] = kd.dS[1];
+    A.s.dsxy[i] = kd.dS[2];
+    A.s.dsxz[i] = kd.dS[3];
+    A.s.dsyz[i] = kd.dS[4];
     bool fin = isfinite(axt) && isfinite(ayt) && isfinite(azt) && isfinite(dud);
 #pragma unroll
     for (int k = 0; k < 5; ++k) fin = fin && isfinite(dS[k]);
     if (!fin) atomicOr(&A.st->err, ERR_NONFINITE);
+    // the kicks of a global step (§2.4): particle i's derivatives are final
+    // here, and no other warp of this pass reads its v, u or S
+    if (A.kick)
+      kick_particle<T>(A.s, A.src, A.w, A.p, i, true, A.p.dt[sy], true, A.src.vx != A.s.vx, kd,
+                       kacc, ktmin, w_upd, nullptr);
+  }
+  if (A.kick) {
+    // the bucket's terms of its system's sums, in a fixed order (warp
+    // tree), and its time-step minimum
+#pragma unroll
+    for (int k = 0; k < kNSum; ++k) {
+      const double t = wsum(kacc[k]);
+      if (lane == 0) A.partials[(int64_t)bk * kNSum + k] = k == 0 ? 0.5 * t : t;
+    }
+    const double tm = wmin(from_t(ktmin));
+    if (lane == 0) atomicMin(&A.p.sys[sy].dtmin_enc, enc_d(tm));
   }
   w_fb += fallback;
   w_pairs += npairs;
   w_cand += cand;
   }  // bucket loop
   const int nfb = wsum(w_fb);
+  const int nupd = wsum(w_upd);
   const long long pw = wsum(w_pairs);
   const bool box_bad = PER && __any_sync(kFull, w_box);
   if (lane == 0) {
     if (box_bad) atomicOr(&A.st->err, ERR_CAPACITY);
     if (nfb) atomicAdd(&A.st->n_cfallback, nfb);
+    if (nupd) atomicAdd(&A.st->updates, (unsigned long long)nupd);
     atomicAdd(&A.st->pairs_force, (unsigned long long)pw);
     atomicAdd(&A.st->cand_force, (unsigned long long)w_cand);
     atomicAdd(&A.st->groups_force, (unsigned long long)w_groups);
   }
 }
 
-cudaError_t launch_forces(sph_ctx *c) {
+template <typename K> int grid_for_buckets(const sph_ctx *c, K kernel, int64_t buckets) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * kWarpsPerBlock, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t need = (buckets + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t have = (int64_t)per_sm * c->num_sms;
+  return (int)(need < have ? (need > 0 ? need : 1) : have);
+}
+
+template <typename T, int CAP, bool PER>
+void launch_forces_t(const ForceArgs &a, const sph_ctx *c, int64_t buckets, cudaStream_t stream) {
+  k_forces<T, CAP, PER><<<grid_for_buckets(c, k_forces<T, CAP, PER>, buckets),
+                          32 * kWarpsPerBlock, 0, stream>>>(a);
+}
+
+// The pair loop over buckets [b0, b1) (b1 < 0: to the last bucket), taken
+// through the counter *ctr, which must be zero, on `stream`.
+cudaError_t launch_forces_range(sph_ctx *c, int b0, int b1, unsigned *ctr, cudaStream_t stream) {
   ForceArgs a;
   a.s = c->st;
   a.w = c->w;
@@ -535,25 +603,28 @@ cudaError_t launch_forces(sph_ctx *c) {
   a.cell_end = c->cell_end;
   a.p = c->kp;
   a.st = c->d_status;
-  cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[1], 0, sizeof(unsigned), c->stream);
-  if (e != cudaSuccess) return e;
+  a.kick = c->fuse_kick;
+  a.src = c->src;
+  a.partials = c->partials;
+  a.b_begin = b0;
+  a.b_end = b1 < 0 ? 0x7fffffff : b1;
+  a.counter = ctr;
+  const int64_t buckets = (b1 < 0 ? c->kp.nbuckets : b1) - b0;
   if (c->kp.precision == SPH_FP32K) {
-    if (c->kp.periodic)
-      k_forces<float, 800, true><<<resident_grid(c, k_forces<float, 800, true>),
-                                   32 * kWarpsPerBlock, 0, c->stream>>>(a);
-    else
-      k_forces<float, 800, false><<<resident_grid(c, k_forces<float, 800, false>),
-                                    32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    if (c->kp.periodic) launch_forces_t<float, 800, true>(a, c, buckets, stream);
+    else launch_forces_t<float, 800, false>(a, c, buckets, stream);
   } else {
-    if (c->kp.periodic)
-      k_forces<double, 256, true><<<resident_grid(c, k_forces<double, 256, true>),
-                                    32 * kWarpsPerBlock, 0, c->stream>>>(a);
-    else
-      k_forces<double, 256, false><<<resident_grid(c, k_forces<double, 256, false>),
-                                     32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    if (c->kp.periodic) launch_forces_t<double, 256, true>(a, c, buckets, stream);
+    else launch_forces_t<double, 256, false>(a, c, buckets, stream);
   }
   c->nlaunch += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_forces(sph_ctx *c) {
+  cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[1], 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return e;
+  return launch_forces_range(c, 0, -1, &c->d_status->next_bucket[1], c->stream);
 }
 
 }  // namespace sphk

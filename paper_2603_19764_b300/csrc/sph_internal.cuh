@@ -139,6 +139,11 @@ struct KParams {
   const int *sys_begin;        // nsys + 1 sorted-position boundaries (device)
   const int *sys_bucket;       // nsys + 1 bucket boundaries (device)
   const int *sys_chunk;        // nsys + 1 chunk boundaries (device)
+  // reduction tiles of the per-bucket partial sums: tile t covers buckets
+  // [red_tile[t], red_tile_end[t]) of one system; the tiles of system s are
+  // [sys_tile[s], sys_tile[s + 1])
+  const int *red_tile, *red_tile_end, *sys_tile;
+  int nred_tiles;
   const double *dt;            // current step of every system (device)
   int span_d, span_f;          // group span of the density / force kernels
   // FP32 copies of the constants the FP32 pair loops use, so that a
@@ -326,6 +331,11 @@ struct LearnArgs {
 };
 
 // ---------------------------------------------------------------- helpers
+// Ask L2 to fetch the line holding p (no register is written).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ unsigned long long enc_d(double d) {
   unsigned long long b = (unsigned long long)__double_as_longlong(d);
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
@@ -584,11 +594,28 @@ struct sph_ctx {
   int max_cells;
   void *tmp;            // permutation scratch: tmp_words words of 8 bytes per particle
   int tmp_words;
-  double *partials;     // per-chunk diagnostic partial sums
+  double *partials;     // partial sums of the step's diagnostics: per
+                        // reduction chunk (k_kick) or per bucket (the
+                        // force pass's kick); room for the larger count
   int nchunks;
+  // global steps: the force pass kicks every particle in its epilogue (no
+  // separate kick kernel); set only while such a step is enqueued
+  int fuse_kick;
+  // sph_step_host with global steps: the force pass runs as copy_chunks
+  // launches over consecutive bucket ranges, alternating between fstream[0]
+  // and fstream[1] (so that one launch's tail overlaps the next one's
+  // start), and each range's final state is copied back as soon as its
+  // launch completes (chunk_ev); chunked_out marks a step enqueued so
+  int copy_chunks;
+  int out_done;                 // the step's last group is already being copied back
+  cudaStream_t fstream[2];
+  cudaEvent_t chunk_ev[SPH_MAX_COPY_CHUNKS], ev_pre;
+  unsigned *d_chunk_ctr;        // one bucket counter per launch
   int nsys;
   int64_t *sys_first;   // host copy of the system boundaries (nsys + 1)
   int *d_sys_begin, *d_sys_bucket, *d_sys_chunk;
+  int *d_red_tile;          // tile starts, tile ends, per-system tile offsets
+  double *tile_partials;    // per reduction tile
   sphk::SysRec *d_sys;
   sphk::SysRec *h_sys;      // pinned mirror
   double *d_dt;             // device copy of the current dt of every system
@@ -675,7 +702,10 @@ cudaError_t launch_predict_pack(sph_ctx *c, int predict, int parts);
 cudaError_t launch_density(sph_ctx *c, int expand);
 cudaError_t launch_eos_pack(sph_ctx *c);
 cudaError_t launch_forces(sph_ctx *c);
+cudaError_t launch_forces_range(sph_ctx *c, int b0, int b1, unsigned *ctr, cudaStream_t stream);
 cudaError_t launch_kick(sph_ctx *c, int kick);
+// the step's sums from the per-bucket partials of a force pass that kicked
+cudaError_t launch_reduce_buckets(sph_ctx *c);
 cudaError_t launch_reset_status(sph_ctx *c, int full);
 cudaError_t launch_rung_init(sph_ctx *c);
 // hierarchical steps: the list of the substep's active particles (KParams::act)

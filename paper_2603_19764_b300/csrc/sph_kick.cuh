@@ -1,0 +1,124 @@
+// sph_kick.cuh -- the per-particle closing kick, radial return and opening
+// kick of §2.4 (Eq. 40-43), with the particle's terms of the step's FP64
+// sums (Eq. 46) and of the time-step minimum (Eq. 38-39). Shared by the
+// kick kernel and by the force pass, whose epilogue kicks each particle
+// of a global step as soon as its derivatives are formed.
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+constexpr int kNSum = 9;   // e_kin (doubled), e_int, e_pot, p[3], L[3]
+constexpr int kRedTile = 512;   // buckets per tile of the per-bucket sums
+
+// Derivatives of particle i at time i, as the force pass wrote them (FP64
+// values; the FP32 form's are exact widenings of FP32 results).
+struct KickIn {
+  double a[3], dudt, dS[5];
+  double edot2;   // 1/2 edot:edot
+  double vsig;    // CFL signal speed of Eq. 39
+};
+
+// Particle i of system sy: with kick, moving particles whose own step ends
+// with this substep are closed to i (v, u, S alike), S is rescaled with Y
+// at (rho_i, u_i), the strain invariant gains dt 1/2 edot:edot and the
+// state is opened to i + 1/2; the others are copied from the read view when
+// copy is set. Adds the particle's terms of the sums (at time i) to acc and
+// its time-step criteria to tmin. sub: length of the substep (the step
+// without rungs); last: every particle's step ends with this substep.
+template <typename T>
+__device__ __forceinline__ void kick_particle(const sph_state &s, const sph_state &src,
+                                              const Work &w, const KParams &P, int64_t i,
+                                              bool kick, double sub, bool last, bool copy,
+                                              const KickIn &d, double acc[kNSum], T &tmin,
+                                              int &updates, int *hist) {
+  const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
+  const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
+  const double m = s.m[i];
+  const double *a = d.a;
+  double v[3] = {src.vx[i], src.vy[i], src.vz[i]};
+  double u = src.u[i];
+  if (kick && !fixed && rung_active(P, i)) {
+    const double dt = sub * (double)rung_len(P, i), hdt = 0.5 * dt;
+    const MatT<T> &M = mat_t<T>(P, s.mat[i]);
+    double S[5] = {src.sxx[i], src.syy[i], src.sxy[i], src.sxz[i], src.syz[i]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] += hdt * a[k];
+    u += hdt * d.dudt;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) S[k] += hdt * d.dS[k];
+    if (M.strength) {
+      const EosT<T> e = eos_t<T>(M, s.rho[i], u);
+      const T St[5] = {to_t<T>(S[0]), to_t<T>(S[1]), to_t<T>(S[2]), to_t<T>(S[3]), to_t<T>(S[4])};
+      const double f = from_t(radial_factor_t<T>(St, yield_t<T>(M, e.P, to_t<T>(u)), P.yield_norm));
+      if (f < 1.0) {   // below the yield surface f is exactly 1
+#pragma unroll
+        for (int k = 0; k < 5; ++k) S[k] *= f;
+      }
+    } else {
+      S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
+    }
+    s.eps_ii[i] = src.eps_ii[i] + dt * d.edot2;
+    // opening kick from the state at i; with rungs over the next step of
+    // the rung the criteria ask for, no coarser than the coarsest rung
+    // whose steps start at the next substep
+    double ho = hdt;
+    if (P.max_rung) {
+      const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      const double h = s.h[i];
+      const double ta = am > 0.0 ? P.eta_a * sqrt(h / am) : INFINITY;
+      const double tc = P.eta_c * h / d.vsig;
+      int r = rung_want(P, sub, ta < tc ? ta : tc);
+      int r_al = P.max_rung;
+      for (int q = P.substep + 1; r_al > 0 && (q & 1) == 0; q >>= 1) --r_al;
+      r = r > r_al ? r : r_al;
+      w.rung[i] = r;
+      ho = 0.5 * sub * (double)(1 << (P.max_rung - r));
+      if (last) atomicAdd(&hist[r], 1);
+    }
+    ++updates;
+    s.vx[i] = v[0] + ho * a[0];
+    s.vy[i] = v[1] + ho * a[1];
+    s.vz[i] = v[2] + ho * a[2];
+    s.u[i] = u + ho * d.dudt;
+    s.sxx[i] = S[0] + ho * d.dS[0];
+    s.syy[i] = S[1] + ho * d.dS[1];
+    s.sxy[i] = S[2] + ho * d.dS[2];
+    s.sxz[i] = S[3] + ho * d.dS[3];
+    s.syz[i] = S[4] + ho * d.dS[4];
+  } else if (copy) {   // not kicked: the state as read
+    s.vx[i] = v[0];
+    s.vy[i] = v[1];
+    s.vz[i] = v[2];
+    s.u[i] = u;
+    s.sxx[i] = src.sxx[i];
+    s.syy[i] = src.syy[i];
+    s.sxy[i] = src.sxy[i];
+    s.sxz[i] = src.sxz[i];
+    s.syz[i] = src.syz[i];
+    s.eps_ii[i] = src.eps_ii[i];
+  }
+  const double x = s.x[i], y = s.y[i], z = s.z[i];
+  T g[3], phi;
+  ext_field_t<T>(P, x, y, z, g, &phi);
+  acc[0] += m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);   // halved when summed
+  acc[1] += m * u;
+  acc[2] += m * from_t(phi);
+  acc[3] += m * v[0];
+  acc[4] += m * v[1];
+  acc[5] += m * v[2];
+  acc[6] += m * (y * v[2] - z * v[1]);
+  acc[7] += m * (z * v[0] - x * v[2]);
+  acc[8] += m * (x * v[1] - y * v[0]);
+  if (!fixed) {
+    const T H = to_t<T>(s.h[i]);
+    const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
+    const T am = sqrt(ax * ax + ay * ay + az * az);
+    const T ta = am > T(0) ? eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
+    const T tc = eta_c * H / to_t<T>(d.vsig);                       // Eq. 39
+    tmin = tmin_(tmin, tmin_(ta, tc));
+  }
+}
+
+}  // namespace sphk

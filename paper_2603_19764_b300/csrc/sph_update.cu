@@ -1,11 +1,9 @@
 // sph_update.cu -- closing and opening kicks with radial return (§2.4,
 // Eq. 41-43), FP64 global sums (energies, momentum, angular momentum Eq. 46)
 // and the time-step minimum of Eq. 38-39.
-#include "sph_internal.cuh"
+#include "sph_kick.cuh"
 
 namespace sphk {
-
-constexpr int kNSum = 9;
 
 // kick = 1: close to i (v, u, S alike), rescale S with Y at (rho_i, u_i),
 // accumulate 1/2 edot:edot dt, sum diagnostics at i, open to i+1/2.
@@ -37,98 +35,16 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, sph_state src, Wor
   int updates = 0;
   double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   T tmin = T(INFINITY);
-  const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
   for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     // hierarchical steps: before the last substep only the kicked particles
     // matter (the sums and the time step are those of the big step's end)
     if (!last && !rung_active(P, i)) continue;
-    const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
-    const double m = s.m[i];
-    const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
-    double v[3] = {src.vx[i], src.vy[i], src.vz[i]};
-    double u = src.u[i];
-    // kicked: moving particles whose own step ends with this substep
-    if (kick && !fixed && rung_active(P, i)) {
-      const double dt = sub * (double)rung_len(P, i), hdt = 0.5 * dt;
-      const MatT<T> &M = mat_t<T>(P, s.mat[i]);
-      const double dS[5] = {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]};
-      double S[5] = {src.sxx[i], src.syy[i], src.sxy[i], src.sxz[i], src.syz[i]};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) v[k] += hdt * a[k];
-      u += hdt * s.dudt[i];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) S[k] += hdt * dS[k];
-      if (M.strength) {
-        const EosT<T> e = eos_t<T>(M, s.rho[i], u);
-        const T St[5] = {to_t<T>(S[0]), to_t<T>(S[1]), to_t<T>(S[2]), to_t<T>(S[3]), to_t<T>(S[4])};
-        const double f = from_t(radial_factor_t<T>(St, yield_t<T>(M, e.P, to_t<T>(u)), P.yield_norm));
-        if (f < 1.0) {   // below the yield surface f is exactly 1
-#pragma unroll
-          for (int k = 0; k < 5; ++k) S[k] *= f;
-        }
-      } else {
-        S[0] = S[1] = S[2] = S[3] = S[4] = 0.0;
-      }
-      s.eps_ii[i] = src.eps_ii[i] + dt * w.edot2[i];
-      // opening kick from the state at i; with rungs over the next step of
-      // the rung the criteria ask for, no coarser than the coarsest rung
-      // whose steps start at the next substep
-      double ho = hdt;
-      if (P.max_rung) {
-        const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-        const double h = s.h[i];
-        const double ta = am > 0.0 ? P.eta_a * sqrt(h / am) : INFINITY;
-        const double tc = P.eta_c * h / w.vsig[i];
-        int r = rung_want(P, sub, ta < tc ? ta : tc);
-        int r_al = P.max_rung;
-        for (int m = P.substep + 1; r_al > 0 && (m & 1) == 0; m >>= 1) --r_al;
-        r = r > r_al ? r : r_al;
-        w.rung[i] = r;
-        ho = 0.5 * sub * (double)(1 << (P.max_rung - r));
-        if (last) atomicAdd(&hist[r], 1);
-      }
-      ++updates;
-      s.vx[i] = v[0] + ho * a[0];
-      s.vy[i] = v[1] + ho * a[1];
-      s.vz[i] = v[2] + ho * a[2];
-      s.u[i] = u + ho * s.dudt[i];
-      s.sxx[i] = S[0] + ho * dS[0];
-      s.syy[i] = S[1] + ho * dS[1];
-      s.sxy[i] = S[2] + ho * dS[2];
-      s.sxz[i] = S[3] + ho * dS[3];
-      s.syz[i] = S[4] + ho * dS[4];
-    } else if (copy) {   // not kicked: the state as read
-      s.vx[i] = v[0];
-      s.vy[i] = v[1];
-      s.vz[i] = v[2];
-      s.u[i] = u;
-      s.sxx[i] = src.sxx[i];
-      s.syy[i] = src.syy[i];
-      s.sxy[i] = src.sxy[i];
-      s.sxz[i] = src.sxz[i];
-      s.syz[i] = src.syz[i];
-      s.eps_ii[i] = src.eps_ii[i];
-    }
-    const double x = s.x[i], y = s.y[i], z = s.z[i];
-    T g[3], phi;
-    ext_field_t<T>(P, x, y, z, g, &phi);
-    acc[0] += m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);   // halved below (exact)
-    acc[1] += m * u;
-    acc[2] += m * from_t(phi);
-    acc[3] += m * v[0];
-    acc[4] += m * v[1];
-    acc[5] += m * v[2];
-    acc[6] += m * (y * v[2] - z * v[1]);
-    acc[7] += m * (z * v[0] - x * v[2]);
-    acc[8] += m * (x * v[1] - y * v[0]);
-    if (!fixed) {
-      const T H = to_t<T>(s.h[i]);
-      const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
-      const T am = sqrt(ax * ax + ay * ay + az * az);
-      const T ta = am > T(0) ? eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
-      const T tc = eta_c * H / to_t<T>(w.vsig[i]);                    // Eq. 39
-      tmin = tmin_(tmin, tmin_(ta, tc));
-    }
+    const KickIn d = {{s.ax[i], s.ay[i], s.az[i]},
+                      s.dudt[i],
+                      {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]},
+                      w.edot2[i],
+                      w.vsig[i]};
+    kick_particle<T>(s, src, w, P, i, kick != 0, sub, last, copy, d, acc, tmin, updates, hist);
   }
   // block sums in a fixed order: every thread parks its nine partial sums
   // in shared memory; warp q then reduces sum q (warp 0 also sum 8) over
@@ -159,25 +75,61 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, sph_state src, Wor
   }
 }
 
-// Per system (one block each): fixed-order sum of its chunks' partials,
-// strided per thread, then a tree over the block.
-__global__ void __launch_bounds__(kBlock) k_reduce_final(const double *partials, KParams P) {
-  __shared__ double red[kBlock / 32];
-  SysRec &R = P.sys[blockIdx.x];
-  const int b0 = R.chunk_off, b1 = P.sys_chunk[blockIdx.x + 1];
-  for (int k = 0; k < kNSum; ++k) {
-    double t = 0.0;
-    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) t += partials[b * kNSum + k];
-    t = wsum(t);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int q = 0; q < kBlock / 32; ++q) s += red[q];
-      R.sums[k] = s;
-    }
-    __syncthreads();
+// Fixed-order sums of partial sums over units [b0, b1): each thread sums a
+// strided subset, all nine sums at once and four units per round so that
+// the loads overlap, then a tree over the block, one warp per sum. The
+// result goes to out[0..kNSum).
+constexpr int kReduceThreads = 1024;
+__device__ __forceinline__ void reduce_units(const double *partials, int b0, int b1,
+                                             double *out) {
+  __shared__ double red[kNSum][kReduceThreads / 32];
+  double t[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  constexpr int kU = 4;
+  int b = b0 + threadIdx.x;
+  for (; b + (kU - 1) * kReduceThreads < b1; b += kU * kReduceThreads) {
+    double v[kU][kNSum];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int k = 0; k < kNSum; ++k) v[u][k] = partials[(int64_t)(b + u * kReduceThreads) * kNSum + k];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int k = 0; k < kNSum; ++k) t[k] += v[u][k];
   }
+  for (; b < b1; b += kReduceThreads)
+#pragma unroll
+    for (int k = 0; k < kNSum; ++k) t[k] += partials[(int64_t)b * kNSum + k];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNSum; ++k) {
+    const double s = wsum(t[k]);
+    if (lane == 0) red[k][w] = s;
+  }
+  __syncthreads();
+  if (w < kNSum) {
+    const double s = wsum(red[w][lane]);   // kReduceThreads / 32 = 32 warp sums
+    if (lane == 0) out[w] = s;
+  }
+}
+
+// Per system (one block each): its sums from the partials of its reduction
+// chunks (k_kick) or from those of its reduction tiles (the force pass's
+// kick, after k_reduce_tiles).
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *partials, KParams P,
+                                                                int per_tile) {
+  SysRec &R = P.sys[blockIdx.x];
+  const int b0 = per_tile ? P.sys_tile[blockIdx.x] : R.chunk_off;
+  const int b1 = per_tile ? P.sys_tile[blockIdx.x + 1] : P.sys_chunk[blockIdx.x + 1];
+  reduce_units(partials, b0, b1, R.sums);
+}
+
+// One block per reduction tile: the fixed-order sum of the partials of its
+// kRedTile buckets.
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_tiles(const double *partials, KParams P,
+                                                                double *tile_partials) {
+  const int t = blockIdx.x;
+  reduce_units(partials, P.red_tile[t], P.red_tile_end[t], tile_partials + (int64_t)t * kNSum);
 }
 
 // Hierarchical steps: at the start of a big step every moving particle
@@ -301,7 +253,17 @@ cudaError_t launch_kick(sph_ctx *c, int kick) {
   else
     k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
                                                           c->partials, c->d_status);
-  k_reduce_final<<<c->nsys, kBlock, 0, c->stream>>>(c->partials, c->kp);
+  k_reduce_final<<<c->nsys, kReduceThreads, 0, c->stream>>>(c->partials, c->kp, 0);
+  c->nlaunch += 2;
+  return cudaGetLastError();
+}
+
+// The sums of a step whose force pass kicked every particle (per-bucket
+// partials): per tile of kRedTile buckets, then per system.
+cudaError_t launch_reduce_buckets(sph_ctx *c) {
+  k_reduce_tiles<<<c->kp.nred_tiles, kReduceThreads, 0, c->stream>>>(c->partials, c->kp,
+                                                                     c->tile_partials);
+  k_reduce_final<<<c->nsys, kReduceThreads, 0, c->stream>>>(c->tile_partials, c->kp, 1);
   c->nlaunch += 2;
   return cudaGetLastError();
 }

@@ -122,7 +122,8 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_mlp_set", "sph_mlp_get", "sph_mlp_fit_norm", "sph_mlp_forward",
            "sph_mlp_loss_grad", "sph_mlp_adam_step", "sph_mlp_train_epoch",
            "sph_set_learned_h", "sph_learn_samples", "sph_check_conversions",
-           "sph_measure_fma_peak", "sph_inject_cuda_failure", "sph_learn_proposal")
+           "sph_measure_fma_peak", "sph_inject_cuda_failure", "sph_learn_proposal",
+           "sph_set_copy_chunks")
 MLP_NPARAM, MLP_NNORM = 4673, 14
 GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
 PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
@@ -205,6 +206,8 @@ def lib():
         L.sph_tune_info.argtypes = [VP, C.POINTER(SphTuneReport)]
         L.sph_set_graph.restype = st
         L.sph_set_graph.argtypes = [VP, C.c_int32]
+        L.sph_set_copy_chunks.restype = st
+        L.sph_set_copy_chunks.argtypes = [VP, C.c_int32]
         L.sph_diagnostics_noalloc.restype = st
         L.sph_diagnostics_noalloc.argtypes = [C.POINTER(SphState), C.c_int64, VP, VP]
         L.sph_learn_proposal.restype = st
@@ -404,6 +407,9 @@ class Simulation:
 
     def set_graph(self, on: bool = True):
         return self._check(lib().sph_set_graph(self.ctx, 1 if on else 0), "sph_set_graph")
+
+    def set_copy_chunks(self, chunks: int):
+        return self._check(lib().sph_set_copy_chunks(self.ctx, int(chunks)), "sph_set_copy_chunks")
 
     def step_host(self, host: "HostState", dt: float) -> dict:
         info = SphStepInfo()

@@ -142,10 +142,12 @@ def test_full_steps_granular_column(precision):
     sim.close()
 
 
-def test_step_host_equals_step():
+@pytest.mark.parametrize("chunks", [1, 3, 16])
+def test_step_host_equals_step(chunks):
     """The host-buffer entry point (copy in, step, overlapped copy-out by
-    array group) leaves exactly the state of device steps, also when the
-    context has a captured graph for its device steps."""
+    array group; the force pass in `chunks` bucket ranges, each copied back
+    as it completes) leaves exactly the state of device steps, also when
+    the context has a captured graph for its device steps."""
     w = WL["impact"]
     p = _params(w, 1)
     a = sph.Simulation(w.arrays, w.materials, p)
@@ -153,6 +155,7 @@ def test_step_host_equals_step():
     a.prime()
     b.prime()
     b.set_graph(True)
+    b.set_copy_chunks(chunks)
     host = sph.HostState(b.to_numpy())
     for _ in range(2):
         ia = a.step(w.dt)
@@ -167,6 +170,32 @@ def test_step_host_equals_step():
     ia = a.step(w.dt)
     ib = b.step(w.dt)
     assert ia["e_kin"] == ib["e_kin"]
+    a.close()
+    b.close()
+
+
+def test_step_host_batch_chunks_equal_step():
+    """A batch through the host-buffer entry point, its force pass in bucket
+    ranges whose bounds fall inside systems: the state of device steps."""
+    w = wl.impact_batch(5, precision=1, scale=0.03)
+    p = dict(w.params, precision=1, h_tol=1e-6)
+    a = sph.Simulation(w.arrays, w.materials, p, systems=w.systems)
+    b = sph.Simulation(w.arrays, w.materials, p, systems=w.systems)
+    a.prime()
+    b.prime()
+    b.set_copy_chunks(7)
+    host = sph.HostState(b.to_numpy())
+    for _ in range(2):
+        a.step(0.0)
+        b.step_host(host, 0.0)
+    ga = a.to_numpy()
+    gb = {k: v.numpy() for k, v in host.t.items()}
+    for f in wl.FIELDS_F64 + ("nngb", "mat", "flags", "id"):
+        assert np.array_equal(ga[f], gb[f]), f
+    with pytest.raises(sph.SphError):
+        b.set_copy_chunks(0)
+    with pytest.raises(sph.SphError):
+        b.set_copy_chunks(17)
     a.close()
     b.close()
 
