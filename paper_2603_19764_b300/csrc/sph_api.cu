@@ -142,8 +142,10 @@ void free_all(sph_ctx *c) {
                  c->w.fj32, c->w.fj64, c->w.posh32, c->w.posh64,
                  c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
-                 c->cell_start, c->cell_end, c->tmp, c->partials, c->d_dt, c->d_status,
-                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_sys_chunk, c->d_red_tile,
+                 c->cell_start, c->cell_end, c->tmp, c->d_dt, c->d_status,
+                 c->d_sys, c->d_sys_begin, c->d_sys_bucket, c->d_red_tile, c->w.tcrit,
+                 c->w.terms[0], c->w.terms[1], c->w.terms[2], c->w.terms[3], c->w.terms[4],
+                 c->w.terms[5], c->w.terms[6], c->w.terms[7], c->w.terms[8],
                  c->tile_partials, c->d_chunk_ctr, c->w.divv,
                  c->learn.hprev, c->learn.hprop, c->learn.feat[0], c->learn.feat[1],
                  c->learn.feat[2], c->learn.x_out, c->learn.y_out, c->dens_spill, c->w.rung,
@@ -435,9 +437,11 @@ sph_status enqueue_step(sph_ctx *c) {
       const cudaError_t e = launch_compact_active(c);
       if (e != cudaSuccess) s = fail_cuda(c, e, "launch_compact_active");
     }
-    // global steps: the force pass kicks each particle as soon as its
-    // derivatives are formed, leaving the sums to one small kernel
-    c->fuse_kick = L == 1;
+    // global steps of sph_step_host: the force pass kicks each particle as
+    // soon as its derivatives are formed (its outputs are then copied back
+    // range by range), leaving the sums to two small kernels; device steps
+    // keep the kick kernel (same bits, same time on the device)
+    c->fuse_kick = L == 1 && c->host_out != nullptr;
     if (s == SPH_OK) s = run_derivatives(c, 1);
     if (s == SPH_OK) {
       const cudaError_t e = c->fuse_kick ? launch_reduce_buckets(c) : launch_kick(c, 1);
@@ -667,13 +671,13 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     }                                      \
   } while (0)
 
-  // Systems: particle ranges, 32-particle buckets and reduction chunks that
-  // never straddle two systems, a cell budget of twice the particle count
-  // (at least 4096, at most 2^24) each.
+  // Systems: particle ranges and 32-particle buckets that never straddle
+  // two systems, a cell budget of twice the particle count (at least 4096,
+  // at most 2^24) each.
   c->sys_first = (int64_t *)malloc(sizeof(int64_t) * (n_sys + 1));
   c->dt_next = (double *)calloc(n_sys, sizeof(double));
   SysRec *rec = (SysRec *)calloc(n_sys, sizeof(SysRec));
-  int *bnd = (int *)malloc(sizeof(int) * 3 * (n_sys + 1));
+  int *bnd = (int *)malloc(sizeof(int) * 2 * (n_sys + 1));
   if (!c->sys_first || !c->dt_next || !rec || !bnd) {
     free(rec);
     free(bnd);
@@ -681,25 +685,22 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     free(c);
     return SPH_E_ARG;
   }
-  int *bb = bnd, *bk = bnd + (n_sys + 1), *bc = bnd + 2 * (n_sys + 1);
-  int64_t buckets = 0, chunks = 0, cells = 0;
+  int *bb = bnd, *bk = bnd + (n_sys + 1);
+  int64_t buckets = 0, cells = 0;
   for (int k = 0; k <= n_sys; ++k) {
     c->sys_first[k] = sys_first[k];
     bb[k] = (int)sys_first[k];
     bk[k] = (int)buckets;
-    bc[k] = (int)chunks;
     if (k == n_sys) break;
     const int64_t cnt = sys_first[k + 1] - sys_first[k];
     rec[k].begin = (int)sys_first[k];
     rec[k].end = (int)sys_first[k + 1];
     rec[k].bucket_off = (int)buckets;
-    rec[k].chunk_off = (int)chunks;
     int64_t cap = 2 * cnt;
     if (cap < 4096) cap = 4096;
     if (cap > (1 << 24)) cap = 1 << 24;
     rec[k].cell_cap = (int)cap;
     buckets += (cnt + 31) / 32;
-    chunks += (cnt + kChunk - 1) / kChunk;
     cells += cap;
   }
   // 32-bit sort keys: the system index above a Morton code of 3 * axis_bits
@@ -707,33 +708,27 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   while ((1 << sys_bits) < n_sys) ++sys_bits;
   int axis_bits = (32 - sys_bits) / 3;
   if (axis_bits > 10) axis_bits = 10;
-  c->nchunks = (int)chunks;
   c->max_cells = (int)cells;
   KParams &kp = c->kp;
   kp.nsys = n_sys;
   kp.axis_bits = axis_bits;
   kp.nbuckets = (int)buckets;
-  kp.nchunks = (int)chunks;
   kp.span_d = 2;
   kp.span_f = 2;
   cudaError_t es = dalloc(&c->d_sys, n_sys);
   if (es == cudaSuccess) es = cudaMemcpy(c->d_sys, rec, sizeof(SysRec) * n_sys, cudaMemcpyHostToDevice);
   if (es == cudaSuccess) es = dalloc(&c->d_sys_begin, n_sys + 1);
   if (es == cudaSuccess) es = dalloc(&c->d_sys_bucket, n_sys + 1);
-  if (es == cudaSuccess) es = dalloc(&c->d_sys_chunk, n_sys + 1);
   if (es == cudaSuccess)
     es = cudaMemcpy(c->d_sys_begin, bb, sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice);
   if (es == cudaSuccess)
     es = cudaMemcpy(c->d_sys_bucket, bk, sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice);
-  if (es == cudaSuccess)
-    es = cudaMemcpy(c->d_sys_chunk, bc, sizeof(int) * (n_sys + 1), cudaMemcpyHostToDevice);
   free(rec);
   free(bnd);
   CKI(es);
   kp.sys = c->d_sys;
   kp.sys_begin = c->d_sys_begin;
   kp.sys_bucket = c->d_sys_bucket;
-  kp.sys_chunk = c->d_sys_chunk;
   {
     // reduction tiles of kRedTile buckets within each system
     std::vector<int> t0, t1, st;
@@ -754,7 +749,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     all.insert(all.end(), st.begin(), st.end());
     CKI(dalloc(&c->d_red_tile, all.size()));
     CKI(cudaMemcpy(c->d_red_tile, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
-    CKI(dalloc(&c->tile_partials, (size_t)nt * kNSum));
+    CKI(dalloc(&c->tile_partials, (size_t)nt * kNSlot));
     kp.red_tile = c->d_red_tile;
     kp.red_tile_end = c->d_red_tile + nt;
     kp.sys_tile = c->d_red_tile + 2 * nt;
@@ -882,8 +877,8 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   c->tmp_words = 32;
   CKI(cudaMalloc(&c->tmp, (size_t)n * c->tmp_words * 8));
   CKI(alloc_density_spill(c));
-  CKI(dalloc(&c->partials,
-             (size_t)(c->nchunks > c->kp.nbuckets ? c->nchunks : c->kp.nbuckets) * kNSum));
+  for (int k = 0; k < kNSum; ++k) CKI(dalloc(&w.terms[k], n));
+  CKI(dalloc(&w.tcrit, n));
   CKI(dalloc(&c->d_dt, n_sys));
   CKI(cudaMemset(c->d_dt, 0, sizeof(double) * n_sys));
   kp.dt = c->d_dt;

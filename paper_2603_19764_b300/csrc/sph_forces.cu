@@ -162,11 +162,10 @@ struct ForceArgs {
   KParams p;
   Status *st;
   // global steps: kick each particle once its derivatives are formed (v,
-  // u, S and the strain invariant read from src, written to s), with the
-  // step's sums per bucket in partials
+  // u, S and the strain invariant read from src, written to s; its terms
+  // of the step's sums to the work arrays)
   int kick;
   sph_state src;
-  double *partials;
   // buckets [b_begin, min(b_end, bucket count)) taken through *counter
   int b_begin, b_end;
   unsigned *counter;
@@ -452,8 +451,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   F4.flush(); F5.flush(); F6.flush(); F7.flush(); F8.flush();
   // ---------------------------------------- finalize (Eq. 21-29, 38-39)
   int fallback = 0;
-  double kacc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // the kick's sums (A.kick)
-  T ktmin = T(INFINITY);
   if (valid) {
     const V4 s0 = V::ld(PK::fs(A.w, 0), i), s1 = V::ld(PK::fs(A.w, 1), i),
              s2 = V::ld(PK::fs(A.w, 2), i);
@@ -542,20 +539,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     if (!fin) atomicOr(&A.st->err, ERR_NONFINITE);
     // the kicks of a global step (§2.4): particle i's derivatives are final
     // here, and no other warp of this pass reads its v, u or S
-    if (A.kick)
+    if (A.kick) {
+      double term[kNSum], tcr;
       kick_particle<T>(A.s, A.src, A.w, A.p, i, true, A.p.dt[sy], true, A.src.vx != A.s.vx, kd,
-                       kacc, ktmin, w_upd, nullptr);
-  }
-  if (A.kick) {
-    // the bucket's terms of its system's sums, in a fixed order (warp
-    // tree), and its time-step minimum
+                       term, &tcr, w_upd, nullptr);
+      // left for the reduction kernels, which add them in the kick
+      // kernel's order
 #pragma unroll
-    for (int k = 0; k < kNSum; ++k) {
-      const double t = wsum(kacc[k]);
-      if (lane == 0) A.partials[(int64_t)bk * kNSum + k] = k == 0 ? 0.5 * t : t;
+      for (int k = 0; k < kNSum; ++k) A.w.terms[k][i] = term[k];
+      A.w.tcrit[i] = tcr;
     }
-    const double tm = wmin(from_t(ktmin));
-    if (lane == 0) atomicMin(&A.p.sys[sy].dtmin_enc, enc_d(tm));
   }
   w_fb += fallback;
   w_pairs += npairs;
@@ -605,7 +598,6 @@ cudaError_t launch_forces_range(sph_ctx *c, int b0, int b1, unsigned *ctr, cudaS
   a.st = c->d_status;
   a.kick = c->fuse_kick;
   a.src = c->src;
-  a.partials = c->partials;
   a.b_begin = b0;
   a.b_end = b1 < 0 ? 0x7fffffff : b1;
   a.counter = ctr;

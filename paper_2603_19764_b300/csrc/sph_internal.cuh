@@ -77,9 +77,7 @@ struct SysRec {
   Grid grid;
   int begin, end;      // sorted positions (= ids) of the system's particles
   int bucket_off;      // first 32-particle bucket of the system
-  int chunk_off;       // first reduction chunk of the system
   int cell_cap;        // cells the system may use
-  int pad_;
   double sums[9];      // e_kin, e_int, e_pot, p[3], L[3]
 };
 
@@ -134,11 +132,10 @@ struct KParams {
   const MatT<double> *matd;
   // systems
   int nsys, axis_bits;         // Morton bits per axis below the system bits
-  int nbuckets, nchunks;
+  int nbuckets;
   SysRec *sys;                 // nsys records (device)
   const int *sys_begin;        // nsys + 1 sorted-position boundaries (device)
   const int *sys_bucket;       // nsys + 1 bucket boundaries (device)
-  const int *sys_chunk;        // nsys + 1 chunk boundaries (device)
   // reduction tiles of the per-bucket partial sums: tile t covers buckets
   // [red_tile[t], red_tile_end[t]) of one system; the tiles of system s are
   // [sys_tile[s], sys_tile[s + 1])
@@ -215,9 +212,8 @@ template <> __device__ __forceinline__ double pconst<double>(double d, float) { 
 constexpr int kNumSpans = 3;
 constexpr int kSpans[kNumSpans] = {1, 2, 3};
 
-constexpr int kChunk = 2048;   // particles per reduction chunk (8 per thread)
 
-// System owning a sorted position / an id / a bucket / a chunk: the last
+// System owning a sorted position / an id / a bucket: the last
 // boundary not above the value (bounds has nsys + 1 entries).
 __device__ __forceinline__ int sys_lookup(const int *bounds, int nsys, int64_t v) {
   int lo = 0, hi = nsys - 1;
@@ -313,6 +309,8 @@ struct Work {
   float4 *fs32[3];              // own stress, shear modulus, c_L, external g
   double4_32a *fs64[3];
   float *divv;                  // tr of the corrected velocity gradient (learned form)
+  double *terms[9];             // each particle's terms of the step's sums (Eq. 46)
+  double *tcrit;                // and its time-step criterion (Eq. 38-39)
   int *rung;                    // hierarchical steps: rung of every particle, or null
   int *act;                     // hierarchical steps of one system: active list (n)
   int *act_tiles;               // and its per-tile counts / offsets
@@ -594,10 +592,6 @@ struct sph_ctx {
   int max_cells;
   void *tmp;            // permutation scratch: tmp_words words of 8 bytes per particle
   int tmp_words;
-  double *partials;     // partial sums of the step's diagnostics: per
-                        // reduction chunk (k_kick) or per bucket (the
-                        // force pass's kick); room for the larger count
-  int nchunks;
   // global steps: the force pass kicks every particle in its epilogue (no
   // separate kick kernel); set only while such a step is enqueued
   int fuse_kick;
@@ -613,7 +607,7 @@ struct sph_ctx {
   unsigned *d_chunk_ctr;        // one bucket counter per launch
   int nsys;
   int64_t *sys_first;   // host copy of the system boundaries (nsys + 1)
-  int *d_sys_begin, *d_sys_bucket, *d_sys_chunk;
+  int *d_sys_begin, *d_sys_bucket;
   int *d_red_tile;          // tile starts, tile ends, per-system tile offsets
   double *tile_partials;    // per reduction tile
   sphk::SysRec *d_sys;
@@ -704,7 +698,8 @@ cudaError_t launch_eos_pack(sph_ctx *c);
 cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_forces_range(sph_ctx *c, int b0, int b1, unsigned *ctr, cudaStream_t stream);
 cudaError_t launch_kick(sph_ctx *c, int kick);
-// the step's sums from the per-bucket partials of a force pass that kicked
+// the step's sums from the per-particle terms the kicks left (per tile, then
+// per system)
 cudaError_t launch_reduce_buckets(sph_ctx *c);
 cudaError_t launch_reset_status(sph_ctx *c, int full);
 cudaError_t launch_rung_init(sph_ctx *c);

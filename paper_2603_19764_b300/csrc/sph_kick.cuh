@@ -10,7 +10,11 @@
 namespace sphk {
 
 constexpr int kNSum = 9;   // e_kin (doubled), e_int, e_pot, p[3], L[3]
-constexpr int kRedTile = 512;   // buckets per tile of the per-bucket sums
+// Slots of the step's reductions: the nine sums, then the time-step
+// minimum of Eq. 38-39
+constexpr int kSlotDt = kNSum, kNSlot = kNSum + 1;
+// Reduction tiles: 64 buckets (2048 sorted positions) of one system
+constexpr int kRedTile = 64;
 
 // Derivatives of particle i at time i, as the force pass wrote them (FP64
 // values; the FP32 form's are exact widenings of FP32 results).
@@ -24,14 +28,15 @@ struct KickIn {
 // with this substep are closed to i (v, u, S alike), S is rescaled with Y
 // at (rho_i, u_i), the strain invariant gains dt 1/2 edot:edot and the
 // state is opened to i + 1/2; the others are copied from the read view when
-// copy is set. Adds the particle's terms of the sums (at time i) to acc and
-// its time-step criteria to tmin. sub: length of the substep (the step
-// without rungs); last: every particle's step ends with this substep.
+// copy is set. Returns the particle's terms of the step's sums (at time i;
+// e_kin doubled) in term[] and its time-step criterion in *tcr (infinite
+// for a fixed particle). sub: length of the substep (the step without
+// rungs); last: every particle's step ends with this substep.
 template <typename T>
 __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_state &src,
                                               const Work &w, const KParams &P, int64_t i,
                                               bool kick, double sub, bool last, bool copy,
-                                              const KickIn &d, double acc[kNSum], T &tmin,
+                                              const KickIn &d, double term[kNSum], double *tcr,
                                               int &updates, int *hist) {
   const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
   const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
@@ -102,23 +107,25 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
   const double x = s.x[i], y = s.y[i], z = s.z[i];
   T g[3], phi;
   ext_field_t<T>(P, x, y, z, g, &phi);
-  acc[0] += m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);   // halved when summed
-  acc[1] += m * u;
-  acc[2] += m * from_t(phi);
-  acc[3] += m * v[0];
-  acc[4] += m * v[1];
-  acc[5] += m * v[2];
-  acc[6] += m * (y * v[2] - z * v[1]);
-  acc[7] += m * (z * v[0] - x * v[2]);
-  acc[8] += m * (x * v[1] - y * v[0]);
+  term[0] = m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);   // halved when summed
+  term[1] = m * u;
+  term[2] = m * from_t(phi);
+  term[3] = m * v[0];
+  term[4] = m * v[1];
+  term[5] = m * v[2];
+  term[6] = m * (y * v[2] - z * v[1]);
+  term[7] = m * (z * v[0] - x * v[2]);
+  term[8] = m * (x * v[1] - y * v[0]);
+  T tc_ = T(INFINITY);
   if (!fixed) {
     const T H = to_t<T>(s.h[i]);
     const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
     const T am = sqrt(ax * ax + ay * ay + az * az);
     const T ta = am > T(0) ? eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
     const T tc = eta_c * H / to_t<T>(d.vsig);                       // Eq. 39
-    tmin = tmin_(tmin, tmin_(ta, tc));
+    tc_ = tmin_(ta, tc);
   }
+  *tcr = from_t(tc_);
 }
 
 }  // namespace sphk

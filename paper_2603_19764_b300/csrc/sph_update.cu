@@ -5,37 +5,85 @@
 
 namespace sphk {
 
+// The step's reductions in a fixed order. Per reduction tile (64 buckets,
+// 2048 sorted positions of one system; one block): every thread adds the
+// terms of 8 particles in sequence, then the block's sums are formed
+// through shared memory, warp q adding sum q (warp 0 also sum 8) over the
+// block, each lane 8 values in sequence before a shuffle tree. A shuffle
+// tree per sum and thread would cost five FP64 additions per value, and
+// FP64 instructions are the expensive ones here. Per system (one block):
+// the tiles' slots in the same way.
+constexpr int kReduceThreads = 256;
+static_assert(kRedTile * 32 == 8 * kReduceThreads, "8 particles per thread and tile");
+static_assert(kNSum <= 2 * (kReduceThreads / 32) && kNSum > kReduceThreads / 32,
+              "one or two sums per warp");
+
+// Block-wide fixed-order reduction of per-thread values acc[0..kNSum) (sums)
+// and tm (minimum); thread 0 holds nothing special, out[0..kNSlot) gets the
+// result (written by several warps; read after a __syncthreads).
+__device__ __forceinline__ void block_slots(const double acc[kNSum], double tm, double *out) {
+  __shared__ double red[kNSum][kReduceThreads];
+  __shared__ double redt[kReduceThreads / 32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNSum; ++k) red[k][threadIdx.x] = acc[k];
+  tm = wmin(tm);
+  if (lane == 0) redt[wi] = tm;
+  __syncthreads();
+  for (int k = wi; k < kNSum; k += kReduceThreads / 32) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kReduceThreads / 32; ++q) t += red[k][32 * q + lane];
+    t = wsum(t);
+    if (lane == 0) out[k] = t;
+  }
+  if (threadIdx.x == 0) {
+    double t = INFINITY;
+    for (int q = 0; q < kReduceThreads / 32; ++q) t = fmin(t, redt[q]);
+    out[kSlotDt] = t;
+  }
+}
+
+// Sorted positions [p0, p1) of reduction tile t and its system.
+__device__ __forceinline__ int tile_range(const KParams &P, int t, int64_t &p0, int64_t &p1) {
+  const int b0 = P.red_tile[t], b1 = P.red_tile_end[t];
+  const int sy = P.nsys > 1 ? sys_lookup(P.sys_bucket, P.nsys, b0) : 0;
+  const SysRec &R = P.sys[sy];
+  p0 = R.begin + (int64_t)(b0 - R.bucket_off) * 32;
+  p1 = R.begin + (int64_t)(b1 - R.bucket_off) * 32;
+  if (p1 > R.end) p1 = R.end;
+  return sy;
+}
+
 // kick = 1: close to i (v, u, S alike), rescale S with Y at (rho_i, u_i),
 // accumulate 1/2 edot:edot dt, sum diagnostics at i, open to i+1/2.
 // kick = 0: diagnostics and time step of the state as it stands. The
 // integration and the sums are FP64; the EOS, yield and time-step criteria
-// are evaluated in T.
-// One block per chunk of kChunk consecutive particles of one system, so
-// that every system's sums are formed in a fixed order of its own.
+// are evaluated in T. One block per reduction tile; each thread kicks 8
+// particles of it and adds their terms in sequence (without contraction),
+// then the tile's slots are formed (block_slots): the order of
+// k_reduce_tiles over the terms that the force pass leaves when it kicks,
+// so both ways give the same bits.
 // src: where v, u, S and the strain invariant are read (the step's read
 // view: their permuted copies when the permutation did not copy them
 // back); s: where they are written, for every particle then.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_kick(sph_state s, sph_state src, Work w, int kick,
-                                                KParams P, double *partials, Status *st) {
+__global__ void __launch_bounds__(kReduceThreads) k_kick(sph_state s, sph_state src, Work w,
+                                                        int kick, KParams P,
+                                                        double *tile_partials, Status *st) {
   const bool copy = src.vx != s.vx;   // lazy step: write every particle
-  __shared__ double red[kNSum][kBlock];
-  __shared__ double redt[kBlock / 32];
   __shared__ int hist[16];
   if (threadIdx.x < 16) hist[threadIdx.x] = 0;
   __syncthreads();
-  const int b = blockIdx.x;
-  const int sy = P.nsys > 1 ? sys_lookup(P.sys_chunk, P.nsys, b) : 0;
-  SysRec &R = P.sys[sy];
-  const int64_t c0 = R.begin + (int64_t)(b - R.chunk_off) * kChunk;
-  const int64_t c1 = c0 + kChunk < R.end ? c0 + kChunk : R.end;
+  int64_t p0, p1;
+  const int sy = tile_range(P, blockIdx.x, p0, p1);
   // the substep; without rungs the step (sub_scale = 1)
   const double sub = kick ? P.dt[sy] * P.sub_scale : 0.0;
   const bool last = P.substep + 1 == (1 << P.max_rung);   // every particle's step ends
   int updates = 0;
   double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  T tmin = T(INFINITY);
-  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+  double tm = INFINITY;
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += kReduceThreads) {
     // hierarchical steps: before the last substep only the kicked particles
     // matter (the sums and the time step are those of the big step's end)
     if (!last && !rung_active(P, i)) continue;
@@ -44,92 +92,50 @@ __global__ void __launch_bounds__(kBlock) k_kick(sph_state s, sph_state src, Wor
                       {s.dsxx[i], s.dsyy[i], s.dsxy[i], s.dsxz[i], s.dsyz[i]},
                       w.edot2[i],
                       w.vsig[i]};
-    kick_particle<T>(s, src, w, P, i, kick != 0, sub, last, copy, d, acc, tmin, updates, hist);
-  }
-  // block sums in a fixed order: every thread parks its nine partial sums
-  // in shared memory; warp q then reduces sum q (warp 0 also sum 8) over
-  // the block, each lane adding kBlock / 32 values in sequence before a
-  // shuffle tree. Nine shuffle trees per thread would cost three times the
-  // FP64 additions, and this kernel is bound by the FP64 unit.
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    double term[kNSum], tcr;
+    kick_particle<T>(s, src, w, P, i, kick != 0, sub, last, copy, d, term, &tcr, updates, hist);
 #pragma unroll
-  for (int k = 0; k < kNSum; ++k) red[k][threadIdx.x] = acc[k];
-  const double tm = wmin(from_t(tmin));
-  if (lane == 0) redt[wi] = tm;
-  __syncthreads();
-  static_assert(kNSum <= 2 * (kBlock / 32) && kNSum > kBlock / 32, "one or two sums per warp");
-  for (int k = wi; k < kNSum; k += kBlock / 32) {
-    double t = 0.0;
-#pragma unroll
-    for (int q = 0; q < kBlock / 32; ++q) t += red[k][32 * q + lane];
-    t = wsum(t);
-    if (lane == 0) partials[blockIdx.x * kNSum + k] = k == 0 ? 0.5 * t : t;
+    for (int k = 0; k < kNSum; ++k) acc[k] = __dadd_rn(acc[k], term[k]);
+    tm = fmin(tm, tcr);
   }
+  block_slots(acc, tm, tile_partials + (int64_t)blockIdx.x * kNSlot);
   const int wu = wsum(updates);
-  if (lane == 0 && wu) atomicAdd(&st->updates, (unsigned long long)wu);
-  if (threadIdx.x < 16 && hist[threadIdx.x]) atomicAdd(&st->rung_hist[threadIdx.x], hist[threadIdx.x]);
-  if (threadIdx.x == 0) {
-    double t = INFINITY;
-    for (int q = 0; q < kBlock / 32; ++q) t = fmin(t, redt[q]);
-    atomicMin(&R.dtmin_enc, enc_d(t));
-  }
-}
-
-// Fixed-order sums of partial sums over units [b0, b1): each thread sums a
-// strided subset, all nine sums at once and four units per round so that
-// the loads overlap, then a tree over the block, one warp per sum. The
-// result goes to out[0..kNSum).
-constexpr int kReduceThreads = 1024;
-__device__ __forceinline__ void reduce_units(const double *partials, int b0, int b1,
-                                             double *out) {
-  __shared__ double red[kNSum][kReduceThreads / 32];
-  double t[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  constexpr int kU = 4;
-  int b = b0 + threadIdx.x;
-  for (; b + (kU - 1) * kReduceThreads < b1; b += kU * kReduceThreads) {
-    double v[kU][kNSum];
-#pragma unroll
-    for (int u = 0; u < kU; ++u)
-#pragma unroll
-      for (int k = 0; k < kNSum; ++k) v[u][k] = partials[(int64_t)(b + u * kReduceThreads) * kNSum + k];
-#pragma unroll
-    for (int u = 0; u < kU; ++u)
-#pragma unroll
-      for (int k = 0; k < kNSum; ++k) t[k] += v[u][k];
-  }
-  for (; b < b1; b += kReduceThreads)
-#pragma unroll
-    for (int k = 0; k < kNSum; ++k) t[k] += partials[(int64_t)b * kNSum + k];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kNSum; ++k) {
-    const double s = wsum(t[k]);
-    if (lane == 0) red[k][w] = s;
-  }
+  if ((threadIdx.x & 31) == 0 && wu) atomicAdd(&st->updates, (unsigned long long)wu);
   __syncthreads();
-  if (w < kNSum) {
-    const double s = wsum(red[w][lane]);   // kReduceThreads / 32 = 32 warp sums
-    if (lane == 0) out[w] = s;
-  }
+  if (threadIdx.x < 16 && hist[threadIdx.x]) atomicAdd(&st->rung_hist[threadIdx.x], hist[threadIdx.x]);
 }
 
-// Per system (one block each): its sums from the partials of its reduction
-// chunks (k_kick) or from those of its reduction tiles (the force pass's
-// kick, after k_reduce_tiles).
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *partials, KParams P,
-                                                                int per_tile) {
-  SysRec &R = P.sys[blockIdx.x];
-  const int b0 = per_tile ? P.sys_tile[blockIdx.x] : R.chunk_off;
-  const int b1 = per_tile ? P.sys_tile[blockIdx.x + 1] : P.sys_chunk[blockIdx.x + 1];
-  reduce_units(partials, b0, b1, R.sums);
-}
-
-// One block per reduction tile: the fixed-order sum of the partials of its
-// kRedTile buckets.
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_tiles(const double *partials, KParams P,
+// The terms the force pass left when it kicked, in k_kick's order.
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_tiles(Work w, KParams P,
                                                                 double *tile_partials) {
-  const int t = blockIdx.x;
-  reduce_units(partials, P.red_tile[t], P.red_tile_end[t], tile_partials + (int64_t)t * kNSum);
+  int64_t p0, p1;
+  tile_range(P, blockIdx.x, p0, p1);
+  double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double tm = INFINITY;
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += kReduceThreads) {
+#pragma unroll
+    for (int k = 0; k < kNSum; ++k) acc[k] = __dadd_rn(acc[k], w.terms[k][i]);
+    tm = fmin(tm, w.tcrit[i]);
+  }
+  block_slots(acc, tm, tile_partials + (int64_t)blockIdx.x * kNSlot);
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *tile_partials,
+                                                                KParams P) {
+  __shared__ double out[kNSlot];
+  SysRec &R = P.sys[blockIdx.x];
+  double acc[kNSum] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double tm = INFINITY;
+  for (int t = P.sys_tile[blockIdx.x] + threadIdx.x; t < P.sys_tile[blockIdx.x + 1];
+       t += kReduceThreads) {
+#pragma unroll
+    for (int k = 0; k < kNSum; ++k) acc[k] += tile_partials[(int64_t)t * kNSlot + k];
+    tm = fmin(tm, tile_partials[(int64_t)t * kNSlot + kSlotDt]);
+  }
+  block_slots(acc, tm, out);
+  __syncthreads();
+  if (threadIdx.x < kNSum) R.sums[threadIdx.x] = threadIdx.x == 0 ? 0.5 * out[0] : out[threadIdx.x];
+  if (threadIdx.x == 0) atomicMin(&R.dtmin_enc, enc_d(out[kSlotDt]));
 }
 
 // Hierarchical steps: at the start of a big step every moving particle
@@ -246,24 +252,25 @@ cudaError_t launch_compact_active(sph_ctx *c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_kick(sph_ctx *c, int kick) {
-  if (c->kp.precision == SPH_FP32K)
-    k_kick<float><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
-                                                         c->partials, c->d_status);
-  else
-    k_kick<double><<<c->nchunks, kBlock, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
-                                                          c->partials, c->d_status);
-  k_reduce_final<<<c->nsys, kReduceThreads, 0, c->stream>>>(c->partials, c->kp, 0);
+// The step's sums from the per-particle terms: per tile of kRedTile
+// buckets, then per system.
+cudaError_t launch_reduce_buckets(sph_ctx *c) {
+  k_reduce_tiles<<<c->kp.nred_tiles, kReduceThreads, 0, c->stream>>>(c->w, c->kp,
+                                                                     c->tile_partials);
+  k_reduce_final<<<c->nsys, kReduceThreads, 0, c->stream>>>(c->tile_partials, c->kp);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
 
-// The sums of a step whose force pass kicked every particle (per-bucket
-// partials): per tile of kRedTile buckets, then per system.
-cudaError_t launch_reduce_buckets(sph_ctx *c) {
-  k_reduce_tiles<<<c->kp.nred_tiles, kReduceThreads, 0, c->stream>>>(c->partials, c->kp,
-                                                                     c->tile_partials);
-  k_reduce_final<<<c->nsys, kReduceThreads, 0, c->stream>>>(c->tile_partials, c->kp, 1);
+cudaError_t launch_kick(sph_ctx *c, int kick) {
+  const int nt = c->kp.nred_tiles;
+  if (c->kp.precision == SPH_FP32K)
+    k_kick<float><<<nt, kReduceThreads, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
+                                                        c->tile_partials, c->d_status);
+  else
+    k_kick<double><<<nt, kReduceThreads, 0, c->stream>>>(c->st, c->src, c->w, kick, c->kp,
+                                                         c->tile_partials, c->d_status);
+  k_reduce_final<<<c->nsys, kReduceThreads, 0, c->stream>>>(c->tile_partials, c->kp);
   c->nlaunch += 2;
   return cudaGetLastError();
 }

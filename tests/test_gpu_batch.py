@@ -91,8 +91,7 @@ def test_single_system_graph_with_changing_dt():
         for k in range(3):
             info = sim.step(d0 * (0.5 + 0.1 * k))
             # drift, box, grid, keys, 4 x 5 radix kernels, permutation (2),
-            # cells (2), predict, density, EOS pack, forces with the kicks,
-            # tile sums, system sums
+            # cells (2), predict, density, EOS pack, forces, kick, sums
             assert info["kernel_launches"] == 34
         sim.step(0.0)   # dt_next of the last step
         sims.append(_by_id(sim.to_numpy()))
