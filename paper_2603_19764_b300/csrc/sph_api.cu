@@ -136,7 +136,8 @@ __global__ void k_validate(sph_state s, int64_t n, int nmat, int check_id, KPara
 }
 
 void free_all(sph_ctx *c) {
-  void *dev[] = {c->d_mats, c->d_matf, c->d_matd, c->d_gtab, c->d_phitab, c->d_radii, c->w.vp[0], c->w.vp[1],
+  void *dev[] = {c->d_mats, c->d_matf, c->d_matd, c->d_gtab, c->d_phitab, c->d_radii,
+                 c->d_gtab_f, c->w.vp[0], c->w.vp[1],
                  c->w.vp[2], c->w.up, c->w.sp[0], c->w.sp[1], c->w.sp[2], c->w.sp[3],
                  c->w.sp[4], c->w.vsig, c->w.edot2, c->w.yld, c->w.cc, c->w.pos32, c->w.pos64,
                  c->w.fj32, c->w.fj64, c->w.posh32, c->w.posh64,
@@ -764,6 +765,13 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     for (int k = 0; k < SPH_MAX_MATERIALS; ++k) {
       mf[k] = mat_copy<float>(c->mats[k]);
       md[k] = mat_copy<double>(c->mats[k]);
+      const double hk = c->mats[k].rho0 > 0.0
+                            ? 3.0 * p->n_ngb / (4.0 * kPi * c->mats[k].rho0)
+                            : 0.0;
+      mf[k].hcap_k = (float)hk;
+      md[k].hcap_k = hk;
+      mf[k].hcap_f = (float)p->h_cap_factor;
+      md[k].hcap_f = p->h_cap_factor;
     }
     CKI(dalloc(&c->d_matf, SPH_MAX_MATERIALS));
     CKI(dalloc(&c->d_matd, SPH_MAX_MATERIALS));
@@ -808,6 +816,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.gravity = p->gravity;
   for (int a = 0; a < 3; ++a) {
     kp.g_uniform[a] = p->g_uniform[a];
+    kp.g_uniform_f[a] = (float)p->g_uniform[a];
     kp.g_center[a] = p->g_center[a];
   }
   kp.mats = c->d_mats;
@@ -815,7 +824,7 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.matd = c->d_matd;
   if (p->gravity == SPH_GRAVITY_RADIAL) {
     const int gn = p->g_n;
-    double *radii = (double *)malloc(sizeof(double) * gn);
+    std::vector<double> radii(gn);
     for (int k = 0; k < gn; ++k)
       radii[k] = p->g_rmin * pow(p->g_rmax / p->g_rmin, (double)k / (double)(gn - 1));
     CKI(dalloc(&c->d_gtab, gn));
@@ -823,8 +832,17 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     CKI(dalloc(&c->d_radii, gn));
     CKI(cudaMemcpy(c->d_gtab, p->g_table, sizeof(double) * gn, cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(c->d_phitab, p->phi_table, sizeof(double) * gn, cudaMemcpyHostToDevice));
-    CKI(cudaMemcpy(c->d_radii, radii, sizeof(double) * gn, cudaMemcpyHostToDevice));
-    free(radii);
+    CKI(cudaMemcpy(c->d_radii, radii.data(), sizeof(double) * gn, cudaMemcpyHostToDevice));
+    {
+      std::vector<float> tf(3 * (size_t)gn);
+      for (int k = 0; k < gn; ++k) {
+        tf[k] = (float)p->g_table[k];
+        tf[gn + k] = (float)p->phi_table[k];
+        tf[2 * gn + k] = (float)radii[k];
+      }
+      CKI(dalloc(&c->d_gtab_f, 3 * (size_t)gn));
+      CKI(cudaMemcpy(c->d_gtab_f, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice));
+    }
     kp.g_table = c->d_gtab;
     kp.phi_table = c->d_phitab;
     kp.g_radii = c->d_radii;
@@ -833,6 +851,13 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
     kp.g_rmax = p->g_rmax;
     kp.g_gm = p->g_gm;
     kp.g_inv_log_ratio = (double)(gn - 1) / log2(p->g_rmax / p->g_rmin);
+    kp.g_table_f = c->d_gtab_f;
+    kp.phi_table_f = c->d_gtab_f + gn;
+    kp.g_radii_f = c->d_gtab_f + 2 * gn;
+    kp.g_rmin_f = (float)kp.g_rmin;
+    kp.g_rmax_f = (float)kp.g_rmax;
+    kp.g_gm_f = (float)kp.g_gm;
+    kp.g_inv_log_ratio_f = (float)kp.g_inv_log_ratio;
   }
   c->params.g_table = c->d_gtab;
   c->params.phi_table = c->d_phitab;

@@ -51,9 +51,11 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
     const double x = s.x[i], y = s.y[i], z = s.z[i], m = s.m[i];
     if (fp32) {
       const int c = w.cc[i];
-      const double ox = g.lo[0] + (c & 1023) * g.L;
-      const double oy = g.lo[1] + ((c >> 10) & 1023) * g.L;
-      const double oz = g.lo[2] + ((c >> 20) & 1023) * g.L;
+      // the cell index as a double through FP32 (exact below 2^24), so
+      // that no conversion runs on the FP64 unit
+      const double ox = g.lo[0] + f2d((float)(c & 1023)) * g.L;
+      const double oy = g.lo[1] + f2d((float)((c >> 10) & 1023)) * g.L;
+      const double oz = g.lo[2] + f2d((float)((c >> 20) & 1023)) * g.L;
       w.pos32[i] = make_float4(d2f(x - ox), d2f(y - oy), d2f(z - oz), d2f(m));
     } else {
       w.pos64[i] = make_double4_32a(x, y, z, m);
@@ -277,18 +279,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
   const V4 p = V::ld(pos, ic);
   const T mi = p.w;
-  const sph_material &M = A.p.mats[A.s.mat[ic] & (SPH_MAX_MATERIALS - 1)];
+  const MatT<T> &Mt = mat_t<T>(A.p, A.s.mat[ic]);
   const T target = (T)A.p.n_ngb * mi;
   const T tol = pconst<T>(A.p.h_tol, A.p.h_tol_f);
   // the Newton state is kept in T: the FP32 form's radius carries 24 bits,
-  // far below h_tol, and its FP64 predicate uses the exact square of it
-  const T Hcap =
-      (T)A.p.h_cap_factor * cbrt((T)(3.0 * A.p.n_ngb / (4.0 * kPi * M.rho0)) * mi);
+  // far below h_tol, and its FP64 predicate uses the exact square of it.
+  // Cap: h_cap_factor times the lattice radius (3 n_ngb m / (4 pi rho0))^(1/3)
+  const T Hcap = Mt.hcap_f * cbrt(Mt.hcap_k * mi);
   // starting radius: the previous H, or the proposal of the learned form
-  T H = (T)A.h_in[ic];
+  // (one with 0 < H <= inf, tested on its bits)
+  T H = to_t<T>(A.h_in[ic]);
   if (A.p.h_guess) {
     const double hg = A.p.h_guess[ic];
-    if (hg > 0.0) H = (T)hg;
+    const long long hb = __double_as_longlong(hg);
+    if (hb > 0 && hb <= 0x7ff0000000000000LL) H = to_t<T>(hg);
   }
   H = tmin(H, Hcap);
   const double xi64 = A.s.x[ic], yi64 = A.s.y[ic], zi64 = A.s.z[ic];
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   }
 
   if (solve) {
-    A.s.h[i] = (double)H_o;
+    A.s.h[i] = from_t(H_o);
     A.s.rho[i] = from_t(rho_o);
     A.s.omega[i] = from_t(om_o);
     A.s.nngb[i] = cnt_o;
@@ -471,12 +475,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   w_swt += solve ? sweeps_o : 0;
   w_nu += state == 3;
   w_ncap += state == 2;
-  w_bad |= (solve && !(isfinite((double)rho_o) && isfinite((double)om_o) && rho_o > T(0))) ? 1u
-                                                                                         : 0u;
+  w_bad |= (solve && !(isfinite(rho_o) && isfinite(om_o) && rho_o > T(0))) ? 1u : 0u;
   {
     // every particle's radius bounds the force pass's search, solved or not
-    const double hb = wmax(valid ? (solve ? (double)H_o : A.h_in[i]) : 0.0);
-    if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, enc_d(hb));
+    // (the maximum of the order-preserving encodings)
+    const unsigned long long hb =
+        wmax(enc_d(valid ? (solve ? from_t(H_o) : A.h_in[i]) : 0.0));
+    if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, hb);
   }
   w_pairs += pairs;
   w_cand += cand;

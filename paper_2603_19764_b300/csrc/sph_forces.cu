@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   const T Lt = grid_L<T>(g), invL = grid_invL<T>(g);
   const int cc = A.w.cc[ic];
   const int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = (cc >> 20) & 1023;
-  const T hmax_all = (T)dec_d(R.hmax2_enc);
+  const T hmax_all = to_t<T>(dec_d(R.hmax2_enc));
 
   // particle i (evaluation state, packed)
   const V4 p = V::ld(posh, ic);

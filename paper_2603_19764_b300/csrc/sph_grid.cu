@@ -80,6 +80,10 @@ __device__ __forceinline__ bool finite_bits(double d) {
 constexpr int kDriftChunk = 8 * kBlock;
 constexpr unsigned long long kEncMax = ~0ull, kEncMin = 0ull;
 
+// PER: a periodic box (a template parameter, so that closed boxes run no
+// FP64 compare or wrap: the compiler evaluates a run-time branch's cheap
+// sides unconditionally)
+template <bool PER>
 __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, KParams P,
                                                       int do_drift) {
   __shared__ unsigned long long red[7][kBlock / 32];
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
       p[0] += dt * s.vx[i];
       p[1] += dt * s.vy[i];
       p[2] += dt * s.vz[i];
-      if (P.periodic) {   // back into [box_lo, box_hi): one box length at most
+      if (PER) {   // back into [box_lo, box_hi): one box length at most
         for (int a = 0; a < 3; ++a) {
           if (p[a] >= P.box_hi[a]) p[a] -= P.box_len[a];
           else if (p[a] < P.box_lo[a]) p[a] += P.box_len[a];
@@ -178,7 +182,10 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
 
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
   const int blocks = (int)((c->n + kDriftChunk - 1) / kDriftChunk);
-  k_drift_bbox<<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
+  if (c->kp.periodic)
+    k_drift_bbox<true><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
+  else
+    k_drift_bbox<false><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -250,9 +257,17 @@ cudaError_t launch_grid_setup(sph_ctx *c) {
   return cudaGetLastError();
 }
 
+// Cell index floor((x - lo) / L) clamped to [0, dim): the scaled offset in
+// FP64, its floor from the IEEE 754 layout in integer arithmetic (no
+// conversion instruction, which would run on the FP64 unit).
 __device__ __forceinline__ int cell_coord(double x, double lo, double invL, int dim) {
-  int k = (int)floor((x - lo) * invL);
-  return k < 0 ? 0 : (k >= dim ? dim - 1 : k);
+  const long long b = __double_as_longlong((x - lo) * invL);
+  if (b < 0x3ff0000000000000LL) return 0;   // below 1 (negative included)
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e >= 31) return dim - 1;              // 2^31 and beyond, infinity, NaN
+  const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const int k = (int)(m >> (52 - e));
+  return k >= dim ? dim - 1 : k;
 }
 
 // Key = system << 3 axis_bits | Morton code of the cell within the system;

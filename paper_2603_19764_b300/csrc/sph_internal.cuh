@@ -113,6 +113,10 @@ template <typename T> struct MatT {
   double rho0_d, Eiv_d, Ecv_d, c0sq_d, p_min_d;
   T rho0, inv_rho0, c0, c0sq, A, B, E0, a, b, alpha, beta, inv_dE, floor2;
   T shear_G, Y0, mu_i, Ym, mu_d, xi, Tm, T0, inv_cv, p_min;
+  // the smoothing-length cap of the density solve: hcap_f (the run's
+  // h_cap_factor) times (hcap_k m)^(1/3), hcap_k = 3 n_ngb / (4 pi rho0),
+  // both rounded from FP64 once on the host
+  T hcap_k, hcap_f;
 };
 
 // Kernel-side copy of the run-time parameters.
@@ -127,6 +131,10 @@ struct KParams {
   const double *g_table, *phi_table, *g_radii;
   int g_n;
   double g_rmin, g_rmax, g_center[3], g_gm, g_inv_log_ratio;
+  // FP32 copies of the field's constants and tables (rounded once on the
+  // host), so that the FP32 form's evaluations convert nothing
+  const float *g_table_f, *phi_table_f, *g_radii_f;
+  float g_rmin_f, g_rmax_f, g_gm_f, g_inv_log_ratio_f, g_uniform_f[3];
   const sph_material *mats;
   const MatT<float> *matf;     // the materials for the FP32 / FP64 forms
   const MatT<double> *matd;
@@ -269,23 +277,36 @@ template <> __device__ __forceinline__ const MatT<double> &mat_t<double>(const K
 // conversion instructions run on the FP64 unit, at 1/64 of the FP32 rate,
 // and the per-particle kernels convert tens of values per particle. Built
 // from the IEEE 754 binary64 / binary32 layouts: round to nearest even for
-// results in the binary32 normal range, the conversion instruction
-// otherwise (zero, subnormal results, overflow to infinity, NaN).
+// results in the binary32 normal range, and zeros, in integer arithmetic;
+// the other cases (subnormal results, overflow to infinity, infinities,
+// NaN) call the conversion instruction out of line. (Written inline, that
+// call was evaluated for every value by the compiler, which runs both
+// sides of a short branch; written in integer arithmetic inline, the rare
+// cases took registers from every kernel that converts.)
+static __device__ __noinline__ float d2f_rare(double d) { return __double2float_rn(d); }
+static __device__ __noinline__ double f2d_rare(float v) { return (double)v; }
 __device__ __forceinline__ float d2f(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const unsigned e = (hi >> 20) & 0x7ffu;   // biased binary64 exponent
-  if (e < 897u || e > 1150u) return __double2float_rn(d);
+  if (e - 897u > 253u) {
+    if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(hi);   // +-0
+    return d2f_rare(d);
+  }
   const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // top 23 fraction bits
   const unsigned rest = lo & 0x1fffffffu;                    // the 29 dropped bits
   unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+  // a carry out of the fraction raises the exponent (2^128: infinity)
   f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
   return __uint_as_float(f);
 }
 __device__ __forceinline__ double f2d(float v) {
   const unsigned u = __float_as_uint(v);
   const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)v;
+  if (e - 1u > 253u) {
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)u, 0);   // +-0
+    return f2d_rare(v);
+  }
   const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
   return __hiloint2double((int)hi, (int)(u << 29));
 }
@@ -516,44 +537,60 @@ template <typename T> __device__ inline T radial_factor_t(const T S[5], T Y, int
   return f < T(1) ? f : T(1);
 }
 
+// The field's constants and tables in the arithmetic type of a form.
+template <typename T> struct FieldT {
+  const T *g, *phi, *r;
+  T rmin, rmax, gm, inv_log_ratio, gu[3];
+};
+__device__ __forceinline__ FieldT<float> field_t(const KParams &P, float) {
+  return {P.g_table_f, P.phi_table_f, P.g_radii_f, P.g_rmin_f, P.g_rmax_f, P.g_gm_f,
+          P.g_inv_log_ratio_f, {P.g_uniform_f[0], P.g_uniform_f[1], P.g_uniform_f[2]}};
+}
+__device__ __forceinline__ FieldT<double> field_t(const KParams &P, double) {
+  return {P.g_table, P.phi_table, P.g_radii, P.g_rmin, P.g_rmax, P.g_gm,
+          P.g_inv_log_ratio, {P.g_uniform[0], P.g_uniform[1], P.g_uniform[2]}};
+}
+
 // External field at an absolute position (uniform, or radial table with
 // linear interpolation between log-spaced radii). The offset from the
-// centre is formed in FP64.
+// centre, and the uniform field's potential, are formed in FP64.
 template <typename T>
 __device__ inline void ext_field_t(const KParams &P, double x, double y, double z, T g[3], T *phi) {
   g[0] = g[1] = g[2] = T(0);
   if (phi) *phi = T(0);
   if (P.gravity == SPH_GRAVITY_UNIFORM) {
-    g[0] = to_t<T>(P.g_uniform[0]);
-    g[1] = to_t<T>(P.g_uniform[1]);
-    g[2] = to_t<T>(P.g_uniform[2]);
-    if (phi) *phi = (T)(-(P.g_uniform[0] * x + P.g_uniform[1] * y + P.g_uniform[2] * z));
+    const FieldT<T> F = field_t(P, T(0));
+    g[0] = F.gu[0];
+    g[1] = F.gu[1];
+    g[2] = F.gu[2];
+    if (phi) *phi = to_t<T>(-(P.g_uniform[0] * x + P.g_uniform[1] * y + P.g_uniform[2] * z));
     return;
   }
   if (P.gravity != SPH_GRAVITY_RADIAL) return;
+  const FieldT<T> F = field_t(P, T(0));
   const T dx = to_t<T>(x - P.g_center[0]), dy = to_t<T>(y - P.g_center[1]),
           dz = to_t<T>(z - P.g_center[2]);
   const T r = sqrt(dx * dx + dy * dy + dz * dz);
   if (!(r > T(0))) return;
-  const T rmin = to_t<T>(P.g_rmin), rmax = to_t<T>(P.g_rmax);
+  const T rmin = F.rmin, rmax = F.rmax;
   T gm, ph;
   if (r >= rmax) {
-    gm = to_t<T>(P.g_gm) / (r * r);
-    ph = -to_t<T>(P.g_gm) / r;
+    gm = F.gm / (r * r);
+    ph = -F.gm / r;
   } else if (r <= rmin) {
-    const T g0 = to_t<T>(P.g_table[0]);
+    const T g0 = F.g[0];
     gm = g0 * r / rmin;
-    ph = to_t<T>(P.phi_table[0]) + T(0.5) * g0 / rmin * (r * r - rmin * rmin);
+    ph = F.phi[0] + T(0.5) * g0 / rmin * (r * r - rmin * rmin);
   } else {
-    int k = (int)floorf(log2f((float)(r / rmin)) * (float)P.g_inv_log_ratio);
+    int k = (int)floorf(log2f((float)(r / rmin)) * (float)F.inv_log_ratio);
     k = max(0, min(k, P.g_n - 2));
-    if (r < to_t<T>(P.g_radii[k]) && k > 0) --k;
-    else if (r >= to_t<T>(P.g_radii[k + 1]) && k < P.g_n - 2) ++k;
-    const T r0 = to_t<T>(P.g_radii[k]), r1 = to_t<T>(P.g_radii[k + 1]);
+    if (r < F.r[k] && k > 0) --k;
+    else if (r >= F.r[k + 1] && k < P.g_n - 2) ++k;
+    const T r0 = F.r[k], r1 = F.r[k + 1];
     const T w = (r - r0) / (r1 - r0);
-    const T ga = to_t<T>(P.g_table[k]), gb = to_t<T>(P.g_table[k + 1]);
+    const T ga = F.g[k], gb = F.g[k + 1];
     gm = ga + w * (gb - ga);
-    const T pa = to_t<T>(P.phi_table[k]), pb = to_t<T>(P.phi_table[k + 1]);
+    const T pa = F.phi[k], pb = F.phi[k + 1];
     ph = pa + w * (pb - pa);
   }
   g[0] = -gm * dx / r;
@@ -582,6 +619,7 @@ struct sph_ctx {
   sphk::MatT<float> *d_matf;
   sphk::MatT<double> *d_matd;
   double *d_gtab, *d_phitab, *d_radii;
+  float *d_gtab_f;       // FP32 copies: g, phi, radii (3 x g_n)
   sphk::Work w;
   // sort and cell list
   unsigned *keys, *keys_alt;

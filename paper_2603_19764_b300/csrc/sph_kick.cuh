@@ -45,7 +45,8 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
   double v[3] = {src.vx[i], src.vy[i], src.vz[i]};
   double u = src.u[i];
   if (kick && !fixed && rung_active(P, i)) {
-    const double dt = sub * (double)rung_len(P, i), hdt = 0.5 * dt;
+    // the particle's own step (no conversion on the FP64 unit without rungs)
+    const double dt = P.max_rung ? sub * (double)rung_len(P, i) : sub, hdt = 0.5 * dt;
     const MatT<T> &M = mat_t<T>(P, s.mat[i]);
     double S[5] = {src.sxx[i], src.syy[i], src.sxy[i], src.sxz[i], src.syz[i]};
 #pragma unroll
@@ -56,8 +57,9 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
     if (M.strength) {
       const EosT<T> e = eos_t<T>(M, s.rho[i], u);
       const T St[5] = {to_t<T>(S[0]), to_t<T>(S[1]), to_t<T>(S[2]), to_t<T>(S[3]), to_t<T>(S[4])};
-      const double f = from_t(radial_factor_t<T>(St, yield_t<T>(M, e.P, to_t<T>(u)), P.yield_norm));
-      if (f < 1.0) {   // below the yield surface f is exactly 1
+      const T ft = radial_factor_t<T>(St, yield_t<T>(M, e.P, to_t<T>(u)), P.yield_norm);
+      if (ft < T(1)) {   // below the yield surface f is exactly 1
+        const double f = from_t(ft);
 #pragma unroll
         for (int k = 0; k < 5; ++k) S[k] *= f;
       }
@@ -107,15 +109,17 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
   const double x = s.x[i], y = s.y[i], z = s.z[i];
   T g[3], phi;
   ext_field_t<T>(P, x, y, z, g, &phi);
-  term[0] = m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);   // halved when summed
-  term[1] = m * u;
-  term[2] = m * from_t(phi);
+  // momentum first; kinetic energy (doubled, halved when summed) and
+  // angular momentum from it
   term[3] = m * v[0];
   term[4] = m * v[1];
   term[5] = m * v[2];
-  term[6] = m * (y * v[2] - z * v[1]);
-  term[7] = m * (z * v[0] - x * v[2]);
-  term[8] = m * (x * v[1] - y * v[0]);
+  term[0] = v[0] * term[3] + v[1] * term[4] + v[2] * term[5];
+  term[1] = m * u;
+  term[2] = m * from_t(phi);
+  term[6] = y * term[5] - z * term[4];
+  term[7] = z * term[3] - x * term[5];
+  term[8] = x * term[4] - y * term[3];
   T tc_ = T(INFINITY);
   if (!fixed) {
     const T H = to_t<T>(s.h[i]);
@@ -126,6 +130,14 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
     tc_ = tmin_(ta, tc);
   }
   *tcr = from_t(tc_);
+}
+
+// The smaller of two time-step criteria: non-negative doubles or +inf,
+// whose bit patterns order like their values (integer compare, no FP64
+// instruction).
+__device__ __forceinline__ double min_crit(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return ia < ib ? a : b;
 }
 
 }  // namespace sphk

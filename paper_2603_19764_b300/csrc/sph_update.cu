@@ -27,7 +27,7 @@ __device__ __forceinline__ void block_slots(const double acc[kNSum], double tm, 
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kNSum; ++k) red[k][threadIdx.x] = acc[k];
-  tm = wmin(tm);
+  tm = __longlong_as_double(wmin(__double_as_longlong(tm)));
   if (lane == 0) redt[wi] = tm;
   __syncthreads();
   for (int k = wi; k < kNSum; k += kReduceThreads / 32) {
@@ -39,7 +39,7 @@ __device__ __forceinline__ void block_slots(const double acc[kNSum], double tm, 
   }
   if (threadIdx.x == 0) {
     double t = INFINITY;
-    for (int q = 0; q < kReduceThreads / 32; ++q) t = fmin(t, redt[q]);
+    for (int q = 0; q < kReduceThreads / 32; ++q) t = min_crit(t, redt[q]);
     out[kSlotDt] = t;
   }
 }
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_kick(sph_state s, sph_state 
     kick_particle<T>(s, src, w, P, i, kick != 0, sub, last, copy, d, term, &tcr, updates, hist);
 #pragma unroll
     for (int k = 0; k < kNSum; ++k) acc[k] = __dadd_rn(acc[k], term[k]);
-    tm = fmin(tm, tcr);
+    tm = min_crit(tm, tcr);
   }
   block_slots(acc, tm, tile_partials + (int64_t)blockIdx.x * kNSlot);
   const int wu = wsum(updates);
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_tiles(Work w, KParams
   for (int64_t i = p0 + threadIdx.x; i < p1; i += kReduceThreads) {
 #pragma unroll
     for (int k = 0; k < kNSum; ++k) acc[k] = __dadd_rn(acc[k], w.terms[k][i]);
-    tm = fmin(tm, w.tcrit[i]);
+    tm = min_crit(tm, w.tcrit[i]);
   }
   block_slots(acc, tm, tile_partials + (int64_t)blockIdx.x * kNSlot);
 }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *t
        t += kReduceThreads) {
 #pragma unroll
     for (int k = 0; k < kNSum; ++k) acc[k] += tile_partials[(int64_t)t * kNSlot + k];
-    tm = fmin(tm, tile_partials[(int64_t)t * kNSlot + kSlotDt]);
+    tm = min_crit(tm, tile_partials[(int64_t)t * kNSlot + kSlotDt]);
   }
   block_slots(acc, tm, out);
   __syncthreads();
