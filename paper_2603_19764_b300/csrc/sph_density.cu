@@ -146,7 +146,8 @@ template <> struct DList<double> {
   }
 };
 
-// Per-lane bit masks over the staged list: bit k set when r_k^2 < R2.
+// Per-lane bit masks over the staged list (mask_word's layout): candidate k
+// marked when r_k^2 < R2.
 // Lanes with store = false compute but keep their previous words.
 template <typename T, typename LV>
 __device__ __forceinline__ void build_masks(const LV &Lp, unsigned (*Lm)[32],
@@ -179,8 +180,7 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
     while (mk == 0u && ++wd < nw) mk = Lm[wd][lane];
     if (mk == 0u) break;
     {
-      const int k = (wd << 5) + __ffs(mk) - 1;
-      mk &= mk - 1u;
+      const int k = (wd << 5) + take_next(mk);
       T qx, qy, qz, qm;
       Lp.get(k, qx, qy, qz, qm);
       const T dx = xi - qx, dy = yi - qy, dz = zi - qz;

@@ -318,8 +318,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
       int kn = 0, jn = 0;
       V4 g0, g1, g2, g3;   // the prefetched record, in two 32-byte loads
       if (more) {
-        kn = (wd << 5) + __ffs(mk) - 1;
-        mk &= mk - 1u;
+        kn = (wd << 5) + take_next(mk);
         jn = (int)checked(Li[kn], A.n, &A.st->err);
         if (PF) {
           V::ld2(rec + 4 * jn, g0, g1);
@@ -341,14 +340,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           if (PF) {
             // without a branch: after the lane's last pair the index stays
             // at the current pair and its record is loaded once more
-            kn = more ? (wd << 5) + __ffs(mk) - 1 : kn;
-            mk &= mk - 1u;
+            const int b = take_next(mk);   // mk stays 0 after the last pair
+            kn = more ? (wd << 5) + b : kn;
             jn = (int)checked(Li[kn], A.n, &A.st->err);
             V::ld2(rec + 4 * jn, g0, g1);
             V::ld2(rec + 4 * jn + 2, g2, g3);
           } else if (more) {
-            kn = (wd << 5) + __ffs(mk) - 1;
-            mk &= mk - 1u;
+            kn = (wd << 5) + take_next(mk);
             jn = (int)checked(Li[kn], A.n, &A.st->err);
           }
           T qx, qy, qz, qw;   // qw = H_j^2

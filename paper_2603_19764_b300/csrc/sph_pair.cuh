@@ -142,21 +142,8 @@ __device__ __forceinline__ double dist2(double dx, double dy, double dz) {
 }
 
 // Staged candidates: x, y, z relative to the group's reference cell and one
-// more value w. Two layouts:
-// * AoS: one 4-vector per candidate (float4 / double4_32a); the walk reads
-//   a candidate with one 16- or 32-byte load.
-// * Paired (FP32): candidates 2m and 2m+1 share a 32-byte slot laid out
-//   (x0 x1 y0 y1 | z0 z1 w0 w1), so that one 16-byte load yields the x and
-//   y pairs and the mask test runs on both candidates with packed
-//   arithmetic; the walk reads a candidate with four 4-byte loads.
-struct F2Slot {
-  float4 a, b;
-};
+// more value w, one 4-vector per candidate (the FP64 form's layout).
 template <typename V4> struct CandAoS {
-  template <typename T>
-  static __device__ __forceinline__ void put(V4 *L, int k, T x, T y, T z, T w) {
-    L[k] = V4T<T>::make(x, y, z, w);
-  }
   template <typename T>
   static __device__ __forceinline__ void get(const V4 *L, int k, T &x, T &y, T &z, T &w) {
     const V4 q = L[k];
@@ -164,24 +151,6 @@ template <typename V4> struct CandAoS {
     y = q.y;
     z = q.z;
     w = q.w;
-  }
-};
-struct CandPaired {
-  static __device__ __forceinline__ void put(F2Slot *L, int k, float x, float y, float z,
-                                             float w) {
-    float *p = reinterpret_cast<float *>(L + (k >> 1)) + (k & 1);
-    p[0] = x;
-    p[2] = y;
-    p[4] = z;
-    p[6] = w;
-  }
-  static __device__ __forceinline__ void get(const F2Slot *L, int k, float &x, float &y, float &z,
-                                             float &w) {
-    const float *p = reinterpret_cast<const float *>(L + (k >> 1)) + (k & 1);
-    x = p[0];
-    y = p[2];
-    z = p[4];
-    w = p[6];
   }
 };
 
@@ -224,43 +193,47 @@ template <int S> struct ViewPlanes {
   }
 };
 
-// One lane's membership word over staged candidates kb .. kb+31 (kb a
-// multiple of 32): bit b set when r^2 < thr(w) for candidate kb + b, for
-// b < count only. The paired form reads whole words, up to 31 slots past
-// the list's end (inside the buffer, whose length is a multiple of 32), and
-// clears those bits.
+// Membership words. A word covers staged candidates kb .. kb+31 (kb a
+// multiple of 32) and holds candidate kb + b at bit 31 - b, so that the
+// walk finds the next marked candidate in list order with one count of
+// leading zeros. The test r^2 < thr of two non-negative values is decided
+// on their bit patterns (which order like the values): the sign of the
+// integer difference, shifted into the word.
+__device__ __forceinline__ unsigned below(float a, float t) {
+  return (unsigned)(__float_as_int(a) - __float_as_int(t));
+}
+__device__ __forceinline__ unsigned below(double a, double t) {
+  return (unsigned)((unsigned long long)(__double_as_longlong(a) - __double_as_longlong(t)) >> 32);
+}
+// word = word << 1 | sign bit of d
+__device__ __forceinline__ unsigned push_bit(unsigned word, unsigned d) {
+  return __funnelshift_l(d, word, 1);
+}
+// The next marked candidate of a nonzero word (its offset b in the word),
+// cleared from the word. For a zero word b is 0 and the word stays zero.
+__device__ __forceinline__ int take_next(unsigned &mk) {
+  const int b = __clz(mk) & 31;
+  mk &= ~(0x80000000u >> b);
+  return b;
+}
+// Keep the bits of the first `count` candidates of a word (1 <= count <= 32).
+__device__ __forceinline__ unsigned first_bits(unsigned mk, int count) {
+  return count < 32 ? mk & (0xffffffffu << (32 - count)) : mk;
+}
+
+// One lane's membership word: bit 31 - b set when r^2 < thr(w) for candidate
+// kb + b, for b < count only.
 template <typename V4, typename T, typename Thr>
 __device__ __forceinline__ unsigned mask_word(const V4 *L, int kb, int count, T xi, T yi, T zi,
                                               Thr thr) {
   unsigned mk = 0;
-#pragma unroll 4
-  for (int b = 0; b < count; ++b) {
-    T x, y, z, w;
-    CandAoS<V4>::get(L, kb + b, x, y, z, w);
+  for (int b = 0; b < 32; ++b) {
+    T x = T(0), y = T(0), z = T(0), w = T(0);
+    if (b < count) CandAoS<V4>::get(L, kb + b, x, y, z, w);
     const T dx = xi - x, dy = yi - y, dz = zi - z;
-    mk |= (dist2(dx, dy, dz) < thr(w) ? 1u : 0u) << b;
+    mk = push_bit(mk, below(dist2(dx, dy, dz), thr(w)));
   }
-  return mk;
-}
-template <typename Thr>
-__device__ __forceinline__ unsigned mask_word(const F2Slot *L, int kb, int count, float xi,
-                                              float yi, float zi, Thr thr) {
-  using namespace px;
-  const u64 X = dup(xi), Y = dup(yi), Z = dup(zi);
-  const ulonglong2 *P = reinterpret_cast<const ulonglong2 *>(L + (kb >> 1));
-  unsigned mk = 0;
-#pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const ulonglong2 a = P[2 * m], b = P[2 * m + 1];   // (x pair, y pair), (z pair, w pair)
-    const u64 dx = sub(X, a.x), dy = sub(Y, a.y), dz = sub(Z, b.x);
-    const u64 r2 = fma(dz, dz, fma(dy, dy, mul(dx, dx)));
-    float r0, r1, w0, w1;
-    split(r2, r0, r1);
-    split(b.y, w0, w1);
-    if (r0 < thr(w0)) mk |= 1u << (2 * m);
-    if (r1 < thr(w1)) mk |= 2u << (2 * m);
-  }
-  return count < 32 ? mk & ((1u << count) - 1u) : mk;
+  return first_bits(mk, count);
 }
 
 template <typename V4, typename T, typename Thr>
@@ -269,7 +242,7 @@ __device__ __forceinline__ unsigned mask_word(const ViewAoS<V4> &L, int kb, int 
   return mask_word(static_cast<const V4 *>(L.p), kb, count, xi, yi, zi, thr);
 }
 // Planes: reads whole 32-candidate words (S a multiple of 32), clearing the
-// bits past the list's end.
+// bits past the list's end; two candidates per packed operation.
 template <int S, typename Thr>
 __device__ __forceinline__ unsigned mask_word(const ViewPlanes<S> &L, int kb, int count,
                                               float xi, float yi, float zi, Thr thr) {
@@ -290,11 +263,11 @@ __device__ __forceinline__ unsigned mask_word(const ViewPlanes<S> &L, int kb, in
       float r0, r1, w0, w1;
       split(r2, r0, r1);
       split(h ? w.y : w.x, w0, w1);
-      if (r0 < thr(w0)) mk |= 1u << (4 * q + 2 * h);
-      if (r1 < thr(w1)) mk |= 2u << (4 * q + 2 * h);
+      mk = push_bit(mk, below(r0, thr(w0)));
+      mk = push_bit(mk, below(r1, thr(w1)));
     }
   }
-  return count < 32 ? mk & ((1u << count) - 1u) : mk;
+  return first_bits(mk, count);
 }
 
 // Squared distance of a point to an axis-aligned box (0 inside).
