@@ -94,6 +94,9 @@ struct DensArgs {
 // Newton sweeps instead of being staged again for every sweep.
 constexpr int kSpill = 1024;
 
+// Staging: chunks of 32 stream positions located and loaded at once
+constexpr int kStageChunksD = 4;
+
 // FP32 form within a full step: a Newton step of at most kExpand H is
 // accepted without a new evaluation of the sums when the second-order
 // expansion of rho(H) about the evaluated H already meets the tolerance at
@@ -338,32 +341,26 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         Hm = T(0);
         complete = false;
         for (int seg = 0;; ++seg) {
-          nl = 0;
-          while (nl <= TCAP - 32) {
-            int j;
-            bool ok;
-            T ox, oy, oz;
-            if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz,
-                                      j, ok, ox, oy, oz, &A.st->err))
-              break;
-            if (ok) j = (int)checked(j, A.n, &A.st->err);
-            const V4 q = ok ? V::ld(pos, j) : V::make(0, 0, 0, 0);
-            const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
-            const bool keep =
-                ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < Rl * Rl;
-            const unsigned bal = __ballot_sync(kFull, keep);
-            if (keep) {
-              const int at = (int)checked(nl + __popc(bal & lanemask_lt()), TCAP, &A.st->err);
-              if (at < CAP) {
-                Lp.put(at, xj, yj, zj, q.w);
-                Li[at] = j;
-              } else {
-                Sp.put(at - CAP, xj, yj, zj, q.w);
-                Sv.i[at - CAP] = j;
-              }
-            }
-            nl += __popc(bal);
-          }
+          nl = stage_list<kStageChunksD, T, REL>(
+              sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, 0, TCAP, A.n,
+              &A.st->err,
+              [&](bool ok, int j) { return ok ? V::ld(pos, j) : V::make(0, 0, 0, 0); },
+              [&](bool ok, const V4 &q, T ox, T oy, T oz, T &xj, T &yj, T &zj) {
+                xj = add_rn(q.x, ox);
+                yj = add_rn(q.y, oy);
+                zj = add_rn(q.z, oz);
+                return ok &&
+                       box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < Rl * Rl;
+              },
+              [&](int at, T xj, T yj, T zj, const V4 &q, int j) {
+                if (at < CAP) {
+                  Lp.put(at, xj, yj, zj, q.w);
+                  Li[at] = j;
+                } else {
+                  Sp.put(at - CAP, xj, yj, zj, q.w);
+                  Sv.i[at - CAP] = j;
+                }
+              });
           cand += nl;
           if (seg == 0 && stager_finished(sg)) {
             complete = true;

@@ -118,6 +118,8 @@ cudaError_t launch_eos_pack(sph_ctx *c) {
 // plainly in both forms: their diagonal terms share one sign, and their
 // rounding error is a few ulp of the matrix norm.
 constexpr int kSumBlock = 8;
+// Staging: chunks of 32 stream positions located and loaded at once
+constexpr int kStageChunksF = 2;
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
@@ -272,28 +274,21 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     auto sg = make_stager_for<T, REL, PER>(bx, Rf, g, invL, A.p, G.rx, G.ry, G.rz);
     for (;;) {
       // stage candidates
-      int nl = 0;
-      while (nl <= CAP - 32) {
-        int j;
-        bool ok;
-        T ox, oy, oz;
-        if (!stager_chunk<T, REL>(sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, j,
-                                  ok, ox, oy, oz, &A.st->err))
-          break;
-        if (ok) j = (int)checked(j, A.n, &A.st->err);
-        const V4 q = ok ? V::ld(posh, j) : V::make(0, 0, 0, 0);
-        const T xj = add_rn(q.x, ox), yj = add_rn(q.y, oy), zj = add_rn(q.z, oz);
-        const T R = tmax(Rb, q.w);
-        const bool keep =
-            ok && box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R + gmax;
-        const unsigned bal = __ballot_sync(kFull, keep);
-        if (keep) {
-          const int at = (int)checked(nl + __popc(bal & lanemask_lt()), CAP, &A.st->err);
-          Lr.put(at, xj, yj, zj, q.w * q.w);
-          Li[at] = j;
-        }
-        nl += __popc(bal);
-      }
+      const int nl = stage_list<kStageChunksF, T, REL>(
+          sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, 0, CAP, A.n, &A.st->err,
+          [&](bool ok, int j) { return ok ? V::ld(posh, j) : V::make(0, 0, 0, 0); },
+          [&](bool ok, const V4 &q, T ox, T oy, T oz, T &xj, T &yj, T &zj) {
+            xj = add_rn(q.x, ox);
+            yj = add_rn(q.y, oy);
+            zj = add_rn(q.z, oz);
+            const T R = tmax(Rb, q.w);
+            return ok &&
+                   box_d2(xj, yj, zj, bx.x0, bx.x1, bx.y0, bx.y1, bx.z0, bx.z1) < R * R + gmax;
+          },
+          [&](int at, T xj, T yj, T zj, const V4 &q, int j) {
+            Lr.put(at, xj, yj, zj, q.w * q.w);
+            Li[at] = j;
+          });
       cand += nl;
       __syncwarp();
       // membership bits: r^2 < max(H_i^2 + gi, H_j^2)

@@ -383,18 +383,15 @@ __device__ __forceinline__ Stager make_stager(const Box<T> &b, T R, const Grid &
   return s;
 }
 
-// The next 32 stream positions, one per lane: particle index j (valid when
-// ok) and its coordinate offset. false when the stream is exhausted
-// (warp-uniform).
-template <typename T, bool REL>
-__device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int *cstart,
-                                             const int *cend, T Lt, int rx, int ry, int rz,
-                                             int &j, bool &ok, T &ox, T &oy, T &oz,
-                                             unsigned *err) {
+// Make the current batch of cells hold unconsumed stream positions,
+// reading the next 32 cells of the range (one per lane) as often as needed.
+// false when the stream is exhausted (warp-uniform).
+__device__ __forceinline__ bool stager_refill(Stager &s, const Grid &g, const int *cstart,
+                                              const int *cend, int rx, int ry, int rz,
+                                              unsigned *err) {
   const int lane = threadIdx.x & 31;
   while (s.pos >= s.total) {
     if (s.c0 >= s.ncell) return false;
-    // the next 32 cells of the range, one per lane
     const int c = s.c0 + lane;
     int cnt = 0, st = 0, off = 0;
     if (c < s.ncell) {
@@ -420,7 +417,14 @@ __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int
     s.pos = 0;
     s.c0 += 32;
   }
-  const int k = s.pos + lane;
+  return true;
+}
+
+// Stream position k of the current batch (every lane calls it, each with
+// its own k): particle index j (valid when ok) and its coordinate offset.
+template <typename T, bool REL>
+__device__ __forceinline__ void stager_at(const Stager &s, int k, T Lt, int &j, bool &ok, T &ox,
+                                          T &oy, T &oz) {
   ok = k < s.total;
   // the lane whose cell holds stream position k: the last one with pre <= k
   int own = 0;
@@ -441,10 +445,7 @@ __device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int
   } else {
     ox = oy = oz = T(0);
   }
-  s.pos += 32;
-  return true;
 }
-
 
 // ------------------------------------------------------------ periodic box
 // In a periodic box the range box +- R may cross the box's faces. The part
@@ -552,12 +553,11 @@ __device__ __forceinline__ T periodic_offset(int k, int r, int shift, T Lt, cons
   return shift == 0 ? T(0) : (T)((double)shift * len);
 }
 
-// As stager_chunk for a closed box, over the periodic runs.
+// As stager_refill and stager_at for a closed box, over the periodic runs.
 template <typename T, bool REL>
-__device__ __forceinline__ bool stager_chunk(StagerP<T> &s, const Grid &g, const int *cstart,
-                                             const int *cend, T Lt, const KParams &P, int rx,
-                                             int ry, int rz, int &j, bool &ok, T &ox, T &oy,
-                                             T &oz, unsigned *err) {
+__device__ __forceinline__ bool stager_refill(StagerP<T> &s, const Grid &g, const int *cstart,
+                                              const int *cend, T Lt, const KParams &P, int rx,
+                                              int ry, int rz, unsigned *err) {
   const int lane = threadIdx.x & 31;
   while (s.pos >= s.total) {
     if (s.c0 >= s.ncell) return false;
@@ -594,7 +594,11 @@ __device__ __forceinline__ bool stager_chunk(StagerP<T> &s, const Grid &g, const
     s.pos = 0;
     s.c0 += 32;
   }
-  const int k = s.pos + lane;
+  return true;
+}
+template <typename T, bool REL>
+__device__ __forceinline__ void stager_at(const StagerP<T> &s, int k, T, int &j, bool &ok, T &ox,
+                                          T &oy, T &oz) {
   ok = k < s.total;
   int own = 0;
 #pragma unroll
@@ -608,8 +612,6 @@ __device__ __forceinline__ bool stager_chunk(StagerP<T> &s, const Grid &g, const
   ox = __shfl_sync(kFull, s.ox, own);
   oy = __shfl_sync(kFull, s.oy, own);
   oz = __shfl_sync(kFull, s.oz, own);
-  s.pos += 32;
-  return true;
 }
 
 // One stager type per box kind, so that the closed-box kernels are
@@ -629,11 +631,56 @@ __device__ __forceinline__ typename StagerOf<T, PER>::type make_stager_for(
     return make_stager<T, REL>(b, R, g, invL, rx, ry, rz);
 }
 template <typename T, bool REL>
-__device__ __forceinline__ bool stager_chunk(Stager &s, const Grid &g, const int *cstart,
-                                             const int *cend, T Lt, const KParams &, int rx,
-                                             int ry, int rz, int &j, bool &ok, T &ox, T &oy,
-                                             T &oz, unsigned *err) {
-  return stager_chunk<T, REL>(s, g, cstart, cend, Lt, rx, ry, rz, j, ok, ox, oy, oz, err);
+__device__ __forceinline__ bool stager_refill(Stager &s, const Grid &g, const int *cstart,
+                                              const int *cend, T, const KParams &, int rx, int ry,
+                                              int rz, unsigned *err) {
+  return stager_refill(s, g, cstart, cend, rx, ry, rz, err);
+}
+
+// Stage the stream into a list from position nl on, while a further 32
+// entries fit below cap: each candidate's record is loaded (load(ok, j)),
+// tested (keep(ok, q, ox, oy, oz, x, y, z) forms its coordinates and
+// decides), and the kept ones are appended in stream order (put(at, x, y,
+// z, q, j)). U chunks of 32 stream positions are located and their records
+// loaded before the first of them is tested, so that U loads are in flight
+// at once; chunks are consumed in order and the stager stops at the first
+// one that finds no room (its loads are dropped), so the list is the one a
+// chunk-by-chunk loop would build. Returns the new list length.
+template <int U, typename T, bool REL, typename St, typename Ld, typename Kp, typename Pt>
+__device__ __forceinline__ int stage_list(St &sg, const Grid &g, const int *cstart,
+                                          const int *cend, T Lt, const KParams &P, int rx, int ry,
+                                          int rz, int nl, int cap, int64_t n, unsigned *err,
+                                          Ld load, Kp keep, Pt put) {
+  const int lane = threadIdx.x & 31;
+  while (nl <= cap - 32) {
+    if (!stager_refill<T, REL>(sg, g, cstart, cend, Lt, P, rx, ry, rz, err)) break;
+    const int avail = (sg.total - sg.pos + 31) >> 5;   // chunks left in this batch
+    int j[U];
+    bool ok[U];
+    T ox[U], oy[U], oz[U];
+    decltype(load(false, 0)) q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      j[u] = 0;
+      ok[u] = false;
+      ox[u] = oy[u] = oz[u] = T(0);
+      if (u < avail) stager_at<T, REL>(sg, sg.pos + 32 * u + lane, Lt, j[u], ok[u], ox[u], oy[u],
+                                       oz[u]);
+      if (ok[u]) j[u] = (int)checked(j[u], n, err);
+      q[u] = load(ok[u], j[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u >= avail || nl > cap - 32) break;   // warp-uniform
+      T x, y, z;
+      const bool kp = keep(ok[u], q[u], ox[u], oy[u], oz[u], x, y, z);
+      const unsigned bal = __ballot_sync(kFull, kp);
+      if (kp) put((int)checked(nl + __popc(bal & lanemask_lt()), cap, err), x, y, z, q[u], j[u]);
+      nl += __popc(bal);
+      sg.pos += 32;
+    }
+  }
+  return nl;
 }
 
 // FP64 squared distance of the neighbour predicate in a periodic box: the
