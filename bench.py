@@ -63,10 +63,11 @@ FP64_NOMINAL_TFLOPS = 1.25
 # 600k-particle impact (bench.py --scale 0.3 --spans 1,2; profiles/ has the
 # command) and scaled by particles. Keyed by a hash of the kernel's sources: once the
 # kernel changes the figure no longer applies and traffic is reported null.
-KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh"),
+KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh",
+                                "sph_kick.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (184.6, "d6177f54f9c4"),
-                        "k_density": (62.1, "1cd71a8ca953")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (185.1, "a63d321b5e7f"),
+                        "k_density": (62.9, "e85f2429c204")}
 
 
 def source_hash(kernel: str) -> str:
