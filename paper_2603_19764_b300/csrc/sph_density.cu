@@ -171,7 +171,7 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
                                              unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              T gb, T H, double xi64, double yi64, double zi64,
-                                             const sph_state &s, const double *blen, int self,
+                                             const sph_state &s, const double *blen,
                                              T &rs, T &rhs, T &rhs2, int &cnt, int64_t n_all,
                                              unsigned *err) {
   // every lane advances through its own words: lanes do not wait for each
@@ -221,8 +221,10 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
         rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
         if (REL)   // H^5 d2W/dH2 / cW = (1-q)^2 (12 + 24q - 264q^2 + 288q^3)
           rhs2 += qm * t * t * (T(12) + qq * (T(24) + qq * (T(-264) + T(288) * qq)));
-        // only a pair at r = 0 can be the particle itself
-        cnt += r2 > T(0) ? 1 : (Li[k] != self);
+        // the particle itself is among the lane's candidates and in range
+        // (r = 0 exactly, see rel_coord): counted here, taken off once by
+        // the caller
+        ++cnt;
       }
     }
   }
@@ -374,10 +376,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           __syncwarp();
           if (act) {
             density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
-                                          yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
+                                          yi64, zi64, A.s, A.p.box_len, rs, rhs, rhs2,
                                           cnt, A.n, &A.st->err);
             density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
-                                          xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
+                                          xi64, yi64, zi64, A.s, A.p.box_len, rs, rhs,
                                           rhs2, cnt, A.n, &A.st->err);
           }
           __syncwarp();
@@ -398,10 +400,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         }
         if (act) {
           density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
-                                        yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs, rhs2,
+                                        yi64, zi64, A.s, A.p.box_len, rs, rhs, rhs2,
                                         cnt, A.n, &A.st->err);
           density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
-                                        xi64, yi64, zi64, A.s, A.p.box_len, (int)i, rs, rhs,
+                                        xi64, yi64, zi64, A.s, A.p.box_len, rs, rhs,
                                         rhs2, cnt, A.n, &A.st->err);
         }
       }
@@ -417,10 +419,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         const T gq = T(4.0 * kPi / 3.0) * Ht * Ht * Ht * rho / target - T(1);
         rho_o = rho;
         om_o = om;
-        cnt_o = cnt;
+        cnt_o = cnt - 1;   // the walk counted the particle itself
         H_o = H;
         sweeps_o = sweep;
-        pairs += cnt;
+        pairs += cnt - 1;
         if (fabs(gq) <= tol) {
           state = 1;
         } else if (gq < T(0) && H >= Hcap) {

@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
                 inH = r2_canon_periodic(A.s.x[i] - A.s.x[j], A.s.y[i] - A.s.y[j],
                                         A.s.z[i] - A.s.z[j], A.p.box_len) < h2;
             }
-            nngb += (inH && (r2 > T(0) || j != (int)i)) ? 1 : 0;
+            nngb += inH ? 1 : 0;   // the particle itself included, taken off below
           }
           // a pair marked only for the count (r^2 in the band past both
           // radii) has no say in the signal velocity and no place in the
@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   // ---------------------------------------- finalize (Eq. 21-29, 38-39)
   int fallback = 0;
   if (valid) {
+    nngb -= 1;   // the walk counted the particle itself (r = 0, always in range)
     const V4 s0 = V::ld(PK::fs(A.w, 0), i), s1 = V::ld(PK::fs(A.w, 1), i),
              s2 = V::ld(PK::fs(A.w, 2), i);
     const bool fixed = A.s.flags[i] & SPH_FLAG_FIXED;

@@ -142,14 +142,14 @@ def test_full_steps_granular_column(precision):
     sim.close()
 
 
-@pytest.mark.parametrize("chunks", [1, 3, 16])
-def test_step_host_equals_step(chunks):
+@pytest.mark.parametrize("precision,chunks", [(1, 1), (1, 3), (1, 16), (0, 3)])
+def test_step_host_equals_step(precision, chunks):
     """The host-buffer entry point (copy in, step, overlapped copy-out by
     array group; the force pass in `chunks` bucket ranges, each copied back
     as it completes) leaves exactly the state of device steps, also when
     the context has a captured graph for its device steps."""
     w = WL["impact"]
-    p = _params(w, 1)
+    p = _params(w, precision)
     a = sph.Simulation(w.arrays, w.materials, p)
     b = sph.Simulation(w.arrays, w.materials, p)
     a.prime()
