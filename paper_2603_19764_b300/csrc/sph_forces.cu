@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           const T gx = gs * dx, gy = gs * dy;
           C0.add(gx * dx); C1.add(gx * dy); C2.add(gx * dz);
           C3.add(gy * dy); C4.add(gy * dz); C5.add(gs * dz * dz);
-          npairs += (r2 > T(0) && inR) ? 1 : 0;
+          npairs += inR ? 1 : 0;   // the particle itself included, taken off below
           if (++blk == kSumBlock) {   // lanes stay in step: one pair per pass each
             blk = 0;
             du.flush(); F0.flush(); F1.flush(); F2.flush(); F3.flush();
@@ -445,7 +445,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
   // ---------------------------------------- finalize (Eq. 21-29, 38-39)
   int fallback = 0;
   if (valid) {
-    nngb -= 1;   // the walk counted the particle itself (r = 0, always in range)
+    // the walk counted the particle itself (r = 0, always in range)
+    nngb -= 1;
+    npairs -= 1;
     const V4 s0 = V::ld(PK::fs(A.w, 0), i), s1 = V::ld(PK::fs(A.w, 1), i),
              s2 = V::ld(PK::fs(A.w, 2), i);
     const bool fixed = A.s.flags[i] & SPH_FLAG_FIXED;
