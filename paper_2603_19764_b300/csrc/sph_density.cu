@@ -164,6 +164,18 @@ __device__ __forceinline__ void build_masks(const LV &Lp, unsigned (*Lm)[32],
   }
 }
 
+// The FP64 predicate r < H of a pair in the guard band of the FP32 form (H
+// the FP32 radius, whose square is exact in FP64): out of line, so that the
+// compiler never evaluates it for the pairs outside the band.
+template <bool PER>
+static __device__ __noinline__ bool guard_in(const double *sx, const double *sy,
+                                             const double *sz, int j, double xi64, double yi64,
+                                             double zi64, const double *blen, double H) {
+  const double c2 = PER ? r2_canon_periodic(xi64 - sx[j], yi64 - sy[j], zi64 - sz[j], blen)
+                        : r2_canon(xi64 - sx[j], yi64 - sy[j], zi64 - sz[j]);
+  return c2 < __dmul_rn(H, H);
+}
+
 // Walk one lane's marked candidates: exact membership r < H_i, then the
 // kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
 template <typename T, bool REL, bool PER, typename LV>
@@ -194,14 +206,9 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
       if (REL) {
         r2 = dist2(dx, dy, dz);
         in = r2 < H2;
-        if (fabs(r2 - H2) < gb) {
-          const int j = (int)checked(Li[k], n_all, err);
-          // the square of an FP32 radius is exact in FP64
-          const double c2 = PER ? r2_canon_periodic(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j],
-                                                    blen)
-                                : r2_canon(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j]);
-          in = c2 < __dmul_rn((double)H, (double)H);
-        }
+        if (fabs(r2 - H2) < gb)   // rare: decided out of line in FP64
+          in = guard_in<PER>(s.x, s.y, s.z, (int)checked(Li[k], n_all, err), xi64, yi64, zi64,
+                             blen, (double)H);
       } else {
         r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
         in = r2 < H2;
@@ -213,19 +220,22 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
           in = r2_canon_periodic(xi64 - s.x[j], yi64 - s.y[j], zi64 - s.z[j], blen) < (double)H2;
         }
       }
-      if (in) {
-        const T qq = root(r2) * invH;
-        const T t = qq < T(1) ? T(1) - qq : T(0);
-        const T mW = qm * t * t * t;
-        rs += mW * t * (T(1) + T(4) * qq);
-        rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
-        if (REL)   // H^5 d2W/dH2 / cW = (1-q)^2 (12 + 24q - 264q^2 + 288q^3)
-          rhs2 += qm * t * t * (T(12) + qq * (T(24) + qq * (T(-264) + T(288) * qq)));
-        // the particle itself is among the lane's candidates and in range
-        // (r = 0 exactly, see rel_coord): counted here, taken off once by
-        // the caller
-        ++cnt;
-      }
+      // FP64 form: out-of-range candidates skip the (FP64) kernel terms.
+      // FP32 form: every marked candidate forms them, a candidate out of
+      // range with weight t = 0 (exact zeros, the sums unchanged), which
+      // costs less than the branch (the marks reach only 1.005 H)
+      if (!REL && !in) continue;
+      const T qq = root(r2) * invH;
+      const T t = in ? tmax(T(1) - qq, T(0)) : T(0);
+      const T mW = qm * t * t * t;
+      rs += mW * t * (T(1) + T(4) * qq);
+      rhs += mW * (T(-3) + qq * (T(-9) + T(32) * qq));
+      if (REL)   // H^5 d2W/dH2 / cW = (1-q)^2 (12 + 24q - 264q^2 + 288q^3)
+        rhs2 += qm * t * t * (T(12) + qq * (T(24) + qq * (T(-264) + T(288) * qq)));
+      // the particle itself is among the lane's candidates and in range
+      // (r = 0 exactly, see rel_coord): counted here, taken off once by
+      // the caller
+      cnt += in ? 1 : 0;
     }
   }
 }
