@@ -164,18 +164,6 @@ __device__ __forceinline__ void build_masks(const LV &Lp, unsigned (*Lm)[32],
   }
 }
 
-// The FP64 predicate r < H of a pair in the guard band of the FP32 form (H
-// the FP32 radius, whose square is exact in FP64): out of line, so that the
-// compiler never evaluates it for the pairs outside the band.
-template <bool PER>
-static __device__ __noinline__ bool guard_in(const double *sx, const double *sy,
-                                             const double *sz, int j, double xi64, double yi64,
-                                             double zi64, const double *blen, double H) {
-  const double c2 = PER ? r2_canon_periodic(xi64 - sx[j], yi64 - sy[j], zi64 - sz[j], blen)
-                        : r2_canon(xi64 - sx[j], yi64 - sy[j], zi64 - sz[j]);
-  return c2 < __dmul_rn(H, H);
-}
-
 // Walk one lane's marked candidates: exact membership r < H_i, then the
 // kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
 template <typename T, bool REL, bool PER, typename LV>
@@ -207,8 +195,8 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
         r2 = dist2(dx, dy, dz);
         in = r2 < H2;
         if (fabs(r2 - H2) < gb)   // rare: decided out of line in FP64
-          in = guard_in<PER>(s.x, s.y, s.z, (int)checked(Li[k], n_all, err), xi64, yi64, zi64,
-                             blen, (double)H);
+          in = fp64_within<PER>(s.x, s.y, s.z, xi64, yi64, zi64,
+                                (int)checked(Li[k], n_all, err), blen, (double)H);
       } else {
         r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
         in = r2 < H2;

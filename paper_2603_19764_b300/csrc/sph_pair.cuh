@@ -690,4 +690,19 @@ __device__ __forceinline__ double r2_canon_periodic(double dx, double dy, double
   return r2_canon(min_image(dx, len[0]), min_image(dy, len[1]), min_image(dz, len[2]));
 }
 
+// The FP64 predicate r < H of a pair inside the FP32 form's guard band
+// (particle i at (xi, yi, zi), candidate j; H the FP32 radius, whose square
+// is exact in FP64). Out of line for the density walk, whose accumulation
+// has no branch: written inline there, the compiler evaluated it for every
+// pair, outside the band too. (The force walk keeps it inline: the call
+// made that kernel spill.)
+template <bool PER>
+static __device__ __noinline__ bool fp64_within(const double *sx, const double *sy,
+                                                const double *sz, double xi, double yi,
+                                                double zi, int j, const double *blen, double H) {
+  const double c2 = PER ? r2_canon_periodic(xi - sx[j], yi - sy[j], zi - sz[j], blen)
+                        : r2_canon(xi - sx[j], yi - sy[j], zi - sz[j]);
+  return c2 < __dmul_rn(H, H);
+}
+
 }  // namespace sphk
