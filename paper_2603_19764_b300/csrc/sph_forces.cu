@@ -119,7 +119,7 @@ cudaError_t launch_eos_pack(sph_ctx *c) {
 // rounding error is a few ulp of the matrix norm.
 constexpr int kSumBlock = 8;
 // Staging: chunks of 32 stream positions located and loaded at once
-constexpr int kStageChunksF = 2;
+constexpr int kStageChunksF = 3;
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
