@@ -66,8 +66,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh",
                                 "sph_kick.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (185.1, "a63d321b5e7f"),
-                        "k_density": (62.9, "e85f2429c204")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (185.0, "318b185c5207"),
+                        "k_density": (63.7, "4e2e217e0fa9")}
 
 
 def source_hash(kernel: str) -> str:
