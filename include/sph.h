@@ -223,8 +223,9 @@ typedef struct {
  * NULL for the legacy default stream). Validates the parameters, copies
  * params, materials and the gravity table, allocates scratch. Does not
  * touch the state. Errors: SPH_E_ARG (n < 1, bad pointer, bad enum, n_mat
- * out of 1..SPH_MAX_MATERIALS, periodic != 0), SPH_E_CUDA. *out is NULL on
- * failure. */
+ * out of 1..SPH_MAX_MATERIALS, periodic not 0 or 1, a periodic box that is
+ * empty or not finite, or one combined with max_rung > 0 or the radial
+ * table), SPH_E_CUDA. *out is NULL on failure. */
 sph_status sph_init(sph_ctx **out, const sph_params *p, const sph_material *mats,
                     int32_t n_mat, const sph_state *st, int64_t n, void *cuda_stream);
 

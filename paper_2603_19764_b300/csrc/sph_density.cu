@@ -164,16 +164,21 @@ __device__ __forceinline__ void build_masks(const LV &Lp, unsigned (*Lm)[32],
   }
 }
 
-// Walk one lane's marked candidates: exact membership r < H_i, then the
-// kernel sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
+// Walk one lane's marked candidates: membership r < H_i, then the kernel
+// sums of Eq. 1 (rs) and Eq. 3 (rhs) without their constant factors.
+// FP32 form: membership by the FP32 r^2; a pair within the guard band gb of
+// H^2 sets `near`, and density_recount then corrects the count with the
+// FP64 predicate (the kernel weight of such a pair is ~(gb / H^2)^4 of a
+// neighbour's, below the rounding of the sums, so only the count depends on
+// the decision).
 template <typename T, bool REL, bool PER, typename LV>
 __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
                                              unsigned (*Lm)[32],
                                              int nl, int lane, T xi, T yi, T zi, T invH, T H2,
                                              T gb, T H, double xi64, double yi64, double zi64,
                                              const sph_state &s, const double *blen,
-                                             T &rs, T &rhs, T &rhs2, int &cnt, int64_t n_all,
-                                             unsigned *err) {
+                                             T &rs, T &rhs, T &rhs2, int &cnt, bool &near,
+                                             int64_t n_all, unsigned *err) {
   // every lane advances through its own words: lanes do not wait for each
   // other at word boundaries
   const int nw = (nl + 31) >> 5;
@@ -194,9 +199,7 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
       if (REL) {
         r2 = dist2(dx, dy, dz);
         in = r2 < H2;
-        if (fabs(r2 - H2) < gb)   // rare: decided out of line in FP64
-          in = fp64_within<PER>(s.x, s.y, s.z, xi64, yi64, zi64,
-                                (int)checked(Li[k], n_all, err), blen, (double)H);
+        near = near || fabs(r2 - H2) < gb;   // rare: the count is corrected afterwards
       } else {
         r2 = (T)r2_canon((double)dx, (double)dy, (double)dz);
         in = r2 < H2;
@@ -226,6 +229,53 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
       cnt += in ? 1 : 0;
     }
   }
+}
+
+// FP32 form, after density_walk set `near`: walk the same marks again and
+// move every pair within the guard band from the FP32 decision to the FP64
+// predicate's, so that the count is that of the canonical predicate.
+// Returns the change of the count.
+template <bool PER, typename LV>
+__device__ __forceinline__ int density_recount(const LV &Lp, const int *Li, unsigned (*Lm)[32],
+                                               int nl, int lane, float xi, float yi, float zi,
+                                               float H2, float gb, float H, double xi64,
+                                               double yi64, double zi64, const double *sx,
+                                               const double *sy, const double *sz,
+                                               const double *blen, int64_t n_all,
+                                               unsigned *err) {
+  int cnt = 0;
+  const int nw = (nl + 31) >> 5;
+  for (int wd = 0; wd < nw; ++wd) {
+    unsigned mk = Lm[wd][lane];
+    while (mk) {
+      const int k = (wd << 5) + take_next(mk);
+      float qx, qy, qz, qm;
+      Lp.get(k, qx, qy, qz, qm);
+      const float r2 = dist2(xi - qx, yi - qy, zi - qz);
+      if (fabs(r2 - H2) < gb) {
+        const bool in = fp64_within<PER>(sx, sy, sz, xi64, yi64, zi64,
+                                         (int)checked(Li[k], n_all, err), blen, (double)H);
+        cnt += (in ? 1 : 0) - (r2 < H2 ? 1 : 0);
+      }
+    }
+  }
+  return cnt;
+}
+
+// Both parts of a list (shared memory and its overflow), out of line: the
+// walks stay free of the FP64 predicate and its registers.
+template <bool PER, int S1, int S2>
+__device__ __noinline__ int recount_lists(ViewPlanes<S1> L1, const int *I1, unsigned (*M1)[32],
+                                          int n1, ViewPlanes<S2> L2, const int *I2,
+                                          unsigned (*M2)[32], int n2, int lane, float xi,
+                                          float yi, float zi, float H2, float gb, float H,
+                                          double xi64, double yi64, double zi64,
+                                          const double *sx, const double *sy, const double *sz,
+                                          const double *blen, int64_t n_all, unsigned *err) {
+  return density_recount<PER>(L1, I1, M1, n1, lane, xi, yi, zi, H2, gb, H, xi64, yi64, zi64, sx,
+                              sy, sz, blen, n_all, err) +
+         density_recount<PER>(L2, I2, M2, n2, lane, xi, yi, zi, H2, gb, H, xi64, yi64, zi64, sx,
+                              sy, sz, blen, n_all, err);
 }
 
 template <typename T, int CAP, bool PER>
@@ -373,12 +423,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           build_masks<T>(Sp, Sv.m, n2, xi, yi, zi, Hq * Hq, act, lane);
           __syncwarp();
           if (act) {
+            bool near = false;
             density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                           yi64, zi64, A.s, A.p.box_len, rs, rhs, rhs2,
-                                          cnt, A.n, &A.st->err);
+                                          cnt, near, A.n, &A.st->err);
             density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
                                           xi64, yi64, zi64, A.s, A.p.box_len, rs, rhs,
-                                          rhs2, cnt, A.n, &A.st->err);
+                                          rhs2, cnt, near, A.n, &A.st->err);
+            if constexpr (REL)
+              if (near)   // rare
+                cnt += recount_lists<PER>(Lp, Li, Lm, n1, Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, H2,
+                                          gb, Ht, xi64, yi64, zi64, A.s.x, A.s.y, A.s.z,
+                                          A.p.box_len, A.n, &A.st->err);
           }
           __syncwarp();
           if (stager_finished(sg)) break;
@@ -397,12 +453,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
           Hm = Hn;
         }
         if (act) {
+          bool near = false;
           density_walk<T, REL, PER>(Lp, Li, Lm, n1, lane, xi, yi, zi, invHt, H2, gb, Ht, xi64,
                                         yi64, zi64, A.s, A.p.box_len, rs, rhs, rhs2,
-                                        cnt, A.n, &A.st->err);
+                                        cnt, near, A.n, &A.st->err);
           density_walk<T, REL, PER>(Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, invHt, H2, gb, Ht,
                                         xi64, yi64, zi64, A.s, A.p.box_len, rs, rhs,
-                                        rhs2, cnt, A.n, &A.st->err);
+                                        rhs2, cnt, near, A.n, &A.st->err);
+          if constexpr (REL)
+            if (near)   // rare
+              cnt += recount_lists<PER>(Lp, Li, Lm, n1, Sp, Sv.i, Sv.m, n2, lane, xi, yi, zi, H2,
+                                        gb, Ht, xi64, yi64, zi64, A.s.x, A.s.y, A.s.z,
+                                        A.p.box_len, A.n, &A.st->err);
         }
       }
 
