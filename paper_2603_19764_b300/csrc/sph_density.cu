@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         Hm = T(0);
         complete = false;
         for (int seg = 0;; ++seg) {
-          nl = stage_list<kStageChunksD, T, REL>(
+          nl = stage_list<kStageChunksD, true, T, REL>(
               sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, 0, TCAP, A.n,
               &A.st->err,
               [&](bool ok, int j) { return ok ? V::ld(pos, j) : V::make(0, 0, 0, 0); },

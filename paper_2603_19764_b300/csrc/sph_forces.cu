@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     auto sg = make_stager_for<T, REL, PER>(bx, Rf, g, invL, A.p, G.rx, G.ry, G.rz);
     for (;;) {
       // stage candidates
-      const int nl = stage_list<kStageChunksF, T, REL>(
+      const int nl = stage_list<kStageChunksF, false, T, REL>(
           sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, 0, CAP, A.n, &A.st->err,
           [&](bool ok, int j) { return ok ? V::ld(posh, j) : V::make(0, 0, 0, 0); },
           [&](bool ok, const V4 &q, T ox, T oy, T oz, T &xj, T &yj, T &zj) {

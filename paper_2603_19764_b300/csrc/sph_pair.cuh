@@ -321,7 +321,9 @@ __device__ __forceinline__ Box<T> group_box(bool act, T x, T y, T z) {
 // Resumable stream of the particles of the cells overlapping box +- R, in
 // cell order (z, then y, then x) and sorted order within a cell. The cell
 // ranges are read 32 cells at a time, one cell per lane, so their loads
-// overlap instead of forming a chain; a prefix sum over the lanes then maps
+// overlap instead of forming a chain, and one batch ahead: the ranges of
+// the next 32 cells are requested when a batch is taken up, so that taking
+// up the next one waits for no load; a prefix sum over the lanes then maps
 // stream positions to (cell, particle), and every chunk of 32 positions
 // fills all lanes whatever the cell sizes. Coordinates are relative to the
 // origin of the reference cell (FP32 form) or absolute (FP64 form): a
@@ -335,6 +337,8 @@ struct Stager {
                            // prefix of the counts, packed offset to the
                            // reference cell (10 bits per axis, biased 512)
   int total, pos;          // particles in the batch, next stream position
+  int nst, nen, noff;      // the next batch's cell of this lane: start, end,
+                           // packed offset (nst < 0: empty or past the range)
 };
 
 // All staged: no cell left and the batch consumed.
@@ -377,33 +381,63 @@ __device__ __forceinline__ Stager make_stager(const Box<T> &b, T R, const Grid &
   s.off = 0;
   s.total = 0;
   s.pos = 0;
+  s.nst = -1;
+  s.nen = 0;
+  s.noff = 0;
   (void)rx;
   (void)ry;
   (void)rz;
   return s;
 }
 
+// Request the cell range of this lane's cell in the batch from range cell
+// c0 on (start, end and packed offset; start -1 past the range). Both loads
+// are issued together; an empty cell's end is read but not used.
+__device__ __forceinline__ void stager_fetch(const Stager &s, int c0, const Grid &g,
+                                             const int *cstart, const int *cend, int rx, int ry,
+                                             int rz, unsigned *err, int &st, int &en, int &off) {
+  const int c = c0 + (int)(threadIdx.x & 31);
+  st = -1;
+  en = 0;
+  off = 0;
+  if (c < s.ncell) {
+    const int x = c % s.nx, t = c / s.nx;
+    const int y = t % s.ny, z = t / s.ny;
+    const int gx = s.kx0 + x, gy = s.ky0 + y, gz = s.kz0 + z;
+    const int cell = g.cell_off + (int)checked((gz * g.dims[1] + gy) * g.dims[0] + gx,
+                                               g.ncells, err);
+    st = cstart[cell];
+    en = cend[cell];
+    off = (gx - rx + 512) | ((gy - ry + 512) << 10) | ((gz - rz + 512) << 20);
+  }
+}
+
 // Make the current batch of cells hold unconsumed stream positions,
 // reading the next 32 cells of the range (one per lane) as often as needed.
-// false when the stream is exhausted (warp-uniform).
+// false when the stream is exhausted (warp-uniform). AHEAD: the ranges of
+// the batch after are requested as a batch is taken up (three registers a
+// lane held while the list is walked; the force pass, at its register
+// limit, fetches each batch when it takes it up instead).
+template <bool AHEAD>
 __device__ __forceinline__ bool stager_refill(Stager &s, const Grid &g, const int *cstart,
                                               const int *cend, int rx, int ry, int rz,
                                               unsigned *err) {
   const int lane = threadIdx.x & 31;
   while (s.pos >= s.total) {
     if (s.c0 >= s.ncell) return false;
-    const int c = s.c0 + lane;
-    int cnt = 0, st = 0, off = 0;
-    if (c < s.ncell) {
-      const int x = c % s.nx, t = c / s.nx;
-      const int y = t % s.ny, z = t / s.ny;
-      const int gx = s.kx0 + x, gy = s.ky0 + y, gz = s.kz0 + z;
-      const int cell = g.cell_off + (int)checked((gz * g.dims[1] + gy) * g.dims[0] + gx,
-                                                 g.ncells, err);
-      st = cstart[cell];
-      if (st >= 0) cnt = cend[cell] - st;
-      off = (gx - rx + 512) | ((gy - ry + 512) << 10) | ((gz - rz + 512) << 20);
+    int st, en, off;
+    if (AHEAD) {
+      // the first batch is fetched here, every later one a batch ahead
+      if (s.c0 == 0)
+        stager_fetch(s, 0, g, cstart, cend, rx, ry, rz, err, s.nst, s.nen, s.noff);
+      st = s.nst;
+      en = s.nen;
+      off = s.noff;
+      stager_fetch(s, s.c0 + 32, g, cstart, cend, rx, ry, rz, err, s.nst, s.nen, s.noff);
+    } else {
+      stager_fetch(s, s.c0, g, cstart, cend, rx, ry, rz, err, st, en, off);
     }
+    const int cnt = st >= 0 ? en - st : 0;
     int inc = cnt;   // inclusive prefix over the lanes
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -553,8 +587,9 @@ __device__ __forceinline__ T periodic_offset(int k, int r, int shift, T Lt, cons
   return shift == 0 ? T(0) : (T)((double)shift * len);
 }
 
-// As stager_refill and stager_at for a closed box, over the periodic runs.
-template <typename T, bool REL>
+// As stager_refill and stager_at for a closed box, over the periodic runs
+// (each batch fetched when it is taken up, whatever AHEAD).
+template <typename T, bool REL, bool AHEAD>
 __device__ __forceinline__ bool stager_refill(StagerP<T> &s, const Grid &g, const int *cstart,
                                               const int *cend, T Lt, const KParams &P, int rx,
                                               int ry, int rz, unsigned *err) {
@@ -630,11 +665,11 @@ __device__ __forceinline__ typename StagerOf<T, PER>::type make_stager_for(
   else
     return make_stager<T, REL>(b, R, g, invL, rx, ry, rz);
 }
-template <typename T, bool REL>
+template <typename T, bool REL, bool AHEAD>
 __device__ __forceinline__ bool stager_refill(Stager &s, const Grid &g, const int *cstart,
                                               const int *cend, T, const KParams &, int rx, int ry,
                                               int rz, unsigned *err) {
-  return stager_refill(s, g, cstart, cend, rx, ry, rz, err);
+  return stager_refill<AHEAD>(s, g, cstart, cend, rx, ry, rz, err);
 }
 
 // Stage the stream into a list from position nl on, while a further 32
@@ -646,14 +681,15 @@ __device__ __forceinline__ bool stager_refill(Stager &s, const Grid &g, const in
 // at once; chunks are consumed in order and the stager stops at the first
 // one that finds no room (its loads are dropped), so the list is the one a
 // chunk-by-chunk loop would build. Returns the new list length.
-template <int U, typename T, bool REL, typename St, typename Ld, typename Kp, typename Pt>
+template <int U, bool AHEAD, typename T, bool REL, typename St, typename Ld, typename Kp,
+          typename Pt>
 __device__ __forceinline__ int stage_list(St &sg, const Grid &g, const int *cstart,
                                           const int *cend, T Lt, const KParams &P, int rx, int ry,
                                           int rz, int nl, int cap, int64_t n, unsigned *err,
                                           Ld load, Kp keep, Pt put) {
   const int lane = threadIdx.x & 31;
   while (nl <= cap - 32) {
-    if (!stager_refill<T, REL>(sg, g, cstart, cend, Lt, P, rx, ry, rz, err)) break;
+    if (!stager_refill<T, REL, AHEAD>(sg, g, cstart, cend, Lt, P, rx, ry, rz, err)) break;
     const int avail = (sg.total - sg.pos + 31) >> 5;   // chunks left in this batch
     int j[U];
     bool ok[U];
