@@ -76,12 +76,12 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
     const typename V::type pp = pos[i];
     const T rho = to_t<T>(rhod), om = to_t<T>(s.omega[i]), m = to_t<T>(s.m[i]),
             H = to_t<T>(s.h[i]);
-    const T inv = m / (om * rho * rho);
-    const T ih = T(1) / H;
+    const T inv = quot(m, om * rho * rho);
+    const T ih = quot(T(1), H);
     const T ih2 = ih * ih;
     const T K = T(cG) * ih2 * ih2 * ih;
     const T Gam = M.strength ? shear_mod_t<T>(M, rho, e.c) : T(0);
-    const T cl = M.strength ? sqrt(e.c * e.c + T(4.0 / 3.0) * Gam / rho) : e.c;
+    const T cl = M.strength ? root(e.c * e.c + quot(T(4.0 / 3.0) * Gam, rho)) : e.c;
     T gx[3];
     ext_field_t<T>(P, s.x[i], s.y[i], s.z[i], gx, nullptr);
     Packed<T>::posh(w)[i] = V::make(pp.x, pp.y, pp.z, H);
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
     rec[0] = V::make(to_t<T>(w.vp[0][i]), to_t<T>(w.vp[1][i]), to_t<T>(w.vp[2][i]), m);
     rec[1] =
         V::make((S[0] - e.P) * inv, (S[1] - e.P) * inv, (-S[0] - S[1] - e.P) * inv, S[2] * inv);
-    rec[2] = V::make(S[3] * inv, S[4] * inv, m / (om * rho), e.c);
+    rec[2] = V::make(S[3] * inv, S[4] * inv, quot(m, om * rho), e.c);
     rec[3] = V::make(rho, ih, K, H);
     Packed<T>::fs(w, 0)[i] = V::make(S[0], S[1], S[2], S[3]);
     Packed<T>::fs(w, 1)[i] = V::make(S[4], Gam, cl, T(0));

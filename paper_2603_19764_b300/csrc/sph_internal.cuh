@@ -423,6 +423,23 @@ __host__ __device__ inline unsigned morton3(unsigned x, unsigned y, unsigned z) 
   return part1by2(x) | (part1by2(y) << 1) | (part1by2(z) << 2);
 }
 
+// Square root of x >= 0 and a quotient: correctly rounded in FP64; in FP32
+// through the hardware reciprocal square root and the fast divide (a few
+// ulp; root gives 0 for x <= 0 or NaN), which the FP32 form's tolerances
+// absorb. The FP32 form's pair loops and per-particle material model use
+// them; a correctly rounded FP32 divide or root costs a refinement sequence,
+// a check and a branch to a slow path.
+template <typename T> __device__ __forceinline__ T root(T x);
+template <> __device__ __forceinline__ float root<float>(float x) {
+  return x > 0.f ? x * rsqrtf(x) : 0.f;
+}
+template <> __device__ __forceinline__ double root<double>(double x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T quot(T a, T b);
+template <> __device__ __forceinline__ float quot<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
+
 // -------------------------------------------------------- material model
 // Equation of state, evaluated in T (FP64 form: double; FP32 form: float).
 // Linear: P = c0^2 (rho - rho0), c = c0. Tillotson (Tillotson 1962; regions
@@ -438,12 +455,12 @@ template <typename T> struct EosT {
 template <typename T>
 __device__ inline void till_dense_t(const MatT<T> &M, T eta, T mu, T rho, T u, T &P, T &Pr, T &Pu) {
   const T e0e2 = M.E0 * eta * eta;
-  const T w = u / e0e2 + T(1);
-  const T bw = M.b / w, bw2 = bw / w;           // b / w, b / w^2
+  const T w = quot(u, e0e2) + T(1);
+  const T bw = quot(M.b, w), bw2 = quot(bw, w);   // b / w, b / w^2
   P = (M.a + bw) * rho * u + mu * (M.A + M.B * mu);
   // dw/drho = -2 (w - 1) / rho, dw/du = 1 / (E0 eta^2)
   Pr = (M.a + bw) * u + bw2 * u * T(2) * (w - T(1)) + (M.A + T(2) * M.B * mu) * M.inv_rho0;
-  Pu = (M.a + bw) * rho - bw2 * rho * u / e0e2;
+  Pu = (M.a + bw) * rho - quot(bw2 * rho * u, e0e2);
 }
 
 template <typename T>
@@ -451,15 +468,15 @@ __device__ inline void till_vapour_t(const MatT<T> &M, T eta, T mu, T rho, T u, 
                                      T &Pu) {
   const T A = M.A, a = M.a, b = M.b, al = M.alpha, be = M.beta;
   const T e0e2 = M.E0 * eta * eta;
-  const T w = u / e0e2 + T(1);
-  const T z = -mu / eta;                       // rho0 / rho - 1
-  const T zr = T(-1) / (eta * rho);            // dz / drho
+  const T w = quot(u, e0e2) + T(1);
+  const T z = quot(-mu, eta);                  // rho0 / rho - 1
+  const T zr = quot(T(-1), eta * rho);         // dz / drho
   const T eb = exp(-be * z), ea = exp(-al * z * z);
-  const T brw = b * rho * u / w;
+  const T brw = quot(b * rho * u, w);
   const T q = brw + A * mu * eb;
-  const T qr = b * u / w + brw / w * T(2) * (w - T(1)) / rho + A * M.inv_rho0 * eb -
-               A * mu * eb * be * zr;
-  const T qu = b * rho / w - brw / w / e0e2;
+  const T qr = quot(b * u, w) + quot(quot(brw, w) * T(2) * (w - T(1)), rho) +
+               A * M.inv_rho0 * eb - A * mu * eb * be * zr;
+  const T qu = quot(b * rho, w) - quot(quot(brw, w), e0e2);
   P = a * rho * u + q * ea;
   Pr = a * u + (qr - q * T(2) * al * z * zr) * ea;
   Pu = a * rho + qu * ea;
@@ -502,10 +519,10 @@ __device__ inline EosT<T> eos_t(const MatT<T> &M, double rhod, double ud) {
     Pr = wv * Pr2 + wd * Pr1;
     Pu = wv * Pu2 + wd * Pu1 + (P2 - P1) * M.inv_dE;
   }
-  T c2 = Pr + P * Pu / (rho * rho);
+  T c2 = Pr + quot(P * Pu, rho * rho);
   if (!(c2 >= M.floor2)) c2 = M.floor2;
   o.P = tmax_(P, M.p_min);
-  o.c = sqrt(c2);
+  o.c = root(c2);
   return o;
 }
 
@@ -517,12 +534,12 @@ template <typename T> __device__ __forceinline__ T shear_mod_t(const MatT<T> &M,
 // Yield strength (Eq. 34-37) with the pressure clipped at zero.
 template <typename T> __device__ inline T yield_t(const MatT<T> &M, T P, T u) {
   const T p = tmax_(P, T(0));
-  const T yi = M.Y0 + M.mu_i * p / (T(1) + M.mu_i * p / (M.Ym - M.Y0));
+  const T yi = M.Y0 + quot(M.mu_i * p, T(1) + quot(M.mu_i * p, M.Ym - M.Y0));
   T y = tmin_(yi, M.mu_d * p);
   if (M.thermal_softening) {
     const T Tk = M.T0 + u * M.inv_cv;
     if (!(Tk > T(0))) return T(0);
-    y *= tmax_(tanh(M.xi * (M.Tm / Tk - T(1))), T(0));
+    y *= tmax_(tanh(M.xi * (quot(M.Tm, Tk) - T(1))), T(0));
   }
   return y;
 }
@@ -533,7 +550,7 @@ template <typename T> __device__ inline T radial_factor_t(const T S[5], T Y, int
   const T j2 = T(0.5) * (S[0] * S[0] + S[1] * S[1] + zz * zz) + S[2] * S[2] + S[3] * S[3] +
                S[4] * S[4];
   if (!(j2 > T(0))) return T(1);
-  const T f = Y / sqrt(norm ? T(3) * j2 : j2);
+  const T f = quot(Y, root(norm ? T(3) * j2 : j2));
   return f < T(1) ? f : T(1);
 }
 
@@ -570,32 +587,32 @@ __device__ inline void ext_field_t(const KParams &P, double x, double y, double 
   const FieldT<T> F = field_t(P, T(0));
   const T dx = to_t<T>(x - P.g_center[0]), dy = to_t<T>(y - P.g_center[1]),
           dz = to_t<T>(z - P.g_center[2]);
-  const T r = sqrt(dx * dx + dy * dy + dz * dz);
+  const T r = root(dx * dx + dy * dy + dz * dz);
   if (!(r > T(0))) return;
   const T rmin = F.rmin, rmax = F.rmax;
   T gm, ph;
   if (r >= rmax) {
-    gm = F.gm / (r * r);
-    ph = -F.gm / r;
+    gm = quot(F.gm, r * r);
+    ph = quot(-F.gm, r);
   } else if (r <= rmin) {
     const T g0 = F.g[0];
-    gm = g0 * r / rmin;
-    ph = F.phi[0] + T(0.5) * g0 / rmin * (r * r - rmin * rmin);
+    gm = quot(g0 * r, rmin);
+    ph = F.phi[0] + quot(T(0.5) * g0, rmin) * (r * r - rmin * rmin);
   } else {
-    int k = (int)floorf(log2f((float)(r / rmin)) * (float)F.inv_log_ratio);
+    int k = (int)floorf(log2f((float)quot(r, rmin)) * (float)F.inv_log_ratio);
     k = max(0, min(k, P.g_n - 2));
     if (r < F.r[k] && k > 0) --k;
     else if (r >= F.r[k + 1] && k < P.g_n - 2) ++k;
     const T r0 = F.r[k], r1 = F.r[k + 1];
-    const T w = (r - r0) / (r1 - r0);
+    const T w = quot(r - r0, r1 - r0);
     const T ga = F.g[k], gb = F.g[k + 1];
     gm = ga + w * (gb - ga);
     const T pa = F.phi[k], pb = F.phi[k + 1];
     ph = pa + w * (pb - pa);
   }
-  g[0] = -gm * dx / r;
-  g[1] = -gm * dy / r;
-  g[2] = -gm * dz / r;
+  g[0] = quot(-gm * dx, r);
+  g[1] = quot(-gm * dy, r);
+  g[2] = quot(-gm * dz, r);
   if (phi) *phi = ph;
 }
 

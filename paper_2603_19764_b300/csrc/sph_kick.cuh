@@ -124,9 +124,9 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
   if (!fixed) {
     const T H = to_t<T>(s.h[i]);
     const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
-    const T am = sqrt(ax * ax + ay * ay + az * az);
-    const T ta = am > T(0) ? eta_a * sqrt(H / am) : T(INFINITY);   // Eq. 38, eps = H
-    const T tc = eta_c * H / to_t<T>(d.vsig);                       // Eq. 39
+    const T am = root(ax * ax + ay * ay + az * az);
+    const T ta = am > T(0) ? eta_a * root(quot(H, am)) : T(INFINITY);   // Eq. 38, eps = H
+    const T tc = quot(eta_c * H, to_t<T>(d.vsig));                      // Eq. 39
     tc_ = tmin_(ta, tc);
   }
   *tcr = from_t(tc_);

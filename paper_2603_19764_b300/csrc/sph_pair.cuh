@@ -97,20 +97,6 @@ template <typename T> __device__ __forceinline__ T rel_coord(T c, int k, T L) {
 __device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
 
-// Square root of x >= 0 and a quotient: correctly rounded in FP64; in FP32
-// through the hardware reciprocal square root and the fast divide (a few
-// ulp), which the FP32 form's tolerances absorb.
-template <typename T> __device__ __forceinline__ T root(T x);
-template <> __device__ __forceinline__ float root<float>(float x) {
-  return x > 0.f ? x * rsqrtf(x) : 0.f;
-}
-template <> __device__ __forceinline__ double root<double>(double x) { return sqrt(x); }
-template <typename T> __device__ __forceinline__ T quot(T a, T b);
-template <> __device__ __forceinline__ float quot<float>(float a, float b) {
-  return __fdividef(a, b);
-}
-template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a / b; }
-
 // Canonical FP64 squared distance (no contraction): the neighbour predicate
 // r < H of every count compares this against H * H.
 __device__ __forceinline__ double r2_canon(double dx, double dy, double dz) {
