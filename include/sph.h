@@ -455,10 +455,11 @@ sph_status sph_prime(sph_ctx *c, sph_step_info *info);
 
 /* Phase timing with CUDA events recorded on the context's stream around the
  * phases of every sph_step: 0 neighbours (drift, keys, sort, permutation,
- * cells), 1 prediction and packing, 2 density solve, 3 EOS, yield and
- * packing, 4 pair loop with finalize (in global steps also the kicks,
- * applied per particle in its epilogue), 5 kicks and reductions (in global
- * steps the reductions only).
+ * cells), 1 position packing, 2 density solve, 3 prediction (Eq. 40), EOS,
+ * yield, radial return and packing, 4 pair loop with finalize (in the
+ * global steps of sph_step_host also the kicks, applied per particle in its
+ * epilogue), 5 kicks and reductions (the reductions only where the pair
+ * loop kicked).
  * sph_set_timing(c, 1) enables it and zeroes the accumulators. Steps
  * replayed from a graph (sph_set_graph) are not phase-timed;
  * sph_phase_times copies up to n accumulated milliseconds per phase into

@@ -137,9 +137,7 @@ __global__ void k_validate(sph_state s, int64_t n, int nmat, int check_id, KPara
 
 void free_all(sph_ctx *c) {
   void *dev[] = {c->d_mats, c->d_matf, c->d_matd, c->d_gtab, c->d_phitab, c->d_radii,
-                 c->d_gtab_f, c->w.vp[0], c->w.vp[1],
-                 c->w.vp[2], c->w.up, c->w.sp[0], c->w.sp[1], c->w.sp[2], c->w.sp[3],
-                 c->w.sp[4], c->w.vsig, c->w.edot2, c->w.yld, c->w.cc, c->w.pos32, c->w.pos64,
+                 c->d_gtab_f, c->w.vsig, c->w.edot2, c->w.yld, c->w.cc, c->w.pos32, c->w.pos64,
                  c->w.fj32, c->w.fj64, c->w.posh32, c->w.posh64,
                  c->w.fs32[0], c->w.fs32[1], c->w.fs32[2], c->w.fs64[0], c->w.fs64[1],
                  c->w.fs64[2], c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->scan_tot,
@@ -365,8 +363,8 @@ cudaError_t tmark(sph_ctx *c, int k) {
 sph_status run_derivatives(sph_ctx *c, int predict) {
   const TraceRange tr("sph derivatives");
   // split copy-in: the density solve needs only the positions; the
-  // predictor waits for the rest of the state
-  CK(launch_predict_pack(c, predict, c->split_in ? 2 : 3));
+  // predictor (in the EOS pass) waits for the rest of the state
+  CK(launch_pack(c));
   CK(mark(c, 2));
   CK(tmark(c, 0));
   CK(launch_density(c, 1));   // the force pass that follows counts the neighbours
@@ -377,9 +375,8 @@ sph_status run_derivatives(sph_ctx *c, int predict) {
   if (c->split_in) {
     CK(cudaStreamWaitEvent(c->stream, c->in_ev, 0));
     CK(launch_permute_rest(c));
-    CK(launch_predict_pack(c, predict, 1));
   }
-  CK(launch_eos_pack(c));
+  CK(launch_eos_pack(c, predict));
   CK(mark(c, 4));
   s = copy_out(c, 2);
   if (s != SPH_OK) return s;
@@ -863,9 +860,6 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   c->params.phi_table = c->d_phitab;
 
   Work &w = c->w;
-  for (int k = 0; k < 3; ++k) CKI(dalloc(&w.vp[k], n));
-  CKI(dalloc(&w.up, n));
-  for (int k = 0; k < 5; ++k) CKI(dalloc(&w.sp[k], n));
   CKI(dalloc(&w.vsig, n));
   CKI(dalloc(&w.edot2, n));
   CKI(dalloc(&w.yld, n));
@@ -1075,7 +1069,7 @@ sph_status sph_neighbours(sph_ctx *c) {
 
 sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
   ENTER(c);
-  CK(launch_predict_pack(c, 0, 3));
+  CK(launch_pack(c));
   CK(launch_density(c, 0));   // standalone: every solve ends on an evaluation
   sph_step_info info;
   const sph_status s = sync_status(c, &info);
@@ -1085,8 +1079,8 @@ sph_status sph_density(sph_ctx *c, int32_t *sweeps) {
 
 sph_status sph_forces_strength(sph_ctx *c) {
   ENTER(c);
-  CK(launch_predict_pack(c, 0, 3));
-  CK(launch_eos_pack(c));
+  CK(launch_pack(c));
+  CK(launch_eos_pack(c, 0));
   CK(launch_forces(c));
   return SPH_OK;
 }

@@ -1,5 +1,5 @@
-// sph_density.cu -- prediction, position packing, and the density /
-// smoothing-length solve (§2.1, Eq. 1-3).
+// sph_density.cu -- position packing and the density / smoothing-length
+// solve (§2.1, Eq. 1-3).
 //
 // One warp owns a bucket of 32 consecutive (cell-sorted) particles, one
 // particle per lane, processed group by group (sph_pair.cuh). A group stages
@@ -21,35 +21,18 @@
 
 namespace sphk {
 
-// Evaluation state and position packing. predict = 1: v, u, S at i from
-// the half-step values and the derivatives at i-1 (Eq. 40); predict = 0:
-// the state as it stands. parts: bit 0 the evaluation state, bit 1 the
-// packed positions (both in one pass, except where sph_step_host's split
-// copy-in packs the positions before the rest of the state has arrived).
-__global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, int64_t n, KParams P,
-                                                        int predict, int fp32, int parts) {
+// Position packing for the pair kernels: in the FP32 form each particle's
+// position relative to the origin of its cell, with its mass; in the FP64
+// form the absolute position. (The evaluation state that the predictor
+// forms from the half-step values is made where it is read, in k_eos_pack.)
+__global__ void __launch_bounds__(kBlock) k_pack(sph_state s, Work w, int64_t n, KParams P,
+                                                int fp32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
-    const Grid &g = P.sys[sy].grid;
-    if (parts & 1) {
-      const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
-      // offset from the half step: dt / 2, or with rungs the time from the
-      // midpoint of the particle's own step to the end of this substep
-      const double k = (fixed || !predict) ? 0.0 : predict_offset(P, i, P.dt[sy] * P.sub_scale);
-      w.vp[0][i] = s.vx[i] + k * s.ax[i];
-      w.vp[1][i] = s.vy[i] + k * s.ay[i];
-      w.vp[2][i] = s.vz[i] + k * s.az[i];
-      w.up[i] = s.u[i] + k * s.dudt[i];
-      w.sp[0][i] = s.sxx[i] + k * s.dsxx[i];
-      w.sp[1][i] = s.syy[i] + k * s.dsyy[i];
-      w.sp[2][i] = s.sxy[i] + k * s.dsxy[i];
-      w.sp[3][i] = s.sxz[i] + k * s.dsxz[i];
-      w.sp[4][i] = s.syz[i] + k * s.dsyz[i];
-    }
-    if (!(parts & 2)) continue;
     const double x = s.x[i], y = s.y[i], z = s.z[i], m = s.m[i];
     if (fp32) {
+      const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
+      const Grid &g = P.sys[sy].grid;
       const int c = w.cc[i];
       // the cell index as a double through FP32 (exact below 2^24), so
       // that no conversion runs on the FP64 unit
@@ -63,13 +46,11 @@ __global__ void __launch_bounds__(kBlock) k_predict_pack(sph_state s, Work w, in
   }
 }
 
-cudaError_t launch_predict_pack(sph_ctx *c, int predict, int parts) {
+cudaError_t launch_pack(sph_ctx *c) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
-  // reads through the step's read view (the permuted copies of v, u, S
-  // and the derivatives when they were not copied back)
-  k_predict_pack<<<(int)b, kBlock, 0, c->stream>>>(c->src, c->w, c->n, c->kp, predict,
-                                                  c->kp.precision == SPH_FP32K, parts);
+  k_pack<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp,
+                                          c->kp.precision == SPH_FP32K);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -46,26 +46,44 @@ template <> struct Packed<double> {
   static __device__ __forceinline__ double4_32a *fs(const Work &w, int k) { return w.fs64[k]; }
 };
 
-// Per particle: EOS at (rho, u_eval), yield, radial return of the
-// evaluation stress, and the packed neighbour / own data of the pair loop:
+// Per particle: the evaluation state (predict = 1: v, u, S at i from the
+// half-step values of the read view src and the derivatives at i-1, Eq. 40;
+// predict = 0: the state as it stands), EOS at (rho, u_eval), yield, radial
+// return of the evaluation stress, and the packed neighbour / own data of
+// the pair loop:
 //   posh = (x, y, z, H), and the neighbour record of 4 consecutive vectors
 //   rec0 = (v, m)   rec1 = m/(Omega rho^2) (sxx, syy, szz, sxy), s = -P I + S
 //   rec2 = (m sxz', m syz', m/(Omega rho), c)   rec3 = (rho, 1/H, cG/H^5, H)
 //   fs0 = (Sxx, Syy, Sxy, Sxz)   fs1 = (Syz, Gamma, c_L, 0)   fs2 = (g, 0)
+// This kernel's own conversions use the conversion instructions: it is not
+// bound by the FP64 unit that runs them (the integer-pipe forms of to_t and
+// from_t serve the kernels that are), and they need no branch.
+template <typename T> __device__ __forceinline__ T cvt_t(double d) { return (T)d; }
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_t n, KParams P) {
+__global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, sph_state src, Work w,
+                                                    int64_t n, KParams P, int predict) {
   using V = V4T<T>;
   const typename V::type *pos = Packed<T>::pos(w);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    // offset from the half step: dt / 2, or with rungs the time from the
+    // midpoint of the particle's own step to the end of this substep
+    const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
+    double k = 0.0;
+    if (predict && !fixed) {
+      const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
+      k = predict_offset(P, i, P.dt[sy] * P.sub_scale);
+    }
+    const double ud = src.u[i] + k * src.dudt[i];
     const MatT<T> &M = mat_t<T>(P, s.mat[i]);
-    const double rhod = s.rho[i], ud = w.up[i];
+    const double rhod = s.rho[i];
     const EosT<T> e = eos_t<T>(M, rhod, ud);
-    s.pres[i] = from_t(e.P);
-    s.cs[i] = from_t(e.c);
-    const T Y = yield_t<T>(M, e.P, to_t<T>(ud));
-    T S[5] = {to_t<T>(w.sp[0][i]), to_t<T>(w.sp[1][i]), to_t<T>(w.sp[2][i]), to_t<T>(w.sp[3][i]),
-              to_t<T>(w.sp[4][i])};
+    s.pres[i] = (double)e.P;
+    s.cs[i] = (double)e.c;
+    const T Y = yield_t<T>(M, e.P, cvt_t<T>(ud));
+    T S[5] = {cvt_t<T>(src.sxx[i] + k * src.dsxx[i]), cvt_t<T>(src.syy[i] + k * src.dsyy[i]),
+              cvt_t<T>(src.sxy[i] + k * src.dsxy[i]), cvt_t<T>(src.sxz[i] + k * src.dsxz[i]),
+              cvt_t<T>(src.syz[i] + k * src.dsyz[i])};
     if (!M.strength) {
       S[0] = S[1] = S[2] = S[3] = S[4] = T(0);
     } else {
@@ -74,8 +92,8 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
       for (int k = 0; k < 5; ++k) S[k] *= f;
     }
     const typename V::type pp = pos[i];
-    const T rho = to_t<T>(rhod), om = to_t<T>(s.omega[i]), m = to_t<T>(s.m[i]),
-            H = to_t<T>(s.h[i]);
+    const T rho = cvt_t<T>(rhod), om = cvt_t<T>(s.omega[i]), m = cvt_t<T>(s.m[i]),
+            H = cvt_t<T>(s.h[i]);
     const T inv = quot(m, om * rho * rho);
     const T ih = quot(T(1), H);
     const T ih2 = ih * ih;
@@ -86,7 +104,8 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
     ext_field_t<T>(P, s.x[i], s.y[i], s.z[i], gx, nullptr);
     Packed<T>::posh(w)[i] = V::make(pp.x, pp.y, pp.z, H);
     typename V::type *rec = Packed<T>::rec(w) + 4 * i;
-    rec[0] = V::make(to_t<T>(w.vp[0][i]), to_t<T>(w.vp[1][i]), to_t<T>(w.vp[2][i]), m);
+    rec[0] = V::make(cvt_t<T>(src.vx[i] + k * src.ax[i]), cvt_t<T>(src.vy[i] + k * src.ay[i]),
+                     cvt_t<T>(src.vz[i] + k * src.az[i]), m);
     rec[1] =
         V::make((S[0] - e.P) * inv, (S[1] - e.P) * inv, (-S[0] - S[1] - e.P) * inv, S[2] * inv);
     rec[2] = V::make(S[3] * inv, S[4] * inv, quot(m, om * rho), e.c);
@@ -97,13 +116,17 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, Work w, int64_
   }
 }
 
-cudaError_t launch_eos_pack(sph_ctx *c) {
+cudaError_t launch_eos_pack(sph_ctx *c, int predict) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
+  // v, u, S and the derivatives at i-1 through the step's read view (the
+  // permuted copies when they were not copied back)
   if (c->kp.precision == SPH_FP32K)
-    k_eos_pack<float><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+    k_eos_pack<float><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->src, c->w, c->n, c->kp,
+                                                        predict);
   else
-    k_eos_pack<double><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+    k_eos_pack<double><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->src, c->w, c->n, c->kp,
+                                                         predict);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -318,7 +318,6 @@ __device__ __forceinline__ double from_t(double v) { return v; }
 
 // Library-owned per-particle work arrays (sorted order).
 struct Work {
-  double *vp[3], *up, *sp[5];   // evaluation (predicted) state
   double *vsig, *edot2, *yld;   // CFL signal, 1/2 edot:edot, yield strength
   int *cc;                      // packed cell coordinates x | y << 10 | z << 20
   float4 *pos32;                // cell-relative x, y, z and m (FP32 form)
@@ -747,9 +746,9 @@ cudaError_t launch_grid_setup(sph_ctx *c);
 cudaError_t launch_sort_permute(sph_ctx *c, int all, int part);
 cudaError_t launch_permute_rest(sph_ctx *c);
 // parts: bit 0 the evaluation (predicted) state, bit 1 the packed positions
-cudaError_t launch_predict_pack(sph_ctx *c, int predict, int parts);
+cudaError_t launch_pack(sph_ctx *c);
 cudaError_t launch_density(sph_ctx *c, int expand);
-cudaError_t launch_eos_pack(sph_ctx *c);
+cudaError_t launch_eos_pack(sph_ctx *c, int predict);
 cudaError_t launch_forces(sph_ctx *c);
 cudaError_t launch_forces_range(sph_ctx *c, int b0, int b1, unsigned *ctr, cudaStream_t stream);
 cudaError_t launch_kick(sph_ctx *c, int kick);

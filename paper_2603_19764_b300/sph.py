@@ -126,7 +126,7 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_set_copy_chunks")
 MLP_NPARAM, MLP_NNORM = 4673, 14
 GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
-PHASES = ("neighbours", "predict_pack", "density", "eos_pack", "forces", "kick")
+PHASES = ("neighbours", "pack", "density", "predict_eos", "forces", "kick")
 
 
 def lib():
