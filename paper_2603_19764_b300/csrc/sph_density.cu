@@ -197,7 +197,7 @@ __device__ __forceinline__ void density_walk(const LV &Lp, const int *Li,
       // range with weight t = 0 (exact zeros, the sums unchanged), which
       // costs less than the branch (the marks reach only 1.005 H)
       if (!REL && !in) continue;
-      const T qq = root(r2) * invH;
+      const T qq = root0(r2) * invH;
       const T t = in ? tmax(T(1) - qq, T(0)) : T(0);
       const T mW = qm * t * t * t;
       rs += mW * t * (T(1) + T(4) * qq);

@@ -53,7 +53,7 @@ template <> struct Packed<double> {
 // the pair loop:
 //   posh = (x, y, z, H), and the neighbour record of 4 consecutive vectors
 //   rec0 = (v, m)   rec1 = m/(Omega rho^2) (sxx, syy, szz, sxy), s = -P I + S
-//   rec2 = (m sxz', m syz', m/(Omega rho), c)   rec3 = (rho, 1/H, cG/H^5, H)
+//   rec2 = (m sxz', m syz', m/(Omega rho), c)   rec3 = (rho/2, 1/H, cG/H^5, H/2)
 //   fs0 = (Sxx, Syy, Sxy, Sxz)   fs1 = (Syz, Gamma, c_L, 0)   fs2 = (g, 0)
 // This kernel's own conversions use the conversion instructions: it is not
 // bound by the FP64 unit that runs them (the integer-pipe forms of to_t and
@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, sph_state src,
     rec[1] =
         V::make((S[0] - e.P) * inv, (S[1] - e.P) * inv, (-S[0] - S[1] - e.P) * inv, S[2] * inv);
     rec[2] = V::make(S[3] * inv, S[4] * inv, quot(m, om * rho), e.c);
-    rec[3] = V::make(rho, ih, K, H);
+    // halves (exact) for the pair means of Eq. 5-8: rho_i/2 + rho_j/2 is
+    // the rounded (rho_i + rho_j)/2 bit for bit
+    rec[3] = V::make(T(0.5) * rho, ih, K, T(0.5) * H);
     Packed<T>::fs(w, 0)[i] = V::make(S[0], S[1], S[2], S[3]);
     Packed<T>::fs(w, 1)[i] = V::make(S[4], Gam, cl, T(0));
     Packed<T>::fs(w, 2)[i] = V::make(gx[0], gx[1], gx[2], T(0));
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           iOr = a2.z * im * pconst<T>(A.p.grad_wi, A.p.grad_wi_f);
   const T Hi = p.w, Hi2 = p.w * p.w, invHi = a3.y, Ki = a3.z;
   const T gi = guard_band(Hi, Lt);   // r^2 band the FP32 sum cannot decide
-  const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi = a3.x;
+  const T vix = a0.x, viy = a0.y, viz = a0.z, ci = a2.w, rhoi_h = a3.x, Hi_h = T(0.5) * Hi;
   // neighbour count of particle i (r < H_i by the canonical predicate):
   // the density solve may close on an expanded sum and leave it to this pass
   int nngb = 0;
@@ -429,10 +431,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
           // FP64 form: branched, its divides being costly
           const bool av = vr < T(0) && inR;
           if (REL || av) {
-            const T hb = T(0.5) * (Hi + f3.w);
+            const T hb = Hi_h + f3.w;   // (H_i + H_j) / 2
             const T mu0 = quot(hb * vr, r2 + ep * hb * hb);
             const T mu = av ? mu0 : T(0);
-            const T Pi = quot((be * mu - al * T(0.5) * (ci + f2.w)) * mu, T(0.5) * (rhoi + f3.x));
+            const T Pi = quot((be * mu - al * T(0.5) * (ci + f2.w)) * mu, rhoi_h + f3.x);
             const T t = T(0.5) * mj * Pi * (Wi + Wj);
             ax -= t * dx;
             ay -= t * dy;

@@ -200,7 +200,7 @@ cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
 __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, KParams P) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double max_axis = (double)(1 << axis_bits);
-  int off = 0;
+  int off = 0, bits = 0;
   for (int k = 0; k < nsys; ++k) {
     SysRec &r = sys[k];
     double lo[3], hi[3];
@@ -247,7 +247,14 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, K
     g.ncells = d[0] * d[1] * d[2];
     g.cell_off = off;
     off += g.ncells;
+    for (int a = 0; a < 3; ++a)
+      if (d[a] > 1) bits = max(bits, 32 - __clz(d[a] - 1));
   }
+  // the sort keys hold the system index right above the Morton bits the
+  // grids use, so that a single system or a batch of small ones needs
+  // fewer radix passes (the order of the keys is the same)
+  st->key_shift = 3 * bits;
+  st->key_or = 0u;
   st->total_cells = off;
 }
 
@@ -270,10 +277,14 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double invL, int 
   return k >= dim ? dim - 1 : k;
 }
 
-// Key = system << 3 axis_bits | Morton code of the cell within the system;
-// values start as the identity.
+// Key = system << key_shift | Morton code of the cell within the system
+// (key_shift: three times the Morton bits per axis the grids need); values
+// start as the identity. The OR of all keys tells the sort which passes
+// it can leave out.
 __global__ void __launch_bounds__(kBlock) k_keys(sph_state s, int64_t n, KParams P, unsigned *keys,
-                                                int *vals) {
+                                                int *vals, Status *st) {
+  const int shift = st->key_shift;
+  unsigned o = 0u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, s.id[i]) : 0;
@@ -282,22 +293,30 @@ __global__ void __launch_bounds__(kBlock) k_keys(sph_state s, int64_t n, KParams
     const int cx = cell_coord(s.x[i], g.lo[0], invL, g.dims[0]);
     const int cy = cell_coord(s.y[i], g.lo[1], invL, g.dims[1]);
     const int cz = cell_coord(s.z[i], g.lo[2], invL, g.dims[2]);
-    keys[i] = ((unsigned)sy << (3 * P.axis_bits)) | morton3(cx, cy, cz);
+    const unsigned k = ((unsigned)sy << shift) | morton3(cx, cy, cz);
+    keys[i] = k;
     vals[i] = (int)i;
+    o |= k;
   }
+  o = __reduce_or_sync(kFull, o);
+  if ((threadIdx.x & 31) == 0 && o) atomicOr(&st->key_or, o);
 }
 
 // ------------------------------------------------------------ radix sort
-// Stable LSD radix sort of (key, value) pairs, 8-bit digits, four passes.
-// Per pass: tile histograms (digit-major), one exclusive scan, and a stable
-// scatter in which each key's rank inside its tile comes from warp match
-// masks plus per-warp digit counts.
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits, up to four
+// passes. Per pass: tile histograms (digit-major), one exclusive scan, and a
+// stable scatter in which each key's rank inside its tile comes from warp
+// match masks plus per-warp digit counts. The kernels of a pass whose digit
+// and every higher one are zero in all keys return at once (sort_passes);
+// the sorted pairs are then in the buffers of the last pass that ran.
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kTile = kSortThreads * kSortItems;
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned *keys, int n, int shift,
-                                                             unsigned *hist, int ntiles) {
+                                                             unsigned *hist, int ntiles,
+                                                             const Status *st) {
+  if ((st->key_or >> shift) == 0u) return;
   __shared__ unsigned h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -339,7 +358,9 @@ __device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned *sh) {
 }
 
 __global__ void __launch_bounds__(kScanSeg) k_scan_totals(const unsigned *hist, int m,
-                                                          unsigned *tot) {
+                                                          unsigned *tot, int shift,
+                                                          const Status *st) {
+  if ((st->key_or >> shift) == 0u) return;
   __shared__ unsigned sh[32];
   const int i = blockIdx.x * kScanSeg + threadIdx.x;
   unsigned v = i < m ? hist[i] : 0u;
@@ -348,7 +369,9 @@ __global__ void __launch_bounds__(kScanSeg) k_scan_totals(const unsigned *hist, 
 }
 
 // One block, chunks of kScanSeg totals with a running carry.
-__global__ void __launch_bounds__(kScanSeg) k_scan_of_totals(unsigned *tot, int nseg) {
+__global__ void __launch_bounds__(kScanSeg) k_scan_of_totals(unsigned *tot, int nseg, int shift,
+                                                             const Status *st) {
+  if ((st->key_or >> shift) == 0u) return;
   __shared__ unsigned sh[32];
   __shared__ unsigned carry;
   if (threadIdx.x == 0) carry = 0u;
@@ -366,7 +389,9 @@ __global__ void __launch_bounds__(kScanSeg) k_scan_of_totals(unsigned *tot, int 
 }
 
 __global__ void __launch_bounds__(kScanSeg) k_scan_apply(unsigned *hist, int m,
-                                                         const unsigned *tot) {
+                                                         const unsigned *tot, int shift,
+                                                         const Status *st) {
+  if ((st->key_or >> shift) == 0u) return;
   __shared__ unsigned sh[32];
   const int i = blockIdx.x * kScanSeg + threadIdx.x;
   const unsigned v = i < m ? hist[i] : 0u;
@@ -377,7 +402,9 @@ __global__ void __launch_bounds__(kScanSeg) k_scan_apply(unsigned *hist, int m,
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const unsigned *kin, const int *vin,
                                                                 unsigned *kout, int *vout, int n,
                                                                 int shift, const unsigned *hist,
-                                                                int ntiles, unsigned *err) {
+                                                                int ntiles, Status *st) {
+  if ((st->key_or >> shift) == 0u) return;
+  unsigned *const err = &st->err;
   constexpr int NW = kSortThreads / 32;
   __shared__ unsigned base[256];
   __shared__ unsigned wcnt[NW][256];
@@ -492,8 +519,12 @@ static PermTable perm_table(const sph_state &s, const Work &w, const LearnArgs &
   return t;
 }
 
-__global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm, int64_t n,
-                                                  unsigned long long *tmp, unsigned *err) {
+__global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm0,
+                                                  const int *perm1, int64_t n,
+                                                  unsigned long long *tmp, Status *st) {
+  // the sort's permutation: in perm1 after an odd number of passes
+  const int *perm = (sort_passes(st->key_or) & 1) ? perm1 : perm0;
+  unsigned *const err = &st->err;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = checked(perm[i], n, err);
@@ -522,10 +553,13 @@ __global__ void __launch_bounds__(kBlock) k_clear_cells(int *start, const Status
     start[i] = -1;
 }
 
-__global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys, int64_t n, KParams P,
-                                                 int *start, int *end, int *cc, int max_cells,
-                                                 unsigned *err) {
-  const int sh = 3 * P.axis_bits;
+__global__ void __launch_bounds__(kBlock) k_cells(const unsigned *keys0, const unsigned *keys1,
+                                                 int64_t n, KParams P, int *start, int *end,
+                                                 int *cc, int max_cells, Status *st) {
+  // the sorted keys: in keys1 after an odd number of passes
+  const unsigned *keys = (sort_passes(st->key_or) & 1) ? keys1 : keys0;
+  unsigned *const err = &st->err;
+  const int sh = st->key_shift;
   const unsigned mask = sh >= 32 ? ~0u : ((1u << sh) - 1u);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -556,7 +590,7 @@ static void enqueue_permute(sph_ctx *c, const PermTable &t, int64_t base) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
   unsigned long long *tmp = (unsigned long long *)c->tmp + base * n;
-  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, n, tmp, &c->d_status->err);
+  k_gather<<<gb, kBlock, 0, c->stream>>>(t, c->vals, c->vals_alt, n, tmp, c->d_status);
   k_scatter_back<<<gb, kBlock, 0, c->stream>>>(t, n, tmp);
   c->nlaunch += 2;
   for (int f = t.nback; f < t.nf64; ++f) {
@@ -589,19 +623,20 @@ cudaError_t launch_permute_rest(sph_ctx *c) {
 cudaError_t launch_sort_permute(sph_ctx *c, int all, int part) {
   const int64_t n = c->n;
   const int gb = grid_for(n, kBlock);
-  k_keys<<<gb, kBlock, 0, c->stream>>>(c->st, n, c->kp, c->keys, c->vals);
+  Status *const st = c->d_status;
+  k_keys<<<gb, kBlock, 0, c->stream>>>(c->st, n, c->kp, c->keys, c->vals, st);
   unsigned *ka = c->keys, *kb = c->keys_alt;
   int *va = c->vals, *vb = c->vals_alt;
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 8 * pass;
-    k_radix_hist<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, (int)n, shift, c->hist, c->ntiles);
+    k_radix_hist<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, (int)n, shift, c->hist, c->ntiles,
+                                                            st);
     const int m = 256 * c->ntiles, nseg = (m + kScanSeg - 1) / kScanSeg;
-    k_scan_totals<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot);
-    k_scan_of_totals<<<1, kScanSeg, 0, c->stream>>>(c->scan_tot, nseg);
-    k_scan_apply<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot);
+    k_scan_totals<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot, shift, st);
+    k_scan_of_totals<<<1, kScanSeg, 0, c->stream>>>(c->scan_tot, nseg, shift, st);
+    k_scan_apply<<<nseg, kScanSeg, 0, c->stream>>>(c->hist, m, c->scan_tot, shift, st);
     k_radix_scatter<<<c->ntiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, (int)n, shift,
-                                                               c->hist, c->ntiles,
-                                                               &c->d_status->err);
+                                                               c->hist, c->ntiles, st);
     unsigned *tk = ka;
     ka = kb;
     kb = tk;
@@ -609,15 +644,17 @@ cudaError_t launch_sort_permute(sph_ctx *c, int all, int part) {
     va = vb;
     vb = tv;
   }
-  // after four passes the sorted pairs are back in keys / vals
+  // the sorted pairs are in keys / vals after an even number of passes that
+  // ran, in keys_alt / vals_alt after an odd one (the kernels that read
+  // them choose on the device)
   c->src = c->st;
   enqueue_permute(c, perm_table(c->st, c->w, c->learn, all != 0, c->kp.max_rung > 0, part,
                                 c->lazy != 0 && all == 0),
                   0);
   k_clear_cells<<<grid_for(c->max_cells, kBlock), kBlock, 0, c->stream>>>(c->cell_start,
                                                                           c->d_status);
-  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, n, c->kp, c->cell_start, c->cell_end, c->w.cc,
-                                        c->max_cells, &c->d_status->err);
+  k_cells<<<gb, kBlock, 0, c->stream>>>(c->keys, c->keys_alt, n, c->kp, c->cell_start,
+                                        c->cell_end, c->w.cc, c->max_cells, st);
   c->nlaunch += 1 + 4 * 5 + 2;   // keys, four radix passes, cells (permutation counted above)
   return cudaGetLastError();
 }
