@@ -59,8 +59,10 @@ template <> struct Packed<double> {
 // bound by the FP64 unit that runs them (the integer-pipe forms of to_t and
 // from_t serve the kernels that are), and they need no branch.
 template <typename T> __device__ __forceinline__ T cvt_t(double d) { return (T)d; }
+// Six blocks per SM (40 registers): latency-bound, so more resident warps
+// help (3 % over five blocks at 48 registers; eight spill).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_eos_pack(sph_state s, sph_state src, Work w,
+__global__ void __launch_bounds__(kBlock, 6) k_eos_pack(sph_state s, sph_state src, Work w,
                                                     int64_t n, KParams P, int predict) {
   using V = V4T<T>;
   const typename V::type *pos = Packed<T>::pos(w);

@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(PermTable t, const int *perm0
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = checked(perm[i], n, err);
-#pragma unroll 4
+#pragma unroll 8
     for (int f = 0; f < t.nf64; ++f) tmp[f * n + i] = t.f64[f][j];
     unsigned *t32 = (unsigned *)(tmp + t.nf64 * n);
     for (int f = 0; f < t.ni32; ++f) t32[f * n + i] = t.i32[f][j];
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter_back(PermTable t, int64_t n,
                                                         const unsigned long long *tmp) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll 4
+#pragma unroll 8
     for (int f = 0; f < t.nback; ++f) t.f64[f][i] = tmp[f * n + i];
     const unsigned *t32 = (const unsigned *)(tmp + t.nf64 * n);
     for (int f = 0; f < t.ni32; ++f) t.i32[f][i] = t32[f * n + i];

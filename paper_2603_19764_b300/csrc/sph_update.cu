@@ -67,10 +67,12 @@ __device__ __forceinline__ int tile_range(const KParams &P, int t, int64_t &p0, 
 // src: where v, u, S and the strain invariant are read (the step's read
 // view: their permuted copies when the permutation did not copy them
 // back); s: where they are written, for every particle then.
-// Three blocks per SM (80 registers, a few spilled): the kernel is bound by
-// its FP64 unit, and 24 resident warps keep it busier than 16 (7 % faster).
+// Four blocks per SM (64 registers, some spilled): the kernel is bound by
+// its FP64 unit, and 32 resident warps keep it busier than 16 (two blocks at
+// 99 registers: 15 % slower) or 24 (three: 8 % slower); five and six blocks
+// spill more than they gain.
 template <typename T>
-__global__ void __launch_bounds__(kReduceThreads, 3) k_kick(sph_state s, sph_state src, Work w,
+__global__ void __launch_bounds__(kReduceThreads, 4) k_kick(sph_state s, sph_state src, Work w,
                                                            int kick, KParams P,
                                                            double *tile_partials, Status *st) {
   const bool copy = src.vx != s.vx;   // lazy step: write every particle
