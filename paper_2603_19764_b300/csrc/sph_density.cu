@@ -76,7 +76,7 @@ struct DensArgs {
 constexpr int kSpill = 1024;
 
 // Staging: chunks of 32 stream positions located and loaded at once
-constexpr int kStageChunksD = 4;
+constexpr int kStageChunksD = 3;
 
 // FP32 form within a full step: a Newton step of at most kExpand H is
 // accepted without a new evaluation of the sums when the second-order

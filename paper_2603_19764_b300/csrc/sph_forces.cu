@@ -146,7 +146,7 @@ cudaError_t launch_eos_pack(sph_ctx *c, int predict) {
 // rounding error is a few ulp of the matrix norm.
 constexpr int kSumBlock = 8;
 // Staging: chunks of 32 stream positions located and loaded at once
-constexpr int kStageChunksF = 3;
+constexpr int kStageChunksF = 4;
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
