@@ -66,8 +66,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh",
                                 "sph_kick.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (185.0, "318b185c5207"),
-                        "k_density": (63.7, "4e2e217e0fa9")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (187.6, "33356ba966bf"),
+                        "k_density": (64.6, "cb2dfb5004d0")}
 
 
 def source_hash(kernel: str) -> str:
