@@ -10,7 +10,12 @@
 * the parameter variants: the stress rate as printed (Eq. 25-29), the
   sqrt(3 J2) yield normalisation, no thermal softening, the shear modulus
   of Eq. 30 (Gamma = 0.6 rho c^2);
-* a batch of many tiny systems (1 to 40 particles each, far apart).
+* a batch of many tiny systems (1 to 40 particles each, far apart);
+* a long thin rod whose cell grid is about 800 cells long, so that the
+  Morton sort keys need more than 24 bits and all four 8-bit radix passes
+  run (the other workloads need one to three; a pass whose digit and every
+  higher one are zero in all keys is left out, and the sorted order is then
+  read from the buffers of the last pass that ran).
 
 Tolerances as in the parity suite: counts bit-exact given the GPU's H;
 density 1e-6 (FP64) / 1e-5 (FP32) relative at the GPU's H, and against the
@@ -189,3 +194,26 @@ def test_batch_of_many_tiny_systems(precision):
         assert infos[k]["e_kin"] == pytest.approx(rinfo["e_kin"], rel=1e-9)
     # the counters are batch totals
     assert infos[0]["n_capped"] == capped
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rod_with_four_sort_passes(precision):
+    rng = wl.SplitMix64(71)
+    mat = wl.basalt_material()
+    nx, ny, nz, sp = 2000, 4, 4, 100.0
+    g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"),
+                 -1).reshape(-1, 3).astype(np.float64) * sp
+    n = g.shape[0]
+    g = g + rng.uniform(3 * n, -0.2 * sp, 0.2 * sp).reshape(n, 3)
+    a = wl._empty_arrays(n)
+    a["x"], a["y"], a["z"] = g[:, 0].copy(), g[:, 1].copy(), g[:, 2].copy()
+    a["m"][:] = mat["rho0"] * sp ** 3
+    a["h"][:] = wl.lattice_h(mat, a["m"])
+    v = rng.normal(3 * n, 10.0).reshape(n, 3)
+    a["vx"], a["vy"], a["vz"] = v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+    a["u"][:] = rng.uniform(n, 0.0, 2.0e6)
+    # the first sort's grid (cell edge: the largest H) needs 10 bits per axis
+    cells_x = int(np.floor((a["x"].max() - a["x"].min()) / a["h"].max())) + 1
+    assert 512 < cells_x <= 1024
+    _prime_check(a, [mat], wl.default_params(), precision)
+
