@@ -337,7 +337,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         sim.set_spans(*[int(v) for v in args.spans.split(",")])
     elif args.tune > 0:
         sim.autotune(args.tune)
-        for _ in range(3 * args.tune):
+        while sim.tune_info()["steps_left"] > 0:   # spans, then staging depths
             sim.step(0.0)
     if not args.no_graph:
         sim.set_graph(True)
@@ -506,7 +506,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         sim.set_graph(graph)
         if tune:
             sim.autotune(tune)
-            for _ in range(3 * tune):
+            while sim.tune_info()["steps_left"] > 0:   # spans, then staging depths
                 sim.step_batch(zeros)
         for _ in range(args.warmup):
             sim.step_batch(zeros)

@@ -207,16 +207,25 @@ typedef struct {
   int32_t rung_counts[16];
 } sph_step_info;
 
-/* Report of the group-span tuner (sph_autotune). The pair kernels give
- * each warp a bucket of 32 sorted particles; lanes whose cells lie within
- * `span` cells of one another share one staged candidate list. */
+/* Report of the tuner (sph_autotune). The pair kernels give each warp a
+ * bucket of 32 sorted particles; lanes whose cells lie within `span` cells
+ * of one another share one staged candidate list (the tile), which the
+ * warp stages `depth` chunks of 32 candidate positions at a time (located
+ * and loaded before the first is tested; the list itself does not depend
+ * on the depth). */
 typedef struct {
   int32_t span_density, span_forces;   /* spans in use */
-  int32_t steps_left;                  /* tuning steps still to run */
-  int32_t n_cand;                      /* candidates (SPH_TUNE_MAX at most) */
+  int32_t steps_left;                  /* tuning steps still to run (both phases) */
+  int32_t n_cand;                      /* span candidates (4 at most) */
   int32_t cand[4];                     /* candidate spans */
-  int32_t timed[4];                    /* steps timed per candidate */
+  int32_t timed[4];                    /* steps timed per span candidate */
   double ms_density[4], ms_forces[4];  /* summed kernel milliseconds */
+  int32_t depth_density, depth_forces; /* staging depths in use */
+  int32_t n_depth;                     /* depth candidates (2 at most; 1 in the FP64 form) */
+  int32_t depth_cand[2];               /* candidate depths */
+  int32_t depth_timed[2];              /* steps timed per depth candidate */
+  int32_t reserved_;
+  double ms_depth_density[2], ms_depth_forces[2];  /* summed kernel milliseconds */
 } sph_tune_report;
 
 /* Create a context for n particles in `st` on `cuda_stream` (a cudaStream_t,
@@ -290,21 +299,31 @@ sph_status sph_batch_info(const sph_ctx *c, sph_step_info *info, int32_t n);
  * sph_set_timing. on = 0 returns to direct launches. */
 sph_status sph_set_graph(sph_ctx *c, int32_t on);
 
-/* Tune the group span of the two pair kernels (the cell extent that shares
- * one staged candidate list; candidates 1, 2 and 3 cells) over the next
- * `rounds` x 3 calls of sph_step / sph_step_batch: each such step runs with
- * one candidate and times both kernels with CUDA events; after the last,
- * each kernel keeps its fastest span and any captured graph is dropped so
- * that the next step captures the tuned launch. Tuning steps are ordinary
- * steps: in the FP64 form their results are bit-identical whatever the
- * span; in the FP32 form the span moves the cell-relative frame, within the
- * form's tolerances. rounds = 0 stops tuning and keeps the current spans.
- * Returns SPH_E_ARG for rounds outside 0..64. */
+/* Tune the two pair kernels' tiles over the next calls of sph_step /
+ * sph_step_batch. First the group span (the cell extent that shares one
+ * staged candidate list; candidates 1, 2 and 3 cells) over `rounds` x 3
+ * steps; then, in the FP32 form, the staging depth (3 or 4 chunks of 32
+ * candidate positions in flight) at the chosen spans over `rounds` x 2
+ * steps. Each tuning step runs with one candidate and times both kernels
+ * with CUDA events; after the last step of a phase each kernel keeps its
+ * fastest candidate and any captured graph is dropped so that the next step
+ * captures the tuned launch (sph_tune_info's steps_left counts both phases).
+ * Tuning steps are ordinary steps: in the FP64 form their results are
+ * bit-identical whatever the span; in the FP32 form the span moves the
+ * cell-relative frame, within the form's tolerances, and the depth changes
+ * no bit. rounds = 0 stops tuning and keeps the current tiles. Returns
+ * SPH_E_ARG for rounds outside 0..64. */
 sph_status sph_autotune(sph_ctx *c, int32_t rounds);
 
 /* Set the group spans by hand (1..3 cells each; SPH_E_ARG otherwise) and
  * stop any tuning in progress. Drops a captured graph. */
 sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces);
+
+/* Set the staging depths of the FP32 form's pair kernels by hand (3 or 4
+ * each; SPH_E_ARG otherwise; the FP64 form runs 3 in the density solve and
+ * 4 in the force pass whatever is set) and stop any tuning in progress.
+ * Results do not depend on the depth. Drops a captured graph. */
+sph_status sph_set_stage_depths(sph_ctx *c, int32_t depth_density, int32_t depth_forces);
 
 /* The tuner's state and timings. */
 sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out);

@@ -479,40 +479,68 @@ void drop_graph(sph_ctx *c) {
   c->graph_exec = nullptr;
 }
 
-// Start of a step: while tuning, the candidate span this step runs with.
+// Start of a step: while tuning, the candidate this step runs with (phase
+// 0: a group span for both kernels; phase 1: a staging depth for both, at
+// the spans phase 0 chose).
 void tune_begin(sph_ctx *c) {
   c->tune_now = c->tune_left > 0;
-  if (c->tune_now) {
+  if (!c->tune_now) return;
+  if (c->tune_phase == 0) {
     const int span = kSpans[c->tune_idx % kNumSpans];
     c->kp.span_d = span;
     c->kp.span_f = span;
+  } else {
+    const int depth = kDepths[c->tune_idx % kNumDepths];
+    c->depth_d = depth;
+    c->depth_f = depth;
   }
 }
 
 // End of a synchronised tuning step: book its kernel times; after the last
-// one, keep each kernel's fastest span.
+// one of a phase, keep each kernel's fastest candidate. The FP32 form then
+// tunes the staging depth (the FP64 form has one compiled depth).
 sph_status tune_end(sph_ctx *c) {
   if (!c->tune_now) return SPH_OK;
   c->tune_now = 0;
   float md = 0.f, mf = 0.f;
   CK(cudaEventElapsedTime(&md, c->tev[0], c->tev[1]));
   CK(cudaEventElapsedTime(&mf, c->tev[2], c->tev[3]));
-  const int k = c->tune_idx % kNumSpans;
-  c->tune_ms_d[k] += md;
-  c->tune_ms_f[k] += mf;
-  c->tune_n[k] += 1;
+  if (c->tune_phase == 0) {
+    const int k = c->tune_idx % kNumSpans;
+    c->tune_ms_d[k] += md;
+    c->tune_ms_f[k] += mf;
+    c->tune_n[k] += 1;
+  } else {
+    const int k = c->tune_idx % kNumDepths;
+    c->tune_dms_d[k] += md;
+    c->tune_dms_f[k] += mf;
+    c->tune_dn[k] += 1;
+  }
   c->tune_idx += 1;
   c->tune_left -= 1;
-  if (c->tune_left == 0) {
-    int bd = 0, bf = 0;
+  if (c->tune_left > 0) return SPH_OK;
+  int bd = 0, bf = 0;
+  if (c->tune_phase == 0) {
     for (int q = 1; q < kNumSpans; ++q) {
       if (c->tune_ms_d[q] / c->tune_n[q] < c->tune_ms_d[bd] / c->tune_n[bd]) bd = q;
       if (c->tune_ms_f[q] / c->tune_n[q] < c->tune_ms_f[bf] / c->tune_n[bf]) bf = q;
     }
     c->kp.span_d = kSpans[bd];
     c->kp.span_f = kSpans[bf];
-    drop_graph(c);
+    if (c->kp.precision == SPH_FP32K) {
+      c->tune_phase = 1;
+      c->tune_idx = 0;
+      c->tune_left = c->tune_rounds * kNumDepths;
+    }
+  } else {
+    for (int q = 1; q < kNumDepths; ++q) {
+      if (c->tune_dms_d[q] / c->tune_dn[q] < c->tune_dms_d[bd] / c->tune_dn[bd]) bd = q;
+      if (c->tune_dms_f[q] / c->tune_dn[q] < c->tune_dms_f[bf] / c->tune_dn[bf]) bf = q;
+    }
+    c->depth_d = kDepths[bd];
+    c->depth_f = kDepths[bf];
   }
+  drop_graph(c);
   return SPH_OK;
 }
 
@@ -713,6 +741,8 @@ sph_status sph_init_batch(sph_ctx **out, const sph_params *p, const sph_material
   kp.nbuckets = (int)buckets;
   kp.span_d = 2;
   kp.span_f = 2;
+  c->depth_d = kDepthDensity;
+  c->depth_f = kDepthForces;
   cudaError_t es = dalloc(&c->d_sys, n_sys);
   if (es == cudaSuccess) es = cudaMemcpy(c->d_sys, rec, sizeof(SysRec) * n_sys, cudaMemcpyHostToDevice);
   if (es == cudaSuccess) es = dalloc(&c->d_sys_begin, n_sys + 1);
@@ -1018,10 +1048,16 @@ sph_status sph_autotune(sph_ctx *c, int32_t rounds) {
   if (rounds > 0 && !c->tev[0])
     for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&c->tev[k]));
   c->tune_left = rounds * kNumSpans;
+  c->tune_rounds = rounds;
+  c->tune_phase = 0;
   c->tune_idx = 0;
   for (int k = 0; k < kNumSpans; ++k) {
     c->tune_ms_d[k] = c->tune_ms_f[k] = 0.0;
     c->tune_n[k] = 0;
+  }
+  for (int k = 0; k < kNumDepths; ++k) {
+    c->tune_dms_d[k] = c->tune_dms_f[k] = 0.0;
+    c->tune_dn[k] = 0;
   }
   return SPH_OK;
 }
@@ -1046,18 +1082,46 @@ sph_status sph_set_spans(sph_ctx *c, int32_t span_density, int32_t span_forces) 
   return SPH_OK;
 }
 
+sph_status sph_set_stage_depths(sph_ctx *c, int32_t depth_density, int32_t depth_forces) {
+  ENTER(c);
+  bool okd = false, okf = false;
+  for (int k = 0; k < kNumDepths; ++k) {
+    okd = okd || depth_density == kDepths[k];
+    okf = okf || depth_forces == kDepths[k];
+  }
+  if (!okd || !okf) return fail(c, SPH_E_ARG, "staging depth must be 3 or 4");
+  c->tune_left = 0;
+  c->depth_d = depth_density;
+  c->depth_f = depth_forces;
+  drop_graph(c);
+  return SPH_OK;
+}
+
 sph_status sph_tune_info(const sph_ctx *c, sph_tune_report *out) {
   if (!c || !out) return SPH_E_ARG;
   memset(out, 0, sizeof(*out));
+  const bool fp32 = c->kp.precision == SPH_FP32K;
   out->span_density = c->kp.span_d;
   out->span_forces = c->kp.span_f;
-  out->steps_left = c->tune_left;
+  // the depth phase still to come after the spans (FP32 form)
+  out->steps_left = c->tune_left +
+                    (c->tune_left > 0 && c->tune_phase == 0 && fp32 ? c->tune_rounds * kNumDepths
+                                                                    : 0);
   out->n_cand = kNumSpans;
   for (int k = 0; k < kNumSpans; ++k) {
     out->cand[k] = kSpans[k];
     out->timed[k] = c->tune_n[k];
     out->ms_density[k] = c->tune_ms_d[k];
     out->ms_forces[k] = c->tune_ms_f[k];
+  }
+  out->depth_density = fp32 ? c->depth_d : kDepthDensity;
+  out->depth_forces = fp32 ? c->depth_f : kDepthForces;
+  out->n_depth = fp32 ? kNumDepths : 1;
+  for (int k = 0; k < out->n_depth; ++k) {
+    out->depth_cand[k] = fp32 ? kDepths[k] : kDepthDensity;
+    out->depth_timed[k] = fp32 ? c->tune_dn[k] : 0;
+    out->ms_depth_density[k] = fp32 ? c->tune_dms_d[k] : 0.0;
+    out->ms_depth_forces[k] = fp32 ? c->tune_dms_f[k] : 0.0;
   }
   return SPH_OK;
 }

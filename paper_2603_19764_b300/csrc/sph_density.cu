@@ -75,8 +75,6 @@ struct DensArgs {
 // Newton sweeps instead of being staged again for every sweep.
 constexpr int kSpill = 1024;
 
-// Staging: chunks of 32 stream positions located and loaded at once
-constexpr int kStageChunksD = 3;
 
 // FP32 form within a full step: a Newton step of at most kExpand H is
 // accepted without a new evaluation of the sums when the second-order
@@ -259,7 +257,9 @@ __device__ __noinline__ int recount_lists(ViewPlanes<S1> L1, const int *I1, unsi
                               sy, sz, blen, n_all, err);
 }
 
-template <typename T, int CAP, bool PER>
+// UD: staging depth, the chunks of 32 stream positions located and loaded
+// at once (kDepths; the lists do not depend on it)
+template <typename T, int CAP, bool PER, int UD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         Hm = T(0);
         complete = false;
         for (int seg = 0;; ++seg) {
-          nl = stage_list<kStageChunksD, true, T, REL>(
+          nl = stage_list<UD, true, T, REL>(
               sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, 0, TCAP, A.n,
               &A.st->err,
               [&](bool ok, int j) { return ok ? V::ld(pos, j) : V::make(0, 0, 0, 0); },
@@ -550,6 +550,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   }
 }
 
+template <typename T, int CAP, bool PER, int UD>
+void launch_density_t(sph_ctx *c, const DensArgs &a) {
+  k_density<T, CAP, PER, UD><<<resident_grid(c, k_density<T, CAP, PER, UD>),
+                               32 * kWarpsPerBlock, 0, c->stream>>>(a);
+}
+
 cudaError_t launch_density(sph_ctx *c, int expand) {
   DensArgs a;
   a.expand = expand;
@@ -566,19 +572,17 @@ cudaError_t launch_density(sph_ctx *c, int expand) {
   cudaError_t e = cudaMemsetAsync(&c->d_status->next_bucket[0], 0, sizeof(unsigned), c->stream);
   if (e != cudaSuccess) return e;
   if (c->kp.precision == SPH_FP32K) {
-    if (c->kp.periodic)
-      k_density<float, 576, true><<<resident_grid(c, k_density<float, 576, true>),
-                                    32 * kWarpsPerBlock, 0, c->stream>>>(a);
-    else
-      k_density<float, 576, false><<<resident_grid(c, k_density<float, 576, false>),
-                                     32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    const bool d4 = c->depth_d == 4;
+    if (c->kp.periodic) {
+      if (d4) launch_density_t<float, 576, true, 4>(c, a);
+      else launch_density_t<float, 576, true, 3>(c, a);
+    } else {
+      if (d4) launch_density_t<float, 576, false, 4>(c, a);
+      else launch_density_t<float, 576, false, 3>(c, a);
+    }
   } else {
-    if (c->kp.periodic)
-      k_density<double, 256, true><<<resident_grid(c, k_density<double, 256, true>),
-                                     32 * kWarpsPerBlock, 0, c->stream>>>(a);
-    else
-      k_density<double, 256, false><<<resident_grid(c, k_density<double, 256, false>),
-                                      32 * kWarpsPerBlock, 0, c->stream>>>(a);
+    if (c->kp.periodic) launch_density_t<double, 256, true, kDepthDensity>(c, a);
+    else launch_density_t<double, 256, false, kDepthDensity>(c, a);
   }
   c->nlaunch += 1;
   return cudaGetLastError();
@@ -595,15 +599,19 @@ cudaError_t alloc_density_spill(sph_ctx *c) {
   // periodic box), so that every launched warp owns a region
   int per_sm = 0;
   cudaError_t e = cudaSuccess;
-  for (int per = 0; per < 2 && e == cudaSuccess; ++per) {
+  for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
     int k = 0;
+    const bool per = v & 1, d4 = v & 2;
     if (c->kp.precision == SPH_FP32K)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &k, per ? k_density<float, 576, true> : k_density<float, 576, false>,
+          &k,
+          per ? (d4 ? k_density<float, 576, true, 4> : k_density<float, 576, true, 3>)
+              : (d4 ? k_density<float, 576, false, 4> : k_density<float, 576, false, 3>),
           32 * kWarpsPerBlock, 0);
     else
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &k, per ? k_density<double, 256, true> : k_density<double, 256, false>,
+          &k, per ? k_density<double, 256, true, kDepthDensity>
+                  : k_density<double, 256, false, kDepthDensity>,
           32 * kWarpsPerBlock, 0);
     per_sm = k > per_sm ? k : per_sm;
   }

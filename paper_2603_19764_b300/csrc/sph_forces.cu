@@ -145,8 +145,6 @@ cudaError_t launch_eos_pack(sph_ctx *c, int predict) {
 // plainly in both forms: their diagonal terms share one sign, and their
 // rounding error is a few ulp of the matrix norm.
 constexpr int kSumBlock = 8;
-// Staging: chunks of 32 stream positions located and loaded at once
-constexpr int kStageChunksF = 4;
 template <typename T> struct Acc {
   T s = 0;
   __device__ __forceinline__ void add(T v) { s += v; }
@@ -203,7 +201,9 @@ struct ForceArgs {
 // Three 4-warp blocks per SM: the pair body and its compensated sums fit in
 // the ~170 registers a thread then has, without spilling (at four blocks,
 // 128 registers, they spill and the kernel runs 1.5 % slower).
-template <typename T, int CAP, bool PER>
+// UF: staging depth, the chunks of 32 stream positions located and loaded
+// at once (kDepths; the lists do not depend on it)
+template <typename T, int CAP, bool PER, int UF>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) {
   constexpr bool REL = std::is_same<T, float>::value;
   using V = V4T<T>;
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     auto sg = make_stager_for<T, REL, PER>(bx, Rf, g, invL, A.p, G.rx, G.ry, G.rz);
     for (;;) {
       // stage candidates
-      const int nl = stage_list<kStageChunksF, false, T, REL>(
+      const int nl = stage_list<UF, false, T, REL>(
           sg, g, A.cell_start, A.cell_end, Lt, A.p, G.rx, G.ry, G.rz, 0, CAP, A.n, &A.st->err,
           [&](bool ok, int j) { return ok ? V::ld(posh, j) : V::make(0, 0, 0, 0); },
           [&](bool ok, const V4 &q, T ox, T oy, T oz, T &xj, T &yj, T &zj) {
@@ -602,10 +602,10 @@ template <typename K> int grid_for_buckets(const sph_ctx *c, K kernel, int64_t b
   return (int)(need < have ? (need > 0 ? need : 1) : have);
 }
 
-template <typename T, int CAP, bool PER>
+template <typename T, int CAP, bool PER, int UF>
 void launch_forces_t(const ForceArgs &a, const sph_ctx *c, int64_t buckets, cudaStream_t stream) {
-  k_forces<T, CAP, PER><<<grid_for_buckets(c, k_forces<T, CAP, PER>, buckets),
-                          32 * kWarpsPerBlock, 0, stream>>>(a);
+  k_forces<T, CAP, PER, UF><<<grid_for_buckets(c, k_forces<T, CAP, PER, UF>, buckets),
+                              32 * kWarpsPerBlock, 0, stream>>>(a);
 }
 
 // The pair loop over buckets [b0, b1) (b1 < 0: to the last bucket), taken
@@ -626,11 +626,17 @@ cudaError_t launch_forces_range(sph_ctx *c, int b0, int b1, unsigned *ctr, cudaS
   a.counter = ctr;
   const int64_t buckets = (b1 < 0 ? c->kp.nbuckets : b1) - b0;
   if (c->kp.precision == SPH_FP32K) {
-    if (c->kp.periodic) launch_forces_t<float, 800, true>(a, c, buckets, stream);
-    else launch_forces_t<float, 800, false>(a, c, buckets, stream);
+    const bool d4 = c->depth_f == 4;
+    if (c->kp.periodic) {
+      if (d4) launch_forces_t<float, 800, true, 4>(a, c, buckets, stream);
+      else launch_forces_t<float, 800, true, 3>(a, c, buckets, stream);
+    } else {
+      if (d4) launch_forces_t<float, 800, false, 4>(a, c, buckets, stream);
+      else launch_forces_t<float, 800, false, 3>(a, c, buckets, stream);
+    }
   } else {
-    if (c->kp.periodic) launch_forces_t<double, 256, true>(a, c, buckets, stream);
-    else launch_forces_t<double, 256, false>(a, c, buckets, stream);
+    if (c->kp.periodic) launch_forces_t<double, 256, true, kDepthForces>(a, c, buckets, stream);
+    else launch_forces_t<double, 256, false, kDepthForces>(a, c, buckets, stream);
   }
   c->nlaunch += 1;
   return cudaGetLastError();

@@ -228,6 +228,12 @@ template <> __device__ __forceinline__ double pconst<double>(double d, float) { 
 // Group spans the tuner chooses among.
 constexpr int kNumSpans = 3;
 constexpr int kSpans[kNumSpans] = {1, 2, 3};
+// Staging depths of the FP32 form's pair kernels (chunks of 32 candidate
+// positions located and loaded at once; compiled variants), the tuner's
+// second knob, and the defaults (the FP64 form runs the defaults only).
+constexpr int kNumDepths = 2;
+constexpr int kDepths[kNumDepths] = {3, 4};
+constexpr int kDepthDensity = 3, kDepthForces = 4;
 
 
 // System owning a sorted position / an id / a bucket: the last
@@ -735,6 +741,11 @@ struct sph_ctx {
   cudaEvent_t tev[4];           // density start / end, forces start / end
   double tune_ms_d[sphk::kNumSpans], tune_ms_f[sphk::kNumSpans];
   int tune_n[sphk::kNumSpans];
+  // staging depths in use (FP32 form) and the tuner's depth phase
+  int depth_d, depth_f;
+  int tune_phase, tune_rounds;   // 0: spans, 1: depths at the chosen spans
+  double tune_dms_d[sphk::kNumDepths], tune_dms_f[sphk::kNumDepths];
+  int tune_dn[sphk::kNumDepths];
   double phase_ms[SPH_NUM_PHASES];
   int timed_steps;
   int primed;

@@ -105,7 +105,11 @@ class SphTuneReport(C.Structure):
     _fields_ = [("span_density", C.c_int32), ("span_forces", C.c_int32),
                 ("steps_left", C.c_int32), ("n_cand", C.c_int32), ("cand", C.c_int32 * 4),
                 ("timed", C.c_int32 * 4), ("ms_density", C.c_double * 4),
-                ("ms_forces", C.c_double * 4)]
+                ("ms_forces", C.c_double * 4), ("depth_density", C.c_int32),
+                ("depth_forces", C.c_int32), ("n_depth", C.c_int32),
+                ("depth_cand", C.c_int32 * 2), ("depth_timed", C.c_int32 * 2),
+                ("reserved_", C.c_int32), ("ms_depth_density", C.c_double * 2),
+                ("ms_depth_forces", C.c_double * 2)]
 
 
 class SphPeakReport(C.Structure):
@@ -123,7 +127,7 @@ EXPORTS = ("sph_init", "sph_neighbours", "sph_density", "sph_forces_strength",
            "sph_mlp_loss_grad", "sph_mlp_adam_step", "sph_mlp_train_epoch",
            "sph_set_learned_h", "sph_learn_samples", "sph_check_conversions",
            "sph_measure_fma_peak", "sph_inject_cuda_failure", "sph_learn_proposal",
-           "sph_set_copy_chunks")
+           "sph_set_copy_chunks", "sph_set_stage_depths")
 MLP_NPARAM, MLP_NNORM = 4673, 14
 GUESS_PREVIOUS, GUESS_CONTINUITY, GUESS_NETWORK = 0, 1, 2
 PHASES = ("neighbours", "pack", "density", "predict_eos", "forces", "kick")
@@ -208,6 +212,8 @@ def lib():
         L.sph_set_graph.argtypes = [VP, C.c_int32]
         L.sph_set_copy_chunks.restype = st
         L.sph_set_copy_chunks.argtypes = [VP, C.c_int32]
+        L.sph_set_stage_depths.restype = st
+        L.sph_set_stage_depths.argtypes = [VP, C.c_int32, C.c_int32]
         L.sph_diagnostics_noalloc.restype = st
         L.sph_diagnostics_noalloc.argtypes = [C.POINTER(SphState), C.c_int64, VP, VP]
         L.sph_learn_proposal.restype = st
@@ -400,10 +406,18 @@ class Simulation:
     def tune_info(self) -> dict:
         r = SphTuneReport()
         self._check(lib().sph_tune_info(self.ctx, C.byref(r)), "sph_tune_info")
-        k = r.n_cand
+        k, q = r.n_cand, r.n_depth
         return {"span_density": r.span_density, "span_forces": r.span_forces,
                 "steps_left": r.steps_left, "cand": list(r.cand[:k]), "timed": list(r.timed[:k]),
-                "ms_density": list(r.ms_density[:k]), "ms_forces": list(r.ms_forces[:k])}
+                "ms_density": list(r.ms_density[:k]), "ms_forces": list(r.ms_forces[:k]),
+                "depth_density": r.depth_density, "depth_forces": r.depth_forces,
+                "depth_cand": list(r.depth_cand[:q]), "depth_timed": list(r.depth_timed[:q]),
+                "ms_depth_density": list(r.ms_depth_density[:q]),
+                "ms_depth_forces": list(r.ms_depth_forces[:q])}
+
+    def set_stage_depths(self, depth_density: int, depth_forces: int):
+        return self._check(lib().sph_set_stage_depths(self.ctx, int(depth_density),
+                                                      int(depth_forces)), "sph_set_stage_depths")
 
     def set_graph(self, on: bool = True):
         return self._check(lib().sph_set_graph(self.ctx, 1 if on else 0), "sph_set_graph")

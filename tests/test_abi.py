@@ -59,6 +59,9 @@ int main(void) {
   O(sph_step_info, kernel_launches) O(sph_step_info, n_expanded)
   O(sph_step_info, particle_updates) O(sph_step_info, rung_counts) O(sph_params, max_rung)
   O(sph_tune_report, timed) O(sph_tune_report, ms_density) O(sph_tune_report, ms_forces)
+  O(sph_tune_report, depth_density) O(sph_tune_report, n_depth)
+  O(sph_tune_report, depth_timed) O(sph_tune_report, ms_depth_density)
+  O(sph_tune_report, ms_depth_forces)
   O(sph_peak_report, sm_mhz) O(sph_peak_report, n_sm)
   return 0;
 }

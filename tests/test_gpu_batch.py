@@ -157,9 +157,11 @@ def test_every_span_fp32_parity_after_tuning(span):
     sim = sph.Simulation(w.arrays, w.materials, p, systems=w.systems)
     sim.prime()
     sim.autotune(1)
-    for _ in range(4):
+    for _ in range(5):   # three span steps, then two staging-depth steps
         sim.step_batch(np.zeros(sim.nsys))
-    assert sim.tune_info()["steps_left"] == 0
+    rep = sim.tune_info()
+    assert rep["steps_left"] == 0 and rep["depth_timed"] == [1, 1]
+    assert rep["depth_density"] in (3, 4) and rep["depth_forces"] in (3, 4)
     sim.set_spans(span, span)
     sim.density()
     sim.forces_strength()
@@ -184,3 +186,38 @@ def test_set_spans_rejects_out_of_range():
         with pytest.raises(sph.SphError):
             sim.set_spans(*bad)
     sim.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_staging_depth_changes_no_bit(graph):
+    """The FP32 form's staging depth (chunks of 32 candidate positions
+    located and loaded before the first is tested) only overlaps loads: the
+    chunks are consumed in order, so every depth builds the same candidate
+    lists and steps to the same bits."""
+    w = _batch(1, n_systems=4)
+    p = dict(w.params, precision=1, h_tol=1e-6)
+    out = []
+    for depths in ((3, 3), (4, 4), (3, 4)):
+        sim = sph.Simulation(w.arrays, w.materials, p, systems=w.systems)
+        sim.set_graph(graph)
+        sim.set_stage_depths(*depths)
+        sim.prime()
+        for _ in range(3):
+            sim.step_batch(np.zeros(sim.nsys))
+        rep = sim.tune_info()
+        assert (rep["depth_density"], rep["depth_forces"]) == depths
+        out.append(_by_id(sim.to_numpy()))
+        sim.close()
+    for g in out[1:]:
+        for f in FIELDS:
+            assert np.array_equal(g[f], out[0][f]), f
+
+
+def test_set_stage_depths_rejects_uncompiled_depths():
+    w = _batch(1, n_systems=2)
+    sim = sph.Simulation(w.arrays, w.materials, dict(w.params, precision=1), systems=w.systems)
+    for bad in ((2, 3), (3, 5), (0, 0)):
+        with pytest.raises(sph.SphError):
+            sim.set_stage_depths(*bad)
+    sim.close()
+
