@@ -114,6 +114,17 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu(libsph):
     assert libsph.sph_destroy(None) == sph.SPH_OK
 
 
+def test_tuning_setters_reject_a_missing_context_without_touching_the_gpu(libsph):
+    for name, args in (("sph_autotune", (2,)), ("sph_set_spans", (1, 2)),
+                       ("sph_set_stage_depths", (3, 4)), ("sph_set_copy_chunks", (8,))):
+        f = getattr(libsph, name)
+        f.restype = C.c_int
+        assert f(None, *[C.c_int32(a) for a in args]) == sph.SPH_E_ARG, name
+    libsph.sph_tune_info.restype = C.c_int
+    r = sph.SphTuneReport()
+    assert libsph.sph_tune_info(None, C.byref(r)) == sph.SPH_E_ARG
+
+
 def test_batch_init_rejects_bad_system_bounds_without_touching_the_gpu(libsph):
     """System bounds are checked on the host before any CUDA call."""
     from paper_2603_19764_b300 import workloads as wl
