@@ -24,6 +24,20 @@ struct KickIn {
   double vsig;    // CFL signal speed of Eq. 39
 };
 
+// Time-step criterion of a moving particle, min(Eq. 38 with eps = H, Eq.
+// 39), in the form's arithmetic type: from its acceleration, its H and the
+// CFL signal speed of the force pass.
+template <typename T>
+__device__ __forceinline__ T crit_t(const KParams &P, const double a[3], double h, double vsig) {
+  const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
+  const T H = to_t<T>(h);
+  const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
+  const T am = root(ax * ax + ay * ay + az * az);
+  const T ta = am > T(0) ? eta_a * root(quot(H, am)) : T(INFINITY);   // Eq. 38, eps = H
+  const T tc = quot(eta_c * H, to_t<T>(vsig));                        // Eq. 39
+  return tmin_(ta, tc);
+}
+
 // Particle i of system sy: with kick, moving particles whose own step ends
 // with this substep are closed to i (v, u, S alike), S is rescaled with Y
 // at (rho_i, u_i), the strain invariant gains dt 1/2 edot:edot and the
@@ -38,7 +52,6 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
                                               bool kick, double sub, bool last, bool copy,
                                               const KickIn &d, double term[kNSum], double *tcr,
                                               int &updates, int *hist) {
-  const T eta_a = to_t<T>(P.eta_a), eta_c = to_t<T>(P.eta_c);
   const bool fixed = s.flags[i] & SPH_FLAG_FIXED;
   const double m = s.m[i];
   const double *a = d.a;
@@ -72,11 +85,9 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
     // whose steps start at the next substep
     double ho = hdt;
     if (P.max_rung) {
-      const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-      const double h = s.h[i];
-      const double ta = am > 0.0 ? P.eta_a * sqrt(h / am) : INFINITY;
-      const double tc = P.eta_c * h / d.vsig;
-      int r = rung_want(P, sub, ta < tc ? ta : tc);
+      // the rung from the criterion in the form's type (the FP32 form's FP64
+      // square roots and divisions here cost the kick a third of its time)
+      int r = rung_want(P, sub, from_t(crit_t<T>(P, a, s.h[i], d.vsig)));
       int r_al = P.max_rung;
       for (int q = P.substep + 1; r_al > 0 && (q & 1) == 0; q >>= 1) --r_al;
       r = r > r_al ? r : r_al;
@@ -120,16 +131,7 @@ __device__ __forceinline__ void kick_particle(const sph_state &s, const sph_stat
   term[6] = y * term[5] - z * term[4];
   term[7] = z * term[3] - x * term[5];
   term[8] = x * term[4] - y * term[3];
-  T tc_ = T(INFINITY);
-  if (!fixed) {
-    const T H = to_t<T>(s.h[i]);
-    const T ax = to_t<T>(a[0]), ay = to_t<T>(a[1]), az = to_t<T>(a[2]);
-    const T am = root(ax * ax + ay * ay + az * az);
-    const T ta = am > T(0) ? eta_a * root(quot(H, am)) : T(INFINITY);   // Eq. 38, eps = H
-    const T tc = quot(eta_c * H, to_t<T>(d.vsig));                      // Eq. 39
-    tc_ = tmin_(ta, tc);
-  }
-  *tcr = from_t(tc_);
+  *tcr = fixed ? double(INFINITY) : from_t(crit_t<T>(P, a, s.h[i], d.vsig));
 }
 
 // The smaller of two time-step criteria: non-negative doubles or +inf,

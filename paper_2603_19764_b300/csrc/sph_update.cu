@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *t
 // Hierarchical steps: at the start of a big step every moving particle
 // takes the rung its criteria ask for (from the last derivatives; every
 // particle is at the same time, so any rung is aligned).
+template <typename T>
 __global__ void __launch_bounds__(kBlock) k_rung_init(sph_state s, Work w, int64_t n, KParams P) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -153,18 +154,18 @@ __global__ void __launch_bounds__(kBlock) k_rung_init(sph_state s, Work w, int64
       continue;
     }
     const int sy = P.nsys > 1 ? sys_lookup(P.sys_begin, P.nsys, i) : 0;
-    const double am = sqrt(s.ax[i] * s.ax[i] + s.ay[i] * s.ay[i] + s.az[i] * s.az[i]);
-    const double h = s.h[i];
-    const double ta = am > 0.0 ? P.eta_a * sqrt(h / am) : INFINITY;
-    const double tc = P.eta_c * h / w.vsig[i];
-    w.rung[i] = rung_want(P, P.dt[sy] * P.sub_scale, ta < tc ? ta : tc);
+    const double a[3] = {s.ax[i], s.ay[i], s.az[i]};
+    w.rung[i] = rung_want(P, P.dt[sy] * P.sub_scale, from_t(crit_t<T>(P, a, s.h[i], w.vsig[i])));
   }
 }
 
 cudaError_t launch_rung_init(sph_ctx *c) {
   int64_t b = (c->n + kBlock - 1) / kBlock;
   if (b > 148 * 16) b = 148 * 16;
-  k_rung_init<<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+  if (c->kp.precision == SPH_FP32K)
+    k_rung_init<float><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
+  else
+    k_rung_init<double><<<(int)b, kBlock, 0, c->stream>>>(c->st, c->w, c->n, c->kp);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
