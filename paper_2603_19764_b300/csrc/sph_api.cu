@@ -344,13 +344,17 @@ sph_status forces_chunked(sph_ctx *c) {
 // steps pass 0 and recompute rho, Omega, P, c_s and the counts in the new
 // order (with hierarchical steps rho, Omega and the counts still follow the
 // sort: particles between their steps keep them).
-sph_status run_neighbours(sph_ctx *c, int drift, int all) {
+// sort = 0 (hierarchical substeps right after a sorted one): drift only;
+// the order, the grid and the cells stay, and the pair kernels search the
+// cells within their radius plus this drift's largest coordinate change.
+sph_status run_neighbours(sph_ctx *c, int drift, int all, int sort = 1) {
   const TraceRange tr("sph neighbours");
   CK(mark(c, 0));
   CK(launch_reset_status(c, 0));
   CK(launch_drift_bbox(c, drift));
-  CK(launch_grid_setup(c));
-  CK(launch_sort_permute(c, all, c->split_in ? 1 : 0));
+  CK(launch_grid_setup(c, sort ? 0 : 1));
+  if (sort) CK(launch_sort_permute(c, all, c->split_in ? 1 : 0));
+  else c->src = c->st;
   CK(mark(c, 1));
   return copy_out(c, 0);
 }
@@ -430,7 +434,13 @@ sph_status enqueue_step(sph_ctx *c) {
   for (int sub = 0; sub < L && s == SPH_OK; ++sub) {
     c->kp.substep = sub;
     c->host_out = sub == L - 1 ? out : nullptr;
-    s = run_neighbours(c, 1, 0);
+    // a substep whose steps end only on the finest rung (sub even: no
+    // coarser rung ends there) follows a sorted substep of this call and
+    // keeps its order: the particles moved by one drift since (not the
+    // call's first substep: the caller may have moved particles between
+    // calls; not a periodic box, whose wrap moves a particle by a box length)
+    const int sort = sub == 0 || (sub & 1) || c->kp.periodic;
+    s = run_neighbours(c, 1, 0, sort);
     if (s == SPH_OK && c->kp.act) {
       const cudaError_t e = launch_compact_active(c);
       if (e != cudaSuccess) s = fail_cuda(c, e, "launch_compact_active");

@@ -368,7 +368,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
         Rl = Rneed * T(1.02);
         if (PER && !(T(2) * Rl < box_min)) w_box = 1u;
         const Box<T> bx = group_box(act, xi, yi, zi);
-        auto sg = make_stager_for<T, REL, PER>(bx, Rl, g, invL, A.p, G.rx, G.ry, G.rz);
+        // the cells within Rl of the box plus the skin (a hierarchical substep
+        // that kept the last order: the particles moved since that sort)
+        auto sg = make_stager_for<T, REL, PER>(bx, Rl + sys_skin<T>(R), g, invL, A.p, G.rx,
+                                               G.ry, G.rz);
         Hm = T(0);
         complete = false;
         for (int seg = 0;; ++seg) {
@@ -518,9 +521,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4) k_density(DensArgs A) 
   w_bad |= (solve && !(isfinite(rho_o) && isfinite(om_o) && rho_o > T(0))) ? 1u : 0u;
   {
     // every particle's radius bounds the force pass's search, solved or not
-    // (the maximum of the order-preserving encodings)
+    // (the maximum of the order-preserving encodings), widened by the
+    // staging skin (0 after a sort)
     const unsigned long long hb =
-        wmax(enc_d(valid ? (solve ? from_t(H_o) : A.h_in[i]) : 0.0));
+        wmax(enc_d(valid ? (solve ? from_t(H_o) : A.h_in[i]) + R.skin : 0.0));
     if (lane == 0) atomicMax(&A.p.sys[sy].hmax2_enc, hb);
   }
   w_pairs += pairs;

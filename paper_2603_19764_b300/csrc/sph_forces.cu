@@ -295,6 +295,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_forces(ForceArgs A) 
     // lists and masks reach r^2 < H_i^2 + gi: no pair with r < H_i by the
     // FP64 predicate escapes the count
     const T gmax = guard_band(Rb, Lt);
+    // (hmax_all includes the staging skin of a substep that kept the last
+    // order: every radius it bounds was raised by the skin)
     const T Rf = tmax(Rb, hmax_all) + T(1e-5) * tmax(Rb, Lt);
     if (PER && !(T(2) * Rf < box_min)) w_box = 1u;
     const Box<T> bx = group_box(act, xi, yi, zi);

@@ -39,6 +39,7 @@ __global__ void k_reset_status(Status *st, SysRec *sys, int nsys, int full, int 
     r.hmax_enc = 0ull;
     r.hmax2_enc = 0ull;
     r.dtmin_enc = ~0ull;
+    r.disp_enc = 0ull;
   }
 }
 
@@ -64,12 +65,13 @@ cudaError_t launch_reset_status(sph_ctx *c, int full) {
 // instructions share the FP64 unit, which runs at 1/64 of the FP32 rate.
 __device__ __forceinline__ void flush_box(SysRec &r, const unsigned long long (&lo)[3],
                                           const unsigned long long (&hi)[3],
-                                          unsigned long long hm) {
+                                          unsigned long long hm, unsigned long long dm) {
   for (int a = 0; a < 3; ++a) {
     atomicMin(&r.lo_enc[a], lo[a]);
     atomicMax(&r.hi_enc[a], hi[a]);
   }
   atomicMax(&r.hmax_enc, hm);
+  if (dm) atomicMax(&r.disp_enc, dm);
 }
 
 // finite by the exponent field alone (no FP64 instruction)
@@ -83,14 +85,17 @@ constexpr unsigned long long kEncMax = ~0ull, kEncMin = 0ull;
 // PER: a periodic box (a template parameter, so that closed boxes run no
 // FP64 compare or wrap: the compiler evaluates a run-time branch's cheap
 // sides unconditionally)
-template <bool PER>
+// TRACK: also record each system's largest coordinate change (hierarchical
+// steps, whose next substep may keep this order and search a skin that
+// wide)
+template <bool PER, bool TRACK>
 __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, KParams P,
                                                       int do_drift) {
-  __shared__ unsigned long long red[7][kBlock / 32];
+  __shared__ unsigned long long red[8][kBlock / 32];
   __shared__ int wsys[kBlock / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long lo[3] = {kEncMax, kEncMax, kEncMax}, hi[3] = {kEncMin, kEncMin, kEncMin};
-  unsigned long long hm = kEncMin;
+  unsigned long long hm = kEncMin, dm = kEncMin;   // largest H; largest coordinate change
   int cur = -1;   // system of the running extrema (-1: none)
   const int64_t c0 = (int64_t)blockIdx.x * kDriftChunk;
   const int64_t c1 = c0 + kDriftChunk < n ? c0 + kDriftChunk : n;
@@ -99,9 +104,17 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
     double p[3] = {s.x[i], s.y[i], s.z[i]};
     if (do_drift && !(s.flags[i] & SPH_FLAG_FIXED)) {
       const double dt = P.dt[sy] * P.sub_scale;   // the substep (the step without rungs)
+      const double p0[3] = {p[0], p[1], p[2]};
       p[0] += dt * s.vx[i];
       p[1] += dt * s.vy[i];
       p[2] += dt * s.vz[i];
+      if (TRACK) {   // the coordinate change, as the order-preserving encoding
+        for (int a = 0; a < 3; ++a) {
+          const double d = p[a] - p0[a];
+          const unsigned long long e = enc_d(fabs(d));
+          dm = finite_bits(d) && e > dm ? e : dm;
+        }
+      }
       if (PER) {   // back into [box_lo, box_hi): one box length at most
         for (int a = 0; a < 3; ++a) {
           if (p[a] >= P.box_hi[a]) p[a] -= P.box_len[a];
@@ -113,13 +126,14 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
       s.z[i] = p[2];
     }
     if (sy != cur) {
-      if (cur >= 0) flush_box(P.sys[cur], lo, hi, hm);
+      if (cur >= 0) flush_box(P.sys[cur], lo, hi, hm, dm);
       cur = sy;
       for (int a = 0; a < 3; ++a) {
         lo[a] = kEncMax;
         hi[a] = kEncMin;
       }
       hm = kEncMin;
+      dm = kEncMin;
     }
     // a non-finite position is left out of the box (the step's checks
     // report it), as the FP64 min / max would
@@ -140,16 +154,16 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
     if (has) any = __shfl_sync(kFull, cur, __ffs(has) - 1);
   }
   const bool warp_uniform = __all_sync(kFull, cur < 0 || cur == any);
-  unsigned long long v[7] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm};
+  unsigned long long v[8] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], hm, dm};
   if (warp_uniform) {
     for (int k = 0; k < 3; ++k) v[k] = wmin(v[k]);
-    for (int k = 3; k < 7; ++k) v[k] = wmax(v[k]);
+    for (int k = 3; k < 8; ++k) v[k] = wmax(v[k]);
   } else if (cur >= 0) {
-    flush_box(P.sys[cur], lo, hi, hm);   // mixed warp: every lane on its own
+    flush_box(P.sys[cur], lo, hi, hm, dm);   // mixed warp: every lane on its own
   }
   if (lane == 0) {
     wsys[w] = warp_uniform ? any : -2;   // -1: no particle, -2: flushed
-    for (int k = 0; k < 7; ++k) red[k][w] = v[k];
+    for (int k = 0; k < 8; ++k) red[k][w] = v[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -161,20 +175,21 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
       else sb = wsys[q];
     }
     if (one && sb >= 0) {
-      unsigned long long b[7] = {kEncMax, kEncMax, kEncMax, kEncMin, kEncMin, kEncMin, kEncMin};
+      unsigned long long b[8] = {kEncMax, kEncMax, kEncMax, kEncMin, kEncMin, kEncMin, kEncMin,
+                                 kEncMin};
       for (int q = 0; q < kBlock / 32; ++q) {
         if (wsys[q] < 0) continue;
         for (int k = 0; k < 3; ++k) b[k] = red[k][q] < b[k] ? red[k][q] : b[k];
-        for (int k = 3; k < 7; ++k) b[k] = red[k][q] > b[k] ? red[k][q] : b[k];
+        for (int k = 3; k < 8; ++k) b[k] = red[k][q] > b[k] ? red[k][q] : b[k];
       }
       const unsigned long long bl[3] = {b[0], b[1], b[2]}, bh[3] = {b[3], b[4], b[5]};
-      flush_box(P.sys[sb], bl, bh, b[6]);
+      flush_box(P.sys[sb], bl, bh, b[6], b[7]);
     } else {
       for (int q = 0; q < kBlock / 32; ++q) {
         if (wsys[q] < 0) continue;
         const unsigned long long bl[3] = {red[0][q], red[1][q], red[2][q]};
         const unsigned long long bh[3] = {red[3][q], red[4][q], red[5][q]};
-        flush_box(P.sys[wsys[q]], bl, bh, red[6][q]);
+        flush_box(P.sys[wsys[q]], bl, bh, red[6][q], red[7][q]);
       }
     }
   }
@@ -183,9 +198,11 @@ __global__ void __launch_bounds__(kBlock) k_drift_bbox(sph_state s, int64_t n, K
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
   const int blocks = (int)((c->n + kDriftChunk - 1) / kDriftChunk);
   if (c->kp.periodic)
-    k_drift_bbox<true><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
+    k_drift_bbox<true, false><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
+  else if (c->kp.max_rung > 0)
+    k_drift_bbox<false, true><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
   else
-    k_drift_bbox<false><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
+    k_drift_bbox<false, false><<<blocks, kBlock, 0, c->stream>>>(c->st, c->n, c->kp, do_drift);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -197,8 +214,24 @@ cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift) {
 // periodic box the grid starts at box_lo and its ceil(box / L_c) cells per
 // axis cover [box_lo, box_hi) (the last one may reach past box_hi, where no
 // particle lies).
-__global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, KParams P) {
+// keep = 1: the grid, the cells and the order stay those of the last sort
+// (hierarchical substeps that do not re-sort); only the staging skin (this
+// drift's largest coordinate change, the only one since that sort) and the
+// force pass's starting search radius are set.
+__global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, KParams P,
+                             int keep) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (keep) {
+    for (int k = 0; k < nsys; ++k) {
+      SysRec &r = sys[k];
+      const double d = r.disp_enc ? dec_d(r.disp_enc) : 0.0;
+      r.skin = d * (1.0 + 1e-6);
+      r.skinf = __double2float_ru(r.skin);
+      // the force pass's search bound (max H) widened by the skin
+      if (P.act) r.hmax2_enc = enc_d(dec_d(r.hmax_enc) + r.skin);
+    }
+    return;
+  }
   const double max_axis = (double)(1 << axis_bits);
   int off = 0, bits = 0;
   for (int k = 0; k < nsys; ++k) {
@@ -246,6 +279,8 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, K
     g.invLf = (float)(1.0 / L);
     g.ncells = d[0] * d[1] * d[2];
     g.cell_off = off;
+    r.skin = 0.0;
+    r.skinf = 0.f;
     off += g.ncells;
     for (int a = 0; a < 3; ++a)
       if (d[a] > 1) bits = max(bits, 32 - __clz(d[a] - 1));
@@ -258,8 +293,9 @@ __global__ void k_grid_setup(Status *st, SysRec *sys, int nsys, int axis_bits, K
   st->total_cells = off;
 }
 
-cudaError_t launch_grid_setup(sph_ctx *c) {
-  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, c->kp.axis_bits, c->kp);
+cudaError_t launch_grid_setup(sph_ctx *c, int keep) {
+  k_grid_setup<<<1, 32, 0, c->stream>>>(c->d_status, c->d_sys, c->nsys, c->kp.axis_bits, c->kp,
+                                        keep);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -67,6 +67,7 @@ template <typename T> __device__ __forceinline__ T grid_invL(const Grid &g);
 template <> __device__ __forceinline__ float grid_invL<float>(const Grid &g) { return g.invLf; }
 template <> __device__ __forceinline__ double grid_invL<double>(const Grid &g) { return g.invL; }
 
+
 // One independent particle system of a context (a context holds one system,
 // or a batch of them that never interact). Its particles occupy the sorted
 // positions [begin, end), which are also its range of caller ids. Encoded
@@ -74,12 +75,22 @@ template <> __device__ __forceinline__ double grid_invL<double>(const Grid &g) {
 // integers (enc_d / dec_d).
 struct SysRec {
   unsigned long long lo_enc[3], hi_enc[3], hmax_enc, hmax2_enc, dtmin_enc;
+  unsigned long long disp_enc;   // largest coordinate change of this drift
   Grid grid;
+  // staging skin: how far a particle may have moved from the cell it was
+  // sorted into (0 right after a sort); a candidate search covers the cells
+  // within its radius + skin, its membership tests use current positions
+  double skin;
+  float skinf;                   // rounded up
   int begin, end;      // sorted positions (= ids) of the system's particles
   int bucket_off;      // first 32-particle bucket of the system
   int cell_cap;        // cells the system may use
   double sums[9];      // e_kin, e_int, e_pot, p[3], L[3]
 };
+
+template <typename T> __device__ __forceinline__ T sys_skin(const SysRec &r);
+template <> __device__ __forceinline__ float sys_skin<float>(const SysRec &r) { return r.skinf; }
+template <> __device__ __forceinline__ double sys_skin<double>(const SysRec &r) { return r.skin; }
 
 // Device-resident step record shared by all systems of a context.
 struct Status {
@@ -769,7 +780,7 @@ template <typename K> inline int resident_grid(const sph_ctx *c, K kernel) {
 // Launch helpers implemented in the .cu files (all stream-ordered).
 namespace sphk {
 cudaError_t launch_drift_bbox(sph_ctx *c, int do_drift);
-cudaError_t launch_grid_setup(sph_ctx *c);
+cudaError_t launch_grid_setup(sph_ctx *c, int keep);
 // all = 0: leave out the arrays a step recomputes before reading them;
 // part 1: only what the drift, sort and density solve read (the rest
 // follows with launch_permute_rest once it has been copied in)
