@@ -66,8 +66,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 KERNEL_SOURCES = {"k_forces": ("sph_forces.cu", "sph_pair.cuh", "sph_internal.cuh",
                                 "sph_kick.cuh"),
                   "k_density": ("sph_density.cu", "sph_pair.cuh", "sph_internal.cuh")}
-TRAFFIC_PER_PARTICLE = {"k_forces": (182.6, "4caaf5020bd7"),
-                        "k_density": (63.6, "8ea6caf70654")}
+TRAFFIC_PER_PARTICLE = {"k_forces": (182.1, "d40545feba64"),
+                        "k_density": (64.2, "59345c92f537")}
 
 
 def source_hash(kernel: str) -> str:
